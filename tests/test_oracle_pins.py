@@ -1,0 +1,467 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+published known-answer vectors, closed forms, hand-worked kinematics, library
+routines (scipy, scikit-learn) and invariants the paper states.  Each test names
+the paper passage (section / equation number in display order) it pins.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+import oracle
+from paper_2607_06499_b300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cfg(name="di_static", **over):
+    sc = W.make(name, seed=0, **over)
+    return sc
+
+
+def _params(cfg, **kw):
+    P = oracle.make_params(cfg)
+    for k, v in kw.items():
+        if k in ("sigma", "u_min", "u_max", "goal", "w"):
+            arr = getattr(P, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(P, k, v)
+    return P
+
+
+# --------------------------------------------------------------------------- Philox
+def test_philox_known_answer_vectors():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_normals_are_standard_gaussian():
+    # Sec. II-A: eps ~ N(0, Sigma).  Kolmogorov-Smirnov against N(0,1) over many
+    # rollouts, plus near-zero lag correlation inside a rollout.
+    z = np.concatenate([oracle.normals(7, 3, k, 64) for k in range(800)])
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 0.02 and abs(z.var() - 1.0) < 0.03
+    a = z.reshape(800, 64)
+    lag = np.mean(a[:, :-1] * a[:, 1:])
+    assert abs(lag) < 0.02
+
+
+def test_normals_depend_on_rollout_counter_and_seed():
+    base = oracle.normals(1, 0, 5, 12)
+    assert not np.allclose(base, oracle.normals(1, 0, 6, 12))
+    assert not np.allclose(base, oracle.normals(1, 1, 5, 12))
+    assert not np.allclose(base, oracle.normals(2, 0, 5, 12))
+    # a prefix request gives the prefix of a longer one (counter = normal index / 4)
+    assert np.array_equal(oracle.normals(1, 0, 5, 7), base[:7])
+
+
+# --------------------------------------------------------------------------- Eq. 17
+def test_obstacle_velocity_telescopes():
+    sc = _cfg("unicycle", K=64)
+    P = oracle.make_params(sc["cfg"])
+    hist = np.random.default_rng(0).normal(size=(5, 7, 2))
+    v = oracle.obstacle_velocity(P, hist)
+    closed = (hist[-1] - hist[0]) / ((5 - 1) * P.obs_dt)
+    np.testing.assert_allclose(v, closed, rtol=1e-12, atol=1e-12)
+    P1 = _params(sc["cfg"], hist_len=1)
+    assert np.all(oracle.obstacle_velocity(P1, hist[:1]) == 0)
+
+
+def test_tracks_constant_velocity_from_newest():
+    sc = _cfg("unicycle", K=64, T=9)
+    P = oracle.make_params(sc["cfg"])
+    hist = np.random.default_rng(1).normal(size=(5, 4, 2))
+    tr = oracle.tracks(P, hist)
+    assert tr.shape == (10, 4, 2)
+    np.testing.assert_array_equal(tr[0], hist[-1])
+    d = np.diff(tr, axis=0)
+    np.testing.assert_allclose(d, np.broadcast_to(d[0], d.shape), atol=1e-12)
+    v = (hist[-1] - hist[0]) / (4 * P.obs_dt)
+    np.testing.assert_allclose(d[0], v * P.dt, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- Eq. 4-5
+def test_double_integrator_closed_form_and_cost():
+    sc = _cfg("di_static", K=16, T=11)
+    cfg = sc["cfg"]
+    P = oracle.make_params(cfg)
+    x0 = np.array([0.3, -0.2, 0.7, 0.1])
+    U = np.random.default_rng(2).uniform(-1, 1, size=(11, 2))
+    far = np.array([[100.0, 100.0]])
+    trk = np.repeat(far[None], 12, axis=0)
+    r = oracle.rollouts(P, x0, U, trk, np.array([0.1]), want_traj=True)
+    dt, N = P.dt, P.T
+    a = U[None] + r["eps"]                               # applied accelerations
+    jw = (N - 1 - np.arange(N))[None, :, None]
+    pN = x0[None, :2] + N * dt * x0[None, 2:] + dt * dt * np.sum(jw * a, axis=1)
+    vN = x0[None, 2:] + dt * np.sum(a, axis=1)
+    np.testing.assert_allclose(r["traj"][:, -1, :2], pN, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r["traj"][:, -1, 2:], vN, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r["pN"], pN, rtol=1e-12, atol=1e-12)
+    # positions p_j from the closed form at every j; Eq. 5 with the DI cost
+    g = np.array(cfg["goal"][:2])
+    S = np.zeros(16)
+    for j in range(N + 1):
+        jwj = np.clip(j - 1 - np.arange(N), 0, None)[None, :, None]
+        pj = x0[None, :2] + j * dt * x0[None, 2:] + dt * dt * np.sum(jwj * a, axis=1)
+        if j < N:
+            S += np.sum((pj - g) ** 2, axis=1) + 0.01 * np.sum(a[:, j] ** 2, axis=1)
+        else:
+            S += np.sum((pj - g) ** 2, axis=1)
+    np.testing.assert_allclose(r["S"], S, rtol=1e-12)
+    # Eq. 3 with clipping: applied controls inside the box, eps' = u - nominal
+    assert np.all(a <= 2.0 + 1e-15) and np.all(a >= -2.0 - 1e-15)
+
+
+def test_perturbation_is_sigma_times_normals_when_unclipped():
+    sc = _cfg("di_static", K=8, T=6)
+    P = _params(sc["cfg"], u_min=[-1e9, -1e9], u_max=[1e9, 1e9], sigma=[0.3, 0.7])
+    trk = np.full((7, 1, 2), 100.0)
+    r = oracle.rollouts(P, np.zeros(4), np.zeros((6, 2)), trk, np.array([0.1]))
+    for k in range(8):
+        z = oracle.normals(P.seed, P.counter, k, 12).reshape(6, 2)
+        np.testing.assert_allclose(r["eps"][k], z * np.array([0.3, 0.7]), rtol=1e-14)
+
+
+def test_unicycle_straight_line_and_arc():
+    sc = _cfg("unicycle", K=4, T=20)
+    cfg = sc["cfg"]
+    P = _params(cfg, sigma=[0.0, 0.0])
+    trk = np.full((21, 1, 2), 1e3)
+    x0 = np.array([1.0, 2.0, 0.3])
+    U = np.tile([1.5, 0.0], (20, 1))
+    r = oracle.rollouts(P, x0, U, trk, np.array([0.1]), want_traj=True)
+    tr = r["traj"][0]
+    dist = 1.5 * P.dt * 20
+    np.testing.assert_allclose(tr[-1, :2], x0[:2] + dist * np.array([math.cos(0.3), math.sin(0.3)]),
+                               rtol=1e-12)
+    # constant omega: Euler polygon, sum of cos(theta0 + j phi) in closed form
+    w, v, N, dt = 0.8, 1.2, 20, P.dt
+    U = np.tile([v, w], (20, 1))
+    tr = oracle.rollouts(P, x0, U, trk, np.array([0.1]), want_traj=True)["traj"][0]
+    phi = w * dt
+    ratio = math.sin(N * phi / 2) / math.sin(phi / 2)
+    xN = x0[0] + v * dt * ratio * math.cos(0.3 + (N - 1) * phi / 2)
+    yN = x0[1] + v * dt * ratio * math.sin(0.3 + (N - 1) * phi / 2)
+    np.testing.assert_allclose(tr[-1], [xN, yN, 0.3 + N * phi], rtol=1e-12)
+
+
+def test_unicycle_cost_at_rest_closed_form():
+    # Eq. 22-23: robot held still (v = 0): S = T * l(x0) + phi(x0)
+    sc = _cfg("unicycle", K=2, T=7)
+    P = _params(sc["cfg"], sigma=[0.0, 0.0])
+    x0 = np.array([3.0, 4.0, 1.0])
+    r = oracle.rollouts(P, x0, np.zeros((7, 2)), np.full((8, 1, 2), 1e3), np.array([0.1]))
+    e = x0 - np.array([19.0, 19.0, math.pi / 4])
+    expect = 7 * (10 * e[0] ** 2 + 10 * e[1] ** 2) + 50 * np.sum(e ** 2)
+    np.testing.assert_allclose(r["S"], expect, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------- arm
+def test_arm_fk_zero_pose_hand_worked():
+    rows = [l.split() for l in open(os.path.join(GOLD, "ur5e_zero_pose.txt"))
+            if l.strip() and not l.startswith("#")]
+    O, R = oracle.arm_fk(np.zeros(6))
+    for r in rows:
+        if r[0] == "R":
+            np.testing.assert_allclose(R.ravel(), [float(x) for x in r[1:]], atol=1e-12)
+        else:
+            np.testing.assert_allclose(O[int(r[0])], [float(x) for x in r[1:]], atol=1e-12)
+
+
+def test_arm_fk_invariants():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        q = rng.uniform(-math.pi, math.pi, 6)
+        O, R = oracle.arm_fk(q)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R) - 1) < 1e-12
+        # joint 1 turns the whole arm about the base z axis
+        dq = 0.7
+        O2, R2 = oracle.arm_fk(q + np.array([dq, 0, 0, 0, 0, 0]))
+        Rz = np.array([[math.cos(dq), -math.sin(dq), 0], [math.sin(dq), math.cos(dq), 0], [0, 0, 1]])
+        np.testing.assert_allclose(O2, O @ Rz.T, atol=1e-12)
+        np.testing.assert_allclose(R2, Rz @ R, atol=1e-12)
+        # link lengths are fixed by the DH table whatever the joint angles
+        np.testing.assert_allclose(np.linalg.norm(O[1] - O[0]), 0.1625, atol=1e-12)
+        np.testing.assert_allclose(np.linalg.norm(O[2] - O[1]), 0.425, atol=1e-12)
+        np.testing.assert_allclose(np.linalg.norm(O[3] - O[2]), 0.3922, atol=1e-12)
+        np.testing.assert_allclose(np.linalg.norm(O[6] - O[5]), 0.0996, atol=1e-12)
+
+
+def test_arm_spheres_on_link_segments():
+    sc = _cfg("arm", K=4)
+    P = oracle.make_params(sc["cfg"])
+    q = np.random.default_rng(4).uniform(-2, 2, 6)
+    pts = oracle.robot_points(P, q)
+    O, _ = oracle.arm_fk(q)
+    assert pts.shape == (24, 3)
+    for link in range(6):
+        for f in range(4):
+            np.testing.assert_allclose(pts[link * 4 + f],
+                                       O[link] + f / 3 * (O[link + 1] - O[link]), atol=1e-12)
+
+
+def test_arm_pose_cost_closed_form():
+    # Eq. 24: goal displaced by d and rotated by alpha about an axis ->
+    # l = w_p |d| + w_R alpha (no collision); with the arm held still
+    # S = (T + 1) * l since phi(x_N) = l(x_N).
+    sc = _cfg("arm", K=2, T=3)
+    q0 = np.array(W.ARM_Q0)
+    O, R = oracle.arm_fk(q0)
+    d = np.array([0.03, -0.04, 0.12])
+    alpha = 0.37
+    ax = np.array([1.0, 2.0, -0.5])
+    ax /= np.linalg.norm(ax)
+    Kx = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    Rot = np.eye(3) + math.sin(alpha) * Kx + (1 - math.cos(alpha)) * Kx @ Kx
+    goal = list(O[6] + d) + list((R @ Rot).ravel())
+    P = _params(sc["cfg"], sigma=[0.0] * 6, goal=goal)
+    trk = np.full((4, 1, 3), 50.0)
+    r = oracle.rollouts(P, q0, np.zeros((3, 6)), trk, np.array([0.1]))
+    expect = 4 * (10 * np.linalg.norm(d) + 3 * alpha)
+    np.testing.assert_allclose(r["S"], expect, rtol=1e-12)
+    # an obstacle touching the end effector at every step adds w_c per state
+    trk2 = np.repeat(O[6][None, None, :], 4, axis=0)
+    r2 = oracle.rollouts(P, q0, np.zeros((3, 6)), trk2, np.array([0.1]))
+    np.testing.assert_allclose(r2["S"], expect + 4 * 1000, rtol=1e-12)
+    assert np.all(r2["col"] == 1) and np.all(r2["hit_j"] == 1)
+
+
+# --------------------------------------------------------------------------- Eq. 8-10
+def test_collision_first_hit_and_pruning():
+    # DI at constant velocity (no noise): p_j = (0.1 j, 0) with dt=0.05, v=2
+    sc = _cfg("di_static", K=3, T=12)
+    P = _params(sc["cfg"], sigma=[0.0, 0.0])
+    x0 = np.array([0.0, 0.0, 2.0, 0.0])
+    cent = np.array([[0.85, 0.0], [0.5, 0.2], [0.3, 5.0], [0.5, -0.02]])
+    rad = np.array([0.06, 0.21, 0.1, 0.03])
+    trk = np.repeat(cent[None], 13, axis=0)
+    r = oracle.rollouts(P, x0, np.zeros((12, 2)), trk, rad)
+    # j = 5 (x = 0.5) is the first time inside obstacles 1 and 3; obstacle 0 from j = 8
+    assert list(r["hit"]) == [1, 1, 1] and list(r["hit_j"]) == [5, 5, 5]
+    pos = np.stack([0.1 * np.arange(1, 13), np.zeros(12)], 1)
+    clear = np.linalg.norm(pos[:, None] - cent[None], axis=2) - rad[None]
+    np.testing.assert_allclose(r["min_abs_clear"], np.abs(clear).min(), rtol=1e-12)
+    # the current state is not tested unless check_j0
+    trk0 = trk.copy()
+    trk0[0] = [[0.0, 0.0], [9, 9], [9, 9], [9, 9]]
+    trk0[1:] = 9.0
+    assert oracle.rollouts(P, x0, np.zeros((12, 2)), trk0, rad)["col"].sum() == 0
+    P.check_j0 = 1
+    rj = oracle.rollouts(P, x0, np.zeros((12, 2)), trk0, rad)
+    assert list(rj["hit_j"]) == [0, 0, 0]
+    col = np.array([0, 1, 1, 0, 1, 0, 0], np.int32)
+    V, Cc = oracle.prune(col)
+    assert list(V) == list(np.flatnonzero(col == 0)) and list(Cc) == list(np.flatnonzero(col))
+
+
+# --------------------------------------------------------------------------- Eq. 11-15
+def test_reference_point_closest_obstacle_and_features():
+    sc = _cfg("di_static", K=6, T=5)
+    P = oracle.make_params(sc["cfg"])
+    x0 = np.array([0.0, 0.0, 0.0, 0.0])
+    trk = np.zeros((6, 3, 2))
+    trk[:] = np.array([[2.0, 0.0], [1.0, 0.0], [5.0, 0.0]])
+    rad = np.array([0.5, 0.2, 0.1])
+    pN = np.array([[1, 1], [2, 2], [3, 0], [4, 4], [9, 9], [5, 1]], float)
+    hit = np.array([-1, 0, 1, 1, -1, 2], np.int32)
+    idxC = np.array([1, 2, 3, 5], np.int32)
+    o, pbar = oracle.reference_point(P, x0, trk, rad, idxC, hit, pN)
+    # clearances 1.5, 0.8, 4.9 -> obstacle 1; mean of rollouts 2 and 3
+    assert o == 1
+    np.testing.assert_allclose(pbar, [3.5, 2.0])
+    P.ref_mode = 1
+    _, pbar1 = oracle.reference_point(P, x0, trk, rad, idxC, hit, pN)
+    np.testing.assert_allclose(pbar1, pN[idxC].mean(axis=0))
+    # single colliding rollout -> pbar is its terminal position
+    P.ref_mode = 0
+    _, pb = oracle.reference_point(P, x0, trk, rad, np.array([5], np.int32), hit, pN)
+    np.testing.assert_allclose(pb, pN[5])
+    z, g = oracle.features(P, x0, pbar, np.array([0, 4], np.int32), pN)
+    for i, k in enumerate([0, 4]):
+        d = pN[k] - pbar
+        assert np.linalg.norm(z[i]) < 1.0
+        np.testing.assert_allclose(z[i] * (np.linalg.norm(d) + 1e-6), d, rtol=1e-13)
+        e = pN[k] - x0[:2]
+        np.testing.assert_allclose(g[i] * (np.linalg.norm(e) + 1e-6), e, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------- DBSCAN
+def _well_separated_points(rng, n, p, eps):
+    """Random points on arcs of the unit circle/sphere whose pairwise distances
+    all stay at least 1e-4 away from eps (FP32 and FP64 predicates agree)."""
+    while True:
+        if p == 2:
+            centres = rng.uniform(0, 2 * math.pi, size=3)
+            ang = centres[rng.integers(0, 3, n)] + rng.normal(scale=0.15, size=n)
+            z = np.stack([np.cos(ang), np.sin(ang)], 1) * 0.999
+            z[rng.integers(0, n, n // 20)] = rng.uniform(-1, 1, (n // 20, 2)) * 0.7
+        else:
+            z = rng.normal(size=(n, 3))
+            z /= np.linalg.norm(z, axis=1, keepdims=True)
+            z[: n // 2] = z[0] + 0.15 * rng.normal(size=(n // 2, 3))
+        z = z.astype(np.float32).astype(np.float64)
+        D = np.sqrt(((z[:, None, :] - z[None, :, :]) ** 2).sum(-1))
+        if np.min(np.abs(D - eps)) > 1e-4:
+            return z
+
+
+@pytest.mark.parametrize("p,n,eps,mp", [(2, 300, 0.25, 20), (2, 200, 0.3, 10), (3, 250, 0.2, 16)])
+def test_dbscan_matches_scikit_learn(p, n, eps, mp):
+    from sklearn.cluster import DBSCAN
+    rng = np.random.default_rng(10 + p + n)
+    z = _well_separated_points(rng, n, p, eps)
+    labels, M = oracle.dbscan(z, eps, mp)
+    sk = DBSCAN(eps=eps, min_samples=mp).fit(z)
+    core = np.zeros(n, bool)
+    core[sk.core_sample_indices_] = True
+    D = np.sqrt(((z[:, None, :] - z[None, :, :]) ** 2).sum(-1))
+    # same noise set
+    assert np.array_equal(labels < 0, sk.labels_ < 0)
+    # same partition of the core points (one-to-one label correspondence)
+    pairs = set(zip(labels[core], sk.labels_[core]))
+    assert len(pairs) == len(set(labels[core])) == len(set(sk.labels_[core])) == M
+    # canonical ids: cluster c's smallest core member precedes cluster c+1's
+    firsts = [np.flatnonzero(core & (labels == c)).min() for c in range(M)]
+    assert firsts == sorted(firsts)
+    # border points: label of the lowest-index core point within eps
+    for a in np.flatnonzero(~core & (labels >= 0)):
+        nbrs = np.flatnonzero(core & (D[a] <= eps))
+        assert labels[a] == labels[nbrs.min()]
+
+
+def test_dbscan_permutation_invariant_and_brute_force_tiny():
+    rng = np.random.default_rng(5)
+    z = _well_separated_points(rng, 120, 2, 0.3)
+    lab, M = oracle.dbscan(z, 0.3, 6)
+    perm = rng.permutation(120)
+    lab2, M2 = oracle.dbscan(z[perm], 0.3, 6)
+    assert M == M2
+    # same co-membership of core points under the permutation
+    D = np.sqrt(((z[:, None] - z[None]) ** 2).sum(-1))
+    core = (D <= 0.3).sum(1) >= 6
+    same = (lab[:, None] == lab[None, :]) & (lab[:, None] >= 0)
+    inv = np.argsort(perm)
+    same2 = (lab2[inv][:, None] == lab2[inv][None, :]) & (lab2[inv][:, None] >= 0)
+    assert np.array_equal(same[np.ix_(core, core)], same2[np.ix_(core, core)])
+    # brute force on 6 points: two pairs and a chain, minPts 2
+    pts = np.array([[0, 0], [0.1, 0], [1, 1], [1.05, 1], [0.5, 0.5], [3, 3]], float)
+    lab, M = oracle.dbscan(pts, 0.2, 2)
+    assert list(lab) == [0, 0, 1, 1, -1, -1] and M == 2
+
+
+def test_dbscan_predicate_is_fp32_inclusive():
+    # distance exactly eps (in FP32) counts as a neighbour (<=)
+    z = np.array([[0.0, 0.0], [0.25, 0.0]], np.float32)
+    lab, M = oracle.dbscan(z, 0.25, 2)
+    assert M == 1 and list(lab) == [0, 0]
+    above = np.nextafter(np.float32(0.25), np.float32(1.0))
+    z = np.array([[0.0, 0.0], [above, 0.0]], np.float32)
+    lab, M = oracle.dbscan(z, 0.25, 2)
+    assert M == 0
+
+
+# --------------------------------------------------------------------------- Eq. 14-18
+def test_selection_static_and_dynamic():
+    sc = _cfg("di_static", K=6)
+    P = oracle.make_params(sc["cfg"])
+    idxV = np.arange(6, dtype=np.int32)
+    labels = np.array([0, 0, 1, 1, -1, 1], np.int32)
+    S = np.array([5.0, 7.0, 1.0, 2.0, -100.0, 3.0])
+    g = np.array([[1, 0], [1, 0], [-1, 0], [-1, 0.1], [0, 1], [-1, -0.1]], float)
+    r = oracle.select(P, labels, idxV, S, g, 2, np.zeros(2))
+    assert r["dynamic"] == 0 and r["sel"] == 1                # means 6 vs 2; noise ignored
+    np.testing.assert_allclose(r["Sbar"], [6.0, 2.0])
+    np.testing.assert_allclose(r["vhat"][0], [1 / (1 + 1e-6), 0])
+    # obstacle moving toward -x: the cluster moving toward +x is "most opposite"
+    r = oracle.select(P, labels, idxV, S, g, 2, np.array([-0.5, 0.0]))
+    assert r["dynamic"] == 1 and r["sel"] == 0
+    r = oracle.select(P, labels, idxV, S, g, 2, np.array([0.5, 0.0]))
+    assert r["sel"] == 1
+    # below the static threshold the cost criterion applies
+    r = oracle.select(P, labels, idxV, S, g, 2, np.array([0.03, 0.0]))
+    assert r["dynamic"] == 0 and r["sel"] == 1
+    # ties go to the lowest id
+    S2 = np.array([1.0, 1.0, 1.0, 1.0, 0.0, 1.0])
+    assert oracle.select(P, labels, idxV, S2, g, 2, np.zeros(2))["sel"] == 0
+
+
+# --------------------------------------------------------------------------- Eq. 6-7, 19-20
+def test_update_matches_softmax_and_limits():
+    sc = _cfg("di_static", K=50, T=4)
+    P = oracle.make_params(sc["cfg"])
+    rng = np.random.default_rng(6)
+    U = rng.uniform(-1, 1, (4, 2))
+    S = rng.uniform(0, 5, 50)
+    eps = rng.normal(size=(50, 4, 2))
+    allk = np.arange(50, dtype=np.int32)
+    U_new, w, smin = oracle.update(P, U, S, eps, allk)
+    ws = special.softmax(-S / P.lam)
+    np.testing.assert_allclose(w, ws, rtol=1e-12)
+    np.testing.assert_allclose(U_new, U + np.einsum("k,kjd->jd", ws, eps), rtol=1e-12)
+    assert abs(w.sum() - 1) < 1e-12 and smin == S.min()
+    # member subset: zero weight outside, renormalised inside (Eq. 19)
+    mem = np.array([3, 9, 20], np.int32)
+    U2, w2, _ = oracle.update(P, U, S, eps, mem)
+    assert np.all(w2[np.setdiff1d(allk, mem)] == 0)
+    np.testing.assert_allclose(w2[mem], special.softmax(-S[mem] / P.lam), rtol=1e-12)
+    # lambda -> infinity: plain mean; lambda -> 0: the arg-min rollout
+    P.lam = 1e12
+    U3, _, _ = oracle.update(P, U, S, eps, allk)
+    np.testing.assert_allclose(U3, U + eps.mean(0), rtol=1e-9, atol=1e-12)
+    P.lam = 1e-6
+    U4, _, _ = oracle.update(P, U, S, eps, allk)
+    np.testing.assert_allclose(U4, U + eps[np.argmin(S)], atol=1e-12)
+    # equal costs: uniform weights; huge costs do not underflow
+    P.lam = 1.0
+    _, w5, _ = oracle.update(P, U, np.full(50, 4e5), eps, allk)
+    np.testing.assert_allclose(w5, 1 / 50, rtol=1e-12)
+
+
+def test_shift_warm_start():
+    sc = _cfg("di_static", K=2, T=4)
+    P = oracle.make_params(sc["cfg"])
+    U = np.arange(8.0).reshape(4, 2)
+    np.testing.assert_array_equal(oracle.shift(P, U), [[2, 3], [4, 5], [6, 7], [6, 7]])
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+def test_replan_without_collision_is_standard_mppi():
+    sc = W.make("di_static", seed=0, K=256)
+    P = oracle.make_params(sc["cfg"])
+    r = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
+    assert r["diag"]["mode"] == oracle.MODE_NOCOL and r["col"].sum() == 0
+    ws = special.softmax(-r["S"] / P.lam)
+    np.testing.assert_allclose(r["U_new"], sc["U0"] + np.einsum("k,kjd->jd", ws, r["eps"]),
+                               rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["di_blocked", "unicycle_paper", "arm_paper", "unicycle_blocked"])
+def test_replan_invariants(name):
+    kw = dict(K=1024) if name == "unicycle_blocked" else {}
+    sc = W.make(name, seed=0, **kw)
+    cfg = sc["cfg"]
+    P = oracle.make_params(cfg)
+    r = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
+    d = r["diag"]
+    assert d["n_col"] > 0 and d["n_valid"] > 0 and d["n_clusters"] >= 1
+    w = r["w"]
+    assert abs(w.sum() - 1) < 1e-12
+    assert np.all(w[r["col"] == 1] == 0)                 # pruned rollouts never weigh in
+    V = np.flatnonzero(r["col"] == 0)
+    sel = V[r["labels"] == d["sel_label"]]
+    assert np.all(w[np.setdiff1d(np.arange(cfg["K"]), sel)] == 0)
+    assert np.all(w[sel] >= 0) and np.argmax(w) == sel[np.argmin(r["S"][sel])]
+    # the update is a convex combination of feasible controls
+    lo, hi = np.array(cfg["u_min"]), np.array(cfg["u_max"])
+    assert np.all(r["U_new"] >= lo - 1e-12) and np.all(r["U_new"] <= hi + 1e-12)
