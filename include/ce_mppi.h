@@ -1,0 +1,226 @@
+/*
+ * ce_mppi.h -- C ABI of the B300 (sm_103a) CE-MPPI replanning library.
+ *
+ * One call of ce_mppi_replan* runs one iteration of Clustering-Embedded MPPI
+ * (Liu, Chang, Chen, "Clustering-Embedded Model Predictive Path Integral
+ * Control", Algorithm 1) entirely on the GPU:
+ *
+ *   sample K perturbed control sequences around the nominal (Sec. II-A, Eq. 3)
+ *   -> forward-simulate each over the horizon T with cost (Eq. 4-5) and
+ *      collision flags against predicted obstacle tracks (Sec. II-B1, Eq. 8)
+ *   -> prune colliding rollouts (Eq. 9-10); reference point from the colliding
+ *      rollouts near the closest obstacle (Eq. 11)
+ *   -> DBSCAN on the direction feature z (Eq. 12-13, Sec. II-B2)
+ *   -> select a cluster: least mean cost when the obstacle is static (Eq. 14),
+ *      most opposite to its motion when it moves (Eq. 15-18)
+ *   -> softmin-weighted update over the selected cluster (Eq. 19-20); with no
+ *      colliding rollout, the standard MPPI update over all K (Eq. 6-7)
+ *   -> receding-horizon shift of the nominal (Algorithm 1, [Execute]).
+ *
+ * Conventions
+ *   - All arithmetic is FP32.  All arrays are row-major (C order).
+ *   - Dimensions by dynamics: double integrator n=4 (px,py,vx,vy), m=2
+ *     (ax,ay), p=2; unicycle n=3 (x,y,theta), m=2 (v,omega), p=2 (Sec. III-A,
+ *     Eq. 21); arm n=6 (joint angles), m=6 (joint velocities), p=3 (end
+ *     effector position, Sec. III-C).
+ *   - Every call returns a ce_status_t and never throws; on failure
+ *     ce_mppi_last_error() returns a thread-local message.  Parameters are
+ *     validated before anything is launched.
+ *   - A handle owns all of its device memory (nominal sequence, replan counter,
+ *     scratch); it is allocated in ce_mppi_create and freed in ce_mppi_destroy.
+ *     Host pointers passed to a call are read or written only during the call.
+ *     Device pointers passed to a *_dev call must stay valid until the work
+ *     queued on the handle's stream has completed.
+ *   - A handle is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef CE_MPPI_H
+#define CE_MPPI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CE_DYN_DOUBLE_INT_2D = 0, /* p += v dt; v += a dt                        */
+  CE_DYN_UNICYCLE = 1,      /* Sec. III-A, Eq. 21                          */
+  CE_DYN_ARM6_KIN = 2       /* q += qdot dt, UR5e-like standard DH chain   */
+} ce_dyn_t;
+
+typedef enum {
+  CE_MPPI_OK = 0,
+  CE_MPPI_ERR_INVALID_ARG = 1, /* a parameter or size is out of range         */
+  CE_MPPI_ERR_NO_MEMORY = 2,   /* device or host allocation failed            */
+  CE_MPPI_ERR_CUDA = 3,        /* a CUDA runtime call failed                  */
+  CE_MPPI_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up          */
+  CE_MPPI_ERR_BUSY = 5         /* result not ready yet                        */
+} ce_status_t;
+
+/* Which update a replan applied (Algorithm 1). */
+typedef enum {
+  CE_MODE_NOCOL = 0,    /* no colliding rollout: standard MPPI over all K (Eq. 6-7) */
+  CE_MODE_ALLCOL = 1,   /* every rollout collides: standard MPPI over all K         */
+  CE_MODE_ALLNOISE = 2, /* DBSCAN found no cluster: standard MPPI over V            */
+  CE_MODE_STATIC = 3,   /* cluster of least mean cost (Eq. 14)                      */
+  CE_MODE_DYNAMIC = 4   /* cluster most opposite to the obstacle motion (Eq. 18)    */
+} ce_mode_t;
+
+typedef struct {
+  int dyn;               /* ce_dyn_t                                               */
+  int K;                 /* rollouts, 1 .. 1<<20                                   */
+  int T;                 /* horizon N, 1 .. 256                                    */
+  float dt;              /* model step (s), > 0                                    */
+  float obs_dt;          /* spacing of the obstacle observations (Delta t of Eq. 17) */
+  float lambda;          /* temperature, > 0                                       */
+  float dbscan_eps;      /* DBSCAN radius on the unit feature z, (0.02, 2]         */
+  int min_pts;           /* DBSCAN minPts, the point itself included, >= 1         */
+  float sigma[6];        /* per control dimension noise std, >= 0                  */
+  float u_min[6], u_max[6]; /* input box, u_min <= u_max                           */
+  float goal[16];        /* 2-D: goal state (n entries); arm: p_g[3], R_g[9]        */
+  float w[8];            /* cost weights: DI (pos, ctrl, terminal);                */
+                         /* unicycle Q[3], H[3] (Eq. 22-23); arm (w_p, w_R, w_c)    */
+  int n_obs_max;         /* largest obstacle count a replan may pass, >= 0         */
+  int hist_len;          /* H, observations per replan, >= 1                       */
+  float robot_radius;    /* 2-D robot disc radius / arm link-sphere radius (m)     */
+  float norm_eps;        /* epsilon of the normalisations of Eq. 13, 15-17, > 0    */
+  float v_static_thresh; /* |v_o*| <= this selects by cost (Eq. 14), else Eq. 18   */
+  unsigned long long seed; /* Philox4x32-10 key of the perturbations               */
+  int ref_mode;          /* 0: colliding rollouts whose first hit is the closest   */
+                         /*    hit obstacle (the method overview); 1: all of C_col */
+  int check_j0;          /* 1: the current state x_0 also counts for collisions    */
+} ce_mppi_params;
+
+/* Per-replan diagnostics. */
+typedef struct {
+  int mode;        /* ce_mode_t                                                   */
+  int n_col;       /* |C_col|                                                     */
+  int n_valid;     /* |V|                                                         */
+  int n_clusters;  /* M_t                                                         */
+  int sel_label;   /* c*, or -1                                                   */
+  int o_star;      /* index of the reference obstacle, or -1                      */
+  int dynamic;     /* 1 when the selection used the obstacle motion              */
+  int status;      /* 0, or a ce_status_t raised on the device                   */
+  float S_min;     /* least cost among the rollouts of the update                 */
+  float pbar[3];   /* reference point (Eq. 11)                                    */
+  float v_obs[3];  /* velocity estimate of the reference obstacle (Eq. 17)        */
+  unsigned long long counter; /* replan counter this replan used                  */
+} ce_mppi_diag;
+
+/* Inputs and outputs of one replan, all in device memory. */
+typedef struct {
+  const float* x0;         /* [n] current state                                    */
+  const float* obs_hist;   /* [H][n_obs][p] obstacle centres, oldest first         */
+  const float* obs_radius; /* [n_obs] obstacle radii                               */
+  int n_obs;               /* 0 .. n_obs_max                                       */
+  long long obs_step;      /* floats obs_hist advances per replan (0: fixed), for  */
+                           /* recorded observation streams replayed by a batch     */
+  float* u_out;            /* [T][m] updated nominal before the shift, or NULL     */
+  float* x_next;           /* [n] f(x0, u_0), or NULL; may alias x0 (closed loop)   */
+  ce_mppi_diag* diag;      /* or NULL                                              */
+} ce_mppi_request;
+
+typedef struct ce_mppi_handle ce_mppi_handle;
+typedef struct ce_mppi_batch ce_mppi_batch;
+
+/* Allocate a planner.  stream is a cudaStream_t (NULL: the legacy default
+ * stream).  The nominal sequence starts at zero, the replan counter at 0.
+ * Errors: INVALID_ARG (bad parameter), NO_MEMORY, CUDA.                        */
+ce_status_t ce_mppi_create(const ce_mppi_params* params, void* stream, ce_mppi_handle** out);
+/* Wait for the handle's queued work and free everything it owns.              */
+ce_status_t ce_mppi_destroy(ce_mppi_handle* h);
+
+/* Nominal control sequence U_t [T][m] (host memory).  Blocking.               */
+ce_status_t ce_mppi_set_nominal(ce_mppi_handle* h, const float* U);
+ce_status_t ce_mppi_get_nominal(ce_mppi_handle* h, float* U);
+/* Replan counter: the upper Philox counter words of the next replan.  Blocking. */
+ce_status_t ce_mppi_set_counter(ce_mppi_handle* h, unsigned long long counter);
+ce_status_t ce_mppi_get_counter(ce_mppi_handle* h, unsigned long long* counter);
+
+/* One replan from host buffers: copies x0 [n], obs_hist [H][n_obs][p] and
+ * obs_radius [n_obs] to the device, runs Algorithm 1, copies the updated
+ * nominal (before the shift) to u_out [T][m] and the diagnostics to diag
+ * (nullable), and returns when done.  Afterwards the handle's nominal is the
+ * shifted sequence and its counter has advanced by one.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT (device-side wait limit reached).       */
+ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_hist,
+                           const float* obs_radius, int n_obs, float* u_out,
+                           ce_mppi_diag* diag);
+
+/* One replan from device buffers, queued on the handle's stream; returns
+ * without waiting.  Device-side faults of the bounded waits are reported in
+ * diag->status.  Errors: INVALID_ARG, CUDA.                                   */
+ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* req);
+
+/* Batches: n handles replanned together, one kernel launch per stage for all of
+ * them (instances of different K, T and obstacle count).  The requests are
+ * fixed at creation (use obs_step to replay recorded observation streams).
+ * With use_graph != 0 the stage chain is captured once as a CUDA graph and
+ * replayed by ce_mppi_batch_run.  stream is the cudaStream_t the batch runs on.
+ * Every handle must have the same dynamics kind.  Results are bitwise those of
+ * replanning each handle alone.  Errors: INVALID_ARG, NO_MEMORY, CUDA.        */
+ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_request* reqs,
+                                 int n, void* stream, int use_graph, ce_mppi_batch** out);
+/* Queue one replan of every instance of the batch; returns without waiting.  */
+ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
+/* Run one replan of the batch stage by stage (no graph) with CUDA events
+ * between the stage launches, wait for it, and write the device time of each
+ * stage in milliseconds to stage_ms[6]: tracks, rollouts, prune + reference
+ * point + features, DBSCAN, cluster statistics + selection + weights, update.
+ * The replan advances the instances like ce_mppi_batch_run.                   */
+ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms);
+ce_status_t ce_mppi_batch_destroy(ce_mppi_batch* b);
+
+/* Internal buffers of the last replan, copied to host memory (blocking), for
+ * diagnostics and stage-by-stage checks.  bytes must equal the buffer size.  */
+typedef enum {
+  CE_BUF_S = 0,       /* float [K]      trajectory costs S (Eq. 5)                  */
+  CE_BUF_HIT = 1,     /* int   [K]      first-hit obstacle, -1 when collision-free  */
+  CE_BUF_PN = 2,      /* float [p][K]   terminal task positions p(x_T)              */
+  CE_BUF_EPS = 3,     /* float [T*m][K] effective perturbations u^(k) - u (Eq. 3)   */
+  CE_BUF_IDXV = 4,    /* int   [K]      V in ascending k (first n_valid used)       */
+  CE_BUF_IDXC = 5,    /* int   [K]      C_col in ascending k (first n_col used)     */
+  CE_BUF_Z = 6,       /* float [p][K]   feature z of V (Eq. 13), V order            */
+  CE_BUF_G = 7,       /* float [p][K]   unit displacement g of V (Eq. 15)           */
+  CE_BUF_LABEL = 8,   /* int   [K]      DBSCAN label of V, -1 noise                 */
+  CE_BUF_W = 9,       /* float [K]      normalised update weights (Eq. 6 / Eq. 19)  */
+  CE_BUF_HITJ = 10    /* int   [K]      horizon step of the first hit, -1 if none   */
+} ce_buf_t;
+ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* host_dst, size_t bytes);
+
+/* ---- stage entry points (device buffers, queued on stream) ---------------- */
+
+/* Philox4x32-10 words of the perturbation stream: out[k][b][4] for rollouts
+ * k < K and blocks b < nblk, counter (k, b, counter_lo, counter_hi), key
+ * (seed_lo, seed_hi) (Salmon et al., SC'11).                                  */
+ce_status_t ce_mppi_philox_dev(unsigned long long seed, unsigned long long counter, int K,
+                               int nblk, unsigned int* out, void* stream);
+/* The first n standard normals of rollouts k < K: out[k][n] (Box-Muller on
+ * 24-bit uniforms of the words above, pairs (w0,w1) and (w2,w3)).            */
+ce_status_t ce_mppi_normals_dev(unsigned long long seed, unsigned long long counter, int K,
+                                int n, float* out, void* stream);
+/* DBSCAN (Sec. II-B2) of n points z stored as [p][ld] (SoA, p = 2 or 3):
+ * neighbours when the FP32 sum of squared coordinate differences (coordinate
+ * order, no fused multiply-add) is <= fl32(eps^2); core when at least min_pts
+ * neighbours (itself included); clusters are connected components of the core
+ * points; a non-core point takes the cluster of its lowest-index core
+ * neighbour, else -1.  Cluster ids 0..M-1 follow the smallest core member.
+ * labels [n] and n_clusters [1] are device outputs.  workspace is device memory
+ * of at least ce_mppi_dbscan_workspace_bytes(n) bytes.                        */
+size_t ce_mppi_dbscan_workspace_bytes(int n);
+ce_status_t ce_mppi_dbscan_dev(const float* z, int n, int ld, int p, float eps, int min_pts,
+                               int* labels, int* n_clusters, void* workspace, size_t ws_bytes,
+                               void* stream);
+
+/* Host helper: forward kinematics of the arm model (standard DH, UR5e-like),
+ * frame origins O[7][3] and end-effector rotation R[3][3], FP64, for turning a
+ * joint-space goal into the pose goal of ce_mppi_params.                      */
+ce_status_t ce_mppi_arm_fk(const double* q, double* O, double* R);
+
+/* Thread-local message of the last failed call on this thread.               */
+const char* ce_mppi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CE_MPPI_H */

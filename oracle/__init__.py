@@ -262,7 +262,7 @@ def dbscan(z, eps: float, min_pts: int):
     """DBSCAN with the FP32 neighbour predicate; returns (labels, M)."""
     zf = np.ascontiguousarray(z, dtype=np.float32)
     n, p = zf.shape
-    eps2 = np.float32(np.float64(eps) * np.float64(eps))
+    eps2 = np.float32(eps) * np.float32(eps)  # FP32 product of the FP32 radius
     labels = np.zeros(n, np.int32)
     M = lib().orc_dbscan(zf.ctypes.data_as(C.POINTER(C.c_float)), n, p, C.c_float(eps2),
                          min_pts, _i(labels))

@@ -598,7 +598,8 @@ void orc_replan(const orc_params* P, const double* x0, const double* U,
     orc_features(P, x0, dg.pbar, idxV.data(), nV, pN.data(), z.data(), g.data());
     std::vector<float> zf((size_t)nV * p);
     for (size_t i = 0; i < zf.size(); ++i) zf[i] = (float)z[i];
-    const float eps2 = (float)(P->dbscan_eps * P->dbscan_eps);
+    const float eps_f = (float)P->dbscan_eps;  // eps^2 as the FP32 product of FP32 eps
+    const float eps2 = eps_f * eps_f;
     const int M = orc_dbscan(zf.data(), nV, p, eps2, P->min_pts, labels.data());
     dg.n_clusters = M;
     if (M == 0) {

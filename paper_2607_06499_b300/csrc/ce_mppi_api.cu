@@ -1,0 +1,673 @@
+// ce_mppi_api.cu -- host side of the C ABI declared in include/ce_mppi.h:
+// parameter validation, device memory of a planner, the stage chain on a
+// stream, batches (one launch per stage for many instances) with optional
+// CUDA-graph capture, and the stage entry points used for checking.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ce_mppi_internal.cuh"
+
+using namespace cem;
+
+namespace {
+
+thread_local std::string g_err;
+
+ce_status_t fail(ce_status_t s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+ce_status_t cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return CE_MPPI_ERR_CUDA;
+}
+
+#define CE_CUDA(call)                                         \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void dims_of(int dyn, int* n, int* m, int* p) {
+  *n = dyn == CE_DYN_DOUBLE_INT_2D ? 4 : (dyn == CE_DYN_UNICYCLE ? 3 : 6);
+  *m = dyn == CE_DYN_ARM6_KIN ? 6 : 2;
+  *p = dyn == CE_DYN_ARM6_KIN ? 3 : 2;
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+// DBSCAN grid: cell side 0.99 eps / sqrt(p) (any two points of a cell are
+// neighbours), G cells per axis over [-1, 1], reach R cells.
+void dbscan_grid(float eps, int p, float* cell_inv, int* G, int* R, int* ncells) {
+  const double ci = std::sqrt((double)p) / (0.99 * (double)eps);
+  *cell_inv = (float)ci;
+  *G = (int)std::floor(2.0 * ci) + 1;
+  *R = (int)std::ceil((double)eps * ci);
+  *ncells = p == 3 ? (*G) * (*G) * (*G) : (*G) * (*G);
+}
+
+float eps_squared(float eps) {
+  volatile float e = eps;
+  return e * e;  // FP32 product of the FP32 radius (the predicate's eps^2)
+}
+
+std::once_flag g_cfg_once;
+
+}  // namespace
+
+namespace cem {
+void configure_kernels() {
+  configure_rollout();
+  configure_cluster();
+}
+}  // namespace cem
+
+struct ce_mppi_handle {
+  ce_mppi_params P;
+  int n, m, p, Kp, TMp, G, R, ncells;
+  cudaStream_t stream;
+  InstDesc hdesc;
+  InstDesc* ddesc = nullptr;
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  int2* dtiles = nullptr;   // rollout tiles then update tiles
+  int n_roll = 0, n_upd = 0;
+  int smem_roll = 0;
+  // host-pointer path staging (device and pinned host)
+  float *d_x0, *d_hist, *d_rad, *d_uout;
+  ce_mppi_diag* d_diag;
+  unsigned char* h_stage = nullptr;
+  size_t in_bytes = 0, out_bytes = 0;
+};
+
+struct ce_mppi_batch {
+  std::vector<ce_mppi_handle*> hs;
+  cudaStream_t stream;
+  int dyn;
+  InstDesc* ddesc = nullptr;
+  Req* dreq = nullptr;
+  int2* dtiles_roll = nullptr;
+  int2* dtiles_upd = nullptr;
+  int n_roll = 0, n_upd = 0, smem_roll = 0, max_cells = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+ce_status_t validate(const ce_mppi_params* P) {
+  if (!P) return fail(CE_MPPI_ERR_INVALID_ARG, "params is NULL");
+  if (P->dyn < 0 || P->dyn > 2) return fail(CE_MPPI_ERR_INVALID_ARG, "dyn must be 0, 1 or 2");
+  if (P->K < 1 || P->K > (1 << 20)) return fail(CE_MPPI_ERR_INVALID_ARG, "K must be in [1, 2^20]");
+  if (P->T < 1 || P->T > kMaxT) return fail(CE_MPPI_ERR_INVALID_ARG, "T must be in [1, 256]");
+  if (!(P->dt > 0) || !finite(P->dt)) return fail(CE_MPPI_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(P->obs_dt > 0) || !finite(P->obs_dt))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "obs_dt must be > 0");
+  if (!(P->lambda > 0) || !finite(P->lambda))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "lambda must be > 0");
+  if (!(P->dbscan_eps > 0.02f) || !(P->dbscan_eps <= 2.0f))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "dbscan_eps must be in (0.02, 2]");
+  if (P->min_pts < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "min_pts must be >= 1");
+  if (P->hist_len < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "hist_len must be >= 1");
+  if (P->n_obs_max < 0 || P->n_obs_max > kMaxObs)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "n_obs_max must be in [0, 4096]");
+  if (!(P->robot_radius >= 0) || !finite(P->robot_radius))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "robot_radius must be >= 0");
+  if (!(P->norm_eps > 0) || !finite(P->norm_eps))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "norm_eps must be > 0");
+  if (!(P->v_static_thresh >= 0) || !finite(P->v_static_thresh))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "v_static_thresh must be >= 0");
+  if (P->ref_mode < 0 || P->ref_mode > 1) return fail(CE_MPPI_ERR_INVALID_ARG, "ref_mode must be 0 or 1");
+  if (P->check_j0 < 0 || P->check_j0 > 1) return fail(CE_MPPI_ERR_INVALID_ARG, "check_j0 must be 0 or 1");
+  int n, m, p;
+  dims_of(P->dyn, &n, &m, &p);
+  for (int i = 0; i < m; ++i) {
+    if (!(P->sigma[i] >= 0) || !finite(P->sigma[i]))
+      return fail(CE_MPPI_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (!finite(P->u_min[i]) || !finite(P->u_max[i]) || P->u_min[i] > P->u_max[i])
+      return fail(CE_MPPI_ERR_INVALID_ARG, "u_min must be <= u_max, both finite");
+  }
+  for (int i = 0; i < 16; ++i)
+    if (!finite(P->goal[i])) return fail(CE_MPPI_ERR_INVALID_ARG, "goal must be finite");
+  for (int i = 0; i < 8; ++i)
+    if (!finite(P->w[i])) return fail(CE_MPPI_ERR_INVALID_ARG, "weights must be finite");
+  float ci;
+  int G, R, nc;
+  dbscan_grid(P->dbscan_eps, p, &ci, &G, &R, &nc);
+  if (nc > kMaxCells)
+    return fail(CE_MPPI_ERR_INVALID_ARG,
+                "dbscan_eps too small for the DBSCAN grid (p=3 needs eps >= 0.19)");
+  const size_t smem = (size_t)(P->T + 1) * track_stride(P->n_obs_max) * 16 + (size_t)P->T * m * 4;
+  if (smem > (size_t)kMaxSmemTracks)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "(T+1) * n_obs_max too large for shared memory");
+  return CE_MPPI_OK;
+}
+
+void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const int2* tupd,
+               int n_upd, int smem_roll, int max_cells, cudaStream_t s) {
+  KArgs a = base;
+  launch_tracks(a, s);
+  a.tiles = troll;
+  a.n_tiles = n_roll;
+  launch_rollout(dyn, a, smem_roll, s);
+  launch_prune(a, s);
+  launch_dbscan(a, max_cells, s);
+  launch_select(a, s);
+  a.tiles = tupd;
+  a.n_tiles = n_upd;
+  launch_update(a, s);
+}
+
+void tiles_of(const ce_mppi_handle* h, int inst, std::vector<int2>& roll, std::vector<int2>& upd) {
+  const int per = h->P.dyn == CE_DYN_ARM6_KIN ? kArmWarps : kRolloutThreads;
+  for (int k0 = 0; k0 < h->P.K; k0 += per) roll.push_back(make_int2(inst, k0));
+  const int TM = h->P.T * h->m;
+  const int cper = h->P.dyn == CE_DYN_ARM6_KIN ? 32 : kUpdateWarps;
+  for (int c0 = 0; c0 < TM; c0 += cper) upd.push_back(make_int2(inst, c0));
+}
+
+Req to_req(const ce_mppi_request* q, unsigned long long counter0) {
+  Req r;
+  std::memset(&r, 0, sizeof(r));
+  r.x0 = q->x0;
+  r.obs_hist = q->obs_hist;
+  r.obs_radius = q->obs_radius;
+  r.n_obs = q->n_obs;
+  r.obs_step = q->obs_step;
+  r.counter0 = counter0;
+  r.u_out = q->u_out;
+  r.x_next = q->x_next;
+  r.diag = q->diag;
+  return r;
+}
+
+ce_status_t check_req(const ce_mppi_handle* h, const ce_mppi_request* q) {
+  if (!q) return fail(CE_MPPI_ERR_INVALID_ARG, "request is NULL");
+  if (!q->x0) return fail(CE_MPPI_ERR_INVALID_ARG, "x0 is NULL");
+  if (q->n_obs < 0 || q->n_obs > h->P.n_obs_max)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "n_obs must be in [0, n_obs_max]");
+  if (q->n_obs > 0 && (!q->obs_hist || !q->obs_radius))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "obs_hist / obs_radius is NULL");
+  return CE_MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ce_mppi_last_error(void) { return g_err.c_str(); }
+
+ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle** out) {
+  if (!out) return fail(CE_MPPI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  ce_status_t st = validate(P);
+  if (st != CE_MPPI_OK) return st;
+  std::call_once(g_cfg_once, cem::configure_kernels);
+  ce_mppi_handle* h = new (std::nothrow) ce_mppi_handle();
+  if (!h) return fail(CE_MPPI_ERR_NO_MEMORY, "host allocation failed");
+  h->P = *P;
+  h->stream = static_cast<cudaStream_t>(stream);
+  dims_of(P->dyn, &h->n, &h->m, &h->p);
+  const int K = P->K, T = P->T, m = h->m, n = h->n, p = h->p;
+  h->Kp = (K + 31) & ~31;
+  h->TMp = (T * m + 3) & ~3;
+  float ci;
+  dbscan_grid(P->dbscan_eps, p, &ci, &h->G, &h->R, &h->ncells);
+  const int Kp = h->Kp, nobs = P->n_obs_max, H = P->hist_len;
+  const size_t A = 256;
+  // carve one allocation
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, A); return o; };
+  const size_t o_ctr = take(8), o_ctl = take(sizeof(Ctl));
+  const size_t o_U = take(sizeof(float) * T * m), o_Unew = take(sizeof(float) * T * m);
+  const size_t o_trk = take((size_t)(T + 1) * track_stride(nobs) * 16);
+  const size_t o_S = take(4 * Kp), o_w = take(4 * Kp);
+  const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
+               o_zs = take(4 * 3 * Kp);
+  const size_t eps_elems = P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
+  const size_t o_eps = take(4 * eps_elems);
+  size_t o_int[8];
+  for (int i = 0; i < 8; ++i) o_int[i] = take(4 * Kp);
+  const size_t o_bbox = take(sizeof(float) * 6 * h->ncells);
+  // host-path staging: inputs then outputs
+  const size_t in_x0 = 0, in_hist = align_up(4 * n, 16),
+               in_rad = align_up(in_hist + 4 * (size_t)H * nobs * p, 16),
+               in_end = align_up(in_rad + 4 * (size_t)nobs, 16);
+  const size_t out_u = 0, out_diag = align_up(4 * (size_t)T * m, 16),
+               out_end = align_up(out_diag + sizeof(ce_mppi_diag), 16);
+  const size_t o_in = take(in_end), o_out = take(out_end);
+  h->dbytes = off;
+  h->in_bytes = in_end;
+  h->out_bytes = out_end;
+  cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
+  if (e != cudaSuccess) { delete h; return fail(CE_MPPI_ERR_NO_MEMORY, "device allocation failed"); }
+  e = cudaHostAlloc((void**)&h->h_stage, in_end + out_end, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaFree(h->dmem);
+    delete h;
+    return fail(CE_MPPI_ERR_NO_MEMORY, "pinned host allocation failed");
+  }
+  char* b = static_cast<char*>(h->dmem);
+  InstDesc& d = h->hdesc;
+  std::memset(&d, 0, sizeof(d));
+  d.dyn = P->dyn; d.K = K; d.Kp = Kp; d.T = T; d.m = m; d.n = n; d.p = p;
+  d.n_obs_max = nobs; d.H = H; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
+  d.check_j0 = P->check_j0; d.G = h->G; d.R = h->R;
+  d.eps_ld_c = P->dyn == CE_DYN_ARM6_KIN ? 1 : Kp;
+  d.eps_ld_k = P->dyn == CE_DYN_ARM6_KIN ? h->TMp : 1;
+  d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;
+  d.eps2 = eps_squared(P->dbscan_eps); d.cell_inv = ci; d.robot_radius = P->robot_radius;
+  d.norm_eps = P->norm_eps; d.v_static_thresh = P->v_static_thresh;
+  for (int i = 0; i < 6; ++i) { d.sigma[i] = P->sigma[i]; d.u_min[i] = P->u_min[i]; d.u_max[i] = P->u_max[i]; }
+  for (int i = 0; i < 16; ++i) d.goal[i] = P->goal[i];
+  for (int i = 0; i < 8; ++i) d.w[i] = P->w[i];
+  d.seed_lo = (unsigned)P->seed; d.seed_hi = (unsigned)(P->seed >> 32);
+  d.counter = reinterpret_cast<unsigned long long*>(b + o_ctr);
+  d.ctl = reinterpret_cast<Ctl*>(b + o_ctl);
+  d.U = reinterpret_cast<float*>(b + o_U);
+  d.Unew = reinterpret_cast<float*>(b + o_Unew);
+  d.tracks = reinterpret_cast<float4*>(b + o_trk);
+  d.S = reinterpret_cast<float*>(b + o_S);
+  d.w_k = reinterpret_cast<float*>(b + o_w);
+  d.pN = reinterpret_cast<float*>(b + o_pN);
+  d.z = reinterpret_cast<float*>(b + o_z);
+  d.g = reinterpret_cast<float*>(b + o_g);
+  d.zs = reinterpret_cast<float*>(b + o_zs);
+  d.eps = reinterpret_cast<float*>(b + o_eps);
+  int** ints[8] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent};
+  for (int i = 0; i < 8; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
+  d.bbox = reinterpret_cast<float*>(b + o_bbox);
+  h->d_x0 = reinterpret_cast<float*>(b + o_in + in_x0);
+  h->d_hist = reinterpret_cast<float*>(b + o_in + in_hist);
+  h->d_rad = reinterpret_cast<float*>(b + o_in + in_rad);
+  h->d_uout = reinterpret_cast<float*>(b + o_out + out_u);
+  h->d_diag = reinterpret_cast<ce_mppi_diag*>(b + o_out + out_diag);
+  std::vector<int2> roll, upd;
+  tiles_of(h, 0, roll, upd);
+  h->n_roll = (int)roll.size();
+  h->n_upd = (int)upd.size();
+  h->smem_roll = (int)((size_t)(T + 1) * track_stride(nobs) * 16 + (size_t)T * m * 4);
+  auto cleanup = [&]() {
+    cudaFree(h->dmem);
+    cudaFree(h->ddesc);
+    cudaFree(h->dtiles);
+    cudaFreeHost(h->h_stage);
+    delete h;
+  };
+  if ((e = cudaMalloc(&h->ddesc, sizeof(InstDesc))) != cudaSuccess ||
+      (e = cudaMalloc(&h->dtiles, sizeof(int2) * (roll.size() + upd.size()))) != cudaSuccess) {
+    cleanup();
+    return fail(CE_MPPI_ERR_NO_MEMORY, "device allocation failed");
+  }
+  std::vector<int2> all(roll);
+  all.insert(all.end(), upd.begin(), upd.end());
+  if ((e = cudaMemsetAsync(h->dmem, 0, h->dbytes, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->ddesc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->dtiles, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice,
+                           h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "create");
+  }
+  *out = h;
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_destroy(ce_mppi_handle* h) {
+  if (!h) return CE_MPPI_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->dmem);
+  cudaFree(h->ddesc);
+  cudaFree(h->dtiles);
+  cudaFreeHost(h->h_stage);
+  delete h;
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_set_nominal(ce_mppi_handle* h, const float* U) {
+  if (!h || !U) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  CE_CUDA(cudaMemcpy(h->hdesc.U, U, sizeof(float) * h->P.T * h->m, cudaMemcpyHostToDevice));
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_get_nominal(ce_mppi_handle* h, float* U) {
+  if (!h || !U) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  CE_CUDA(cudaMemcpy(U, h->hdesc.U, sizeof(float) * h->P.T * h->m, cudaMemcpyDeviceToHost));
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_set_counter(ce_mppi_handle* h, unsigned long long c) {
+  if (!h) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle");
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  CE_CUDA(cudaMemcpy(h->hdesc.counter, &c, 8, cudaMemcpyHostToDevice));
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_get_counter(ce_mppi_handle* h, unsigned long long* c) {
+  if (!h || !c) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  CE_CUDA(cudaMemcpy(c, h->hdesc.counter, 8, cudaMemcpyDeviceToHost));
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* q) {
+  if (!h) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle");
+  ce_status_t st = check_req(h, q);
+  if (st != CE_MPPI_OK) return st;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.D = h->ddesc;
+  a.R = nullptr;
+  a.r0 = to_req(q, 0);
+  a.r0.obs_step = 0;  // a single replan reads obs_hist as given
+  a.n_inst = 1;
+  run_chain(h->P.dyn, a, h->dtiles, h->n_roll, h->dtiles + h->n_roll, h->n_upd, h->smem_roll,
+            h->ncells, h->stream);
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_hist,
+                           const float* obs_radius, int n_obs, float* u_out, ce_mppi_diag* diag) {
+  if (!h || !x0 || !u_out) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  if (n_obs < 0 || n_obs > h->P.n_obs_max)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "n_obs must be in [0, n_obs_max]");
+  if (n_obs > 0 && (!obs_hist || !obs_radius))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "obs_hist / obs_radius is NULL");
+  const int n = h->n, p = h->p, H = h->P.hist_len, TM = h->P.T * h->m;
+  unsigned char* hin = h->h_stage;
+  unsigned char* hout = h->h_stage + h->in_bytes;
+  const size_t hist_off = (char*)h->d_hist - (char*)h->d_x0, rad_off = (char*)h->d_rad - (char*)h->d_x0;
+  std::memcpy(hin, x0, sizeof(float) * n);
+  if (n_obs > 0) {
+    std::memcpy(hin + hist_off, obs_hist, sizeof(float) * (size_t)H * n_obs * p);
+    std::memcpy(hin + rad_off, obs_radius, sizeof(float) * n_obs);
+  }
+  CE_CUDA(cudaMemcpyAsync(h->d_x0, hin, h->in_bytes, cudaMemcpyHostToDevice, h->stream));
+  ce_mppi_request q;
+  std::memset(&q, 0, sizeof(q));
+  q.x0 = h->d_x0;
+  q.obs_hist = h->d_hist;
+  q.obs_radius = h->d_rad;
+  q.n_obs = n_obs;
+  q.u_out = h->d_uout;
+  q.diag = h->d_diag;
+  ce_status_t st = ce_mppi_replan_dev(h, &q);
+  if (st != CE_MPPI_OK) return st;
+  CE_CUDA(cudaMemcpyAsync(hout, h->d_uout, h->out_bytes, cudaMemcpyDeviceToHost, h->stream));
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  std::memcpy(u_out, hout, sizeof(float) * TM);
+  ce_mppi_diag dg;
+  std::memcpy(&dg, hout + ((char*)h->d_diag - (char*)h->d_uout), sizeof(dg));
+  if (diag) *diag = dg;
+  if (dg.status != 0) return fail((ce_status_t)dg.status, "device-side bounded wait gave up");
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
+                                 void* stream, int use_graph, ce_mppi_batch** out) {
+  if (!out) return fail(CE_MPPI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!hs || !reqs || n < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "empty batch");
+  const int dyn = hs[0] ? hs[0]->P.dyn : -1;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle in batch");
+    if (hs[i]->P.dyn != dyn) return fail(CE_MPPI_ERR_INVALID_ARG, "mixed dynamics in one batch");
+    ce_status_t st = check_req(hs[i], &reqs[i]);
+    if (st != CE_MPPI_OK) return st;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "a handle appears twice");
+  }
+  ce_mppi_batch* b = new (std::nothrow) ce_mppi_batch();
+  if (!b) return fail(CE_MPPI_ERR_NO_MEMORY, "host allocation failed");
+  b->hs.assign(hs, hs + n);
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->dyn = dyn;
+  std::vector<InstDesc> descs(n);
+  std::vector<Req> rq(n);
+  std::vector<int2> roll, upd;
+  for (int i = 0; i < n; ++i) {
+    ce_mppi_handle* h = hs[i];
+    unsigned long long c0 = 0;
+    cudaStreamSynchronize(h->stream);
+    cudaMemcpy(&c0, h->hdesc.counter, 8, cudaMemcpyDeviceToHost);
+    descs[i] = h->hdesc;
+    rq[i] = to_req(&reqs[i], c0);
+    tiles_of(h, i, roll, upd);
+    b->smem_roll = std::max(b->smem_roll, h->smem_roll);
+    b->max_cells = std::max(b->max_cells, h->ncells);
+  }
+  b->n_roll = (int)roll.size();
+  b->n_upd = (int)upd.size();
+  auto cleanup = [&]() {
+    cudaFree(b->ddesc); cudaFree(b->dreq); cudaFree(b->dtiles_roll); cudaFree(b->dtiles_upd);
+    delete b;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->ddesc, sizeof(InstDesc) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&b->dreq, sizeof(Req) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&b->dtiles_roll, sizeof(int2) * roll.size())) != cudaSuccess ||
+      (e = cudaMalloc(&b->dtiles_upd, sizeof(int2) * upd.size())) != cudaSuccess) {
+    cleanup();
+    return fail(CE_MPPI_ERR_NO_MEMORY, "device allocation failed");
+  }
+  if ((e = cudaMemcpy(b->ddesc, descs.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->dreq, rq.data(), sizeof(Req) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->dtiles_roll, roll.data(), sizeof(int2) * roll.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->dtiles_upd, upd.data(), sizeof(int2) * upd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "batch upload");
+  }
+  if (use_graph) {
+    KArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.D = b->ddesc;
+    a.R = b->dreq;
+    a.n_inst = n;
+    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    run_chain(dyn, a, b->dtiles_roll, b->n_roll, b->dtiles_upd, b->n_upd, b->smem_roll,
+              b->max_cells, b->stream);
+    e = cudaStreamEndCapture(b->stream, &b->graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+      if (b->graph) cudaGraphDestroy(b->graph);
+      cleanup();
+      return cuda_fail(e, "graph capture");
+    }
+  }
+  *out = b;
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_batch_run(ce_mppi_batch* b) {
+  if (!b) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL batch");
+  if (b->exec) {
+    CE_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    return CE_MPPI_OK;
+  }
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.D = b->ddesc;
+  a.R = b->dreq;
+  a.n_inst = (int)b->hs.size();
+  run_chain(b->dyn, a, b->dtiles_roll, b->n_roll, b->dtiles_upd, b->n_upd, b->smem_roll,
+            b->max_cells, b->stream);
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms) {
+  if (!b || !stage_ms) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) CE_CUDA(cudaEventCreate(&ev[i]));
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.D = b->ddesc;
+  a.R = b->dreq;
+  a.n_inst = (int)b->hs.size();
+  cudaStream_t s = b->stream;
+  cudaEventRecord(ev[0], s);
+  launch_tracks(a, s);
+  cudaEventRecord(ev[1], s);
+  a.tiles = b->dtiles_roll;
+  a.n_tiles = b->n_roll;
+  launch_rollout(b->dyn, a, b->smem_roll, s);
+  cudaEventRecord(ev[2], s);
+  launch_prune(a, s);
+  cudaEventRecord(ev[3], s);
+  launch_dbscan(a, b->max_cells, s);
+  cudaEventRecord(ev[4], s);
+  launch_select(a, s);
+  cudaEventRecord(ev[5], s);
+  a.tiles = b->dtiles_upd;
+  a.n_tiles = b->n_upd;
+  launch_update(a, s);
+  cudaEventRecord(ev[6], s);
+  cudaError_t e = cudaEventSynchronize(ev[6]);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return cuda_fail(e, "batch profile");
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_batch_destroy(ce_mppi_batch* b) {
+  if (!b) return CE_MPPI_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->ddesc);
+  cudaFree(b->dreq);
+  cudaFree(b->dtiles_roll);
+  cudaFree(b->dtiles_upd);
+  delete b;
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* dst, size_t bytes) {
+  if (!h || !dst) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  const InstDesc& d = h->hdesc;
+  const size_t K = h->P.K, Kp = h->Kp, p = h->p, TM = (size_t)h->P.T * h->m;
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  auto want = [&](size_t b) -> ce_status_t {
+    return bytes == b ? CE_MPPI_OK : fail(CE_MPPI_ERR_INVALID_ARG, "peek: wrong byte count");
+  };
+  const void* src1 = nullptr;
+  switch (which) {
+    case CE_BUF_S: src1 = d.S; break;
+    case CE_BUF_HIT: src1 = d.hit; break;
+    case CE_BUF_IDXV: src1 = d.idxV; break;
+    case CE_BUF_IDXC: src1 = d.idxC; break;
+    case CE_BUF_LABEL: src1 = d.label; break;
+    case CE_BUF_W: src1 = d.w_k; break;
+    case CE_BUF_HITJ: src1 = d.hitj; break;
+    default: break;
+  }
+  if (src1) {
+    if (want(4 * K) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
+    CE_CUDA(cudaMemcpy(dst, src1, 4 * K, cudaMemcpyDeviceToHost));
+    return CE_MPPI_OK;
+  }
+  if (which == CE_BUF_PN || which == CE_BUF_Z || which == CE_BUF_G) {
+    if (want(4 * p * K) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
+    const float* s = which == CE_BUF_PN ? d.pN : (which == CE_BUF_Z ? d.z : d.g);
+    CE_CUDA(cudaMemcpy2D(dst, 4 * K, s, 4 * Kp, 4 * K, p, cudaMemcpyDeviceToHost));
+    return CE_MPPI_OK;
+  }
+  if (which == CE_BUF_EPS) {
+    if (want(4 * K * TM) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
+    float* o = static_cast<float*>(dst);
+    if (h->P.dyn == CE_DYN_ARM6_KIN) {
+      CE_CUDA(cudaMemcpy2D(o, 4 * TM, d.eps, 4 * (size_t)h->TMp, 4 * TM, K, cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> tmp(TM * K);
+      CE_CUDA(cudaMemcpy2D(tmp.data(), 4 * K, d.eps, 4 * Kp, 4 * K, TM, cudaMemcpyDeviceToHost));
+      for (size_t c = 0; c < TM; ++c)
+        for (size_t k = 0; k < K; ++k) o[k * TM + c] = tmp[c * K + k];
+    }
+    return CE_MPPI_OK;
+  }
+  return fail(CE_MPPI_ERR_INVALID_ARG, "peek: unknown buffer");
+}
+
+ce_status_t ce_mppi_philox_dev(unsigned long long seed, unsigned long long counter, int K, int nblk,
+                               unsigned int* out, void* stream) {
+  if (K < 0 || nblk < 0 || (!out && K * nblk > 0)) return fail(CE_MPPI_ERR_INVALID_ARG, "bad sizes");
+  if ((long long)K * nblk == 0) return CE_MPPI_OK;
+  launch_philox(seed, counter, K, nblk, out, static_cast<cudaStream_t>(stream));
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_normals_dev(unsigned long long seed, unsigned long long counter, int K, int n,
+                                float* out, void* stream) {
+  if (K < 0 || n < 0 || (!out && K * n > 0)) return fail(CE_MPPI_ERR_INVALID_ARG, "bad sizes");
+  if ((long long)K * n == 0) return CE_MPPI_OK;
+  launch_normals(seed, counter, K, n, out, static_cast<cudaStream_t>(stream));
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
+size_t ce_mppi_dbscan_workspace_bytes(int n) { return n < 0 ? 0 : dbscan_ws_bytes(n); }
+
+ce_status_t ce_mppi_dbscan_dev(const float* z, int n, int ld, int p, float eps, int min_pts,
+                               int* labels, int* n_clusters, void* ws, size_t ws_bytes,
+                               void* stream) {
+  if (p != 2 && p != 3) return fail(CE_MPPI_ERR_INVALID_ARG, "p must be 2 or 3");
+  if (n < 0 || ld < n || min_pts < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "bad sizes");
+  if (!(eps > 0.02f) || !(eps <= 2.0f)) return fail(CE_MPPI_ERR_INVALID_ARG, "eps must be in (0.02, 2]");
+  if (!n_clusters || (n > 0 && (!z || !labels || !ws)))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "NULL pointer");
+  if (ws_bytes < dbscan_ws_bytes(n)) return fail(CE_MPPI_ERR_INVALID_ARG, "workspace too small");
+  float ci;
+  int G, R, nc;
+  dbscan_grid(eps, p, &ci, &G, &R, &nc);
+  if (nc > kMaxCells) return fail(CE_MPPI_ERR_INVALID_ARG, "eps too small for the DBSCAN grid");
+  std::call_once(g_cfg_once, cem::configure_kernels);
+  launch_dbscan_standalone(z, n, ld, p, eps_squared(eps), ci, G, R, min_pts, labels, n_clusters,
+                           ws, static_cast<cudaStream_t>(stream));
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_arm_fk(const double* q, double* O, double* R) {
+  if (!q || !O || !R) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  const double d[6] = {0.1625, 0.0, 0.0, 0.1333, 0.0997, 0.0996};
+  const double a[6] = {0.0, -0.425, -0.3922, 0.0, 0.0, 0.0};
+  const double ca[6] = {0, 1, 1, 0, 0, 1}, sa[6] = {1, 0, 0, 1, -1, 0};
+  double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+  O[0] = O[1] = O[2] = 0.0;
+  for (int i = 0; i < 6; ++i) {
+    const double ct = std::cos(q[i]), st = std::sin(q[i]);
+    const double A[12] = {ct, -st * ca[i], st * sa[i], a[i] * ct,
+                          st, ct * ca[i], -ct * sa[i], a[i] * st,
+                          0, sa[i], ca[i], d[i]};
+    double N[12];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 4; ++c) {
+        double s = (c == 3) ? T[r * 4 + 3] : 0.0;
+        for (int e = 0; e < 3; ++e) s += T[r * 4 + e] * A[e * 4 + c];
+        N[r * 4 + c] = s;
+      }
+    std::memcpy(T, N, sizeof(T));
+    for (int r = 0; r < 3; ++r) O[(i + 1) * 3 + r] = T[r * 4 + 3];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) R[r * 3 + c] = T[r * 4 + c];
+  return CE_MPPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+// ce_mppi_internal.cuh -- device-side data layout and helpers shared by the
+// CE-MPPI kernels (sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ce_mppi.h"
+
+namespace cem {
+
+constexpr int kMaxM = 6;
+constexpr int kRolloutThreads = 128;    // 2-D rollouts: one rollout per thread
+constexpr int kArmWarps = 8;            // arm rollouts: one warp per rollout
+constexpr int kBlock = 1024;            // per-instance CTAs (prune, DBSCAN, select)
+constexpr int kUpdateWarps = 8;         // update CTA: one warp per column
+constexpr int kMaxCells = 8192;         // DBSCAN grid cells held in shared memory
+constexpr int kMaxObs = 4096;           // obstacle bitmap in shared memory
+constexpr int kMaxT = 256;
+constexpr int kMaxSmemTracks = 200 * 1024;
+constexpr long long kSpinLimit = 1ll << 22;   // bounded waits (mbarrier, union-find)
+
+// Per-instance control block written by the stages of one replan.
+struct Ctl {
+  int nV, nC, M, mode, sel, o_star, dynamic, status;
+  float S_min, invZ;
+  float pbar[3], v_obs[3], p0[3];
+  unsigned int done;              // last-CTA ticket of the update stage
+  int pad;
+  unsigned long long counter_used;
+};
+
+// Static description of one planner instance: parameters and device buffers.
+// Layout of the scratch buffers (Kp = K rounded up to a multiple of 32):
+//   tracks float4 [(T+1)][n_obs_max]  (x, y, z, (r_o + r_robot)^2)
+//   S, w float [Kp]; hit, hitj, idxV, idxC, label, cell, sorted, parent int [Kp]
+//   pN, z, g, zs float [p][Kp] (SoA)
+//   eps    2-D: float [T*m][Kp] (k fastest); arm: float [Kp][T*m] (k slowest)
+struct InstDesc {
+  int dyn, K, Kp, T, m, n, p, n_obs_max, H, min_pts, ref_mode, check_j0;
+  int G, R, eps_ld_c, eps_ld_k;   // DBSCAN grid size/reach; eps strides (column, rollout)
+  float dt, obs_dt, inv_lambda, eps2, cell_inv, robot_radius, norm_eps, v_static_thresh;
+  float sigma[6], u_min[6], u_max[6], goal[16], w[8];
+  unsigned int seed_lo, seed_hi;
+  unsigned long long* counter;
+  float* U;      // [T][m] nominal
+  float* Unew;   // [T][m] updated nominal before the shift
+  float4* tracks;
+  float *S, *w_k, *pN, *eps, *z, *g, *zs;
+  int *hit, *hitj, *idxV, *idxC, *label, *cell, *sorted, *parent;
+  float* bbox;   // [G^p][6] DBSCAN per-cell core bounding boxes
+  Ctl* ctl;
+};
+
+// One replan's inputs and outputs (device pointers).
+struct Req {
+  const float* x0;
+  const float* obs_hist;
+  const float* obs_radius;
+  int n_obs;
+  int pad;
+  long long obs_step;
+  unsigned long long counter0;
+  float* u_out;
+  float* x_next;
+  ce_mppi_diag* diag;
+};
+
+// Arguments common to every stage kernel.  Instance i's request is R[i] when
+// R is non-null (batches, graph replays) else r0 (single replans).
+struct KArgs {
+  const InstDesc* D;
+  const Req* R;
+  Req r0;
+  const int2* tiles;   // rollout / update tiles: (instance, first index)
+  int n_inst;
+  int n_tiles;
+};
+
+// Row stride (in float4) of the obstacle track table: odd, so that lanes
+// reading different horizon rows hit different shared-memory banks.
+__host__ __device__ __forceinline__ int track_stride(int n_obs) { return n_obs | 1; }
+
+__device__ __forceinline__ const Req& req_of(const KArgs& a, int i) {
+  return a.R ? a.R[i] : a.r0;
+}
+
+__device__ __forceinline__ const float* hist_of(const Req& r, const InstDesc& d) {
+  const unsigned long long c = *d.counter;
+  return r.obs_hist + (long long)(c - r.counter0) * r.obs_step;
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: ten rounds, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl
+// key increments 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Four standard normals from one Philox block: Box-Muller on the 24-bit
+// uniforms ((w >> 8) + 1/2) 2^-24 of the pairs (w0, w1) and (w2, w3).
+__device__ __forceinline__ float4 normals4(uint4 w) {
+  const float s24 = 5.9604644775390625e-8f;  // 2^-24
+  const float u1a = ((float)(w.x >> 8) + 0.5f) * s24, u2a = ((float)(w.y >> 8) + 0.5f) * s24;
+  const float u1b = ((float)(w.z >> 8) + 0.5f) * s24, u2b = ((float)(w.w >> 8) + 0.5f) * s24;
+  const float ra = sqrtf(-2.0f * logf(u1a)), rb = sqrtf(-2.0f * logf(u1b));
+  float sa, ca, sb, cb;
+  sincospif(2.0f * u2a, &sa, &ca);
+  sincospif(2.0f * u2b, &sb, &cb);
+  return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
+}
+
+__device__ __forceinline__ float4 philox_normals(const InstDesc& d, unsigned long long ctr,
+                                                 int k, int b) {
+  const uint4 c = make_uint4((uint32_t)k, (uint32_t)b, (uint32_t)ctr, (uint32_t)(ctr >> 32));
+  return normals4(philox10(c, make_uint2(d.seed_lo, d.seed_hi)));
+}
+
+// ---------------------------------------------------------------- TMA bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Global -> shared bulk copy (non-multicast), completion counted on bar.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of bar; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void raise_status(Ctl* c, int code) { atomicCAS(&c->status, 0, code); }
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Deterministic warp sum (fixed butterfly order).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Order-preserving map of a float to an unsigned int (for packed argmin).
+__device__ __forceinline__ uint32_t float_key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ---------------------------------------------------------------- models
+// Standard DH chain of the UR5e-like arm (d, a from the workload description,
+// alpha from the published UR convention): frame origins O[7][3], rotation R.
+__device__ __forceinline__ float dh_d(int i) {
+  return i == 0 ? 0.1625f : i == 3 ? 0.1333f : i == 4 ? 0.0997f : i == 5 ? 0.0996f : 0.0f;
+}
+__device__ __forceinline__ float dh_a(int i) { return i == 1 ? -0.425f : i == 2 ? -0.3922f : 0.0f; }
+// cos/sin of alpha = (pi/2, 0, 0, pi/2, -pi/2, 0), exact
+__device__ __forceinline__ float dh_ca(int i) { return (i == 0 || i == 3 || i == 4) ? 0.0f : 1.0f; }
+__device__ __forceinline__ float dh_sa(int i) {
+  return (i == 0 || i == 3) ? 1.0f : i == 4 ? -1.0f : 0.0f;
+}
+
+__device__ __forceinline__ void arm_fk(const float q[6], float O[7][3], float R[9]) {
+  float T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4, rows (R | t)
+  O[0][0] = O[0][1] = O[0][2] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float st, ct;
+    sincosf(q[i], &st, &ct);
+    const float ca = dh_ca(i), sa = dh_sa(i), ai = dh_a(i), di = dh_d(i);
+    // A = [[ct, -st ca, st sa, a ct], [st, ct ca, -ct sa, a st], [0, sa, ca, d]]
+    const float A00 = ct, A01 = -st * ca, A02 = st * sa, A03 = ai * ct;
+    const float A10 = st, A11 = ct * ca, A12 = -ct * sa, A13 = ai * st;
+    const float A21 = sa, A22 = ca, A23 = di;
+    float N[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float t0 = T[r * 4 + 0], t1 = T[r * 4 + 1], t2 = T[r * 4 + 2], t3 = T[r * 4 + 3];
+      N[r * 4 + 0] = t0 * A00 + t1 * A10;
+      N[r * 4 + 1] = t0 * A01 + t1 * A11 + t2 * A21;
+      N[r * 4 + 2] = t0 * A02 + t1 * A12 + t2 * A22;
+      N[r * 4 + 3] = t0 * A03 + t1 * A13 + t2 * A23 + t3;
+    }
+#pragma unroll
+    for (int e = 0; e < 12; ++e) T[e] = N[e];
+    O[i + 1][0] = T[3];
+    O[i + 1][1] = T[7];
+    O[i + 1][2] = T[11];
+  }
+  R[0] = T[0]; R[1] = T[1]; R[2] = T[2];
+  R[3] = T[4]; R[4] = T[5]; R[5] = T[6];
+  R[6] = T[8]; R[7] = T[9]; R[8] = T[10];
+}
+
+// Geodesic angle between R and the goal rotation Rg: atan2(|axis|, tr - 1)
+// with M = Rg^T R (well conditioned near 0 and pi, equal to acos((tr-1)/2)).
+__device__ __forceinline__ float rot_angle(const float R[9], const float* Rg) {
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      M[r * 3 + c] = Rg[0 * 3 + r] * R[0 * 3 + c] + Rg[1 * 3 + r] * R[1 * 3 + c] +
+                     Rg[2 * 3 + r] * R[2 * 3 + c];
+  const float tr = M[0] + M[4] + M[8];
+  const float ax = M[7] - M[5], ay = M[2] - M[6], az = M[3] - M[1];
+  return atan2f(sqrtf(ax * ax + ay * ay + az * az), tr - 1.0f);
+}
+
+// ---------------------------------------------------------------- launchers
+// Host-side launchers of each stage (defined in the .cu files).
+void launch_tracks(const KArgs& a, cudaStream_t s);
+void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s);
+void launch_prune(const KArgs& a, cudaStream_t s);
+void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s);
+void launch_select(const KArgs& a, cudaStream_t s);
+void launch_update(const KArgs& a, cudaStream_t s);
+void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
+                   unsigned int* out, cudaStream_t s);
+void launch_normals(unsigned long long seed, unsigned long long counter, int K, int n,
+                    float* out, cudaStream_t s);
+void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, float cell_inv,
+                              int G, int R, int min_pts, int* labels, int* n_clusters,
+                              void* ws, cudaStream_t s);
+int rollout_threads(int dyn);
+void configure_rollout();
+void configure_cluster();
+size_t dbscan_ws_bytes(int n);
+
+}  // namespace cem

@@ -1,0 +1,346 @@
+// k_rollout.cu -- obstacle tracks and the fused sample + rollout + cost +
+// collision kernels of the CE-MPPI replan (Algorithm 1, [Rollouts]).
+//
+// Noise: normal i of rollout k is element i % 4 of Philox4x32-10 block i / 4
+// with counter (k, i / 4, replan_lo, replan_hi) and key (seed_lo, seed_hi),
+// generated in registers (never stored as raw noise).  The effective
+// perturbation eps' = clip(u + sigma z) - u (Sec. II-A, Eq. 3) is written once
+// for the update stage.
+#include "ce_mppi_internal.cuh"
+
+namespace cem {
+
+// ------------------------------------------------------------------ tracks
+// Eq. 17 telescoped: v_o = (o_t - o_{t-H+1}) / ((H-1) Delta t); the predicted
+// centre at horizon step j is o_t + v_o (j dt).  One CTA per instance.
+__global__ void k_tracks(KArgs a) {
+  const int inst = blockIdx.x;
+  const InstDesc& d = a.D[inst];
+  const Req& r = req_of(a, inst);
+  const float* h = hist_of(r, d);
+  const int n_obs = r.n_obs, p = d.p, H = d.H;
+  const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
+  const int ts = track_stride(n_obs);
+  const int total = (d.T + 1) * n_obs;
+  if (threadIdx.x == 0) {   // a new replan: clear the control block's flags
+    d.ctl->status = 0;
+    d.ctl->done = 0u;
+  }
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int j = e / n_obs, o = e - j * n_obs;
+    const float* newest = h + ((size_t)(H - 1) * n_obs + o) * p;
+    const float* oldest = h + (size_t)o * p;
+    const float tj = (float)j * d.dt;
+    float c[3] = {0.0f, 0.0f, 0.0f};
+    for (int i = 0; i < p; ++i) c[i] = newest[i] + ((newest[i] - oldest[i]) * inv) * tj;
+    const float R = r.obs_radius[o] + d.robot_radius;
+    d.tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R * R);
+  }
+}
+
+// Stage the instance's tracks (TMA bulk copy) and nominal into shared memory.
+// Returns false (and records a timeout) if the copy did not land in time.
+__device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float4* trk,
+                                             float* Us, uint64_t* bar) {
+  const uint32_t bytes = n_obs > 0 ? (uint32_t)((d.T + 1) * track_stride(n_obs)) * 16u : 0u;
+  if (threadIdx.x == 0 && bytes > 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && bytes > 0) {
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(trk, d.tracks, bytes, bar);
+  }
+  for (int i = threadIdx.x; i < d.T * d.m; i += blockDim.x) Us[i] = d.U[i];
+  bool ok = true;
+  if (bytes > 0 && !mbar_wait(bar, 0)) {
+    raise_status(d.ctl, CE_MPPI_ERR_TIMEOUT);
+    mbar_wait(bar, 0);  // give the copy in flight one more bounded chance
+    ok = false;
+  }
+  __syncthreads();
+  return ok;
+}
+
+// ------------------------------------------------------------------ 2-D robots
+// One thread per rollout.  DYN 0: double integrator (p += v dt; v += a dt),
+// cost |p-g|^2 w0 + |u|^2 w1, terminal w2 |p_T - g|^2.  DYN 1: unicycle
+// (Eq. 21), cost Eq. 22-23 with Q = w[0..2], H = w[3..5].  Collision: first
+// horizon step j (1..T, plus 0 when check_j0) and lowest obstacle index with
+// |p_j - o_j|^2 < (r_o + r_robot)^2.
+template <int DYN>
+__global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  const int2 tile = a.tiles[blockIdx.x];
+  const InstDesc& d = a.D[tile.x];
+  const Req& r = req_of(a, tile.x);
+  const int n_obs = r.n_obs, T = d.T, Kp = d.Kp, ts = track_stride(n_obs);
+  float4* trk = reinterpret_cast<float4*>(smem_raw);
+  float* Us = reinterpret_cast<float*>(trk + (size_t)(T + 1) * ts);
+  if (!stage_tracks(d, n_obs, trk, Us, &bar)) return;
+  const int k = tile.y + threadIdx.x;
+  if (k >= d.K) return;
+  const unsigned long long ctr = *d.counter;
+
+  float s0 = r.x0[0], s1 = r.x0[1], s2 = r.x0[2], s3 = DYN == 0 ? r.x0[3] : 0.0f;
+  // parameters into registers (the output stores below may alias the descriptor)
+  const float dt = d.dt;
+  const float g0 = d.goal[0], g1 = d.goal[1], g2 = d.goal[2];
+  const float sg0 = d.sigma[0], sg1 = d.sigma[1];
+  const float lo0 = d.u_min[0], lo1 = d.u_min[1], hi0 = d.u_max[0], hi1 = d.u_max[1];
+  const float w0 = d.w[0], w1 = d.w[1], w2 = d.w[2], w3 = d.w[3], w4 = d.w[4], w5 = d.w[5];
+  float* __restrict__ eps = d.eps;
+  float S = 0.0f, Sc = 0.0f;
+  int first = -1, first_j = -1;
+  if (d.check_j0) {
+    int h = n_obs;
+    for (int o = n_obs - 1; o >= 0; --o) {
+      const float4 t = trk[o];
+      const float dx = s0 - t.x, dy = s1 - t.y;
+      h = (dx * dx + dy * dy < t.w) ? o : h;
+    }
+    if (h < n_obs) { first = h; first_j = 0; }
+  }
+  float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = 0; j < T; ++j) {
+    if ((j & 1) == 0) z4 = philox_normals(d, ctr, k, j >> 1);
+    const float z0 = (j & 1) ? z4.z : z4.x, z1 = (j & 1) ? z4.w : z4.y;
+    const float n0 = Us[2 * j], n1 = Us[2 * j + 1];
+    const float u0 = fminf(fmaxf(n0 + sg0 * z0, lo0), hi0);
+    const float u1 = fminf(fmaxf(n1 + sg1 * z1, lo1), hi1);
+    eps[(size_t)(2 * j) * Kp + k] = u0 - n0;
+    eps[(size_t)(2 * j + 1) * Kp + k] = u1 - n1;
+    if (DYN == 0) {
+      const float ex = s0 - g0, ey = s1 - g1;
+      kahan_add(S, Sc, w0 * (ex * ex + ey * ey) + w1 * (u0 * u0 + u1 * u1));
+      s0 += s2 * dt;
+      s1 += s3 * dt;
+      s2 += u0 * dt;
+      s3 += u1 * dt;
+    } else {
+      const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
+      kahan_add(S, Sc, w0 * ex * ex + w1 * ey * ey + w2 * et * et);
+      float sn, cs;
+      sincosf(s2, &sn, &cs);
+      s0 += u0 * cs * dt;
+      s1 += u0 * sn * dt;
+      s2 += u1 * dt;
+    }
+    if (first < 0) {
+      const float4* tj = trk + (size_t)(j + 1) * ts;
+      int h = n_obs;
+      for (int o = n_obs - 1; o >= 0; --o) {
+        const float4 t = tj[o];
+        const float dx = s0 - t.x, dy = s1 - t.y;
+        h = (dx * dx + dy * dy < t.w) ? o : h;
+      }
+      if (h < n_obs) { first = h; first_j = j + 1; }
+    }
+  }
+  if (DYN == 0) {
+    const float ex = s0 - g0, ey = s1 - g1;
+    kahan_add(S, Sc, w2 * (ex * ex + ey * ey));
+  } else {
+    const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
+    kahan_add(S, Sc, w3 * ex * ex + w4 * ey * ey + w5 * et * et);
+  }
+  d.S[k] = S;
+  d.hit[k] = first;
+  d.hitj[k] = first_j;
+  d.pN[k] = s0;
+  d.pN[Kp + k] = s1;
+}
+
+// ------------------------------------------------------------------ 6-DoF arm
+// One warp per rollout, lane l holds horizon step j = c*32 + l of chunk c:
+// control u_j, state q_{j+1} = q_0 + dt sum_{i<=j} u_i (warp prefix sum),
+// forward kinematics, 4 spheres per link against every obstacle, and the pose
+// cost of Eq. 24 (w_p |p_ee - p_g| + w_R angle(R, R_g) + w_c I_col).
+// S = sum_{j=0..T} l(q_j) (the terminal cost has the stage form).
+__device__ __forceinline__ int arm_collide(const float O[7][3], const float4* tj, int n_obs) {
+  float C[24][3];
+#pragma unroll
+  for (int link = 0; link < 6; ++link)
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        C[link * 4 + f][i] = O[link][i] + ((float)f * (1.0f / 3.0f)) * (O[link + 1][i] - O[link][i]);
+  for (int o = 0; o < n_obs; ++o) {
+    const float4 t = tj[o];
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < 24; ++s) {
+      const float dx = C[s][0] - t.x, dy = C[s][1] - t.y, dz = C[s][2] - t.z;
+      any |= (dx * dx + dy * dy + dz * dz < t.w);
+    }
+    if (any) return o;
+  }
+  return n_obs;
+}
+
+__device__ __forceinline__ float arm_cost(const InstDesc& d, const float O[7][3],
+                                          const float R[9], int collide) {
+  const float ex = O[6][0] - d.goal[0], ey = O[6][1] - d.goal[1], ez = O[6][2] - d.goal[2];
+  return d.w[0] * sqrtf(ex * ex + ey * ey + ez * ez) + d.w[1] * rot_angle(R, d.goal + 3) +
+         (collide ? d.w[2] : 0.0f);
+}
+
+__global__ void __launch_bounds__(kArmWarps * 32) k_rollout_arm(KArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  const int2 tile = a.tiles[blockIdx.x];
+  const InstDesc& d = a.D[tile.x];
+  const Req& r = req_of(a, tile.x);
+  const int n_obs = r.n_obs, T = d.T, ts = track_stride(n_obs);
+  float4* trk = reinterpret_cast<float4*>(smem_raw);
+  float* Us = reinterpret_cast<float*>(trk + (size_t)(T + 1) * ts);
+  if (!stage_tracks(d, n_obs, trk, Us, &bar)) return;
+  const int lane = threadIdx.x & 31;
+  const int k = tile.y + (threadIdx.x >> 5);
+  if (k >= d.K) return;
+  const unsigned long long ctr = *d.counter;
+  const float dt = d.dt;
+
+  float q[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) q[i] = r.x0[i];
+  float O[7][3], R[9];
+  // the shared initial state: its cost term (and optional collision test)
+  arm_fk(q, O, R);
+  const int c0 = arm_collide(O, trk, n_obs);
+  float S = 0.0f, Sc = 0.0f;
+  if (lane == 0) S = arm_cost(d, O, R, c0 < n_obs);
+  int first = -1, first_j = -1;
+  if (d.check_j0 && c0 < n_obs) { first = c0; first_j = 0; }
+  float pN[3] = {0.f, 0.f, 0.f};
+  for (int base = 0; base < T; base += 32) {
+    const int j = base + lane;
+    const bool act = j < T;
+    float u[6];
+    if (act) {
+      // normals 6j .. 6j+5 live in Philox blocks (6j)/4 and (6j)/4 + 1
+      const int n0 = 6 * j, b0 = n0 >> 2, off = n0 & 3;
+      const float4 za = philox_normals(d, ctr, k, b0);
+      const float4 zb = philox_normals(d, ctr, k, b0 + 1);
+      const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const float z = off == 0 ? zz[i] : zz[i + 2];
+        const float nom = Us[j * 6 + i];
+        u[i] = fminf(fmaxf(nom + d.sigma[i] * z, d.u_min[i]), d.u_max[i]);
+        d.eps[(size_t)k * d.eps_ld_k + n0 + i] = u[i] - nom;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) u[i] = 0.0f;
+    }
+    // inclusive warp prefix sum of u: displacement up to and including step j
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      float v = u[i];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      u[i] = v;
+    }
+    float qj[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) qj[i] = q[i] + u[i] * dt;
+    int hit_here = n_obs;
+    float cost = 0.0f;
+    if (act) {
+      arm_fk(qj, O, R);
+      hit_here = arm_collide(O, trk + (size_t)(j + 1) * ts, n_obs);
+      cost = arm_cost(d, O, R, hit_here < n_obs);
+      if (j == T - 1) { pN[0] = O[6][0]; pN[1] = O[6][1]; pN[2] = O[6][2]; }
+    }
+    kahan_add(S, Sc, cost);
+    const unsigned hm = __ballot_sync(0xffffffffu, hit_here < n_obs);
+    if (first < 0 && hm) {
+      const int l = __ffs(hm) - 1;
+      first = __shfl_sync(0xffffffffu, hit_here, l);
+      first_j = base + l + 1;
+    }
+    // carry the chunk's final state to the next chunk
+    const int last = min(31, T - 1 - base);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q[i] = __shfl_sync(0xffffffffu, qj[i], last);
+  }
+  S = warp_sum(S);
+  const int lt = (T - 1) & 31;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pN[i] = __shfl_sync(0xffffffffu, pN[i], lt);
+  if (lane == 0) {
+    d.S[k] = S;
+    d.hit[k] = first;
+    d.hitj[k] = first_j;
+    d.pN[k] = pN[0];
+    d.pN[d.Kp + k] = pN[1];
+    d.pN[2 * d.Kp + k] = pN[2];
+  }
+}
+
+// ------------------------------------------------------------------ test stages
+__global__ void k_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
+                         unsigned int* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)K * nblk) return;
+  const int k = (int)(i / nblk), b = (int)(i % nblk);
+  const uint4 w = philox10(make_uint4((uint32_t)k, (uint32_t)b, (uint32_t)counter,
+                                      (uint32_t)(counter >> 32)),
+                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  reinterpret_cast<uint4*>(out)[i] = w;
+}
+
+__global__ void k_normals(unsigned long long seed, unsigned long long counter, int K, int n,
+                          float* out) {
+  const int nb = (n + 3) / 4;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)K * nb) return;
+  const int k = (int)(i / nb), b = (int)(i % nb);
+  const uint4 w = philox10(make_uint4((uint32_t)k, (uint32_t)b, (uint32_t)counter,
+                                      (uint32_t)(counter >> 32)),
+                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float4 z = normals4(w);
+  const float zz[4] = {z.x, z.y, z.z, z.w};
+  for (int s = 0; s < 4 && 4 * b + s < n; ++s) out[(size_t)k * n + 4 * b + s] = zz[s];
+}
+
+// ------------------------------------------------------------------ launchers
+int rollout_threads(int dyn) { return dyn == CE_DYN_ARM6_KIN ? kArmWarps * 32 : kRolloutThreads; }
+
+void launch_tracks(const KArgs& a, cudaStream_t s) { k_tracks<<<a.n_inst, 256, 0, s>>>(a); }
+
+void configure_rollout() {
+  cudaFuncSetAttribute(k_rollout2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMaxSmemTracks + 8192);
+  cudaFuncSetAttribute(k_rollout2d<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMaxSmemTracks + 8192);
+  cudaFuncSetAttribute(k_rollout_arm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMaxSmemTracks + 8192);
+}
+
+void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s) {
+  if (dyn == CE_DYN_DOUBLE_INT_2D)
+    k_rollout2d<0><<<a.n_tiles, kRolloutThreads, smem_bytes, s>>>(a);
+  else if (dyn == CE_DYN_UNICYCLE)
+    k_rollout2d<1><<<a.n_tiles, kRolloutThreads, smem_bytes, s>>>(a);
+  else
+    k_rollout_arm<<<a.n_tiles, kArmWarps * 32, smem_bytes, s>>>(a);
+}
+
+void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
+                   unsigned int* out, cudaStream_t s) {
+  const long long n = (long long)K * nblk;
+  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, counter, K, nblk, out);
+}
+
+void launch_normals(unsigned long long seed, unsigned long long counter, int K, int n,
+                    float* out, cudaStream_t s) {
+  const long long tot = (long long)K * ((n + 3) / 4);
+  k_normals<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(seed, counter, K, n, out);
+}
+
+}  // namespace cem

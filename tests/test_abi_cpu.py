@@ -1,0 +1,86 @@
+"""CPU checks of the C ABI: the library loads without a GPU, exports every
+entry point the header declares, rejects bad parameters before any launch, and
+its host FK helper agrees with the oracle's."""
+import ctypes as C
+import math
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2607_06499_b300 as pkg
+from paper_2607_06499_b300 import workloads as W
+
+
+def _declared():
+    src = open(pkg.HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ce_mppi_\w+)\s*\(", src)))
+
+
+def test_header_declares_every_binding_export():
+    assert set(_declared()) == set(pkg.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = pkg.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def _params(**kw):
+    sc = W.make("unicycle", seed=0, K=256)
+    P = pkg.make_params(sc["cfg"], 50)
+    for k, v in kw.items():
+        if k in ("sigma", "u_min", "u_max"):
+            arr = getattr(P, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(P, k, v)
+    return P
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dyn=5), "dyn"), (dict(K=0), "K must"), (dict(T=0), "T must"), (dict(T=1000), "T must"),
+    (dict(dt=0.0), "dt"), (dict(dt=float("nan")), "dt"), (dict(lam=0.0), "lambda"),
+    (dict(dbscan_eps=0.0), "dbscan_eps"), (dict(min_pts=0), "min_pts"),
+    (dict(sigma=[-1.0, 0.5]), "sigma"), (dict(u_min=[3.0, -2.0]), "u_min"),
+    (dict(n_obs_max=100000), "n_obs_max"), (dict(hist_len=0), "hist_len"),
+    (dict(norm_eps=0.0), "norm_eps"), (dict(ref_mode=3), "ref_mode"),
+    (dict(n_obs_max=4000, T=100), "shared memory"),
+])
+def test_invalid_parameters_rejected_before_launch(kw, msg):
+    P = _params(**kw)
+    h = C.c_void_p()
+    st = pkg.lib().ce_mppi_create(C.byref(P), None, C.byref(h))
+    assert st == 1 and not h.value
+    assert msg in pkg.lib().ce_mppi_last_error().decode()
+
+
+def test_dbscan_grid_limit_for_3d_features():
+    sc = W.make("arm", seed=0, K=64)
+    P = pkg.make_params(sc["cfg"], 20)
+    P.dbscan_eps = 0.1
+    h = C.c_void_p()
+    assert pkg.lib().ce_mppi_create(C.byref(P), None, C.byref(h)) == 1
+    assert "grid" in pkg.lib().ce_mppi_last_error().decode()
+
+
+def test_arm_fk_helper_matches_oracle():
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        q = rng.uniform(-math.pi, math.pi, 6)
+        O1, R1 = pkg.arm_fk(q)
+        O2, R2 = oracle.arm_fk(q)
+        np.testing.assert_allclose(O1, O2, atol=1e-12)
+        np.testing.assert_allclose(R1, R2, atol=1e-12)
+
+
+def test_null_arguments_rejected():
+    L = pkg.lib()
+    assert L.ce_mppi_create(None, None, None) == 1
+    assert L.ce_mppi_replan(None, None, None, None, 0, None, None) == 1
+    assert L.ce_mppi_batch_create(None, None, 0, None, 0, None) == 1
+    assert L.ce_mppi_dbscan_dev(None, 4, 4, 5, 0.3, 3, None, None, None, 0, None) == 1

@@ -1,0 +1,308 @@
+"""GPU parity of the CE-MPPI replan against the FP64 oracle, stage by stage.
+
+Each stage of the CUDA path is compared with the oracle's stage run on the
+GPU stage's own inputs (stage hand-off), so that one boundary decision in FP32
+does not cascade.  Pass criteria:
+  * Philox words, pruning lists, DBSCAN partitions: bit-exact;
+  * collision flags, first hit: exact wherever the oracle's smallest
+    |clearance| of the rollout exceeds the band BAND (1e-5 m);
+  * costs, terminal positions, perturbations, reference point, features and the
+    updated nominal: relative error <= 1e-4 against max(|ref|, floor).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2607_06499_b300 as pkg
+from paper_2607_06499_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-5
+RTOL = 1e-4
+
+
+def _rel(a, ref, floor):
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if a.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - ref) / np.maximum(np.abs(ref), floor)))
+
+
+def _run(sc, r=0, counter=0):
+    cfg = sc["cfg"]
+    pl = pkg.Planner(cfg, n_obs_max=max(1, sc["radius"].shape[0]))
+    pl.set_nominal(sc["U0"])
+    pl.set_counter(counter)
+    hist = W.history(sc, r)
+    u, diag = pl.replan(sc["x0"], hist, sc["radius"])
+    out = {k: pl.peek(k) for k in ("S", "HIT", "HITJ", "PN", "EPS", "IDXV", "IDXC", "Z", "G",
+                                     "LABEL", "W")}
+    out["nominal_after"] = pl.get_nominal()
+    out["counter_after"] = pl.get_counter()
+    pl.close()
+    return u, diag, out, hist
+
+
+def _check_replan(sc, counter=0, report=None):
+    cfg = sc["cfg"]
+    n, m, p = pkg.DIMS[cfg["dyn"]]
+    K = cfg["K"]
+    u, diag, out, hist = _run(sc, counter=counter)
+    assert diag["status"] == 0
+    P = oracle.make_params(cfg, counter=counter)
+    trk = oracle.tracks(P, hist)
+    ref = oracle.rollouts(P, sc["x0"], sc["U0"], trk, sc["radius"])
+    # ---- rollouts: flags outside the band, first hit, costs, positions, perturbations
+    col_g = out["HIT"] >= 0
+    col_o = ref["col"] == 1
+    clear = ref["min_abs_clear"] > BAND
+    assert not np.any((col_g != col_o) & clear), "collision flag differs outside the band"
+    assert np.array_equal(out["HIT"][clear], ref["hit"][clear])
+    assert np.array_equal(out["HITJ"][clear], ref["hit_j"][clear])
+    errS = _rel(out["S"][clear], ref["S"][clear], 1.0)
+    errP = _rel(out["PN"].T[clear], ref["pN"][clear], 1.0)
+    sig = np.array(cfg["sigma"])[None, None, :]
+    errE = float(np.max(np.abs(out["EPS"] - ref["eps"]) / np.maximum(np.abs(ref["eps"]), 1e-3 * sig)))
+    assert errS < RTOL and errP < RTOL and errE < RTOL, (errS, errP, errE)
+    # ---- pruning (bit-exact on the GPU's flags)
+    idxV, idxC = oracle.prune(col_g.astype(np.int32))
+    nV, nC = diag["n_valid"], diag["n_col"]
+    assert (nV, nC) == (len(idxV), len(idxC))
+    assert np.array_equal(out["IDXV"][:nV], idxV) and np.array_equal(out["IDXC"][:nC], idxC)
+    S_g = out["S"].astype(np.float64)
+    eps_g = out["EPS"].astype(np.float64)
+    pN_g = out["PN"].T.astype(np.float64)
+    errs = dict(S=errS, pN=errP, eps=errE)
+    if nC == 0 or nV == 0:
+        assert diag["mode"] == (0 if nC == 0 else 1)
+        members = np.arange(K, dtype=np.int32)
+    else:
+        # ---- reference point and features (GPU flags and positions handed in)
+        o_star, pbar = oracle.reference_point(P, sc["x0"], trk, sc["radius"], idxC,
+                                              out["HIT"], pN_g)
+        assert o_star == diag["o_star"]
+        errs["pbar"] = _rel(np.array(diag["pbar"][:p]), pbar, 1.0)
+        assert errs["pbar"] < RTOL
+        z_ref, g_ref = oracle.features(P, sc["x0"], pbar, idxV, pN_g)
+        dnorm = np.linalg.norm(pN_g[idxV] - pbar[None, :], axis=1)
+        tol_z = RTOL + 4e-6 / np.maximum(dnorm, 1e-9)
+        z_g = out["Z"][:, :nV].T.astype(np.float64)
+        g_g = out["G"][:, :nV].T.astype(np.float64)
+        assert np.all(np.abs(z_g - z_ref).max(axis=1) <= tol_z)
+        enorm = np.linalg.norm(pN_g[idxV] - oracle.task_pos(P, sc["x0"])[None, :], axis=1)
+        assert np.all(np.abs(g_g - g_ref).max(axis=1) <= RTOL + 4e-6 / np.maximum(enorm, 1e-9))
+        # ---- DBSCAN on the GPU's own features: bit-exact
+        lab_o, M_o = oracle.dbscan(out["Z"][:, :nV].T, cfg["dbscan_eps"], cfg["min_pts"])
+        assert M_o == diag["n_clusters"]
+        assert np.array_equal(lab_o, out["LABEL"][:nV])
+        if M_o == 0:
+            assert diag["mode"] == 2
+            members = idxV
+        else:
+            v_obs = oracle.obstacle_velocity(P, hist)[o_star]
+            sel = oracle.select(P, lab_o, idxV, S_g, g_g, M_o, v_obs)
+            assert diag["dynamic"] == sel["dynamic"]
+            assert diag["mode"] == (4 if sel["dynamic"] else 3)
+            crit = sel["Sbar"] if not sel["dynamic"] else sel["vhat"] @ (v_obs / (np.linalg.norm(v_obs) + 1e-6))
+            srt = np.sort(crit)
+            near_tie = len(srt) > 1 and (srt[1] - srt[0]) <= 1e-5 * max(1.0, abs(srt[0]))
+            if not near_tie:
+                assert diag["sel_label"] == sel["sel"]
+            members = idxV[lab_o == diag["sel_label"]]
+    # ---- update (GPU costs, perturbations and selection handed in)
+    U_ref, w_ref, smin = oracle.update(P, sc["U0"], S_g, eps_g, members)
+    sig2 = np.array(cfg["sigma"])[None, :]
+    errs["U"] = float(np.max(np.abs(u - U_ref) / np.maximum(np.abs(U_ref), 1e-3 * sig2)))
+    errs["w"] = float(np.max(np.abs(out["W"] - w_ref)))
+    assert errs["U"] < RTOL, errs
+    assert errs["w"] < 1e-5 + 1e-4 * w_ref.max()
+    assert abs(out["W"].sum() - 1.0) < 1e-5
+    # ---- receding-horizon shift and counter
+    np.testing.assert_array_equal(out["nominal_after"], np.vstack([u[1:], u[-1:]]))
+    assert out["counter_after"] == counter + 1 and diag["counter"] == counter
+    if report is not None:
+        report.update(errs)
+    return diag, errs
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("di_static", {}), ("di_blocked", {}), ("unicycle_paper", {}), ("arm_paper", {}),
+    ("unicycle_blocked", dict(K=2000)), ("arm_blocked", dict(K=1000)),
+    ("unicycle", dict(K=777, T=23)), ("di_blocked", dict(K=4099, T=17)),
+])
+def test_stage_parity_small(name, kw):
+    sc = W.make(name, seed=0, **kw)
+    diag, errs = _check_replan(sc)
+    print(f"PARITY {name} {kw} mode={pkg.MODES[diag['mode']]} n_col={diag['n_col']} "
+          f"M={diag['n_clusters']} " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_stage_parity_other_seeds_and_counters(seed):
+    sc = W.make("unicycle_blocked", seed=seed, K=1500)
+    _check_replan(sc, counter=seed * 1000 + 7)
+    sc = W.make("arm_blocked", seed=seed, K=300)
+    _check_replan(sc, counter=(1 << 40) + seed)
+
+
+def test_stage_parity_full_size_unicycle():
+    """The benchmark's workload: unicycle, K=16384, T=50, 50 (+1) moving discs."""
+    sc = W.make("unicycle_blocked", seed=0)
+    diag, errs = _check_replan(sc)
+    assert diag["n_col"] > 0 and diag["n_clusters"] >= 1
+    print("PARITY full unicycle_blocked", diag["mode"], errs)
+
+
+def test_stage_parity_full_size_arm():
+    sc = W.make("arm_blocked", seed=0)
+    diag, errs = _check_replan(sc)
+    print("PARITY full arm_blocked", diag["mode"], errs)
+
+
+def test_philox_words_bit_exact():
+    dev = torch.device("cuda")
+    for seed, ctr, K, nb in [(0, 0, 37, 13), (0xDEADBEEFCAFEF00D, (1 << 33) + 5, 64, 7),
+                             (12345, 2**64 - 1, 5, 3)]:
+        out = torch.zeros(K * nb * 4, dtype=torch.int32, device=dev)
+        pkg.philox_dev(seed, ctr, K, nb, out)
+        torch.cuda.synchronize()
+        g = out.cpu().numpy().view(np.uint32).reshape(K, nb, 4)
+        for k in range(K):
+            for b in range(nb):
+                ctrw = [k, b, ctr & 0xFFFFFFFF, ctr >> 32]
+                key = [seed & 0xFFFFFFFF, seed >> 32]
+                assert np.array_equal(g[k, b], oracle.philox4x32_10(ctrw, key))
+
+
+def test_normals_close_to_fp64():
+    K, n = 50, 37
+    out = torch.zeros(K * n, dtype=torch.float32, device="cuda")
+    pkg.normals_dev(99, 4, K, n, out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy().reshape(K, n).astype(np.float64)
+    ref = np.stack([oracle.normals(99, 4, k, n) for k in range(K)])
+    err = np.abs(g - ref) / np.maximum(np.abs(ref), 1.0)
+    assert err.max() < 2e-6, err.max()
+
+
+def _features(rng, n, p, eps):
+    if p == 2:
+        c = rng.uniform(0, 2 * math.pi, size=4)
+        ang = c[rng.integers(0, 4, n)] + rng.normal(scale=0.12, size=n)
+        z = np.stack([np.cos(ang), np.sin(ang)], 1) * rng.uniform(0.9, 0.999, (n, 1))
+        k = max(1, n // 25)
+        z[rng.integers(0, n, k)] = rng.uniform(-1, 1, (k, 2)) * 0.7
+    else:
+        z = rng.normal(size=(n, 3))
+        z /= np.linalg.norm(z, axis=1, keepdims=True)
+        z[: n // 2] = z[0] + 0.1 * rng.normal(size=(n // 2, 3))
+        z = np.clip(z, -1, 1)
+    return z.astype(np.float32)
+
+
+@pytest.mark.parametrize("p,n,eps,mp", [(2, 1000, 0.25, 20), (2, 3333, 0.3, 10), (2, 97, 0.25, 5),
+                                        (3, 2049, 0.2, 16), (3, 500, 0.3, 5), (2, 16384, 0.25, 20)])
+def test_dbscan_standalone_bit_exact(p, n, eps, mp):
+    rng = np.random.default_rng(n + p)
+    z = _features(rng, n, p, eps)
+    zt = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
+    lab, M = pkg.dbscan_dev(zt, eps, mp)
+    torch.cuda.synchronize()
+    lab_o, M_o = oracle.dbscan(z, eps, mp)
+    assert int(M.item()) == M_o
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+
+
+def test_dbscan_edge_cases():
+    def run(z, eps, mp):
+        zt = torch.from_numpy(np.ascontiguousarray(np.asarray(z, np.float32).T.reshape(2, -1))).cuda()
+        lab, M = pkg.dbscan_dev(zt, eps, mp)
+        torch.cuda.synchronize()
+        return lab.cpu().numpy(), int(M.item())
+    lab, M = run(np.zeros((0, 2)), 0.3, 3)
+    assert M == 0 and lab.size == 0
+    lab, M = run([[0.1, 0.2]], 0.3, 1)
+    assert M == 1 and list(lab) == [0]
+    lab, M = run([[0.1, 0.2]], 0.3, 2)
+    assert M == 0 and list(lab) == [-1]
+    lab, M = run(np.full((500, 2), 0.5), 0.25, 20)          # one dense cell
+    assert M == 1 and np.all(lab == 0)
+    z = np.array([[0.0, 0.0], [0.25, 0.0], [0.5, 0.0], [0.9, 0.9]])  # chain at exactly eps
+    lab, M = run(z, 0.25, 2)
+    lab_o, M_o = oracle.dbscan(z, 0.25, 2)
+    assert M == M_o and np.array_equal(lab, lab_o)
+    # coordinates outside [-1, 1] are refused on the device
+    lab, M = run([[2.0, 0.0], [0.0, 0.0]], 0.3, 1)
+    assert M < 0
+
+
+def test_replan_deterministic_and_batch_equals_single():
+    scs = [W.make("batch_instance", seed=s) for s in (3, 4, 5)]
+    scs = [s for s in scs] + [W.make("unicycle_blocked", seed=0, K=3000)]
+    singles = []
+    for sc in scs:
+        u1, d1, _, _ = _run(sc)
+        u2, d2, _, _ = _run(sc)
+        assert np.array_equal(u1, u2)                       # bitwise repeatable
+        singles.append(u1)
+    for use_graph in (0, 1):
+        pls, reqs = [], []
+        for sc in scs:
+            pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+            pl.set_nominal(sc["U0"])
+            reqs.append(dict(x0=torch.tensor(sc["x0"], dtype=torch.float32, device="cuda"),
+                             hist=torch.tensor(W.history(sc, 0), dtype=torch.float32, device="cuda"),
+                             radius=torch.tensor(sc["radius"], dtype=torch.float32, device="cuda"),
+                             u_out=torch.zeros((sc["cfg"]["T"], 2), device="cuda")))
+            pls.append(pl)
+        b = pkg.Batch(pls, reqs, use_graph=bool(use_graph))
+        b.run()
+        torch.cuda.synchronize()
+        for i, r in enumerate(reqs):
+            assert np.array_equal(r["u_out"].cpu().numpy(), singles[i]), i
+        b.close()
+        for pl in pls:
+            pl.close()
+
+
+def test_closed_loop_episode_on_device():
+    """Device-resident closed loop: recorded observations advance per replan
+    (obs_step) and x_next aliases x0, all inside one captured graph."""
+    R = 30
+    sc = W.make("unicycle", seed=0, K=4096, n_replans=R)
+    cfg = sc["cfg"]
+    pl = pkg.Planner(cfg, n_obs_max=sc["radius"].shape[0])
+    pl.set_nominal(np.tile([1.0, 0.0], (cfg["T"], 1)))
+    x = torch.tensor(sc["x0"], dtype=torch.float32, device="cuda")
+    obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda").contiguous()
+    rad = torch.tensor(sc["radius"], dtype=torch.float32, device="cuda")
+    diag = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    req = dict(x0=x, hist=obs, radius=rad, x_next=x, diag=diag,
+               obs_step=sc["radius"].shape[0] * 2)
+    b = pkg.Batch([pl], [req], use_graph=True)
+    goal = np.array(cfg["goal"][:2])
+    d0 = np.linalg.norm(sc["x0"][:2] - goal)
+    for _ in range(R):
+        b.run()
+    torch.cuda.synchronize()
+    xf = x.cpu().numpy()
+    assert np.all(np.isfinite(xf))
+    assert np.linalg.norm(xf[:2] - goal) < d0 - 0.5      # made progress toward the goal
+    assert pl.get_counter() == R
+    st = np.frombuffer(diag.cpu().numpy().tobytes(), dtype=np.int32)[7]
+    assert st == 0
+    b.close()
+    pl.close()
+
+
+def test_host_replan_rejects_too_many_obstacles():
+    sc = W.make("di_static", seed=0, K=64)
+    pl = pkg.Planner(sc["cfg"], n_obs_max=3)
+    with pytest.raises(pkg.CeError):
+        pl.replan(sc["x0"], W.history(sc, 0), sc["radius"])
+    pl.close()
