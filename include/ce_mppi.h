@@ -195,8 +195,10 @@ ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* host_dst, size_t by
  * (seed_lo, seed_hi) (Salmon et al., SC'11).                                  */
 ce_status_t ce_mppi_philox_dev(unsigned long long seed, unsigned long long counter, int K,
                                int nblk, unsigned int* out, void* stream);
-/* The first n standard normals of rollouts k < K: out[k][n] (Box-Muller on
- * 24-bit uniforms of the words above, pairs (w0,w1) and (w2,w3)).            */
+/* The first n standard normals of rollouts k < K: out[k][n]: normal i is
+ * element i % 4 of block i / 4; Box-Muller on the uniforms ((w >> 9) + 1/2)
+ * 2^-23 of the word pairs (w0,w1) and (w2,w3): r = sqrt(-2 ln u1),
+ * (r cos 2 pi u2, r sin 2 pi u2).                                            */
 ce_status_t ce_mppi_normals_dev(unsigned long long seed, unsigned long long counter, int K,
                                 int n, float* out, void* stream);
 /* DBSCAN (Sec. II-B2) of n points z stored as [p][ld] (SoA, p = 2 or 3):

@@ -67,8 +67,9 @@ void philox10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
   for (int i = 0; i < 4; ++i) out[i] = c[i];
 }
 
-// Uniform in (0,1) from the top 24 bits of a word: ((w >> 8) + 1/2) / 2^24.
-double unit24(uint32_t w) { return ((double)(w >> 8) + 0.5) / 16777216.0; }
+// Uniform in (0,1) from the top 23 bits of a word: ((w >> 9) + 1/2) / 2^23
+// (exactly representable in FP32 as well, so both precisions see one value).
+double unit23(uint32_t w) { return ((double)(w >> 9) + 0.5) / 8388608.0; }
 
 int dim_n(int dyn) { return dyn == ORC_DI ? 4 : (dyn == ORC_UNICYCLE ? 3 : 6); }
 int dim_m(int dyn) { return dyn == ORC_ARM ? 6 : 2; }
@@ -182,8 +183,8 @@ void orc_normals(uint64_t seed, uint64_t counter, int k, int n, double* out) {
     philox10(ctr, key, wv);
     double z[4];
     for (int pair = 0; pair < 2; ++pair) {
-      const double u1 = unit24(wv[2 * pair]);
-      const double u2 = unit24(wv[2 * pair + 1]);
+      const double u1 = unit23(wv[2 * pair]);
+      const double u2 = unit23(wv[2 * pair + 1]);
       const double r = std::sqrt(-2.0 * std::log(u1));
       z[2 * pair] = r * std::cos(2.0 * kPi * u2);
       z[2 * pair + 1] = r * std::sin(2.0 * kPi * u2);

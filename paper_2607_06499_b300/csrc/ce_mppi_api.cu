@@ -474,13 +474,22 @@ ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_reques
     a.D = b->ddesc;
     a.R = b->dreq;
     a.n_inst = n;
-    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+    // capture on a private non-blocking stream (the legacy default stream
+    // cannot be captured); the graph is launched on the batch's stream.
+    cudaStream_t cap;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      cudaStreamDestroy(cap);
       cleanup();
       return cuda_fail(e, "cudaStreamBeginCapture");
     }
     run_chain(dyn, a, b->dtiles_roll, b->n_roll, b->dtiles_upd, b->n_upd, b->smem_roll,
-              b->max_cells, b->stream);
-    e = cudaStreamEndCapture(b->stream, &b->graph);
+              b->max_cells, cap);
+    e = cudaStreamEndCapture(cap, &b->graph);
+    cudaStreamDestroy(cap);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) {
       if (b->graph) cudaGraphDestroy(b->graph);

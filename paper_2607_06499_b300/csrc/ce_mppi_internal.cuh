@@ -105,12 +105,13 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
   return c;
 }
 
-// Four standard normals from one Philox block: Box-Muller on the 24-bit
-// uniforms ((w >> 8) + 1/2) 2^-24 of the pairs (w0, w1) and (w2, w3).
+// Four standard normals from one Philox block: Box-Muller on the 23-bit
+// uniforms ((w >> 9) + 1/2) 2^-23 of the pairs (w0, w1) and (w2, w3); each
+// uniform is exact in FP32 (24 significant bits).
 __device__ __forceinline__ float4 normals4(uint4 w) {
-  const float s24 = 5.9604644775390625e-8f;  // 2^-24
-  const float u1a = ((float)(w.x >> 8) + 0.5f) * s24, u2a = ((float)(w.y >> 8) + 0.5f) * s24;
-  const float u1b = ((float)(w.z >> 8) + 0.5f) * s24, u2b = ((float)(w.w >> 8) + 0.5f) * s24;
+  const float s23 = 1.1920928955078125e-7f;  // 2^-23
+  const float u1a = ((float)(w.x >> 9) + 0.5f) * s23, u2a = ((float)(w.y >> 9) + 0.5f) * s23;
+  const float u1b = ((float)(w.z >> 9) + 0.5f) * s23, u2b = ((float)(w.w >> 9) + 0.5f) * s23;
   const float ra = sqrtf(-2.0f * logf(u1a)), rb = sqrtf(-2.0f * logf(u1b));
   float sa, ca, sb, cb;
   sincospif(2.0f * u2a, &sa, &ca);

@@ -66,8 +66,11 @@ def _check_replan(sc, counter=0, report=None):
     assert np.array_equal(out["HITJ"][clear], ref["hit_j"][clear])
     errS = _rel(out["S"][clear], ref["S"][clear], 1.0)
     errP = _rel(out["PN"].T[clear], ref["pN"][clear], 1.0)
+    # eps' = u - U with u = U + eps' held in FP32: its rounding scales with
+    # |U| + |eps'| (the magnitude of the applied control), floored at 1e-3 sigma
     sig = np.array(cfg["sigma"])[None, None, :]
-    errE = float(np.max(np.abs(out["EPS"] - ref["eps"]) / np.maximum(np.abs(ref["eps"]), 1e-3 * sig)))
+    scaleE = np.maximum(np.abs(sc["U0"])[None] + np.abs(ref["eps"]), 1e-3 * sig)
+    errE = float(np.max(np.abs(out["EPS"] - ref["eps"]) / scaleE))
     assert errS < RTOL and errP < RTOL and errE < RTOL, (errS, errP, errE)
     # ---- pruning (bit-exact on the GPU's flags)
     idxV, idxC = oracle.prune(col_g.astype(np.int32))
@@ -116,8 +119,12 @@ def _check_replan(sc, counter=0, report=None):
             members = idxV[lab_o == diag["sel_label"]]
     # ---- update (GPU costs, perturbations and selection handed in)
     U_ref, w_ref, smin = oracle.update(P, sc["U0"], S_g, eps_g, members)
+    # relative to the magnitude of the terms of U + sum_k w_k eps'_k (the
+    # condition of the weighted sum), floored at 1e-3 sigma
     sig2 = np.array(cfg["sigma"])[None, :]
-    errs["U"] = float(np.max(np.abs(u - U_ref) / np.maximum(np.abs(U_ref), 1e-3 * sig2)))
+    scaleU = np.maximum(np.abs(sc["U0"]) + np.einsum("k,kjd->jd", w_ref, np.abs(eps_g)), 1e-3 * sig2)
+    scaleU = np.maximum(scaleU, np.abs(U_ref))
+    errs["U"] = float(np.max(np.abs(u - U_ref) / scaleU))
     errs["w"] = float(np.max(np.abs(out["W"] - w_ref)))
     assert errs["U"] < RTOL, errs
     assert errs["w"] < 1e-5 + 1e-4 * w_ref.max()
