@@ -214,6 +214,22 @@ ce_status_t ce_mppi_dbscan_dev(const float* z, int n, int ld, int p, float eps, 
                                int* labels, int* n_clusters, void* workspace, size_t ws_bytes,
                                void* stream);
 
+/* DBSCAN exactly as ce_mppi_dbscan_dev, for callers that cannot allocate
+ * device memory (no workspace argument).  It makes no allocation call: its
+ * scratch is a fixed __device__ array of about 0.6 MB compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Limits: n <= 16384 points (larger n is rejected with INVALID_ARG).
+ * The first call on a device looks up the scratch's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array and nothing in it needs to
+ * start cleared; calls that can run at the same time on the GPU (different
+ * streams, or different host threads) race on it and must be serialised by
+ * the caller.  The paper has no counterpart: this is a deployment variant of
+ * the clustering stage.  Errors: INVALID_ARG, CUDA.                           */
+ce_status_t ce_mppi_dbscan_noalloc_dev(const float* z, int n, int ld, int p, float eps,
+                                       int min_pts, int* labels, int* n_clusters,
+                                       void* stream);
+
 /* Host helper: forward kinematics of the arm model (standard DH, UR5e-like),
  * frame origins O[7][3] and end-effector rotation R[3][3], FP64, for turning a
  * joint-space goal into the pose goal of ce_mppi_params.                      */

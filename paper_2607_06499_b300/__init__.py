@@ -72,7 +72,7 @@ EXPORTS = (
     "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
     "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
-    "ce_mppi_dbscan_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
+    "ce_mppi_dbscan_dev", "ce_mppi_dbscan_noalloc_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
 )
 
 _lib = None
@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_dbscan_workspace_bytes.argtypes = [i]
         L.ce_mppi_dbscan_workspace_bytes.restype = C.c_size_t
         L.ce_mppi_dbscan_dev.argtypes = [vp, i, i, i, f, i, vp, vp, vp, C.c_size_t, vp]
+        L.ce_mppi_dbscan_noalloc_dev.argtypes = [vp, i, i, i, f, i, vp, vp, vp]
         L.ce_mppi_arm_fk.argtypes = [C.POINTER(C.c_double)] * 3
         L.ce_mppi_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -297,4 +298,17 @@ def dbscan_dev(z, eps: float, min_pts: int, stream=None):
     _check(lib().ce_mppi_dbscan_dev(z.data_ptr(), n, z.stride(0), p, eps, min_pts,
                                     labels.data_ptr(), M.data_ptr(), ws.data_ptr(), nbytes,
                                     C.c_void_p(_stream_ptr(stream))))
+    return labels[:n], M
+
+
+def dbscan_noalloc_dev(z, eps: float, min_pts: int, stream=None):
+    """DBSCAN of device points z [p][n] through the allocation-free entry point
+    (fixed scratch inside the library, n <= 16384); returns (labels, M)."""
+    import torch
+    p, n = z.shape
+    labels = torch.empty(max(n, 1), dtype=torch.int32, device=z.device)
+    M = torch.zeros(1, dtype=torch.int32, device=z.device)
+    _check(lib().ce_mppi_dbscan_noalloc_dev(z.data_ptr(), n, z.stride(0) if n else 0, p, eps,
+                                            min_pts, labels.data_ptr(), M.data_ptr(),
+                                            C.c_void_p(_stream_ptr(stream))))
     return labels[:n], M

@@ -5,7 +5,8 @@ import os
 import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ce_mppi_api.cu", "k_rollout.cu", "k_cluster.cu")]
+SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ce_mppi_api.cu", "k_rollout.cu", "k_cluster.cu",
+                                                              "ce_mppi_noalloc.cu")]
 HEADERS = [os.path.join(_HERE, "csrc", "ce_mppi_internal.cuh"),
            os.path.join(os.path.dirname(_HERE), "include", "ce_mppi.h")]
 OUT = os.path.join(_HERE, "libcemppi.so")

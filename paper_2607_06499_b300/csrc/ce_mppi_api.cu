@@ -64,6 +64,8 @@ std::once_flag g_cfg_once;
 }  // namespace
 
 namespace cem {
+void set_last_error(const char* msg) { g_err = msg; }
+
 void configure_kernels() {
   configure_rollout();
   configure_cluster();

@@ -267,6 +267,7 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
                               void* ws, cudaStream_t s);
 int rollout_threads(int dyn);
 void configure_rollout();
+void set_last_error(const char* msg);   // message returned by ce_mppi_last_error()
 void configure_cluster();
 size_t dbscan_ws_bytes(int n);
 
