@@ -8,7 +8,8 @@ from paper_2607_06499_b300.workloads; observation streams and robot states are
 resident on the device and the loop is closed on the device (x_next = x0).
 
 One step = one replan of each of the 16 episodes, one launch per stage for all
-of them, replayed from a captured CUDA graph.  value = rollout-steps/s
+of them, replayed from a captured CUDA graph; an episode is 200 closed-loop
+replans and restarts (untimed) after that.  value = rollout-steps/s
 (16 * K * T per step).  The same replans run one instance at a time through the
 blocking host-buffer call (the plain form) for comparison.
 
@@ -35,9 +36,27 @@ N_EPISODES = 16
 WORKLOAD = dict(workload="ce-mppi replan, unicycle closed loop, moving obstacles", dyn="unicycle",
                 K=16384, T=50, n_obs=50, episodes=N_EPISODES, dbscan_eps=0.25, min_pts=20,
                 lam=1.0, sigma=[0.5, 0.5], l2="flushed between timed steps (256 MB write)")
+# Other workloads (--workload): the 6-DoF arm (K=4096, T=32, 20 moving spheres,
+# 500-replan episodes) and the uneven batch (256 unicycle instances, K
+# log-uniform in [512, 16384], T in [20, 60], 5-100 discs, 50 replans each).
+WORKLOADS = {
+    "unicycle": dict(scene="unicycle", n=N_EPISODES, episode=200, u_init=(1.0, 0.0),
+                     config=WORKLOAD),
+    "arm": dict(scene="arm", n=N_EPISODES, episode=500, u_init=None,
+                config=dict(workload="ce-mppi replan, 6-DoF arm closed loop, moving spheres",
+                            dyn="arm", K=4096, T=32, n_obs=20, episodes=N_EPISODES,
+                            dbscan_eps=0.2, min_pts=16, lam=1.0, sigma=[0.3] * 6,
+                            l2="flushed between timed steps (256 MB write)")),
+    "batch": dict(scene="batch_instance", n=256, episode=50, u_init=(1.0, 0.0),
+                  config=dict(workload="ce-mppi replan, 256 uneven unicycle instances",
+                              dyn="unicycle", K="log-uniform [512, 16384]", T="[20, 60]",
+                              n_obs="[5, 100]", instances=256, static_fraction=0.5,
+                              l2="flushed between timed steps (256 MB write)")),
+}
 METRIC = "CE-MPPI replan throughput (rollout-steps/s)"
 UNIT = "rollout-steps/s"
 STAGES = ("tracks", "rollout", "prune", "dbscan", "select", "update")
+EPISODE = 200   # closed-loop replans per episode
 
 
 def peaks():
@@ -55,11 +74,9 @@ def alu_peak_tflops(sm_count: int, mhz: float) -> float:
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def rollout_flops_per_step(n_obs: int) -> int:
-    """Algorithmic FP32 operations of one unicycle rollout-step: 6 per circle
-    test (2 sub, mul, fma counted 2, compare) and 60 for sampling clip, cost
-    and the model step (Eq. 3-5, Eq. 21-23)."""
-    return 6 * n_obs + 60
+# Algorithmic FP32 operations of a unicycle rollout: 6 per circle test (2 sub,
+# mul, fma counted 2, compare) over the obstacle tests the track builder keeps,
+# plus 60 per step for the clip, the cost and the model step (Eq. 3-5, 21-23).
 
 
 class ClockSampler:
@@ -99,28 +116,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(scenes, max_threads: int, budget_s: float = 20.0) -> dict:
+def cpu_baseline(scenes, u_init, max_threads: int, budget_s: float = 10.0) -> dict:
     """The FP64 oracle on the host cores: independent replans of the workload's
-    episodes (first replan each), one per thread, repeated while within budget."""
+    instances (first replan, the bench's initial nominal), one per thread, with
+    successive replan counters, repeated while within the time budget."""
     import oracle
     nthr = max(1, min(max_threads, os.cpu_count() or 1))
-    Ps = [oracle.make_params(s["cfg"]) for s in scenes]
-    args = ([s["x0"] for s in scenes], [s["U0"] for s in scenes],
-            [W.history(s, 0) for s in scenes], [s["radius"] for s in scenes])
-    done, secs = 0, 0.0
+    done, secs, rnd, units = 0, 0.0, 0, 0
     t0 = time.perf_counter()
     while True:
-        n = min(nthr, len(scenes))
-        _, dt = oracle.replan_many(Ps[:n], *[a[:n] for a in args], n_threads=n)
-        done += n
+        batch = [scenes[(done + i) % len(scenes)] for i in range(nthr)]
+        Ps = [oracle.make_params(s["cfg"], counter=rnd) for s in batch]
+        _, dt = oracle.replan_many(Ps, [s["x0"] for s in batch], [u_init(s) for s in batch],
+                                   [W.history(s, 0) for s in batch], [s["radius"] for s in batch],
+                                   n_threads=nthr)
+        done += nthr
+        units += sum(s["cfg"]["K"] * s["cfg"]["T"] for s in batch)
         secs += dt
-        if time.perf_counter() - t0 > budget_s or done >= len(scenes):
+        rnd += 1
+        if time.perf_counter() - t0 > budget_s:
             break
-    cfg = scenes[0]["cfg"]
-    return {"value": done * cfg["K"] * cfg["T"] / secs, "unit": UNIT, "cores": min(nthr, len(scenes)),
+    return {"value": units / secs, "unit": UNIT, "cores": nthr,
             "kind": "oracle", "seconds": secs,
-            "sample": f"{done} full replans (first replan of episodes 0..{done - 1}), one per host "
-                      f"thread; FP64, O(|V|^2) DBSCAN"}
+            "sample": f"{done} full replans (first replan of the episodes, warm nominal, "
+                      f"successive counters), {nthr} host threads; FP64, O(|V|^2) DBSCAN"}
 
 
 def run_reference(args) -> None:
@@ -155,14 +174,118 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: float = 200.0) -> dict:
+    """The served request loop: controller sessions arrive as a Poisson process
+    (rate_hz), 70 % unicycle (K in {1024, 4096, 16384}, T=50, 50 discs) and 30 %
+    arm (K in {2048, 4096}, T=32, 20 spheres); each asks for a replan every 20 ms
+    for a lifetime U[2, 20] s.  Sessions are admitted by the server's
+    device-memory budget.  Requests are submitted in real time (1 ms ticks);
+    a session's request that is still queued when its next one arrives is
+    replaced by the newer one.  Returns served throughput and latency."""
+    arrivals = W.session_arrivals(rate_hz, seconds, seed=seed)
+    n_rep = int(20.0 / 0.02) + 8
+    tmpl = {"unicycle": [W.make("unicycle", seed=100 + i, n_replans=n_rep) for i in range(8)],
+            "arm": [W.make("arm", seed=200 + i, n_replans=n_rep) for i in range(8)]}
+    obs = {k: np.stack([t["obs"] for t in v]).astype(np.float32) for k, v in tmpl.items()}
+    rad = {k: np.stack([t["radius"] for t in v]).astype(np.float32) for k, v in tmpl.items()}
+    x0s = {k: np.stack([t["x0"] for t in v]).astype(np.float32) for k, v in tmpl.items()}
+    H = 5
+    srv = pkg.Server(mem_budget_bytes=int(budget_gb * (1 << 30)), max_sessions=4096,
+                     max_batch=1024, n_streams=3)
+    active = {}   # sid -> [kind, template, t_start, t_end, next_due, K, T]
+    rejected = opened = 0
+    submitted = {"unicycle": 0, "arm": 0}
+    steps_sub = 0.0
+    nxt = 0
+    t0 = time.perf_counter()
+    while True:
+        t = time.perf_counter() - t0
+        if t >= seconds:
+            break
+        while nxt < len(arrivals) and arrivals[nxt]["t"] <= t:
+            a = arrivals[nxt]
+            nxt += 1
+            tid = a["seed"] % 8
+            cfg = dict(tmpl[a["kind"]][tid]["cfg"])
+            cfg["K"] = a["K"]
+            sid = srv.open(cfg, int(rad[a["kind"]].shape[1]))
+            if sid is None:
+                rejected += 1
+                continue
+            opened += 1
+            active[sid] = [a["kind"], tid, t, t + a["lifetime"], t, cfg["K"], cfg["T"]]
+        for sid in [s_ for s_, v in active.items() if v[3] <= t]:
+            srv.close_session(sid)
+            del active[sid]
+        for kind in ("unicycle", "arm"):
+            due = [s_ for s_, v in active.items() if v[0] == kind and v[4] <= t]
+            if not due:
+                continue
+            tids = np.array([active[s_][1] for s_ in due])
+            r = np.array([int((t - active[s_][2]) / 0.02) % (n_rep - 8) for s_ in due])
+            win = obs[kind][tids[:, None], r[:, None] + np.arange(H)[None, :]]
+            srv.submit_many(np.array(due, np.int32), x0s[kind][tids], win, rad[kind][tids],
+                            np.full(len(due), rad[kind].shape[1], np.int32))
+            submitted[kind] += len(due)
+            for s_ in due:
+                active[s_][4] += 0.02
+                steps_sub += active[s_][5] * active[s_][6]
+        time.sleep(max(0.0, 0.001 - ((time.perf_counter() - t0) - t)))
+    st = srv.stats()
+    elapsed = time.perf_counter() - t0
+    for sid in list(active):
+        srv.close_session(sid)
+    srv.close()
+    n_sub = sum(submitted.values())
+    frac_served = st["replans"] / max(1, n_sub)
+    return {"seconds": elapsed, "sessions_opened": opened, "sessions_rejected": rejected,
+            "requests_submitted": n_sub, "replans_served": st["replans"],
+            "superseded": st["superseded"], "replans_per_s": st["replans"] / elapsed,
+            "rollout_steps_per_s": steps_sub * frac_served / elapsed,
+            "p50_ms": 1e3 * st["p50_latency_s"], "p99_ms": 1e3 * st["p99_latency_s"],
+            "mean_batch": st["mean_batch"], "budget_gb": budget_gb, "arrival_rate_hz": rate_hz}
+
+
+def plain_mix_latency(pkg, n_each: int = 20) -> dict:
+    """Plain form on the served mix: each replan alone through the blocking
+    host-buffer call (launch chain + stream sync per replan)."""
+    lat, steps = [], 0
+    mix = [("unicycle", 1024, 0.7 / 3), ("unicycle", 4096, 0.7 / 3), ("unicycle", 16384, 0.7 / 3),
+           ("arm", 2048, 0.15), ("arm", 4096, 0.15)]
+    per_kind = {}
+    for kind, K, w in mix:
+        sc = W.make(kind, seed=300, K=K, n_replans=n_each + 2)
+        pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+        ls = []
+        for r in range(n_each + 2):
+            t1 = time.perf_counter()
+            pl.replan(sc["x0"], W.history(sc, r), sc["radius"])
+            ls.append(time.perf_counter() - t1)
+        pl.close()
+        per_kind[(kind, K)] = (np.array(ls[2:]), w, K * sc["cfg"]["T"])
+    # the mix-weighted latency distribution and capacity of one sequential loop
+    samples = np.concatenate([np.repeat(v[0], int(round(v[1] * 100))) for v in per_kind.values()])
+    mean_s = sum(v[1] * v[0].mean() for v in per_kind.values())
+    steps = sum(v[1] * v[2] for v in per_kind.values())
+    return {"p50_ms": 1e3 * float(np.percentile(samples, 50)),
+            "p99_ms": 1e3 * float(np.percentile(samples, 99)),
+            "replans_per_s": 1.0 / mean_s, "rollout_steps_per_s": steps / mean_s}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=600,
+                    help="timed steps (the 200-replan episodes restart every 200 steps)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--profile-steps", type=int, default=40)
+    ap.add_argument("--workload", default="unicycle", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the served run (0: skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -170,6 +293,20 @@ def main() -> None:
 
     import torch
     import paper_2607_06499_b300 as pkg
+
+    if args.workload == "serve":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        served = run_serve(pkg, max(args.serve_seconds, 1.0), args.serve_budget_gb)
+        plain = plain_mix_latency(pkg)
+        line = {"metric": "CE-MPPI served replans (rollout-steps/s)",
+                "value": served["rollout_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+                "steps": served["replans_served"], "warmup": 0, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "served request loop, Poisson sessions at 200/s, "
+                                       "70 % unicycle / 30 % arm, replan every 20 ms"},
+                "served": served, "plain": plain}
+        print(json.dumps(line), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -183,72 +320,113 @@ def main() -> None:
     stream = torch.cuda.current_stream()
     props = torch.cuda.get_device_properties(dev)
 
-    total_replans = args.warmup + args.steps + args.plain_steps + args.steps + 8
-    seeds = [rank * N_EPISODES + i for i in range(N_EPISODES)]
-    scenes = [W.make("unicycle", seed=s, n_replans=total_replans) for s in seeds]
+    wl = WORKLOADS[args.workload]
+    EPISODE = wl["episode"]
+    N_INST = wl["n"]
+    seeds = [rank * N_INST + i for i in range(N_INST)]
+    scenes = [W.make(wl["scene"], seed=s, n_replans=EPISODE + 8) for s in seeds]
     cfg0 = scenes[0]["cfg"]
-    K, T = cfg0["K"], cfg0["T"]
+    m = pkg.DIMS[cfg0["dyn"]][1]
+    p_dim = pkg.DIMS[cfg0["dyn"]][2]
+
+    def u_init(sc):
+        T_ = sc["cfg"]["T"]
+        return np.zeros((T_, m)) if wl["u_init"] is None else np.tile(wl["u_init"], (T_, 1))
+
+    units_per_step = sum(sc["cfg"]["K"] * sc["cfg"]["T"] for sc in scenes)
     planners, reqs = [], []
     for sc in scenes:
         pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
-        pl.set_nominal(np.tile([1.0, 0.0], (T, 1)))
         n_obs = sc["radius"].shape[0]
         reqs.append(dict(
             x0=torch.tensor(sc["x0"], dtype=torch.float32, device=dev),
             hist=torch.tensor(sc["obs"], dtype=torch.float32, device=dev).contiguous(),
             radius=torch.tensor(sc["radius"], dtype=torch.float32, device=dev),
-            u_out=torch.zeros((T, 2), dtype=torch.float32, device=dev),
-            diag=torch.zeros(128, dtype=torch.uint8, device=dev), obs_step=n_obs * 2))
+            u_out=torch.zeros((sc["cfg"]["T"], m), dtype=torch.float32, device=dev),
+            diag=torch.zeros(128, dtype=torch.uint8, device=dev), obs_step=n_obs * p_dim))
         reqs[-1]["x_next"] = reqs[-1]["x0"]
         planners.append(pl)
+
+    def reset_episodes():
+        """Every episode back to its start: state, nominal, replan counter."""
+        torch.cuda.synchronize()
+        for sc, pl, rq in zip(scenes, planners, reqs):
+            rq["x0"].copy_(torch.tensor(sc["x0"], dtype=torch.float32))
+            pl.set_nominal(u_init(sc))
+            pl.set_counter(0)
+        torch.cuda.synchronize()
+
+    reset_episodes()
     batch = pkg.Batch(planners, reqs, stream=stream, use_graph=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
         batch.run()
-    torch.cuda.synchronize()
+    reset_episodes()
+    assert args.steps >= 1
     if dist:
         dist.barrier()
     clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        batch.run()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    step_ms = []
+    done = 0
+    while done < args.steps:
+        n = min(EPISODE, args.steps - done)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        for i in range(n):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            batch.run()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        step_ms += [a.elapsed_time(b) for a, b in ev]
+        done += n
+        if done < args.steps:
+            reset_episodes()
     clk = clocks.stop()
+    step_ms = np.array(step_ms)
     tot_ms = float(step_ms.sum())
     if dist:
         t = torch.tensor([tot_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
         dist.barrier()
-    units = world * N_EPISODES * K * T * args.steps
+    units = world * units_per_step * args.steps
     value = units / (tot_ms / 1e3)
+    modes = {}
+    for r in reqs:
+        d = np.frombuffer(r["diag"].cpu().numpy().tobytes()[:32], dtype=np.int32)
+        modes[pkg.MODES[int(d[0])]] = modes.get(pkg.MODES[int(d[0])], 0) + 1
+        assert d[7] == 0, f"device status {d[7]}"
 
-    # per-stage device times (stage-by-stage replans, same workload, L2 flushed)
+    # per-stage device times: stage-by-stage replans over the start of the
+    # episodes, L2 flushed before each; obstacle tests per rollout from diag
+    reset_episodes()
     prof = {s: [] for s in STAGES}
-    for i in range(args.steps):
+    tests = []
+    for i in range(args.profile_steps):
         flush.fill_(float(i))
         for s, ms in batch.profile().items():
             prof[s].append(ms)
+        for r in reqs:
+            tests.append(int(np.frombuffer(r["diag"].cpu().numpy().tobytes()[72:76], np.int32)[0]))
     stage_ms = {s: float(np.mean(v)) for s, v in prof.items()}
     roll_ms = stage_ms["rollout"]
-    n_obs = scenes[0]["radius"].shape[0]
-    flops = N_EPISODES * K * T * rollout_flops_per_step(n_obs)
-    achieved = flops / (roll_ms * 1e-3) / 1e12
+    # per instance: obstacle tests per rollout (after culling) from diag
+    tests = np.array(tests, dtype=np.float64).reshape(args.profile_steps, N_INST).mean(0)
+    Ks = np.array([sc["cfg"]["K"] for sc in scenes], dtype=np.float64)
+    Ts = np.array([sc["cfg"]["T"] for sc in scenes], dtype=np.float64)
+    if cfg0["dyn"] == pkg.DYN_ARM:
+        # per step: FK (6 DH transforms ~ 6*40) + 24 sphere centres (3*3*24)
+        # + pose cost (~60); per sphere test 8 (3 sub, mul, 2 fma x2, compare)
+        flops_roll = Ks * (Ts * (240 + 216 + 60) + 24 * 8 * tests)
+    else:
+        flops_roll = Ks * (6.0 * tests + 60.0 * Ts)
+    tests_per_rollout = float(np.mean(tests))
+    flops_per_rollout = float(flops_roll.sum() / Ks.sum())
+    achieved = float(flops_roll.sum()) / (roll_ms * 1e-3) / 1e12
     pk, pk_kind = peaks()
     peak = alu_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2032.0))
-
-    # diagnostics of the last replan of each episode
-    modes = []
-    for r in reqs:
-        d = np.frombuffer(r["diag"].cpu().numpy().tobytes()[:32], dtype=np.int32)
-        modes.append(int(d[0]))
-        assert d[7] == 0, f"device status {d[7]}"
 
     # end to end through the public API with host buffers: per step, the
     # observation windows go host -> device, the new nominals come back.
@@ -256,20 +434,20 @@ def main() -> None:
     e2e_pl, e2e_req = [], []
     for sc in scenes:
         pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
-        pl.set_nominal(np.tile([1.0, 0.0], (T, 1)))
+        pl.set_nominal(u_init(sc))
         n_o = sc["radius"].shape[0]
         e2e_req.append(dict(
             x0=torch.tensor(sc["x0"], dtype=torch.float32, device=dev),
-            hist=torch.zeros((H, n_o, 2), dtype=torch.float32, device=dev),
+            hist=torch.zeros((H, n_o, p_dim), dtype=torch.float32, device=dev),
             radius=torch.tensor(sc["radius"], dtype=torch.float32, device=dev),
-            u_out=torch.zeros((T, 2), dtype=torch.float32, device=dev)))
+            u_out=torch.zeros((sc["cfg"]["T"], m), dtype=torch.float32, device=dev)))
         e2e_req[-1]["x_next"] = e2e_req[-1]["x0"]
         e2e_pl.append(pl)
     e2e_batch = pkg.Batch(e2e_pl, e2e_req, stream=stream, use_graph=True)
     host_obs = [torch.tensor(sc["obs"], dtype=torch.float32).pin_memory() for sc in scenes]
-    host_u = torch.zeros((N_EPISODES, T, 2), dtype=torch.float32).pin_memory()
+    host_u = [torch.zeros((sc["cfg"]["T"], m), dtype=torch.float32).pin_memory() for sc in scenes]
     h2d = sum(r["hist"].numel() * 4 for r in e2e_req)
-    d2h = host_u.numel() * 4
+    d2h = sum(u.numel() * 4 for u in host_u)
 
     def e2e_step(r):
         for i, q in enumerate(e2e_req):
@@ -279,54 +457,62 @@ def main() -> None:
             host_u[i].copy_(q["u_out"], non_blocking=True)
         stream.synchronize()
 
-    for r in range(args.warmup):
+    n_e2e = min(args.steps, EPISODE)
+    for r in range(min(args.warmup, 3)):
         e2e_step(r)
     t0 = time.perf_counter()
-    for r in range(args.steps):
-        e2e_step(args.warmup + r)
+    for r in range(n_e2e):
+        e2e_step(r)
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * N_EPISODES * K * T * args.steps / e2e_s
+    e2e_value = world * units_per_step * n_e2e / e2e_s
 
     # plain form: one instance per launch chain, blocking host-buffer call
     plain_pl = [pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0]) for sc in scenes]
-    for pl in plain_pl:
-        pl.set_nominal(np.tile([1.0, 0.0], (T, 1)))
+    for pl, sc in zip(plain_pl, scenes):
+        pl.set_nominal(u_init(sc))
     lat = []
+    t_plain = time.perf_counter()
     for r in range(args.plain_steps):
         for i, sc in enumerate(scenes):
             t1 = time.perf_counter()
             plain_pl[i].replan(sc["x0"], W.history(sc, r), sc["radius"])
             lat.append(time.perf_counter() - t1)
-    lat = np.array(lat[N_EPISODES:]) * 1e3  # first round is warm-up
+    t_plain = time.perf_counter() - t_plain
+    lat = np.array(lat[N_INST:]) * 1e3  # first round is warm-up
     plain = {"replans_per_s": 1e3 / float(lat.mean()), "p50_ms": float(np.percentile(lat, 50)),
              "p99_ms": float(np.percentile(lat, 99)),
-             "rollout_steps_per_s": K * T * 1e3 / float(lat.mean())}
+             "rollout_steps_per_s": units_per_step * args.plain_steps / t_plain}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism=f"replicas x{world}, episodes sharded by rank"),
-        "replans_per_s": world * N_EPISODES * args.steps / (tot_ms / 1e3),
+        "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank"),
+        "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),
-                       "note": "batched step: all 16 replans complete"},
+                       "note": f"batched step: all {N_INST} replans complete"},
         "plain": plain,
         "stage_ms": stage_ms,
-        "modes_last_step": {pkg.MODES[m]: modes.count(m) for m in sorted(set(modes))},
-        "roofline": {"kernel": "k_rollout2d<unicycle>", "bound": "alu", "achieved": achieved,
+        "modes_last_step": modes,
+        "roofline": {"kernel": "k_rollout_arm" if cfg0["dyn"] == pkg.DYN_ARM else "k_rollout2d<unicycle>",
+                     "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_kind": f"FP32 lanes x 2 x max SM clock ({pk_kind} clock)",
-                     "flops_per_rollout_step": rollout_flops_per_step(n_obs)},
+                     "flops_per_rollout": flops_per_rollout,
+                     "obstacle_tests_per_rollout": tests_per_rollout},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
     }
+    if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":
+        line["served"] = run_serve(pkg, args.serve_seconds, args.serve_budget_gb)
+        line["served"]["plain_mix"] = plain_mix_latency(pkg)
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
-        line["cpu_baseline"] = cpu_baseline(scenes, max_threads=N_EPISODES)
+        line["cpu_baseline"] = cpu_baseline(scenes, u_init, max_threads=16)
     if rank == 0:
         print(json.dumps(line), flush=True)
     for obj in [batch, e2e_batch] + planners + e2e_pl + plain_pl:

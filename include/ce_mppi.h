@@ -105,6 +105,8 @@ typedef struct {
   float pbar[3];   /* reference point (Eq. 11)                                    */
   float v_obs[3];  /* velocity estimate of the reference obstacle (Eq. 17)        */
   unsigned long long counter; /* replan counter this replan used                  */
+  int col_tests;   /* obstacle tests per rollout over the horizon after the reach */
+                   /* culling of the track builder (at most T * n_obs)           */
 } ce_mppi_diag;
 
 /* Inputs and outputs of one replan, all in device memory. */
@@ -171,6 +173,65 @@ ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
 ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms);
 ce_status_t ce_mppi_batch_destroy(ce_mppi_batch* b);
 
+/* ---- continuous-batching server ------------------------------------------
+ * Controller sessions are admitted against a device-memory budget and keep
+ * their planner state (nominal, replan counter, scratch) on the device.  A
+ * worker thread batches the queued replan requests of one dynamics kind as
+ * soon as one of n_streams in-flight slots is free: one input transfer, one
+ * launch per stage for the whole batch, one output transfer; batches on
+ * different slots overlap.  A session is in at most one batch at a time; a
+ * request submitted while the session's previous one is still queued replaces
+ * it, and every ticket of the replaced request receives the newer result.
+ * Each replan's result is bitwise the result of replanning that session alone.
+ * Thread-safe: any number of host threads may submit and poll.               */
+typedef struct ce_mppi_server ce_mppi_server;
+typedef struct {
+  size_t mem_budget_bytes; /* device bytes all sessions together may hold     */
+  int max_sessions;        /* session slots, 1 .. 65536                        */
+  int max_batch;           /* most replans in one batch, >= 1                  */
+  int n_streams;           /* batches in flight at once, 1 .. 16 (>= 2 overlaps) */
+  int device;              /* CUDA device ordinal                              */
+} ce_server_params;
+typedef struct {
+  unsigned long long replans, batches, sessions_opened, sessions_rejected, superseded;
+  size_t mem_in_use;       /* device bytes held by open sessions               */
+  int sessions_open;
+  double mean_batch;       /* replans per batch                                */
+  double p50_latency_s, p99_latency_s, mean_latency_s; /* submit -> result ready */
+} ce_server_stats;
+
+/* Start a server (and its worker thread) on `device`.
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA.                                      */
+ce_status_t ce_mppi_server_create(const ce_server_params* params, ce_mppi_server** out);
+/* Stop the worker, finish the batches in flight, free every session.        */
+ce_status_t ce_mppi_server_destroy(ce_mppi_server* s);
+/* Admit a session with its own planner parameters; NO_MEMORY when the budget
+ * or the slots are exhausted (the session is rejected, nothing is held).     */
+ce_status_t ce_mppi_server_open(ce_mppi_server* s, const ce_mppi_params* params, int* session);
+/* Close a session; its memory is released once its batch in flight is done. */
+ce_status_t ce_mppi_server_close(ce_mppi_server* s, int session);
+/* Queue a replan from host buffers (x0 [n], obs_hist [H][n_obs][p],
+ * obs_radius [n_obs]), copied before the call returns.  ticket (nullable)
+ * receives an id for ce_mppi_server_poll; with NULL the result is dropped and
+ * only counted in the statistics.                                            */
+ce_status_t ce_mppi_server_submit(ce_mppi_server* s, int session, const float* x0,
+                                  const float* obs_hist, const float* obs_radius, int n_obs,
+                                  unsigned long long* ticket);
+/* Queue n replans at once without tickets (results only counted in the
+ * statistics): session ids sids[n]; the inputs of request i follow those of
+ * request i-1 in x0s (n floats each), hists ([H][n_obs[i]][p] each) and radii
+ * (n_obs[i] each).  For load generators.                                     */
+ce_status_t ce_mppi_server_submit_many(ce_mppi_server* s, int n, const int* sids,
+                                       const float* x0s, const float* hists,
+                                       const float* radii, const int* n_obs);
+/* BUSY until the ticket's replan is done; then copies the updated nominal
+ * (u_out [T][m]), the diagnostics and the latency (seconds from submit to
+ * result) and forgets the ticket.                                            */
+ce_status_t ce_mppi_server_poll(ce_mppi_server* s, unsigned long long ticket, float* u_out,
+                                ce_mppi_diag* diag, double* latency_s);
+/* Counters and latency percentiles since the last reset (reset != 0 clears). */
+ce_status_t ce_mppi_server_stats(ce_mppi_server* s, ce_server_stats* out, int reset);
+
 /* Internal buffers of the last replan, copied to host memory (blocking), for
  * diagnostics and stage-by-stage checks.  bytes must equal the buffer size.  */
 typedef enum {
@@ -184,7 +245,8 @@ typedef enum {
   CE_BUF_G = 7,       /* float [p][K]   unit displacement g of V (Eq. 15)           */
   CE_BUF_LABEL = 8,   /* int   [K]      DBSCAN label of V, -1 noise                 */
   CE_BUF_W = 9,       /* float [K]      normalised update weights (Eq. 6 / Eq. 19)  */
-  CE_BUF_HITJ = 10    /* int   [K]      horizon step of the first hit, -1 if none   */
+  CE_BUF_HITJ = 10,   /* int   [K]      horizon step of the first hit, -1 if none   */
+  CE_BUF_DBCYC = 11   /* long long [12] SM clock stamps of the DBSCAN phases        */
 } ce_buf_t;
 ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* host_dst, size_t bytes);
 

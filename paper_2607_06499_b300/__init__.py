@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ce_mppi.h")
 DYN_DI, DYN_UNICYCLE, DYN_ARM = 0, 1, 2
 DIMS = {DYN_DI: (4, 2, 2), DYN_UNICYCLE: (3, 2, 2), DYN_ARM: (6, 6, 3)}  # (n, m, p)
 MODES = {0: "nocol", 1: "allcol", 2: "allnoise", 3: "static", 4: "dynamic"}
-BUF = dict(S=0, HIT=1, PN=2, EPS=3, IDXV=4, IDXC=5, Z=6, G=7, LABEL=8, W=9, HITJ=10)
+BUF = dict(S=0, HIT=1, PN=2, EPS=3, IDXV=4, IDXC=5, Z=6, G=7, LABEL=8, W=9, HITJ=10, DBCYC=11)
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NO_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY"}
 
 
@@ -48,14 +48,15 @@ class Diag(C.Structure):
         ("mode", C.c_int), ("n_col", C.c_int), ("n_valid", C.c_int), ("n_clusters", C.c_int),
         ("sel_label", C.c_int), ("o_star", C.c_int), ("dynamic", C.c_int), ("status", C.c_int),
         ("S_min", C.c_float), ("pbar", C.c_float * 3), ("v_obs", C.c_float * 3),
-        ("counter", C.c_ulonglong),
+        ("counter", C.c_ulonglong), ("col_tests", C.c_int),
     ]
 
     def as_dict(self) -> dict:
         return dict(mode=self.mode, n_col=self.n_col, n_valid=self.n_valid,
                     n_clusters=self.n_clusters, sel_label=self.sel_label, o_star=self.o_star,
                     dynamic=self.dynamic, status=self.status, S_min=self.S_min,
-                    pbar=list(self.pbar), v_obs=list(self.v_obs), counter=self.counter)
+                    pbar=list(self.pbar), v_obs=list(self.v_obs), counter=self.counter,
+                    col_tests=self.col_tests)
 
 
 class Request(C.Structure):
@@ -73,6 +74,10 @@ EXPORTS = (
     "ce_mppi_batch_destroy", "ce_mppi_peek",
     "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
     "ce_mppi_dbscan_dev", "ce_mppi_dbscan_noalloc_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
+    "ce_mppi_server_create", "ce_mppi_server_destroy", "ce_mppi_server_open",
+    "ce_mppi_server_close", "ce_mppi_server_submit", "ce_mppi_server_submit_many",
+    "ce_mppi_server_poll",
+    "ce_mppi_server_stats",
 )
 
 _lib = None
@@ -225,9 +230,10 @@ class Planner:
     def peek(self, name: str) -> np.ndarray:
         K, p, TM = self.K, self.p, self.T * self.m
         shapes = dict(S=(K,), HIT=(K,), PN=(p, K), EPS=(K, self.T, self.m), IDXV=(K,),
-                      IDXC=(K,), Z=(p, K), G=(p, K), LABEL=(K,), W=(K,), HITJ=(K,))
+                      IDXC=(K,), Z=(p, K), G=(p, K), LABEL=(K,), W=(K,), HITJ=(K,), DBCYC=(12,))
         ints = ("HIT", "IDXV", "IDXC", "LABEL", "HITJ")
-        out = np.zeros(shapes[name], np.int32 if name in ints else np.float32)
+        dt = np.int64 if name == "DBCYC" else (np.int32 if name in ints else np.float32)
+        out = np.zeros(shapes[name], dt)
         _check(lib().ce_mppi_peek(self.h, BUF[name], out.ctypes.data, out.nbytes))
         return out
 
@@ -312,3 +318,120 @@ def dbscan_noalloc_dev(z, eps: float, min_pts: int, stream=None):
                                             min_pts, labels.data_ptr(), M.data_ptr(),
                                             C.c_void_p(_stream_ptr(stream))))
     return labels[:n], M
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_sessions", C.c_int),
+                ("max_batch", C.c_int), ("n_streams", C.c_int), ("device", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("replans", C.c_ulonglong), ("batches", C.c_ulonglong),
+                ("sessions_opened", C.c_ulonglong), ("sessions_rejected", C.c_ulonglong),
+                ("superseded", C.c_ulonglong), ("mem_in_use", C.c_size_t),
+                ("sessions_open", C.c_int), ("mean_batch", C.c_double),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
+                ("mean_latency_s", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_SERVER_BOUND = False
+
+
+def _bind_server():
+    global _SERVER_BOUND
+    if _SERVER_BOUND:
+        return
+    L = lib()
+    vp, i = C.c_void_p, C.c_int
+    L.ce_mppi_server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(vp)]
+    L.ce_mppi_server_destroy.argtypes = [vp]
+    L.ce_mppi_server_open.argtypes = [vp, C.POINTER(Params), C.POINTER(i)]
+    L.ce_mppi_server_close.argtypes = [vp, i]
+    L.ce_mppi_server_submit.argtypes = [vp, i, vp, vp, vp, i, C.POINTER(C.c_ulonglong)]
+    L.ce_mppi_server_submit_many.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    L.ce_mppi_server_poll.argtypes = [vp, C.c_ulonglong, vp, C.POINTER(Diag),
+                                      C.POINTER(C.c_double)]
+    L.ce_mppi_server_stats.argtypes = [vp, C.POINTER(ServerStats), i]
+    for n in ("create", "destroy", "open", "close", "submit", "submit_many", "poll", "stats"):
+        getattr(L, "ce_mppi_server_" + n).restype = C.c_int
+    _SERVER_BOUND = True
+
+
+class Server:
+    """Continuous-batching replan server (sessions resident on the device)."""
+
+    def __init__(self, mem_budget_bytes: int, max_sessions: int = 4096, max_batch: int = 512,
+                 n_streams: int = 3, device: int = 0):
+        _bind_server()
+        self.P = ServerParams(mem_budget_bytes, max_sessions, max_batch, n_streams, device)
+        s = C.c_void_p()
+        _check(lib().ce_mppi_server_create(C.byref(self.P), C.byref(s)))
+        self.s = s
+        self.shapes = {}
+
+    def open(self, cfg: dict, n_obs_max: int):
+        """Admit a session; returns its id, or None when the budget is exhausted."""
+        P = make_params(cfg, n_obs_max)
+        sid = C.c_int(-1)
+        st = lib().ce_mppi_server_open(self.s, C.byref(P), C.byref(sid))
+        if st == 2:
+            return None
+        _check(st)
+        n, m, p = DIMS[cfg["dyn"]]
+        self.shapes[sid.value] = (cfg["T"], m)
+        return sid.value
+
+    def close_session(self, sid: int):
+        _check(lib().ce_mppi_server_close(self.s, sid))
+
+    def submit(self, sid: int, x0, hist, radius, want_result: bool = True):
+        x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        hist = np.ascontiguousarray(hist, dtype=np.float32)
+        radius = np.ascontiguousarray(radius, dtype=np.float32)
+        tk = C.c_ulonglong(0)
+        _check(lib().ce_mppi_server_submit(self.s, sid, x0.ctypes.data, hist.ctypes.data,
+                                           radius.ctypes.data, int(radius.shape[0]),
+                                           C.byref(tk) if want_result else None))
+        return tk.value if want_result else None
+
+    def submit_many(self, sids, x0s, hists, radii, n_obs):
+        """Bulk submit without tickets; packed float32 arrays, inputs in order."""
+        sids = np.ascontiguousarray(sids, dtype=np.int32)
+        x0s = np.ascontiguousarray(x0s, dtype=np.float32)
+        hists = np.ascontiguousarray(hists, dtype=np.float32)
+        radii = np.ascontiguousarray(radii, dtype=np.float32)
+        n_obs = np.ascontiguousarray(n_obs, dtype=np.int32)
+        _check(lib().ce_mppi_server_submit_many(self.s, int(sids.shape[0]), sids.ctypes.data,
+                                                x0s.ctypes.data, hists.ctypes.data,
+                                                radii.ctypes.data, n_obs.ctypes.data))
+
+    def poll(self, ticket: int, sid: int):
+        """(u_out, diag, latency_s) when done, else None."""
+        T, m = self.shapes[sid]
+        u = np.zeros((T, m), np.float32)
+        dg = Diag()
+        lat = C.c_double()
+        st = lib().ce_mppi_server_poll(self.s, ticket, u.ctypes.data, C.byref(dg), C.byref(lat))
+        if st == 5:
+            return None
+        _check(st)
+        return u, dg.as_dict(), lat.value
+
+    def stats(self, reset: bool = False) -> dict:
+        out = ServerStats()
+        _check(lib().ce_mppi_server_stats(self.s, C.byref(out), int(reset)))
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().ce_mppi_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

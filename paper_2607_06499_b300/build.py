@@ -6,8 +6,10 @@ import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ce_mppi_api.cu", "k_rollout.cu", "k_cluster.cu",
-                                                              "ce_mppi_noalloc.cu")]
+                                                              "ce_mppi_noalloc.cu",
+                                                              "ce_mppi_server.cu")]
 HEADERS = [os.path.join(_HERE, "csrc", "ce_mppi_internal.cuh"),
+           os.path.join(_HERE, "csrc", "ce_mppi_host.h"),
            os.path.join(os.path.dirname(_HERE), "include", "ce_mppi.h")]
 OUT = os.path.join(_HERE, "libcemppi.so")
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

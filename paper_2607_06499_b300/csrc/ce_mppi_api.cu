@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "ce_mppi_internal.cuh"
+#include "ce_mppi_host.h"
 
 using namespace cem;
 
@@ -72,37 +72,6 @@ void configure_kernels() {
 }
 }  // namespace cem
 
-struct ce_mppi_handle {
-  ce_mppi_params P;
-  int n, m, p, Kp, TMp, G, R, ncells;
-  cudaStream_t stream;
-  InstDesc hdesc;
-  InstDesc* ddesc = nullptr;
-  void* dmem = nullptr;
-  size_t dbytes = 0;
-  int2* dtiles = nullptr;   // rollout tiles then update tiles
-  int n_roll = 0, n_upd = 0;
-  int smem_roll = 0;
-  // host-pointer path staging (device and pinned host)
-  float *d_x0, *d_hist, *d_rad, *d_uout;
-  ce_mppi_diag* d_diag;
-  unsigned char* h_stage = nullptr;
-  size_t in_bytes = 0, out_bytes = 0;
-};
-
-struct ce_mppi_batch {
-  std::vector<ce_mppi_handle*> hs;
-  cudaStream_t stream;
-  int dyn;
-  InstDesc* ddesc = nullptr;
-  Req* dreq = nullptr;
-  int2* dtiles_roll = nullptr;
-  int2* dtiles_upd = nullptr;
-  int n_roll = 0, n_upd = 0, smem_roll = 0, max_cells = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-};
-
 namespace {
 
 ce_status_t validate(const ce_mppi_params* P) {
@@ -147,33 +116,74 @@ ce_status_t validate(const ce_mppi_params* P) {
   if (nc > kMaxCells)
     return fail(CE_MPPI_ERR_INVALID_ARG,
                 "dbscan_eps too small for the DBSCAN grid (p=3 needs eps >= 0.19)");
-  const size_t smem = (size_t)(P->T + 1) * track_stride(P->n_obs_max) * 16 + (size_t)P->T * m * 4;
+  const size_t smem = track_bytes(P->T, P->n_obs_max) + (size_t)P->T * m * 4;
   if (smem > (size_t)kMaxSmemTracks)
     return fail(CE_MPPI_ERR_INVALID_ARG, "(T+1) * n_obs_max too large for shared memory");
   return CE_MPPI_OK;
 }
 
+}  // namespace
+
+namespace {
+void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h);
+}  // namespace
+
+namespace cem {
 void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const int2* tupd,
-               int n_upd, int smem_roll, int max_cells, cudaStream_t s) {
+               int n_upd, int smem_roll, int max_cells, cudaStream_t s, const int* pre_roll,
+               const int* pre_upd) {
   KArgs a = base;
   launch_tracks(a, s);
   a.tiles = troll;
+  a.tprefix = pre_roll;
   a.n_tiles = n_roll;
   launch_rollout(dyn, a, smem_roll, s);
   launch_prune(a, s);
   launch_dbscan(a, max_cells, s);
   launch_select(a, s);
   a.tiles = tupd;
+  a.tprefix = pre_upd;
   a.n_tiles = n_upd;
   launch_update(a, s);
 }
 
+ce_status_t validate_params(const ce_mppi_params* P) { return validate(P); }
+
+bool same_layout(const ce_mppi_handle* h, const ce_mppi_params* P) {
+  float ci;
+  int G, R, nc;
+  int n, m, p;
+  dims_of(P->dyn, &n, &m, &p);
+  dbscan_grid(P->dbscan_eps, p, &ci, &G, &R, &nc);
+  return P->dyn == h->P.dyn && P->K == h->P.K && P->T == h->P.T &&
+         P->n_obs_max == h->P.n_obs_max && P->hist_len == h->P.hist_len && nc == h->ncells;
+}
+
+ce_status_t handle_retarget(ce_mppi_handle* h, const ce_mppi_params* P) {
+  if (!same_layout(h, P)) return fail(CE_MPPI_ERR_INVALID_ARG, "different buffer layout");
+  h->P = *P;
+  fill_scalars(h->hdesc, P, h);
+  float ci;
+  dbscan_grid(P->dbscan_eps, h->p, &ci, &h->G, &h->R, &h->ncells);
+  CE_CUDA(cudaMemsetAsync(h->hdesc.U, 0, sizeof(float) * P->T * h->m, h->stream));
+  CE_CUDA(cudaMemsetAsync(h->hdesc.counter, 0, 8, h->stream));
+  CE_CUDA(cudaMemcpyAsync(h->ddesc, &h->hdesc, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
+  CE_CUDA(cudaStreamSynchronize(h->stream));
+  return CE_MPPI_OK;
+}
+}  // namespace cem
+
+namespace {
+
 void tiles_of(const ce_mppi_handle* h, int inst, std::vector<int2>& roll, std::vector<int2>& upd) {
   const int per = h->P.dyn == CE_DYN_ARM6_KIN ? kArmWarps : kRolloutThreads;
-  for (int k0 = 0; k0 < h->P.K; k0 += per) roll.push_back(make_int2(inst, k0));
+  for (int t = 0; t * per < h->P.K; ++t) roll.push_back(make_int2(inst, t));
+  // update tiles: (column block, rollout chunk) enumerated as kc * ncb + cb
   const int TM = h->P.T * h->m;
-  const int cper = h->P.dyn == CE_DYN_ARM6_KIN ? 32 : kUpdateWarps;
-  for (int c0 = 0; c0 < TM; c0 += cper) upd.push_back(make_int2(inst, c0));
+  const bool arm = h->P.dyn == CE_DYN_ARM6_KIN;
+  const int cper = arm ? 32 : kUpdateWarps, kch = arm ? kUpdChunkArm : kUpdChunk2D;
+  const int ncb = (TM + cper - 1) / cper, nkc = (h->P.K + kch - 1) / kch;
+  for (int t = 0; t < ncb * nkc; ++t) upd.push_back(make_int2(inst, t));
 }
 
 Req to_req(const ce_mppi_request* q, unsigned long long counter0) {
@@ -189,6 +199,27 @@ Req to_req(const ce_mppi_request* q, unsigned long long counter0) {
   r.x_next = q->x_next;
   r.diag = q->diag;
   return r;
+}
+
+// Parameter-derived fields of a descriptor (everything but the buffers).
+void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h) {
+  const int K = P->K, Kp = h->Kp;
+  float ci;
+  int G, R, nc;
+  dbscan_grid(P->dbscan_eps, h->p, &ci, &G, &R, &nc);
+  d.dyn = P->dyn; d.K = K; d.Kp = Kp; d.T = P->T; d.m = h->m; d.n = h->n; d.p = h->p;
+  d.n_obs_max = P->n_obs_max; d.H = P->hist_len; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
+  d.check_j0 = P->check_j0; d.G = G; d.R = R;
+  d.eps_ld_c = P->dyn == CE_DYN_ARM6_KIN ? 1 : Kp;
+  d.eps_ld_k = P->dyn == CE_DYN_ARM6_KIN ? h->TMp : 1;
+  d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;
+  d.eps2 = eps_squared(P->dbscan_eps); d.cell_inv = ci; d.robot_radius = P->robot_radius;
+  d.norm_eps = P->norm_eps; d.v_static_thresh = P->v_static_thresh;
+  for (int i = 0; i < 6; ++i) { d.sigma[i] = P->sigma[i]; d.u_min[i] = P->u_min[i]; d.u_max[i] = P->u_max[i]; }
+  for (int i = 0; i < 16; ++i) d.goal[i] = P->goal[i];
+  for (int i = 0; i < 8; ++i) d.w[i] = P->w[i];
+  d.seed_lo = (unsigned)P->seed; d.seed_hi = (unsigned)(P->seed >> 32);
+  d.TMp = h->TMp;
 }
 
 ce_status_t check_req(const ce_mppi_handle* h, const ce_mppi_request* q) {
@@ -230,7 +261,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, A); return o; };
   const size_t o_ctr = take(8), o_ctl = take(sizeof(Ctl));
   const size_t o_U = take(sizeof(float) * T * m), o_Unew = take(sizeof(float) * T * m);
-  const size_t o_trk = take((size_t)(T + 1) * track_stride(nobs) * 16);
+  const size_t o_trk = take(track_bytes(T, nobs));
   const size_t o_S = take(4 * Kp), o_w = take(4 * Kp);
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
@@ -239,6 +270,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   size_t o_int[8];
   for (int i = 0; i < 8; ++i) o_int[i] = take(4 * Kp);
   const size_t o_bbox = take(sizeof(float) * 6 * h->ncells);
+  const size_t o_upart = take(sizeof(float) * (size_t)((K + kUpdChunkArm - 1) / kUpdChunkArm) * h->TMp);
   // host-path staging: inputs then outputs
   const size_t in_x0 = 0, in_hist = align_up(4 * n, 16),
                in_rad = align_up(in_hist + 4 * (size_t)H * nobs * p, 16),
@@ -260,18 +292,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   char* b = static_cast<char*>(h->dmem);
   InstDesc& d = h->hdesc;
   std::memset(&d, 0, sizeof(d));
-  d.dyn = P->dyn; d.K = K; d.Kp = Kp; d.T = T; d.m = m; d.n = n; d.p = p;
-  d.n_obs_max = nobs; d.H = H; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
-  d.check_j0 = P->check_j0; d.G = h->G; d.R = h->R;
-  d.eps_ld_c = P->dyn == CE_DYN_ARM6_KIN ? 1 : Kp;
-  d.eps_ld_k = P->dyn == CE_DYN_ARM6_KIN ? h->TMp : 1;
-  d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;
-  d.eps2 = eps_squared(P->dbscan_eps); d.cell_inv = ci; d.robot_radius = P->robot_radius;
-  d.norm_eps = P->norm_eps; d.v_static_thresh = P->v_static_thresh;
-  for (int i = 0; i < 6; ++i) { d.sigma[i] = P->sigma[i]; d.u_min[i] = P->u_min[i]; d.u_max[i] = P->u_max[i]; }
-  for (int i = 0; i < 16; ++i) d.goal[i] = P->goal[i];
-  for (int i = 0; i < 8; ++i) d.w[i] = P->w[i];
-  d.seed_lo = (unsigned)P->seed; d.seed_hi = (unsigned)(P->seed >> 32);
+  fill_scalars(d, P, h);
   d.counter = reinterpret_cast<unsigned long long*>(b + o_ctr);
   d.ctl = reinterpret_cast<Ctl*>(b + o_ctl);
   d.U = reinterpret_cast<float*>(b + o_U);
@@ -287,6 +308,8 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   int** ints[8] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent};
   for (int i = 0; i < 8; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
   d.bbox = reinterpret_cast<float*>(b + o_bbox);
+  d.upart = reinterpret_cast<float*>(b + o_upart);
+  d.TMp = h->TMp;
   h->d_x0 = reinterpret_cast<float*>(b + o_in + in_x0);
   h->d_hist = reinterpret_cast<float*>(b + o_in + in_hist);
   h->d_rad = reinterpret_cast<float*>(b + o_in + in_rad);
@@ -296,7 +319,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   tiles_of(h, 0, roll, upd);
   h->n_roll = (int)roll.size();
   h->n_upd = (int)upd.size();
-  h->smem_roll = (int)((size_t)(T + 1) * track_stride(nobs) * 16 + (size_t)T * m * 4);
+  h->smem_roll = (int)(track_bytes(T, nobs) + (size_t)T * m * 4);
   auto cleanup = [&]() {
     cudaFree(h->dmem);
     cudaFree(h->ddesc);
@@ -596,6 +619,11 @@ ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* dst, size_t bytes) 
     if (want(4 * p * K) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
     const float* s = which == CE_BUF_PN ? d.pN : (which == CE_BUF_Z ? d.z : d.g);
     CE_CUDA(cudaMemcpy2D(dst, 4 * K, s, 4 * Kp, 4 * K, p, cudaMemcpyDeviceToHost));
+    return CE_MPPI_OK;
+  }
+  if (which == CE_BUF_DBCYC) {
+    if (want(sizeof(long long) * 12) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
+    CE_CUDA(cudaMemcpy(dst, d.ctl->dbcyc, sizeof(long long) * 12, cudaMemcpyDeviceToHost));
     return CE_MPPI_OK;
   }
   if (which == CE_BUF_EPS) {

@@ -1,0 +1,60 @@
+// ce_mppi_host.h -- host-side objects of the library shared by the C-ABI
+// implementation files (planner handle, batch) and the stage-chain launcher.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "ce_mppi_internal.cuh"
+
+using cem::InstDesc;
+using cem::Req;
+
+struct ce_mppi_handle {
+  ce_mppi_params P;
+  int n, m, p, Kp, TMp, G, R, ncells;
+  cudaStream_t stream;
+  InstDesc hdesc;
+  InstDesc* ddesc = nullptr;
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  int2* dtiles = nullptr;   // rollout tiles then update tiles
+  int n_roll = 0, n_upd = 0;
+  int smem_roll = 0;
+  // host-pointer path staging (device and pinned host)
+  float *d_x0, *d_hist, *d_rad, *d_uout;
+  ce_mppi_diag* d_diag;
+  unsigned char* h_stage = nullptr;
+  size_t in_bytes = 0, out_bytes = 0;
+};
+
+struct ce_mppi_batch {
+  std::vector<ce_mppi_handle*> hs;
+  cudaStream_t stream;
+  int dyn;
+  InstDesc* ddesc = nullptr;
+  Req* dreq = nullptr;
+  int2* dtiles_roll = nullptr;
+  int2* dtiles_upd = nullptr;
+  int n_roll = 0, n_upd = 0, smem_roll = 0, max_cells = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+
+namespace cem {
+// Queue the six stages of one replan of the instances described by base.
+// Tiles come from troll / tupd, or (when those are null) from the per-instance
+// prefix counts pre_roll / pre_upd.
+void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const int2* tupd,
+               int n_upd, int smem_roll, int max_cells, cudaStream_t s,
+               const int* pre_roll = nullptr, const int* pre_upd = nullptr);
+ce_status_t validate_params(const ce_mppi_params* P);
+// True when a planner created with P would have h's buffer layout.
+bool same_layout(const ce_mppi_handle* h, const ce_mppi_params* P);
+// Reuse h's buffers for parameters P of the same layout: new parameters,
+// nominal and replan counter back to zero (blocking on h's stream).
+ce_status_t handle_retarget(ce_mppi_handle* h, const ce_mppi_params* P);
+void configure_kernels();
+}  // namespace cem

@@ -14,7 +14,10 @@ constexpr int kRolloutThreads = 128;    // 2-D rollouts: one rollout per thread
 constexpr int kArmWarps = 8;            // arm rollouts: one warp per rollout
 constexpr int kBlock = 1024;            // per-instance CTAs (prune, DBSCAN, select)
 constexpr int kUpdateWarps = 8;         // update CTA: one warp per column
-constexpr int kMaxCells = 8192;         // DBSCAN grid cells held in shared memory
+constexpr int kUpdChunk2D = 4096;       // rollouts per update tile (2-D layout)
+constexpr int kUpdChunkArm = 512;       // rollouts per update tile (arm layout)
+constexpr int kMaxCells = 8192;         // DBSCAN grid cells (cell -> occupied map in smem)
+constexpr int kMaxOcc = 2048;           // DBSCAN occupied cells held in shared memory
 constexpr int kMaxObs = 4096;           // obstacle bitmap in shared memory
 constexpr int kMaxT = 256;
 constexpr int kMaxSmemTracks = 200 * 1024;
@@ -26,8 +29,9 @@ struct Ctl {
   float S_min, invZ;
   float pbar[3], v_obs[3], p0[3];
   unsigned int done;              // last-CTA ticket of the update stage
-  int pad;
+  int col_tests;                  // circle/sphere tests per rollout after reach culling
   unsigned long long counter_used;
+  long long dbcyc[12];            // DBSCAN phase clock stamps of the last replan
 };
 
 // Static description of one planner instance: parameters and device buffers.
@@ -47,6 +51,8 @@ struct InstDesc {
   float* Unew;   // [T][m] updated nominal before the shift
   float4* tracks;
   float *S, *w_k, *pN, *eps, *z, *g, *zs;
+  float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
+  int TMp;       // T*m rounded up to a multiple of 4
   int *hit, *hitj, *idxV, *idxC, *label, *cell, *sorted, *parent;
   float* bbox;   // [G^p][6] DBSCAN per-cell core bounding boxes
   Ctl* ctl;
@@ -66,22 +72,57 @@ struct Req {
   ce_mppi_diag* diag;
 };
 
-// Arguments common to every stage kernel.  Instance i's request is R[i] when
-// R is non-null (batches, graph replays) else r0 (single replans).
+// Arguments common to every stage kernel.  Instance i of a launch uses the
+// descriptor D[slot[i]] (D[i] when slot is null) and the request R[i] (r0 when
+// R is null).  Tiled stages (rollouts, update) map blockIdx.x to a tile
+// (instance, local tile index) from the explicit list `tiles`, or, when that is
+// null, by searching the per-instance tile prefix counts tprefix[n_inst + 1].
 struct KArgs {
   const InstDesc* D;
+  const int* slot;
   const Req* R;
   Req r0;
-  const int2* tiles;   // rollout / update tiles: (instance, first index)
+  const int2* tiles;
+  const int* tprefix;
   int n_inst;
   int n_tiles;
 };
 
+__device__ __forceinline__ const InstDesc& desc_of(const KArgs& a, int i) {
+  return a.D[a.slot ? a.slot[i] : i];
+}
+
+__device__ __forceinline__ int2 tile_of(const KArgs& a) {
+  const int b = blockIdx.x;
+  if (a.tiles) return a.tiles[b];
+  int lo = 0, hi = a.n_inst - 1;   // largest i with tprefix[i] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.tprefix[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return make_int2(lo, b - a.tprefix[lo]);
+}
+
 // Row stride (in float4) of the obstacle track table: odd, so that lanes
 // reading different horizon rows hit different shared-memory banks.
 __host__ __device__ __forceinline__ int track_stride(int n_obs) { return n_obs | 1; }
+// Bytes of the track table: (T+1) rows of track_stride float4, then the
+// (T+1) row counts (int), padded to 16 bytes.
+__host__ __device__ __forceinline__ size_t track_bytes(int T, int n_obs) {
+  return (size_t)(T + 1) * track_stride(n_obs) * 16 + (((size_t)(T + 1) * 4 + 15) & ~(size_t)15);
+}
+template <typename P>
+__host__ __device__ __forceinline__ int* track_counts(P* tracks, int T, int n_obs) {
+  return reinterpret_cast<int*>(reinterpret_cast<char*>(tracks) +
+                                (size_t)(T + 1) * track_stride(n_obs) * 16);
+}
+template <typename P>
+__host__ __device__ __forceinline__ const int* track_counts(const P* tracks, int T, int n_obs) {
+  return reinterpret_cast<const int*>(reinterpret_cast<const char*>(tracks) +
+                                      (size_t)(T + 1) * track_stride(n_obs) * 16);
+}
 
-__device__ __forceinline__ const Req& req_of(const KArgs& a, int i) {
+__device__ __forceinline__ Req req_of(const KArgs& a, int i) {
   return a.R ? a.R[i] : a.r0;
 }
 

@@ -93,8 +93,8 @@ __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, fl
 // (Eq. 12-13) and g (Eq. 15) of V, and the velocity estimate of o* (Eq. 17).
 __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
   const int inst = blockIdx.x;
-  const InstDesc& d = a.D[inst];
-  const Req& r = req_of(a, inst);
+  const InstDesc& d = desc_of(a, inst);
+  const Req r = req_of(a, inst);
   Ctl* ctl = d.ctl;
   __shared__ int wsum[33];
   __shared__ float red[33];
@@ -132,12 +132,11 @@ __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
   }
   // o*: least clearance |p(x_0) - o_t| - r_o among obstacles hit first by some
   // rollout; ties to the lowest index (packed key, atomicMin).
-  const int ts = track_stride(n_obs);
-  (void)ts;
+  const float* hn = hist_of(r, d) + (size_t)(d.H - 1) * n_obs * p;   // newest observation
   for (int o = tid; o < n_obs; o += blockDim.x) {
     if (!((hitmask[o >> 5] >> (o & 31)) & 1u)) continue;
-    const float4 t = d.tracks[o];   // horizon row 0 = newest observation
-    const float dx = p0s[0] - t.x, dy = p0s[1] - t.y, dz = p0s[2] - t.z;
+    const float dx = p0s[0] - hn[o * p], dy = p0s[1] - hn[o * p + 1];
+    const float dz = p == 3 ? p0s[2] - hn[o * p + 2] : 0.f;
     const float clear = sqrtf(dx * dx + dy * dy + dz * dz) - r.obs_radius[o];
     atomicMin(&best, ((unsigned long long)float_key(clear) << 32) | (unsigned)o);
   }
@@ -151,17 +150,22 @@ __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
     const int k = d.idxC[i];
     if (d.ref_mode == 0 && d.hit[k] != o_star) continue;
     ++cnt;
-    for (int c = 0; c < p; ++c) kahan_add(acc[c], cmp[c], d.pN[(size_t)c * Kp + k]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < p) kahan_add(acc[c], cmp[c], d.pN[(size_t)c * Kp + k]);
   }
   const float ncnt = block_sum((float)cnt, red);
   float pbar[3] = {0.f, 0.f, 0.f};
-  for (int c = 0; c < p; ++c) pbar[c] = block_sum(acc[c], red) / ncnt;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) pbar[c] = c < p ? block_sum(acc[c], red) / ncnt : 0.f;
   // features of V
   const float ne = d.norm_eps;
   for (int i = tid; i < nV; i += blockDim.x) {
     const int k = d.idxV[i];
-    float dv[3], ev[3], nd = 0.f, nn = 0.f;
-    for (int c = 0; c < p; ++c) {
+    float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c >= p) continue;
       const float pk = d.pN[(size_t)c * Kp + k];
       dv[c] = pk - pbar[c];
       ev[c] = pk - p0s[c];
@@ -169,7 +173,9 @@ __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
       nn += ev[c] * ev[c];
     }
     const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
-    for (int c = 0; c < p; ++c) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c >= p) continue;
       d.z[(size_t)c * Kp + i] = dv[c] * izd;
       d.g[(size_t)c * Kp + i] = ev[c] * izn;
     }
@@ -205,7 +211,8 @@ struct DbWork {
   float* bbox;   // [ncells][6] core bounding box (min xyz, max xyz)
 };
 
-__device__ __forceinline__ bool nb_pred(const float* za, const float* zb, int p, float eps2) {
+template <int p>
+__device__ __forceinline__ bool nb_pred_t(const float* za, const float* zb, float eps2) {
   const float dx = __fsub_rn(za[0], zb[0]);
   float s = __fmul_rn(dx, dx);
   const float dy = __fsub_rn(za[1], zb[1]);
@@ -222,18 +229,7 @@ __device__ __forceinline__ int cell_coord(float v, float cell_inv, int G) {
   return (int)fminf(fmaxf(f, 0.0f), (float)(G - 1));
 }
 
-// squared distance from point a to the box [lo, hi] (per coordinate)
-__device__ __forceinline__ float box_d2(const float* za, const float* bb, int p) {
-  float s = 0.f;
-  for (int c = 0; c < p; ++c) {
-    const float lo = bb[c], hi = bb[3 + c];
-    const float e = za[c] < lo ? lo - za[c] : (za[c] > hi ? za[c] - hi : 0.f);
-    s += e * e;
-  }
-  return s;
-}
-
-__device__ int cfind(int* par, int x) {
+__device__ __forceinline__ int cfind(int* par, int x) {
   for (int it = 0; it < 1 << 20; ++it) {
     const int p = par[x];
     if (p == x) return x;
@@ -244,7 +240,7 @@ __device__ int cfind(int* par, int x) {
   return x;
 }
 
-__device__ bool cunion(int* par, int a, int b) {
+__device__ __forceinline__ bool cunion(int* par, int a, int b) {
   for (int it = 0; it < 1 << 20; ++it) {
     a = cfind(par, a);
     b = cfind(par, b);
@@ -257,86 +253,187 @@ __device__ bool cunion(int* par, int a, int b) {
   return false;
 }
 
-__device__ void dbscan_block(const float* __restrict__ z, int ld, int n, int p, float eps2,
-                             float cell_inv, int G, int R, int min_pts, DbWork w, int* labels,
-                             int* M_out, int* status, int* smem) {
+// Inverse of float_key.
+__device__ __forceinline__ float key_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Squared distances from point a to the nearest and to the farthest point of
+// the box given by keys bb[q] (min, stride S) and bb[3S + q] (max).
+template <int p>
+__device__ __forceinline__ void box_dist2(const float* za, const uint32_t* bb, int S,
+                                          float* near2, float* far2) {
+  float sn = 0.f, sf = 0.f;
+#pragma unroll
+  for (int q = 0; q < p; ++q) {
+    const float lo = key_float(bb[q * S]), hi = key_float(bb[(3 + q) * S]);
+    const float e = za[q] < lo ? lo - za[q] : (za[q] > hi ? za[q] - hi : 0.f);
+    const float f = fmaxf(fabsf(za[q] - lo), fabsf(za[q] - hi));
+    sn += e * e;
+    sf += f * f;
+  }
+  *near2 = sn;
+  *far2 = sf;
+}
+
+// Shared memory of dbscan_block: map[nc] (cell -> occupied-cell id), then per
+// occupied cell: ostart[kMaxOcc + 1], ocell, ofill, opar, omin (kMaxOcc each),
+// obox[6][kMaxOcc] (all points) and ocbox[6][kMaxOcc] (core points) as keys.
+__host__ __device__ __forceinline__ size_t dbscan_smem_bytes(int nc) {
+  return ((size_t)nc + 1 + 17 * (size_t)kMaxOcc) * 4;
+}
+
+template <int p>
+__device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld, int n,
+                                             float eps2, float cell_inv, int G, int R, int min_pts,
+                                             DbWork w, int* labels, int* M_out, int* status,
+                                             int* smem, long long* cyc) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
   const int nc = p == 3 ? G * G * G : G * G;
-  int* start = smem;            // [nc + 1]
-  int* fill = start + nc + 1;   // [nc]   scatter cursor, then min core id of the cell
-  int* cpar = fill + nc;        // [nc]   cell union-find parent (-1: no core)
-  int* aux = cpar + nc;         // [nc]   component minimum, then canonical id
+  const float far_ok = eps2 * 0.9999f;              // whole box within eps
+  const float near_no = eps2 * 1.0001f + 1e-12f;    // whole box beyond eps
+  const int S = kMaxOcc;
+  int* map = smem;                  // [nc]
+  int* ostart = map + nc;           // [S + 1]
+  int* ocell = ostart + S + 1;      // [S]
+  int* ofill = ocell + S;           // [S] scatter cursor, later canonical id of a root
+  int* opar = ofill + S;            // [S] union-find parent (-1: no core point)
+  int* omin = opar + S;             // [S] smallest core id of the cell / component
+  uint32_t* obox = reinterpret_cast<uint32_t*>(omin + S);   // [6][S]
+  uint32_t* ocbox = obox + 6 * S;                           // [6][S]
   __shared__ int wsum[33];
-  __shared__ int bad;
+  __shared__ int bad, n_occ_s;
+  auto stamp = [&](int k) {
+    if (cyc && tid == 0) cyc[k] = clock64();
+  };
+  stamp(0);
   if (tid == 0) bad = 0;
-  for (int c = tid; c < nc; c += blockDim.x) start[c] = 0;
+  for (int c = tid; c < nc; c += blockDim.x) map[c] = 0;
   __syncthreads();
-  // 1. cell of each point; per-cell counts
-  for (int i = tid; i < n; i += blockDim.x) {
-    int ci = 0, mul = 1;
-    for (int c = 0; c < p; ++c) {
-      const float v = z[(size_t)c * ld + i];
-      if (!(v >= -1.0f && v <= 1.0f)) bad = 1;
-      ci += cell_coord(v, cell_inv, G) * mul;
-      mul *= G;
+  // 1. cell of each point; per-cell counts (one atomic per cell per warp)
+  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+    const int i = i0 + tid;
+    int ci = -1;
+    if (i < n) {
+      int mul = 1;
+      ci = 0;
+      for (int c = 0; c < p; ++c) {
+        const float v = z[(size_t)c * ld + i];
+        if (!(v >= -1.0f && v <= 1.0f)) bad = 1;
+        ci += cell_coord(v, cell_inv, G) * mul;
+        mul *= G;
+      }
+      w.cell[i] = ci;
     }
-    w.cell[i] = ci;
-    atomicAdd(&start[ci], 1);
+    const unsigned peers = __match_any_sync(FULL, ci);
+    if (ci >= 0 && lane == __ffs(peers) - 1) atomicAdd(&map[ci], __popc(peers));
   }
   __syncthreads();
-  // 2. exclusive scan of the counts (each thread a contiguous run of cells)
+  stamp(1);
+  // 2. occupied cells in cell order: id, offsets (prefix of counts), reset of
+  //    the per-cell summaries; map becomes cell -> occupied id
   {
-    const int per = (nc + blockDim.x - 1) / blockDim.x;
-    const int c0 = min(tid * per, nc), c1 = min(c0 + per, nc);
-    int loc = 0;
-    for (int c = c0; c < c1; ++c) loc += start[c];
-    // block exclusive scan of loc
-    int s = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(FULL, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane == 31) wsum[wid] = s;
-    __syncthreads();
-    if (wid == 0) {
-      const int v = lane < nwarp ? wsum[lane] : 0;
-      int t = v;
+    int base = 0, off = 0;
+    for (int c0 = 0; c0 < nc; c0 += blockDim.x) {
+      const int c = c0 + tid;
+      const int cnt = c < nc ? map[c] : 0;
+      int tot;
+      const int rk = block_scan_flag(cnt > 0, wsum, &tot);
+      // offsets: block exclusive sum of cnt over this chunk
+      int s = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, t, o);
-        if (lane >= o) t += y;
+        const int y = __shfl_up_sync(FULL, s, o);
+        if (lane >= o) s += y;
       }
-      if (lane < nwarp) wsum[lane] = t - v;
+      if (lane == 31) wsum[wid] = s;
+      __syncthreads();
+      if (wid == 0) {
+        const int v = lane < nwarp ? wsum[lane] : 0;
+        int t = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(FULL, t, o);
+          if (lane >= o) t += y;
+        }
+        if (lane < nwarp) wsum[lane] = t - v;
+        if (lane == nwarp - 1) wsum[32] = t;
+      }
+      __syncthreads();
+      const int excl = off + wsum[wid] + s - cnt;
+      const int chunk_tot = wsum[32];
+      __syncthreads();
+      if (c < nc) {
+        if (cnt > 0) {
+          const int o = base + rk;
+          if (o < S) {
+            ocell[o] = c;
+            ostart[o] = excl;
+            ofill[o] = excl;
+            opar[o] = -1;
+            omin[o] = 0x7fffffff;
+            for (int q = 0; q < 3; ++q) {
+              obox[q * S + o] = 0xffffffffu; obox[(3 + q) * S + o] = 0u;
+              ocbox[q * S + o] = 0xffffffffu; ocbox[(3 + q) * S + o] = 0u;
+            }
+          }
+          map[c] = o;
+        } else {
+          map[c] = -1;
+        }
+      }
+      base += tot;
+      off += chunk_tot;
     }
-    __syncthreads();
-    int run = wsum[wid] + s - loc;
-    for (int c = c0; c < c1; ++c) {
-      const int cnt = start[c];
-      start[c] = run;
-      fill[c] = run;
-      run += cnt;
+    if (tid == 0) {
+      n_occ_s = base;
+      if (base <= S) ostart[base] = n;
     }
-    if (tid == 0) start[nc] = n;
   }
   __syncthreads();
-  if (bad) {
+  const int n_occ = n_occ_s;
+  if (bad || n_occ > S) {
     for (int i = tid; i < n; i += blockDim.x) labels[i] = -1;
     if (tid == 0) { *M_out = 0; atomicCAS(status, 0, CE_MPPI_ERR_INVALID_ARG); }
     return;
   }
-  // 3. scatter into cell order
-  for (int i = tid; i < n; i += blockDim.x) {
-    const int pos = atomicAdd(&fill[w.cell[i]], 1);
-    w.sorted[pos] = i;
-    for (int c = 0; c < p; ++c) w.zs[(size_t)c * w.ld_s + pos] = z[(size_t)c * ld + i];
+  stamp(2);
+  // 3. scatter into cell order (one cursor atomic per cell per warp) and the
+  //    bounding box of all points of each cell
+  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+    const int i = i0 + tid;
+    const int o = i < n ? map[w.cell[i]] : -1;
+    const unsigned peers = __match_any_sync(FULL, o);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (o >= 0 && lane == leader) base = atomicAdd(&ofill[o], __popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    if (o >= 0) {
+      const int pos = base + __popc(peers & ((1u << lane) - 1u));
+      w.sorted[pos] = i;
+      unsigned lo[3], hi[3];
+      for (int q = 0; q < 3; ++q) {
+        const float v = q < p ? z[(size_t)q * ld + i] : 0.f;
+        if (q < p) w.zs[(size_t)q * w.ld_s + pos] = v;
+        const unsigned kk = float_key(v);
+        lo[q] = __reduce_min_sync(peers, kk);
+        hi[q] = __reduce_max_sync(peers, kk);
+      }
+      if (lane == leader)
+        for (int q = 0; q < 3; ++q) {
+          atomicMin(&obox[q * S + o], lo[q]);
+          atomicMax(&obox[(3 + q) * S + o], hi[q]);
+        }
+    }
   }
   __syncthreads();
+  stamp(3);
   // 4. core flags: a cell with >= min_pts points is all core; otherwise count
-  //    neighbours over the (2R+1)^p surrounding cells, stopping at min_pts.
+  //    neighbours cell by cell: a box entirely within eps counts whole, a box
+  //    entirely beyond eps is skipped, others are scanned; stop at min_pts.
   for (int i = tid; i < n; i += blockDim.x) {
-    const int ci = w.cell[i];
-    int core = (start[ci + 1] - start[ci]) >= min_pts;
+    const int ci = w.cell[i], oi = map[ci];
+    int core = (ostart[oi + 1] - ostart[oi]) >= min_pts;
     if (!core) {
       float za[3];
       for (int c = 0; c < p; ++c) za[c] = z[(size_t)c * ld + i];
@@ -348,73 +445,70 @@ __device__ void dbscan_block(const float* __restrict__ z, int ld, int n, int p, 
           for (int ox = -R; ox <= R && !core; ++ox) {
             const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
             if (nx < 0 || ny < 0 || nz < 0 || nx >= G || ny >= G || (p == 3 && nz >= G)) continue;
-            const int nb = (nz * G + ny) * G + nx;
-            for (int pos = start[nb]; pos < start[nb + 1]; ++pos) {
+            const int ob = map[(nz * G + ny) * G + nx];
+            if (ob < 0) continue;
+            float n2, f2;
+            box_dist2<p>(za, obox + ob, S, &n2, &f2);
+            if (n2 > near_no) continue;
+            if (f2 <= far_ok) {
+              count += ostart[ob + 1] - ostart[ob];
+              if (count >= min_pts) core = 1;
+              continue;
+            }
+            for (int pos = ostart[ob]; pos < ostart[ob + 1]; ++pos) {
               float zb[3];
               for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pos];
-              if (nb_pred(za, zb, p, eps2) && ++count >= min_pts) { core = 1; break; }
+              if (nb_pred_t<p>(za, zb, eps2) && ++count >= min_pts) { core = 1; break; }
             }
           }
     }
     w.core[i] = core;
   }
   __syncthreads();
-  // 5. per-cell core summary: parent, min core id, bounding box of core points
-  for (int c = tid; c < nc; c += blockDim.x) { cpar[c] = -1; fill[c] = 0x7fffffff; }
-  __syncthreads();
-  for (int c = wid; c < nc; c += nwarp) {
-    const int s0 = start[c], s1 = start[c + 1];
-    if (s0 == s1) continue;
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int mn = 0x7fffffff;
-    for (int pos = s0 + lane; pos < s1; pos += 32) {
-      const int i = w.sorted[pos];
-      if (!w.core[i]) continue;
-      mn = min(mn, i);
-      for (int q = 0; q < p; ++q) {
-        const float v = w.zs[(size_t)q * w.ld_s + pos];
-        lo[q] = fminf(lo[q], v);
-        hi[q] = fmaxf(hi[q], v);
-      }
+  stamp(4);
+  // 5. per-cell core summary in cell order (warps see one cell at a time):
+  //    parent, smallest core id, bounding box of the core points
+  for (int s0 = 0; s0 < n; s0 += blockDim.x) {
+    const int pos = s0 + tid;
+    int o = -1, i = 0;
+    if (pos < n) {
+      i = w.sorted[pos];
+      if (w.core[i]) o = map[w.cell[i]];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+    const unsigned peers = __match_any_sync(FULL, o);
+    if (o >= 0) {
+      const int leader = __ffs(peers) - 1;
+      const unsigned mn = __reduce_min_sync(peers, (unsigned)i);
+      unsigned lo[3], hi[3];
       for (int q = 0; q < 3; ++q) {
-        lo[q] = fminf(lo[q], __shfl_xor_sync(FULL, lo[q], o));
-        hi[q] = fmaxf(hi[q], __shfl_xor_sync(FULL, hi[q], o));
+        const unsigned kk = float_key(q < p ? w.zs[(size_t)q * w.ld_s + pos] : 0.f);
+        lo[q] = __reduce_min_sync(peers, kk);
+        hi[q] = __reduce_max_sync(peers, kk);
+      }
+      if (lane == leader) {
+        opar[o] = o;
+        atomicMin(&omin[o], (int)mn);
+        for (int q = 0; q < 3; ++q) {
+          atomicMin(&ocbox[q * S + o], lo[q]);
+          atomicMax(&ocbox[(3 + q) * S + o], hi[q]);
+        }
       }
     }
-    if (lane == 0 && mn != 0x7fffffff) {
-      cpar[c] = c;
-      fill[c] = mn;
-      for (int q = 0; q < 3; ++q) { w.bbox[c * 6 + q] = lo[q]; w.bbox[c * 6 + 3 + q] = hi[q]; }
-    }
   }
   __syncthreads();
-  // 6. cell-level union.  Occupied core cells are listed first; then one warp
-  //    per cell A: the lanes screen the neighbour offsets in parallel (B > A,
-  //    B has core points, core bounding boxes within eps, not yet joined) and
-  //    the warp searches each surviving pair for a core pair within eps.
-  int n_occ;
-  {
-    int base = 0;
-    for (int c0 = 0; c0 < nc; c0 += blockDim.x) {
-      const int c = c0 + tid;
-      const bool occ = c < nc && cpar[c] >= 0;
-      int tot;
-      const int rk = block_scan_flag(occ, wsum, &tot);
-      if (occ) aux[base + rk] = c;
-      base += tot;
-    }
-    n_occ = base;
-  }
-  __syncthreads();
+  stamp(5);
+  // 6. cell-level union, one warp per occupied cell A with core points: the
+  //    lanes screen the neighbour offsets in parallel (B > A with core points,
+  //    core boxes within eps, not yet joined) and the warp searches each
+  //    surviving pair for a core pair within eps.
   {
     const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
-    for (int ia = wid; ia < n_occ; ia += nwarp) {
-      const int A = aux[ia];
-      const int ax = A % G, ay = (A / G) % G, az = p == 3 ? A / (G * G) : 0;
+    for (int A = wid; A < n_occ; A += nwarp) {
+      if (opar[A] < 0) continue;
+      const int cA = ocell[A];
+      const int ax = cA % G, ay = (cA / G) % G, az = p == 3 ? cA / (G * G) : 0;
+      float alo[3], ahi[3];
+      for (int q = 0; q < 3; ++q) { alo[q] = key_float(ocbox[q * S + A]); ahi[q] = key_float(ocbox[(3 + q) * S + A]); }
       for (int of0 = 0; of0 < nofs; of0 += 32) {
         const int of = of0 + lane;
         bool cand = false;
@@ -424,16 +518,16 @@ __device__ void dbscan_block(const float* __restrict__ z, int ld, int n, int p, 
           const int oz = p == 3 ? of / (side * side) - R : 0;
           const int bx = ax + ox, by = ay + oy, bz = az + oz;
           if (bx >= 0 && by >= 0 && bz >= 0 && bx < G && by < G && (p != 3 || bz < G)) {
-            B = (bz * G + by) * G + bx;
-            if (B > A && cpar[B] >= 0) {
+            B = map[(bz * G + by) * G + bx];
+            if (B > A && opar[B] >= 0) {
               float s2 = 0.f;
               for (int q = 0; q < p; ++q) {
-                const float g1 = w.bbox[B * 6 + q] - w.bbox[A * 6 + 3 + q];
-                const float g2 = w.bbox[A * 6 + q] - w.bbox[B * 6 + 3 + q];
+                const float g1 = key_float(ocbox[q * S + B]) - ahi[q];
+                const float g2 = alo[q] - key_float(ocbox[(3 + q) * S + B]);
                 const float gq = fmaxf(fmaxf(g1, g2), 0.f);
                 s2 += gq * gq;
               }
-              cand = s2 <= eps2 * 1.0001f + 1e-12f;
+              cand = s2 <= near_no;
             }
           }
         }
@@ -443,87 +537,135 @@ __device__ void dbscan_block(const float* __restrict__ z, int ld, int n, int p, 
           cm &= cm - 1;
           const int Bc = __shfl_sync(FULL, B, src);
           int joined = 0;
-          if (lane == 0) joined = cfind(cpar, A) == cfind(cpar, Bc);
+          if (lane == 0) joined = cfind(opar, A) == cfind(opar, Bc);
           if (__shfl_sync(FULL, joined, 0)) continue;   // warp-uniform decision
           bool found = false;
-          for (int pa = start[A]; pa < start[A + 1] && !found; pa += 32) {
+          for (int pa = ostart[A]; pa < ostart[A + 1] && !found; pa += 32) {
             bool mine = false;
             const int posa = pa + lane;
-            if (posa < start[A + 1] && w.core[w.sorted[posa]]) {
+            if (posa < ostart[A + 1] && w.core[w.sorted[posa]]) {
               float za[3];
               for (int q = 0; q < p; ++q) za[q] = w.zs[(size_t)q * w.ld_s + posa];
-              if (box_d2(za, w.bbox + Bc * 6, p) <= eps2 * 1.0001f + 1e-12f) {
-                for (int pb = start[Bc]; pb < start[Bc + 1]; ++pb) {
+              float n2, f2;
+              box_dist2<p>(za, ocbox + Bc, S, &n2, &f2);
+              if (n2 <= near_no) {
+                for (int pb = ostart[Bc]; pb < ostart[Bc + 1]; ++pb) {
                   if (!w.core[w.sorted[pb]]) continue;
                   float zb[3];
                   for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + pb];
-                  if (nb_pred(za, zb, p, eps2)) { mine = true; break; }
+                  if (nb_pred_t<p>(za, zb, eps2)) { mine = true; break; }
                 }
               }
             }
             found = __any_sync(FULL, mine);
           }
-          if (found && lane == 0 && !cunion(cpar, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
+          if (found && lane == 0 && !cunion(opar, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
           __syncwarp();
         }
       }
     }
   }
   __syncthreads();
-  // 7. components: root cell, component minimum core id
-  for (int c = tid; c < nc; c += blockDim.x) aux[c] = 0x7fffffff;
+  stamp(6);
+  // 7. components: compress to the root; component minimum core id
+  for (int o = tid; o < n_occ; o += blockDim.x)
+    if (opar[o] >= 0) opar[o] = cfind(opar, o);
   __syncthreads();
-  for (int c = tid; c < nc; c += blockDim.x)
-    if (cpar[c] >= 0) {
-      const int rt = cfind(cpar, c);
-      cpar[c] = rt;
-      atomicMin(&aux[rt], fill[c]);
-    }
+  for (int o = tid; o < n_occ; o += blockDim.x)
+    if (opar[o] >= 0 && opar[o] != o) atomicMin(&omin[opar[o]], omin[o]);
   __syncthreads();
-  // 8. canonical ids: rank of each component minimum in point order
-  int M = 0;
+  // 8. canonical ids (rank of each component minimum in point order), labels
+  //    of the core points, and the core / border point lists in index order
+  //    (the cell-ordered arrays are free now: sorted / zs take the core list,
+  //    cell the border list)
+  __shared__ int wcnt[3][32];
+  int M = 0, n_core = 0, n_border = 0;
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     const int i = i0 + tid;
-    bool first = false;
+    const bool valid = i < n;
+    const bool isc = valid && w.core[i], isb = valid && !w.core[i];
     int rt = -1;
-    if (i < n && w.core[i]) {
-      rt = cpar[w.cell[i]];
-      first = aux[rt] == i;
+    bool first = false;
+    if (isc) {
+      rt = opar[map[w.cell[i]]];
+      first = omin[rt] == i;
     }
-    int tot;
-    const int rk = block_scan_flag(first, wsum, &tot);
-    if (first) fill[rt] = M + rk;   // fill: canonical id of the root cell
-    M += tot;
+    const unsigned bf = __ballot_sync(FULL, first), bc = __ballot_sync(FULL, isc),
+                   bb = __ballot_sync(FULL, isb);
+    if (lane == 0) { wcnt[0][wid] = __popc(bf); wcnt[1][wid] = __popc(bc); wcnt[2][wid] = __popc(bb); }
+    __syncthreads();
+    int pf = 0, pc = 0, pb = 0, tf = 0, tc = 0, tb = 0;
+    for (int q = 0; q < nwarp; ++q) {
+      const int f = wcnt[0][q], c = wcnt[1][q], bq = wcnt[2][q];
+      if (q < wid) { pf += f; pc += c; pb += bq; }
+      tf += f; tc += c; tb += bq;
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    if (first) ofill[rt] = M + pf + __popc(bf & lt);
+    __syncthreads();   // canonical ids of this chunk's firsts are visible
+    if (isc) {
+      labels[i] = ofill[rt];
+      const int j = n_core + pc + __popc(bc & lt);
+      w.sorted[j] = i;
+      for (int q = 0; q < p; ++q) w.zs[(size_t)q * w.ld_s + j] = z[(size_t)q * ld + i];
+    }
+    if (isb) w.cell[n_border + pb + __popc(bb & lt)] = i;
+    M += tf;
+    n_core += tc;
+    n_border += tb;
+    __syncthreads();
   }
-  __syncthreads();
-  // 9. labels: core -> its component; border -> component of the lowest-index
-  //    core neighbour; else noise.
-  for (int i = tid; i < n; i += blockDim.x) {
-    const int ci = w.cell[i];
-    if (w.core[i]) { labels[i] = fill[cpar[ci]]; continue; }
+  stamp(7);
+  // 9. border points: one warp per non-core point scans the core points in
+  //    ascending index, 32 at a time; the first neighbour found is the
+  //    lowest-index core neighbour (none: noise).
+  const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
+  for (int ib = wid; ib < n_border; ib += nwarp) {
+    const int a = w.cell[ib];
     float za[3];
-    for (int c = 0; c < p; ++c) za[c] = z[(size_t)c * ld + i];
-    const int cx = ci % G, cy = (ci / G) % G, cz = p == 3 ? ci / (G * G) : 0;
-    int bestb = 0x7fffffff;
-    const int zr = p == 3 ? R : 0;
-    for (int oz = -zr; oz <= zr; ++oz)
-      for (int oy = -R; oy <= R; ++oy)
-        for (int ox = -R; ox <= R; ++ox) {
-          const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
-          if (nx < 0 || ny < 0 || nz < 0 || nx >= G || ny >= G || (p == 3 && nz >= G)) continue;
-          const int nb = (nz * G + ny) * G + nx;
-          if (cpar[nb] < 0) continue;
-          if (box_d2(za, w.bbox + nb * 6, p) > eps2 * 1.0001f + 1e-12f) continue;
-          for (int pos = start[nb]; pos < start[nb + 1]; ++pos) {
-            const int b = w.sorted[pos];
-            if (b >= bestb || !w.core[b]) continue;
-            float zb[3];
-            for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pos];
-            if (nb_pred(za, zb, p, eps2)) bestb = b;
+    for (int q = 0; q < p; ++q) za[q] = z[(size_t)q * ld + a];
+    int lab = -1;
+    // a point with no core box within eps in its neighbourhood is noise
+    bool near_core = false;
+    {
+      int cc[3];
+      for (int q = 0; q < p; ++q) cc[q] = cell_coord(za[q], cell_inv, G);
+      for (int of0 = 0; of0 < nofs && !near_core; of0 += 32) {
+        const int of = of0 + lane;
+        bool nb = false;
+        if (of < nofs) {
+          const int bx = cc[0] + of % side - R, by = cc[1] + (of / side) % side - R;
+          const int bz = p == 3 ? cc[2] + of / (side * side) - R : 0;
+          if (bx >= 0 && by >= 0 && bz >= 0 && bx < G && by < G && (p != 3 || bz < G)) {
+            const int ob = map[(bz * G + by) * G + bx];
+            if (ob >= 0 && opar[ob] >= 0) {
+              float n2, f2;
+              box_dist2<p>(za, ocbox + ob, S, &n2, &f2);
+              nb = n2 <= near_no;
+            }
           }
         }
-    labels[i] = bestb == 0x7fffffff ? -1 : fill[cpar[w.cell[bestb]]];
+        near_core = __any_sync(FULL, nb);
+      }
+    }
+    for (int j0 = 0; near_core && j0 < n_core; j0 += 32) {
+      const int j = j0 + lane;
+      bool hit = false;
+      if (j < n_core) {
+        float zb[3];
+        for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + j];
+        hit = nb_pred_t<p>(za, zb, eps2);
+      }
+      const unsigned hm = __ballot_sync(FULL, hit);
+      if (hm) {
+        lab = labels[w.sorted[j0 + __ffs(hm) - 1]];
+        break;
+      }
+    }
+    if (lane == 0) labels[a] = lab;
   }
+  __syncthreads();
+  stamp(8);
   if (tid == 0) *M_out = M;
 }
 
@@ -538,18 +680,22 @@ __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
   return w;
 }
 
-__global__ void __launch_bounds__(kBlock) k_dbscan(KArgs a) {
+__global__ void __maxnreg__(64) k_dbscan(KArgs a) {
   extern __shared__ int smem_i[];
   const int inst = blockIdx.x;
-  const InstDesc& d = a.D[inst];
+  const InstDesc& d = desc_of(a, inst);
   Ctl* ctl = d.ctl;
   const int mode = ctl->mode;
   if (mode != CE_MODE_STATIC) return;   // fallback replans skip clustering
   const int nV = ctl->nV;
   const DbWork w = db_work_of(d);
   __shared__ int M;
-  dbscan_block(d.z, d.Kp, nV, d.p, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
-               &ctl->status, smem_i);
+  if (d.p == 3)
+    dbscan_block<3>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
+                    &ctl->status, smem_i, ctl->dbcyc);
+  else
+    dbscan_block<2>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
+                    &ctl->status, smem_i, ctl->dbcyc);
   __syncthreads();
   if (threadIdx.x == 0) {
     ctl->M = M;
@@ -557,7 +703,7 @@ __global__ void __launch_bounds__(kBlock) k_dbscan(KArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_dbscan_standalone(const float* z, int n, int ld, int p,
+__global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int ld, int p,
                                                               float eps2, float cell_inv, int G,
                                                               int R, int min_pts, int* labels,
                                                               int* n_clusters, DbWork w) {
@@ -566,7 +712,12 @@ __global__ void __launch_bounds__(kBlock) k_dbscan_standalone(const float* z, in
   __shared__ int status;
   if (threadIdx.x == 0) status = 0;
   __syncthreads();
-  dbscan_block(z, ld, n, p, eps2, cell_inv, G, R, min_pts, w, labels, &M, &status, smem_i);
+  if (p == 3)
+    dbscan_block<3>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, &status, smem_i,
+                    nullptr);
+  else
+    dbscan_block<2>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, &status, smem_i,
+                    nullptr);
   __syncthreads();
   if (threadIdx.x == 0) *n_clusters = status ? -status : M;
 }
@@ -582,7 +733,7 @@ constexpr int kWin = 512;   // clusters per statistics window
 
 __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
   const int inst = blockIdx.x;
-  const InstDesc& d = a.D[inst];
+  const InstDesc& d = desc_of(a, inst);
   Ctl* ctl = d.ctl;
   __shared__ unsigned long long accS[kWin], accG[3][kWin];
   __shared__ int accN[kWin];
@@ -622,7 +773,9 @@ __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
           L = d.label[i];
           if (L >= w0 && L < w0 + kWin) {
             vS = __float2ll_rn(ldexpf(d.S[d.idxV[i]], eS));
-            for (int q = 0; q < p; ++q) vG[q] = __float2ll_rn(ldexpf(d.g[(size_t)q * Kp + i], eG));
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < p) vG[q] = __float2ll_rn(ldexpf(d.g[(size_t)q * Kp + i], eG));
           } else {
             L = -1;
           }
@@ -755,6 +908,7 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
       g.status = ctl->status; g.S_min = ctl->S_min;
       for (int i = 0; i < 3; ++i) { g.pbar[i] = ctl->pbar[i]; g.v_obs[i] = ctl->v_obs[i]; }
       g.counter = c;
+      g.col_tests = ctl->col_tests;
       *r.diag = g;
     }
     ctl->counter_used = c;
@@ -763,56 +917,78 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
   }
 }
 
-// 2-D layout eps[T*m][Kp]: one warp per column, lanes over k (coalesced).
-// Arm layout eps[Kp][T*m]: lanes over 32 columns, warps over k.
+// 2-D layout eps[T*m][Kp]: tile = (8 columns, 4096 rollouts), one warp per
+// column with lanes over k (coalesced), four independent Kahan accumulators.
+// Arm layout eps[Kp][T*m]: tile = (32 columns, 512 rollouts), lanes over the
+// columns, warps over k.  Each tile writes its partial sums; the last tile of
+// the instance adds them in chunk order (deterministic) and finalizes.
 __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   __shared__ float part[kUpdateWarps][32];
   __shared__ int last;
-  const int2 tile = a.tiles[blockIdx.x];
-  const InstDesc& d = a.D[tile.x];
+  const int2 tile = tile_of(a);
+  const InstDesc& d = desc_of(a, tile.x);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int K = d.K, TM = d.T * d.m;
+  const bool arm = d.dyn == CE_DYN_ARM6_KIN;
+  const int kch = arm ? kUpdChunkArm : kUpdChunk2D;
+  const int cper = arm ? 32 : kUpdateWarps;
+  const int ncb = (TM + cper - 1) / cper;
+  const int cb = tile.y % ncb, kc = tile.y / ncb;
+  const int c0 = cb * cper, k0 = kc * kch, k1 = min(K, k0 + kch);
   const float* __restrict__ w = d.w_k;
   const float* __restrict__ eps = d.eps;
-  if (d.dyn != CE_DYN_ARM6_KIN) {
-    const int c = tile.y + wid;
+  if (!arm) {
+    const int c = c0 + wid;
     if (c < TM) {
-      float s = 0.f, sc = 0.f;
       const float* col = eps + (size_t)c * d.eps_ld_c;
-      for (int k = lane; k < K; k += 32) kahan_add(s, sc, w[k] * col[k]);
-      s = warp_sum(s);
-      if (lane == 0) d.Unew[c] = d.U[c] + s;
+      float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+      int k = k0 + lane;
+      for (; k + 96 < k1; k += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) kahan_add(s[u], e[u], w[k + 32 * u] * col[k + 32 * u]);
+      }
+      for (; k < k1; k += 32) kahan_add(s[0], e[0], w[k] * col[k]);
+      float t = (s[0] + s[1]) + (s[2] + s[3]);
+      t = warp_sum(t);
+      if (lane == 0) d.upart[(size_t)kc * d.TMp + c] = t;
     }
   } else {
-    const int c = tile.y + lane;
-    float s = 0.f, sc = 0.f;
+    const int c = c0 + lane;
+    float s = 0.f, e = 0.f;
     if (c < TM)
-      for (int k = wid; k < K; k += kUpdateWarps) kahan_add(s, sc, w[k] * eps[(size_t)k * d.eps_ld_k + c]);
+      for (int k = k0 + wid; k < k1; k += kUpdateWarps) kahan_add(s, e, w[k] * eps[(size_t)k * d.eps_ld_k + c]);
     part[wid][lane] = s;
     __syncthreads();
     if (wid == 0 && c < TM) {
       float t = 0.f;
       for (int q = 0; q < kUpdateWarps; ++q) t += part[q][lane];
-      d.Unew[c] = d.U[c] + t;
+      d.upart[(size_t)kc * d.TMp + c] = t;
     }
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int per = d.dyn != CE_DYN_ARM6_KIN ? kUpdateWarps : 32;
-    const unsigned nblk = (unsigned)((TM + per - 1) / per);
-    last = atomicAdd(&d.ctl->done, 1u) == nblk - 1;
+    const unsigned ntile = (unsigned)(ncb * ((K + kch - 1) / kch));
+    last = atomicAdd(&d.ctl->done, 1u) == ntile - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
+  const int nkc = (K + kch - 1) / kch;
+  for (int c = threadIdx.x; c < TM; c += blockDim.x) {
+    float t = 0.f;
+    for (int q = 0; q < nkc; ++q) t += __ldcg(d.upart + (size_t)q * d.TMp + c);
+    d.Unew[c] = d.U[c] + t;
+  }
+  __threadfence();
+  __syncthreads();
   finalize(d, req_of(a, tile.x));
 }
 
 // ========================================================================= launchers
 void launch_prune(const KArgs& a, cudaStream_t s) { k_prune<<<a.n_inst, kBlock, 0, s>>>(a); }
 
-static size_t dbscan_smem(int nc) { return (size_t)(4 * nc + 1) * sizeof(int); }
+static size_t dbscan_smem(int nc) { return dbscan_smem_bytes(nc); }
 
 void configure_cluster() {
   cudaFuncSetAttribute(k_dbscan, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -13,36 +13,100 @@ namespace cem {
 // ------------------------------------------------------------------ tracks
 // Eq. 17 telescoped: v_o = (o_t - o_{t-H+1}) / ((H-1) Delta t); the predicted
 // centre at horizon step j is o_t + v_o (j dt).  One CTA per instance.
+//
+// 2-D robots: row j of the table lists, in ascending obstacle index, only the
+// obstacles that some rollout can reach at step j: every rollout's position
+// lies in a disc of centre c_j and radius r_j fixed by x_0 and the input box
+// (unicycle: c_j = p_0, r_j = j dt max|v|; double integrator: c_j = p_0 + j dt
+// v_0, r_j = dt^2 j (j-1)/2 |a|max), so an obstacle farther than
+// r_j + r_o + r_robot (+1 mm slack) from c_j cannot be hit at step j and is
+// left out.  This changes no collision result.  Entries are (x, y, (r_o +
+// r_robot)^2, obstacle index as int bits); the row counts follow the rows.
+// Arm: every row holds every obstacle as (x, y, z, (r_o + r_robot)^2).
 __global__ void k_tracks(KArgs a) {
   const int inst = blockIdx.x;
-  const InstDesc& d = a.D[inst];
-  const Req& r = req_of(a, inst);
+  const InstDesc& d = desc_of(a, inst);
+  const Req r = req_of(a, inst);
   const float* h = hist_of(r, d);
-  const int n_obs = r.n_obs, p = d.p, H = d.H;
+  const int n_obs = r.n_obs, p = d.p, H = d.H, T = d.T;
   const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
   const int ts = track_stride(n_obs);
-  const int total = (d.T + 1) * n_obs;
+  int* counts = track_counts(d.tracks, T, n_obs);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {   // a new replan: clear the control block's flags
     d.ctl->status = 0;
     d.ctl->done = 0u;
   }
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int j = e / n_obs, o = e - j * n_obs;
-    const float* newest = h + ((size_t)(H - 1) * n_obs + o) * p;
-    const float* oldest = h + (size_t)o * p;
-    const float tj = (float)j * d.dt;
-    float c[3] = {0.0f, 0.0f, 0.0f};
-    for (int i = 0; i < p; ++i) c[i] = newest[i] + ((newest[i] - oldest[i]) * inv) * tj;
-    const float R = r.obs_radius[o] + d.robot_radius;
-    d.tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R * R);
+  if (d.dyn == CE_DYN_ARM6_KIN) {
+    const int total = (T + 1) * n_obs;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int j = e / n_obs, o = e - j * n_obs;
+      const float* newest = h + ((size_t)(H - 1) * n_obs + o) * p;
+      const float* oldest = h + (size_t)o * p;
+      const float tj = (float)j * d.dt;
+      float c[3];
+      for (int i = 0; i < 3; ++i) c[i] = newest[i] + ((newest[i] - oldest[i]) * inv) * tj;
+      const float R = r.obs_radius[o] + d.robot_radius;
+      d.tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R * R);
+    }
+    for (int j = threadIdx.x; j <= T; j += blockDim.x) counts[j] = n_obs;
+    if (threadIdx.x == 0) d.ctl->col_tests = T * n_obs;
+    return;
   }
+  const float x0 = r.x0[0], y0 = r.x0[1];
+  const float vx0 = d.dyn == CE_DYN_DOUBLE_INT_2D ? r.x0[2] : 0.f;
+  const float vy0 = d.dyn == CE_DYN_DOUBLE_INT_2D ? r.x0[3] : 0.f;
+  const float m0 = fmaxf(fabsf(d.u_min[0]), fabsf(d.u_max[0]));
+  const float m1 = fmaxf(fabsf(d.u_min[1]), fabsf(d.u_max[1]));
+  const float amax = sqrtf(m0 * m0 + m1 * m1);
+  __shared__ int tests;
+  if (threadIdx.x == 0) tests = 0;
+  __syncthreads();
+  for (int j = wid; j <= T; j += nw) {
+    const float tj = (float)j * d.dt;
+    float cx = x0, cy = y0, rj;
+    if (d.dyn == CE_DYN_DOUBLE_INT_2D) {
+      cx = x0 + tj * vx0;
+      cy = y0 + tj * vy0;
+      rj = d.dt * d.dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
+    } else {
+      rj = tj * m0;
+    }
+    int cnt = 0;
+    for (int o0 = 0; o0 < n_obs; o0 += 32) {
+      const int o = o0 + lane;
+      bool keep = false;
+      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (o < n_obs) {
+        const float* newest = h + ((size_t)(H - 1) * n_obs + o) * 2;
+        const float* oldest = h + (size_t)o * 2;
+        const float ox = newest[0] + ((newest[0] - oldest[0]) * inv) * tj;
+        const float oy = newest[1] + ((newest[1] - oldest[1]) * inv) * tj;
+        const float R = r.obs_radius[o] + d.robot_radius;
+        const float reach = rj + R + 1e-3f * (1.0f + rj);
+        const float ddx = ox - cx, ddy = oy - cy;
+        keep = ddx * ddx + ddy * ddy <= reach * reach;
+        e = make_float4(ox, oy, R * R, __int_as_float(o));
+      }
+      const unsigned b = __ballot_sync(0xffffffffu, keep);
+      if (keep) d.tracks[(size_t)j * ts + cnt + __popc(b & ((1u << lane) - 1u))] = e;
+      cnt += __popc(b);
+    }
+    if (lane == 0) {
+      counts[j] = cnt;
+      if (j >= 1) atomicAdd(&tests, cnt);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) d.ctl->col_tests = tests;
 }
 
-// Stage the instance's tracks (TMA bulk copy) and nominal into shared memory.
-// Returns false (and records a timeout) if the copy did not land in time.
+// Stage the instance's tracks and row counts (TMA bulk copy) and the nominal
+// into shared memory.  Returns false (and records a timeout) if the copy did
+// not land in time.
 __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float4* trk,
                                              float* Us, uint64_t* bar) {
-  const uint32_t bytes = n_obs > 0 ? (uint32_t)((d.T + 1) * track_stride(n_obs)) * 16u : 0u;
+  const uint32_t bytes = n_obs > 0 ? (uint32_t)track_bytes(d.T, n_obs) : 0u;
   if (threadIdx.x == 0 && bytes > 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0 && bytes > 0) {
@@ -70,14 +134,15 @@ template <int DYN>
 __global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
-  const int2 tile = a.tiles[blockIdx.x];
-  const InstDesc& d = a.D[tile.x];
-  const Req& r = req_of(a, tile.x);
+  const int2 tile = tile_of(a);
+  const InstDesc& d = desc_of(a, tile.x);
+  const Req r = req_of(a, tile.x);
   const int n_obs = r.n_obs, T = d.T, Kp = d.Kp, ts = track_stride(n_obs);
   float4* trk = reinterpret_cast<float4*>(smem_raw);
-  float* Us = reinterpret_cast<float*>(trk + (size_t)(T + 1) * ts);
+  const int* cnts = track_counts(trk, T, n_obs);
+  float* Us = reinterpret_cast<float*>(smem_raw + (n_obs > 0 ? track_bytes(T, n_obs) : 0));
   if (!stage_tracks(d, n_obs, trk, Us, &bar)) return;
-  const int k = tile.y + threadIdx.x;
+  const int k = tile.y * kRolloutThreads + threadIdx.x;
   if (k >= d.K) return;
   const unsigned long long ctr = *d.counter;
 
@@ -91,12 +156,13 @@ __global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
   float* __restrict__ eps = d.eps;
   float S = 0.0f, Sc = 0.0f;
   int first = -1, first_j = -1;
-  if (d.check_j0) {
+  if (d.check_j0 && n_obs > 0) {
+    const int c = cnts[0];
     int h = n_obs;
-    for (int o = n_obs - 1; o >= 0; --o) {
-      const float4 t = trk[o];
+    for (int e = c - 1; e >= 0; --e) {
+      const float4 t = trk[e];
       const float dx = s0 - t.x, dy = s1 - t.y;
-      h = (dx * dx + dy * dy < t.w) ? o : h;
+      h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
     }
     if (h < n_obs) { first = h; first_j = 0; }
   }
@@ -125,13 +191,14 @@ __global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
       s1 += u0 * sn * dt;
       s2 += u1 * dt;
     }
-    if (first < 0) {
+    if (first < 0 && n_obs > 0) {
       const float4* tj = trk + (size_t)(j + 1) * ts;
+      const int c = cnts[j + 1];
       int h = n_obs;
-      for (int o = n_obs - 1; o >= 0; --o) {
-        const float4 t = tj[o];
+      for (int e = c - 1; e >= 0; --e) {   // descending: the lowest index wins
+        const float4 t = tj[e];
         const float dx = s0 - t.x, dy = s1 - t.y;
-        h = (dx * dx + dy * dy < t.w) ? o : h;
+        h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
       }
       if (h < n_obs) { first = h; first_j = j + 1; }
     }
@@ -188,15 +255,15 @@ __device__ __forceinline__ float arm_cost(const InstDesc& d, const float O[7][3]
 __global__ void __launch_bounds__(kArmWarps * 32) k_rollout_arm(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
-  const int2 tile = a.tiles[blockIdx.x];
-  const InstDesc& d = a.D[tile.x];
-  const Req& r = req_of(a, tile.x);
+  const int2 tile = tile_of(a);
+  const InstDesc& d = desc_of(a, tile.x);
+  const Req r = req_of(a, tile.x);
   const int n_obs = r.n_obs, T = d.T, ts = track_stride(n_obs);
   float4* trk = reinterpret_cast<float4*>(smem_raw);
-  float* Us = reinterpret_cast<float*>(trk + (size_t)(T + 1) * ts);
+  float* Us = reinterpret_cast<float*>(smem_raw + (n_obs > 0 ? track_bytes(T, n_obs) : 0));
   if (!stage_tracks(d, n_obs, trk, Us, &bar)) return;
   const int lane = threadIdx.x & 31;
-  const int k = tile.y + (threadIdx.x >> 5);
+  const int k = tile.y * kArmWarps + (threadIdx.x >> 5);
   if (k >= d.K) return;
   const unsigned long long ctr = *d.counter;
   const float dt = d.dt;

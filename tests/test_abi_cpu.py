@@ -84,3 +84,25 @@ def test_null_arguments_rejected():
     assert L.ce_mppi_replan(None, None, None, None, 0, None, None) == 1
     assert L.ce_mppi_batch_create(None, None, 0, None, 0, None) == 1
     assert L.ce_mppi_dbscan_dev(None, 4, 4, 5, 0.3, 3, None, None, None, 0, None) == 1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof / offsetof of the ABI structs as compiled by gcc from
+    include/ce_mppi.h equal the ctypes mirrors of the binding."""
+    import subprocess
+    src = tmp_path / "sizes.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "ce_mppi.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(ce_mppi_params),"
+        " sizeof(ce_mppi_diag), sizeof(ce_mppi_request), offsetof(ce_mppi_params, seed),"
+        " offsetof(ce_mppi_diag, counter), offsetof(ce_mppi_diag, col_tests),"
+        " offsetof(ce_mppi_request, obs_step));return 0;}\n")
+    exe = tmp_path / "sizes"
+    inc = pkg.HEADER.rsplit("/", 1)[0]
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [C.sizeof(pkg.Params), C.sizeof(pkg.Diag), C.sizeof(pkg.Request),
+            pkg.Params.seed.offset, pkg.Diag.counter.offset, pkg.Diag.col_tests.offset,
+            pkg.Request.obs_step.offset]
+    assert got == want

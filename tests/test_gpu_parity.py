@@ -288,7 +288,7 @@ def test_closed_loop_episode_on_device():
     x = torch.tensor(sc["x0"], dtype=torch.float32, device="cuda")
     obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda").contiguous()
     rad = torch.tensor(sc["radius"], dtype=torch.float32, device="cuda")
-    diag = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    diag = torch.zeros(128, dtype=torch.uint8, device="cuda")
     req = dict(x0=x, hist=obs, radius=rad, x_next=x, diag=diag,
                obs_step=sc["radius"].shape[0] * 2)
     b = pkg.Batch([pl], [req], use_graph=True)
