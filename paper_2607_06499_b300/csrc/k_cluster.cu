@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
 // the union-find runs over cells: two cells join when some core pair between
 // them is within eps.  Shared memory: 4 int arrays of G^p (+1) entries.
 struct DbWork {
+  int* labels_tmp;  // [n] list of the points of sparse cells (the labels buffer)
   int* cell;     // [n] cell id of each point
   int* sorted;   // [n] point ids in cell order
   float* zs;     // [p][ld_s] coordinates in cell order
@@ -274,6 +275,97 @@ __device__ __forceinline__ void box_dist2(const float* za, const uint32_t* bb, i
   }
   *near2 = sn;
   *far2 = sf;
+}
+
+// Per-cell boxes (and, for core points, the smallest point id) over the
+// positions [0, n) in cell order.  Warp w takes a contiguous range of
+// positions, 32 at a time; a step whose lanes all fall in one cell is reduced
+// across the warp and merged into a running accumulator that is written
+// (shared-memory atomics) only when the cell changes, so a cell of thousands of
+// points costs a handful of atomics; mixed steps reduce per cell group.
+template <int p, bool CORE>
+__device__ __forceinline__ void cell_boxes(int n, const DbWork& w, const int* map, uint32_t* box,
+                                           int S, int* opar, int* omin) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int L = (((n + nwarp - 1) / nwarp) + 31) & ~31;
+  const int beg = wid * L, end = min(n, beg + L);
+  int run = -1;
+  uint32_t rlo[3], rhi[3], rmn = 0xffffffffu;
+  auto flush = [&]() {
+    if (run >= 0 && lane == 0) {
+#pragma unroll
+      for (int q = 0; q < p; ++q) {
+        atomicMin(&box[q * S + run], rlo[q]);
+        atomicMax(&box[(3 + q) * S + run], rhi[q]);
+      }
+      if (CORE) {
+        opar[run] = run;
+        atomicMin(&omin[run], (int)rmn);
+      }
+    }
+  };
+  for (int s0 = beg; s0 < end; s0 += 32) {
+    const int pos = s0 + lane;
+    int o = -1;
+    uint32_t kk[3] = {0u, 0u, 0u}, idx = 0xffffffffu;
+    if (pos < end) {
+      const int i = w.sorted[pos];
+      if (!CORE || w.core[i]) {
+        o = map[w.cell[i]];
+        idx = (uint32_t)i;
+#pragma unroll
+        for (int q = 0; q < p; ++q) kk[q] = float_key(w.zs[(size_t)q * w.ld_s + pos]);
+      }
+    }
+    const int k0 = __shfl_sync(FULL, o, 0);
+    if (__all_sync(FULL, o == k0)) {
+      if (k0 < 0) continue;
+      uint32_t lo[3], hi[3];
+#pragma unroll
+      for (int q = 0; q < p; ++q) {
+        lo[q] = __reduce_min_sync(FULL, kk[q]);
+        hi[q] = __reduce_max_sync(FULL, kk[q]);
+      }
+      const uint32_t mn = CORE ? __reduce_min_sync(FULL, idx) : 0u;
+      if (k0 == run) {
+#pragma unroll
+        for (int q = 0; q < p; ++q) { rlo[q] = min(rlo[q], lo[q]); rhi[q] = max(rhi[q], hi[q]); }
+        rmn = min(rmn, mn);
+      } else {
+        flush();
+        run = k0;
+#pragma unroll
+        for (int q = 0; q < p; ++q) { rlo[q] = lo[q]; rhi[q] = hi[q]; }
+        rmn = mn;
+      }
+    } else {
+      flush();
+      run = -1;
+      const unsigned peers = __match_any_sync(FULL, o);
+      if (o >= 0) {
+        const int leader = __ffs(peers) - 1;
+        uint32_t lo[3], hi[3];
+#pragma unroll
+        for (int q = 0; q < p; ++q) {
+          lo[q] = __reduce_min_sync(peers, kk[q]);
+          hi[q] = __reduce_max_sync(peers, kk[q]);
+        }
+        const uint32_t mn = CORE ? __reduce_min_sync(peers, idx) : 0u;
+        if (lane == leader) {
+#pragma unroll
+          for (int q = 0; q < p; ++q) {
+            atomicMin(&box[q * S + o], lo[q]);
+            atomicMax(&box[(3 + q) * S + o], hi[q]);
+          }
+          if (CORE) {
+            opar[o] = o;
+            atomicMin(&omin[o], (int)mn);
+          }
+        }
+      }
+    }
+  }
+  flush();
 }
 
 // Shared memory of dbscan_block: map[nc] (cell -> occupied-cell id), then per
@@ -398,7 +490,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
     return;
   }
   stamp(2);
-  // 3. scatter into cell order (one cursor atomic per cell per warp) and the
+  // 3. scatter into cell order (one cursor atomic per cell per warp), then the
   //    bounding box of all points of each cell
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     const int i = i0 + tid;
@@ -411,38 +503,48 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
     if (o >= 0) {
       const int pos = base + __popc(peers & ((1u << lane) - 1u));
       w.sorted[pos] = i;
-      unsigned lo[3], hi[3];
-      for (int q = 0; q < 3; ++q) {
-        const float v = q < p ? z[(size_t)q * ld + i] : 0.f;
-        if (q < p) w.zs[(size_t)q * w.ld_s + pos] = v;
-        const unsigned kk = float_key(v);
-        lo[q] = __reduce_min_sync(peers, kk);
-        hi[q] = __reduce_max_sync(peers, kk);
-      }
-      if (lane == leader)
-        for (int q = 0; q < 3; ++q) {
-          atomicMin(&obox[q * S + o], lo[q]);
-          atomicMax(&obox[(3 + q) * S + o], hi[q]);
-        }
+#pragma unroll
+      for (int q = 0; q < p; ++q) w.zs[(size_t)q * w.ld_s + pos] = z[(size_t)q * ld + i];
     }
   }
   __syncthreads();
+  cell_boxes<p, false>(n, w, map, obox, S, opar, omin);
+  __syncthreads();
   stamp(3);
-  // 4. core flags: a cell with >= min_pts points is all core; otherwise count
+  // 4. core flags.  A cell with >= min_pts points is all core.  The points of
+  //    the other cells are listed, then one warp per listed point counts its
   //    neighbours cell by cell: a box entirely within eps counts whole, a box
-  //    entirely beyond eps is skipped, others are scanned; stop at min_pts.
-  for (int i = tid; i < n; i += blockDim.x) {
-    const int ci = w.cell[i], oi = map[ci];
-    int core = (ostart[oi + 1] - ostart[oi]) >= min_pts;
-    if (!core) {
+  //    entirely beyond eps is skipped, other cells are scanned 32 points per
+  //    step; the count stops at min_pts.
+  {
+    int n_sparse = 0;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+      const int i = i0 + tid;
+      bool sparse = false;
+      if (i < n) {
+        const int oi = map[w.cell[i]];
+        const bool dense = (ostart[oi + 1] - ostart[oi]) >= min_pts;
+        w.core[i] = dense ? 1 : 0;
+        sparse = !dense;
+      }
+      int tot;
+      const int rk = block_scan_flag(sparse, wsum, &tot);
+      if (sparse) w.labels_tmp[n_sparse + rk] = i;
+      n_sparse += tot;
+    }
+    __syncthreads();
+    for (int is = wid; is < n_sparse; is += nwarp) {
+      const int i = w.labels_tmp[is];
+      const int ci = w.cell[i];
       float za[3];
+#pragma unroll
       for (int c = 0; c < p; ++c) za[c] = z[(size_t)c * ld + i];
       const int cx = ci % G, cy = (ci / G) % G, cz = p == 3 ? ci / (G * G) : 0;
       int count = 0;
       const int zr = p == 3 ? R : 0;
-      for (int oz = -zr; oz <= zr && !core; ++oz)
-        for (int oy = -R; oy <= R && !core; ++oy)
-          for (int ox = -R; ox <= R && !core; ++ox) {
+      for (int oz = -zr; oz <= zr && count < min_pts; ++oz)
+        for (int oy = -R; oy <= R && count < min_pts; ++oy)
+          for (int ox = -R; ox <= R && count < min_pts; ++ox) {
             const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
             if (nx < 0 || ny < 0 || nz < 0 || nx >= G || ny >= G || (p == 3 && nz >= G)) continue;
             const int ob = map[(nz * G + ny) * G + nx];
@@ -452,49 +554,28 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
             if (n2 > near_no) continue;
             if (f2 <= far_ok) {
               count += ostart[ob + 1] - ostart[ob];
-              if (count >= min_pts) core = 1;
               continue;
             }
-            for (int pos = ostart[ob]; pos < ostart[ob + 1]; ++pos) {
-              float zb[3];
-              for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pos];
-              if (nb_pred_t<p>(za, zb, eps2) && ++count >= min_pts) { core = 1; break; }
+            for (int pb0 = ostart[ob]; pb0 < ostart[ob + 1] && count < min_pts; pb0 += 32) {
+              const int pb = pb0 + lane;
+              bool hit = false;
+              if (pb < ostart[ob + 1]) {
+                float zb[3];
+#pragma unroll
+                for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pb];
+                hit = nb_pred_t<p>(za, zb, eps2);
+              }
+              count += __popc(__ballot_sync(FULL, hit));
             }
           }
+      if (lane == 0) w.core[i] = count >= min_pts ? 1 : 0;
     }
-    w.core[i] = core;
   }
   __syncthreads();
   stamp(4);
-  // 5. per-cell core summary in cell order (warps see one cell at a time):
-  //    parent, smallest core id, bounding box of the core points
-  for (int s0 = 0; s0 < n; s0 += blockDim.x) {
-    const int pos = s0 + tid;
-    int o = -1, i = 0;
-    if (pos < n) {
-      i = w.sorted[pos];
-      if (w.core[i]) o = map[w.cell[i]];
-    }
-    const unsigned peers = __match_any_sync(FULL, o);
-    if (o >= 0) {
-      const int leader = __ffs(peers) - 1;
-      const unsigned mn = __reduce_min_sync(peers, (unsigned)i);
-      unsigned lo[3], hi[3];
-      for (int q = 0; q < 3; ++q) {
-        const unsigned kk = float_key(q < p ? w.zs[(size_t)q * w.ld_s + pos] : 0.f);
-        lo[q] = __reduce_min_sync(peers, kk);
-        hi[q] = __reduce_max_sync(peers, kk);
-      }
-      if (lane == leader) {
-        opar[o] = o;
-        atomicMin(&omin[o], (int)mn);
-        for (int q = 0; q < 3; ++q) {
-          atomicMin(&ocbox[q * S + o], lo[q]);
-          atomicMax(&ocbox[(3 + q) * S + o], hi[q]);
-        }
-      }
-    }
-  }
+  // 5. per-cell core summary: parent, smallest core id, bounding box of the
+  //    core points
+  cell_boxes<p, true>(n, w, map, ocbox, S, opar, omin);
   __syncthreads();
   stamp(5);
   // 6. cell-level union, one warp per occupied cell A with core points: the
@@ -539,25 +620,30 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           int joined = 0;
           if (lane == 0) joined = cfind(opar, A) == cfind(opar, Bc);
           if (__shfl_sync(FULL, joined, 0)) continue;   // warp-uniform decision
+          // one point of the smaller cell at a time (warp-uniform); the lanes
+          // test 32 points of the other cell per step
+          int X = A, Y = Bc;
+          if (ostart[Bc + 1] - ostart[Bc] < ostart[A + 1] - ostart[A]) { X = Bc; Y = A; }
           bool found = false;
-          for (int pa = ostart[A]; pa < ostart[A + 1] && !found; pa += 32) {
-            bool mine = false;
-            const int posa = pa + lane;
-            if (posa < ostart[A + 1] && w.core[w.sorted[posa]]) {
-              float za[3];
-              for (int q = 0; q < p; ++q) za[q] = w.zs[(size_t)q * w.ld_s + posa];
-              float n2, f2;
-              box_dist2<p>(za, ocbox + Bc, S, &n2, &f2);
-              if (n2 <= near_no) {
-                for (int pb = ostart[Bc]; pb < ostart[Bc + 1]; ++pb) {
-                  if (!w.core[w.sorted[pb]]) continue;
-                  float zb[3];
-                  for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + pb];
-                  if (nb_pred_t<p>(za, zb, eps2)) { mine = true; break; }
-                }
+          for (int px = ostart[X]; px < ostart[X + 1] && !found; ++px) {
+            if (!w.core[w.sorted[px]]) continue;
+            float za[3];
+#pragma unroll
+            for (int q = 0; q < p; ++q) za[q] = w.zs[(size_t)q * w.ld_s + px];
+            float n2, f2;
+            box_dist2<p>(za, ocbox + Y, S, &n2, &f2);
+            if (n2 > near_no) continue;
+            for (int py0 = ostart[Y]; py0 < ostart[Y + 1]; py0 += 32) {
+              const int py = py0 + lane;
+              bool hit = false;
+              if (py < ostart[Y + 1] && w.core[w.sorted[py]]) {
+                float zb[3];
+#pragma unroll
+                for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + py];
+                hit = nb_pred_t<p>(za, zb, eps2);
               }
+              if (__any_sync(FULL, hit)) { found = true; break; }
             }
-            found = __any_sync(FULL, mine);
           }
           if (found && lane == 0 && !cunion(opar, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
           __syncwarp();
@@ -578,7 +664,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    of the core points, and the core / border point lists in index order
   //    (the cell-ordered arrays are free now: sorted / zs take the core list,
   //    cell the border list)
-  __shared__ int wcnt[3][32];
+  __shared__ unsigned long long wpack[33];
   int M = 0, n_core = 0, n_border = 0;
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     const int i = i0 + tid;
@@ -592,14 +678,27 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
     }
     const unsigned bf = __ballot_sync(FULL, first), bc = __ballot_sync(FULL, isc),
                    bb = __ballot_sync(FULL, isb);
-    if (lane == 0) { wcnt[0][wid] = __popc(bf); wcnt[1][wid] = __popc(bc); wcnt[2][wid] = __popc(bb); }
+    // per-warp counts packed 21 bits apart; warp 0 scans the 32 warps
+    if (lane == 0)
+      wpack[wid] = (unsigned long long)__popc(bf) | ((unsigned long long)__popc(bc) << 21) |
+                   ((unsigned long long)__popc(bb) << 42);
     __syncthreads();
-    int pf = 0, pc = 0, pb = 0, tf = 0, tc = 0, tb = 0;
-    for (int q = 0; q < nwarp; ++q) {
-      const int f = wcnt[0][q], c = wcnt[1][q], bq = wcnt[2][q];
-      if (q < wid) { pf += f; pc += c; pb += bq; }
-      tf += f; tc += c; tb += bq;
+    if (wid == 0) {
+      const unsigned long long v = lane < nwarp ? wpack[lane] : 0ull;
+      unsigned long long x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      wpack[lane] = x - v;                 // exclusive prefix of warp `lane`
+      if (lane == 31) wpack[32] = x;       // chunk totals
     }
+    __syncthreads();
+    const unsigned long long pre = wpack[wid], tot = wpack[32];
+    const int msk = (1 << 21) - 1;
+    const int pf = (int)(pre & msk), pc = (int)((pre >> 21) & msk), pb = (int)(pre >> 42);
+    const int tf = (int)(tot & msk), tc = (int)((tot >> 21) & msk), tb = (int)(tot >> 42);
     const unsigned lt = (1u << lane) - 1u;
     if (first) ofill[rt] = M + pf + __popc(bf & lt);
     __syncthreads();   // canonical ids of this chunk's firsts are visible
@@ -677,6 +776,7 @@ __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
   w.ld_s = d.Kp;
   w.core = d.parent;
   w.bbox = d.bbox;
+  w.labels_tmp = d.label;
   return w;
 }
 
@@ -710,6 +810,7 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
   extern __shared__ int smem_i[];
   __shared__ int M;
   __shared__ int status;
+  w.labels_tmp = labels;
   if (threadIdx.x == 0) status = 0;
   __syncthreads();
   if (p == 3)
