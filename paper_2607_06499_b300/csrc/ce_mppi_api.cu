@@ -267,8 +267,8 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
                o_zs = take(4 * 3 * Kp);
   const size_t eps_elems = P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
   const size_t o_eps = take(4 * eps_elems);
-  size_t o_int[8];
-  for (int i = 0; i < 8; ++i) o_int[i] = take(4 * Kp);
+  size_t o_int[9];
+  for (int i = 0; i < 9; ++i) o_int[i] = take(4 * Kp);
   const size_t o_bbox = take(sizeof(float) * 6 * h->ncells);
   const size_t o_upart = take(sizeof(float) * (size_t)((K + kUpdChunkArm - 1) / kUpdChunkArm) * h->TMp);
   // host-path staging: inputs then outputs
@@ -305,8 +305,9 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.g = reinterpret_cast<float*>(b + o_g);
   d.zs = reinterpret_cast<float*>(b + o_zs);
   d.eps = reinterpret_cast<float*>(b + o_eps);
-  int** ints[8] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent};
-  for (int i = 0; i < 8; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
+  int** ints[9] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent,
+                   &d.vpos};
+  for (int i = 0; i < 9; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
   d.bbox = reinterpret_cast<float*>(b + o_bbox);
   d.upart = reinterpret_cast<float*>(b + o_upart);
   d.TMp = h->TMp;
@@ -613,6 +614,12 @@ ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* dst, size_t bytes) 
   if (src1) {
     if (want(4 * K) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
     CE_CUDA(cudaMemcpy(dst, src1, 4 * K, cudaMemcpyDeviceToHost));
+    if (which == CE_BUF_W) {   // the device keeps exp(-(S - S_min)/lambda) and 1/Z
+      float iz = 0.f;
+      CE_CUDA(cudaMemcpy(&iz, &d.ctl->invZ, sizeof(float), cudaMemcpyDeviceToHost));
+      float* wv = static_cast<float*>(dst);
+      for (size_t k = 0; k < K; ++k) wv[k] *= iz;
+    }
     return CE_MPPI_OK;
   }
   if (which == CE_BUF_PN || which == CE_BUF_Z || which == CE_BUF_G) {

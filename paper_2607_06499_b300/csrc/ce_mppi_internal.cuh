@@ -36,7 +36,8 @@ struct Ctl {
 
 // Static description of one planner instance: parameters and device buffers.
 // Layout of the scratch buffers (Kp = K rounded up to a multiple of 32):
-//   tracks float4 [(T+1)][n_obs_max]  (x, y, z, (r_o + r_robot)^2)
+//   tracks float4 [(T+1)][track_stride]: 2-D (x, y, (r_o + r_robot)^2, index),
+//          arm (x, y, z, r_o + r_robot); then the (T+1) row counts
 //   S, w float [Kp]; hit, hitj, idxV, idxC, label, cell, sorted, parent int [Kp]
 //   pN, z, g, zs float [p][Kp] (SoA)
 //   eps    2-D: float [T*m][Kp] (k fastest); arm: float [Kp][T*m] (k slowest)
@@ -54,6 +55,7 @@ struct InstDesc {
   float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
   int TMp;       // T*m rounded up to a multiple of 4
   int *hit, *hitj, *idxV, *idxC, *label, *cell, *sorted, *parent;
+  int* vpos;     // [Kp] position of rollout k in V, -1 when it collides
   float* bbox;   // [G^p][6] DBSCAN per-cell core bounding boxes
   Ctl* ctl;
 };

@@ -91,13 +91,11 @@ __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, fl
 // Eq. 9-10 (stable ballot/prefix-sum compaction of V and C_col), the closest
 // hit obstacle o* and the reference point pbar (Eq. 11), the features z
 // (Eq. 12-13) and g (Eq. 15) of V, and the velocity estimate of o* (Eq. 17).
-__global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
+__global__ void __maxnreg__(64) k_prune(KArgs a) {
   const int inst = blockIdx.x;
   const InstDesc& d = desc_of(a, inst);
   const Req r = req_of(a, inst);
   Ctl* ctl = d.ctl;
-  __shared__ int wsum[33];
-  __shared__ float red[33];
   __shared__ unsigned hitmask[kMaxObs / 32];
   __shared__ unsigned long long best;
   __shared__ float p0s[3];
@@ -108,19 +106,58 @@ __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
     task_pos0(d, r.x0, p0s);
   }
   __syncthreads();
-  int nV = 0, nC = 0;
-  for (int k0 = 0; k0 < K; k0 += blockDim.x) {
-    const int k = k0 + tid;
-    const int h = k < K ? d.hit[k] : -1;
-    const bool isV = k < K && h < 0, isC = k < K && h >= 0;
-    if (isC) atomicOr(&hitmask[h >> 5], 1u << (h & 31));
-    int tV, tC;
-    const int rv = block_scan_flag(isV, wsum, &tV);
-    const int rc = block_scan_flag(isC, wsum, &tC);
-    if (isV) d.idxV[nV + rv] = k;
-    if (isC) d.idxC[nC + rc] = k;
-    nV += tV;
-    nC += tC;
+  // stable two-pass compaction: each warp owns a contiguous range of k; pass 1
+  // counts (and marks the obstacles hit first), warp 0 scans the warp counts,
+  // pass 2 writes V, C_col and the position of each k in V (-1 if colliding)
+  __shared__ unsigned long long wpack[33];
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int L = (((K + nw - 1) / nw) + 31) & ~31;
+  const int beg = min(K, wid * L), end = min(K, beg + L);
+  const unsigned lt = (1u << lane) - 1u;
+  {
+    unsigned long long cnt = 0;
+    for (int s0 = beg; s0 < end; s0 += 32) {
+      const int k = s0 + lane;
+      const int h = k < end ? d.hit[k] : -1;
+      if (h >= 0) atomicOr(&hitmask[h >> 5], 1u << (h & 31));
+      cnt += __popc(__ballot_sync(0xffffffffu, k < end && h < 0)) |
+             ((unsigned long long)__popc(__ballot_sync(0xffffffffu, h >= 0)) << 32);
+    }
+    if (lane == 0) wpack[wid] = cnt;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned long long v = lane < nw ? wpack[lane] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wpack[lane] = x - v;
+    if (lane == 31) wpack[32] = x;
+  }
+  __syncthreads();
+  const int nV = (int)(wpack[32] & 0xffffffffull), nC = (int)(wpack[32] >> 32);
+  {
+    int bv = (int)(wpack[wid] & 0xffffffffull), bc = (int)(wpack[wid] >> 32);
+    for (int s0 = beg; s0 < end; s0 += 32) {
+      const int k = s0 + lane;
+      const int h = k < end ? d.hit[k] : -1;
+      const bool isV = k < end && h < 0, isC = h >= 0;
+      const unsigned mv = __ballot_sync(0xffffffffu, isV), mc = __ballot_sync(0xffffffffu, isC);
+      if (isV) {
+        const int pos = bv + __popc(mv & lt);
+        d.idxV[pos] = k;
+        d.vpos[k] = pos;
+      }
+      if (isC) {
+        d.idxC[bc + __popc(mc & lt)] = k;
+        d.vpos[k] = -1;
+      }
+      bv += __popc(mv);
+      bc += __popc(mc);
+    }
   }
   if (nC == 0 || nV == 0) {
     if (tid == 0) {
@@ -154,10 +191,29 @@ __global__ void __launch_bounds__(kBlock) k_prune(KArgs a) {
     for (int c = 0; c < 3; ++c)
       if (c < p) kahan_add(acc[c], cmp[c], d.pN[(size_t)c * Kp + k]);
   }
-  const float ncnt = block_sum((float)cnt, red);
+  // one block reduction of (count, sum x, sum y, sum z)
+  __shared__ float red4[4][33];
+  {
+    float v4[4] = {(float)cnt, acc[0], acc[1], acc[2]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v4[q] = warp_sum(v4[q]);
+      if (lane == 0) red4[q][wid] = v4[q];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float t = warp_sum(lane < nw ? red4[q][lane] : 0.f);
+        if (lane == 0) red4[q][32] = t;
+      }
+    }
+    __syncthreads();
+  }
+  const float ncnt = red4[0][32];
   float pbar[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) pbar[c] = c < p ? block_sum(acc[c], red) / ncnt : 0.f;
+  for (int c = 0; c < 3; ++c) pbar[c] = c < p ? red4[1 + c][32] / ncnt : 0.f;
   // features of V
   const float ne = d.norm_eps;
   for (int i = tid; i < nV; i += blockDim.x) {
@@ -831,8 +887,9 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
 // (Eq. 19, or Eq. 6 over all K / over V in the fallbacks), normalised, with
 // the minimum subtracted before exp.
 constexpr int kWin = 512;   // clusters per statistics window
+constexpr int kSlots = 3;   // per-warp label cache of the cluster statistics
 
-__global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
+__global__ void __maxnreg__(64) k_select(KArgs a) {
   const int inst = blockIdx.x;
   const InstDesc& d = desc_of(a, inst);
   Ctl* ctl = d.ctl;
@@ -840,7 +897,7 @@ __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
   __shared__ int accN[kWin];
   __shared__ float red[33];
   __shared__ unsigned long long bestkey;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int K = d.K, Kp = d.Kp, p = d.p;
   const int mode0 = ctl->mode;
   const int nV = ctl->nV, M = ctl->M;
@@ -860,17 +917,53 @@ __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
     const float ivn = 1.0f / (vn + d.norm_eps);
     const float vh[3] = {vx * ivn, vy * ivn, vz * ivn};
     if (tid == 0) bestkey = ~0ull;
+    // each warp owns a contiguous range of V and keeps per-lane partial sums
+    // for up to kSlots labels (warp-uniform slot labels); a slot is reduced
+    // across the warp and added to shared memory only when evicted or at the
+    // end -- exact int64 sums, so the result does not depend on the order.
+    const int Lr = (((nV + nw - 1) / nw) + 31) & ~31;
+    const int beg = min(nV, wid * Lr), end = min(nV, beg + Lr);
     for (int w0 = 0; w0 < M; w0 += kWin) {
       for (int c = tid; c < kWin; c += blockDim.x) {
         accS[c] = 0ull; accN[c] = 0;
         accG[0][c] = accG[1][c] = accG[2][c] = 0ull;
       }
       __syncthreads();
-      for (int i0 = 0; i0 < nV; i0 += blockDim.x) {
-        const int i = i0 + tid;
+      int cl[kSlots];
+      long long aS[kSlots], aG[kSlots][3];
+      int aN[kSlots];
+#pragma unroll
+      for (int sl = 0; sl < kSlots; ++sl) {
+        cl[sl] = -1; aS[sl] = 0; aN[sl] = 0;
+        aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
+      }
+      auto flush = [&](int sl) {
+        long long s = aS[sl], g0 = aG[sl][0], g1 = aG[sl][1], g2 = aG[sl][2];
+        int nn = aN[sl];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s += __shfl_xor_sync(FULL, s, o);
+          g0 += __shfl_xor_sync(FULL, g0, o);
+          g1 += __shfl_xor_sync(FULL, g1, o);
+          g2 += __shfl_xor_sync(FULL, g2, o);
+          nn += __shfl_xor_sync(FULL, nn, o);
+        }
+        if (lane == 0 && cl[sl] >= 0) {
+          const int c = cl[sl] - w0;
+          atomicAdd(&accS[c], (unsigned long long)s);
+          atomicAdd(&accG[0][c], (unsigned long long)g0);
+          atomicAdd(&accG[1][c], (unsigned long long)g1);
+          atomicAdd(&accG[2][c], (unsigned long long)g2);
+          atomicAdd(&accN[c], nn);
+        }
+        cl[sl] = -1; aS[sl] = 0; aN[sl] = 0;
+        aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
+      };
+      for (int s0 = beg; s0 < end; s0 += 32) {
+        const int i = s0 + lane;
         int L = -1;
         long long vS = 0, vG[3] = {0, 0, 0};
-        if (i < nV) {
+        if (i < end) {
           L = d.label[i];
           if (L >= w0 && L < w0 + kWin) {
             vS = __float2ll_rn(ldexpf(d.S[d.idxV[i]], eS));
@@ -881,32 +974,36 @@ __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
             L = -1;
           }
         }
-        // one atomic per distinct label present in the warp (exact integer sums)
-        unsigned pending = __ballot_sync(FULL, L >= 0);
-        while (pending) {
-          const int Lw = __shfl_sync(FULL, L, __ffs(pending) - 1);
-          const bool mine = L == Lw;
-          const unsigned mm = __ballot_sync(FULL, mine);
-          long long s = mine ? vS : 0, g0 = mine ? vG[0] : 0, g1 = mine ? vG[1] : 0,
-                    g2 = mine ? vG[2] : 0;
+        // accumulate the lanes whose label is cached; while some are not, flush
+        // the slots and load up to kSlots of the missing labels (each round
+        // retires at least one label, so at most 32 rounds)
+        auto cached = [&](int x) {
+          bool hit = false;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(FULL, s, o);
-            g0 += __shfl_xor_sync(FULL, g0, o);
-            g1 += __shfl_xor_sync(FULL, g1, o);
-            g2 += __shfl_xor_sync(FULL, g2, o);
+          for (int sl = 0; sl < kSlots; ++sl) hit |= (cl[sl] == x);
+          return hit;
+        };
+        bool done = L < 0;
+        for (int round = 0; round <= 32; ++round) {
+#pragma unroll
+          for (int sl = 0; sl < kSlots; ++sl)
+            if (!done && L == cl[sl]) {
+              aS[sl] += vS; aN[sl] += 1;
+              aG[sl][0] += vG[0]; aG[sl][1] += vG[1]; aG[sl][2] += vG[2];
+              done = true;
+            }
+          if (!__any_sync(FULL, !done)) break;
+#pragma unroll
+          for (int sl = 0; sl < kSlots; ++sl) flush(sl);
+#pragma unroll
+          for (int sl = 0; sl < kSlots; ++sl) {
+            const unsigned pend = __ballot_sync(FULL, !done && !cached(L));
+            if (pend) cl[sl] = __shfl_sync(FULL, L, __ffs(pend) - 1);
           }
-          if (lane == 0) {
-            const int c = Lw - w0;
-            atomicAdd(&accS[c], (unsigned long long)s);
-            atomicAdd(&accG[0][c], (unsigned long long)g0);
-            atomicAdd(&accG[1][c], (unsigned long long)g1);
-            atomicAdd(&accG[2][c], (unsigned long long)g2);
-            atomicAdd(&accN[c], __popc(mm));
-          }
-          pending &= ~mm;
         }
       }
+#pragma unroll
+      for (int sl = 0; sl < kSlots; ++sl) flush(sl);
       __syncthreads();
       for (int c = tid; c < kWin && w0 + c < M; c += blockDim.x) {
         const float n = (float)accN[c];
@@ -915,6 +1012,7 @@ __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
           crit = ldexpf(__ll2float_rn((long long)accS[c]), -eS) / n;
         } else {
           float v[3], nn = 0.f;
+#pragma unroll
           for (int q = 0; q < 3; ++q) {
             v[q] = q < p ? ldexpf(__ll2float_rn((long long)accG[q][c]), -eG) / n : 0.f;
             nn += v[q] * v[q];
@@ -928,42 +1026,38 @@ __global__ void __launch_bounds__(kBlock) k_select(KArgs a) {
     }
     sel = (int)(bestkey & 0xffffffffull);
   }
-  // update set membership, S_min, normaliser, weights
+  // update set (all K / V / the selected cluster), S_min over it, then one
+  // pass over all K writing e_k = exp(-(S_k - S_min)/lambda) (0 outside) and
+  // the normaliser Z; the update multiplies its sums by 1/Z.
   const int mode = mode0 == CE_MODE_STATIC ? (dynamic ? CE_MODE_DYNAMIC : CE_MODE_STATIC) : mode0;
-  for (int k = tid; k < K; k += blockDim.x) d.w_k[k] = 0.f;
-  __syncthreads();
   const bool over_all = mode == CE_MODE_NOCOL || mode == CE_MODE_ALLCOL;
-  const int nIt = over_all ? K : nV;
+  const bool over_V = mode == CE_MODE_ALLNOISE;
+  auto member = [&](int k) {
+    if (over_all) return true;
+    const int v = d.vpos[k];
+    return v >= 0 && (over_V || d.label[v] == sel);
+  };
   float smin = INFINITY;
-  for (int i = tid; i < nIt; i += blockDim.x) {
-    const bool mem = over_all || mode == CE_MODE_ALLNOISE || d.label[i] == sel;
-    if (mem) smin = fminf(smin, d.S[over_all ? i : d.idxV[i]]);
-  }
+  for (int k = tid; k < K; k += blockDim.x)
+    if (member(k)) smin = fminf(smin, d.S[k]);
   smin = -block_max(-smin, red);
   const float il = d.inv_lambda;
   float z = 0.f, zc = 0.f;
-  for (int i = tid; i < nIt; i += blockDim.x) {
-    const bool mem = over_all || mode == CE_MODE_ALLNOISE || d.label[i] == sel;
-    if (!mem) continue;
-    const int k = over_all ? i : d.idxV[i];
-    const float e = expf(-(d.S[k] - smin) * il);
+  for (int k = tid; k < K; k += blockDim.x) {
+    float e = 0.f;
+    if (member(k)) {
+      e = expf(-(d.S[k] - smin) * il);
+      kahan_add(z, zc, e);
+    }
     d.w_k[k] = e;
-    kahan_add(z, zc, e);
   }
   const float Z = block_sum(z, red);
-  const float iz = 1.0f / Z;
-  for (int i = tid; i < nIt; i += blockDim.x) {
-    const bool mem = over_all || mode == CE_MODE_ALLNOISE || d.label[i] == sel;
-    if (!mem) continue;
-    const int k = over_all ? i : d.idxV[i];
-    d.w_k[k] = d.w_k[k] * iz;
-  }
   if (tid == 0) {
     ctl->mode = mode;
     ctl->sel = sel;
     ctl->dynamic = dynamic;
     ctl->S_min = smin;
-    ctl->invZ = iz;
+    ctl->invZ = 1.0f / Z;
   }
 }
 
@@ -1076,10 +1170,11 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   if (!last) return;
   __threadfence();
   const int nkc = (K + kch - 1) / kch;
+  const float iz = __ldcg(&d.ctl->invZ);
   for (int c = threadIdx.x; c < TM; c += blockDim.x) {
     float t = 0.f;
     for (int q = 0; q < nkc; ++q) t += __ldcg(d.upart + (size_t)q * d.TMp + c);
-    d.Unew[c] = d.U[c] + t;
+    d.Unew[c] = d.U[c] + t * iz;
   }
   __threadfence();
   __syncthreads();

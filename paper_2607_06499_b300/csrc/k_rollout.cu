@@ -22,7 +22,7 @@ namespace cem {
 // r_j + r_o + r_robot (+1 mm slack) from c_j cannot be hit at step j and is
 // left out.  This changes no collision result.  Entries are (x, y, (r_o +
 // r_robot)^2, obstacle index as int bits); the row counts follow the rows.
-// Arm: every row holds every obstacle as (x, y, z, (r_o + r_robot)^2).
+// Arm: every row holds every obstacle as (x, y, z, r_o + r_robot).
 __global__ void k_tracks(KArgs a) {
   const int inst = blockIdx.x;
   const InstDesc& d = desc_of(a, inst);
@@ -47,7 +47,7 @@ __global__ void k_tracks(KArgs a) {
       float c[3];
       for (int i = 0; i < 3; ++i) c[i] = newest[i] + ((newest[i] - oldest[i]) * inv) * tj;
       const float R = r.obs_radius[o] + d.robot_radius;
-      d.tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R * R);
+      d.tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R);
     }
     for (int j = threadIdx.x; j <= T; j += blockDim.x) counts[j] = n_obs;
     if (threadIdx.x == 0) d.ctl->col_tests = T * n_obs;
@@ -223,22 +223,60 @@ __global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
 // forward kinematics, 4 spheres per link against every obstacle, and the pose
 // cost of Eq. 24 (w_p |p_ee - p_g| + w_R angle(R, R_g) + w_c I_col).
 // S = sum_{j=0..T} l(q_j) (the terminal cost has the stage form).
+// Two-level broad phase before the 24 sphere tests: an obstacle farther from
+// the arm's bounding sphere (centre of the 7 frame origins, radius to the
+// farthest) than its radius is skipped; then per link, an obstacle farther from
+// the link's midpoint than half the link plus its radius is skipped.  Sphere
+// centres lie on the link segments, so no colliding pair is skipped (a 1e-5
+// relative slack covers FP32 rounding).  Entries are (x, y, z, r_o + r_robot).
 __device__ __forceinline__ int arm_collide(const float O[7][3], const float4* tj, int n_obs) {
-  float C[24][3];
+  float lc[6][3], lh[6], ac[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int link = 0; link < 6; ++link)
+  for (int i = 0; i < 7; ++i)
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+    for (int q = 0; q < 3; ++q) ac[q] += O[i][q] * (1.0f / 7.0f);
+  float ar2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-        C[link * 4 + f][i] = O[link][i] + ((float)f * (1.0f / 3.0f)) * (O[link + 1][i] - O[link][i]);
+  for (int i = 0; i < 7; ++i) {
+    const float dx = O[i][0] - ac[0], dy = O[i][1] - ac[1], dz = O[i][2] - ac[2];
+    ar2 = fmaxf(ar2, dx * dx + dy * dy + dz * dz);
+  }
+  const float ar = sqrtf(ar2) * 1.00001f + 1e-6f;
+#pragma unroll
+  for (int l = 0; l < 6; ++l) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      lc[l][q] = 0.5f * (O[l][q] + O[l + 1][q]);
+      const float e = O[l + 1][q] - O[l][q];
+      s2 += e * e;
+    }
+    lh[l] = 0.5f * sqrtf(s2) * 1.00001f + 1e-6f;
+  }
   for (int o = 0; o < n_obs; ++o) {
     const float4 t = tj[o];
+    const float R = t.w;
+    {
+      const float dx = ac[0] - t.x, dy = ac[1] - t.y, dz = ac[2] - t.z;
+      const float rr = ar + R;
+      if (dx * dx + dy * dy + dz * dz >= rr * rr) continue;
+    }
+    const float R2 = R * R;
     bool any = false;
 #pragma unroll
-    for (int s = 0; s < 24; ++s) {
-      const float dx = C[s][0] - t.x, dy = C[s][1] - t.y, dz = C[s][2] - t.z;
-      any |= (dx * dx + dy * dy + dz * dz < t.w);
+    for (int l = 0; l < 6; ++l) {
+      const float dx = lc[l][0] - t.x, dy = lc[l][1] - t.y, dz = lc[l][2] - t.z;
+      const float rr = lh[l] + R;
+      if (dx * dx + dy * dy + dz * dz >= rr * rr) continue;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float fr = (float)f * (1.0f / 3.0f);
+        const float cx = O[l][0] + fr * (O[l + 1][0] - O[l][0]);
+        const float cy = O[l][1] + fr * (O[l + 1][1] - O[l][1]);
+        const float cz = O[l][2] + fr * (O[l + 1][2] - O[l][2]);
+        const float ex = cx - t.x, ey = cy - t.y, ez = cz - t.z;
+        any |= (ex * ex + ey * ey + ez * ez < R2);
+      }
     }
     if (any) return o;
   }
@@ -252,7 +290,7 @@ __device__ __forceinline__ float arm_cost(const InstDesc& d, const float O[7][3]
          (collide ? d.w[2] : 0.0f);
 }
 
-__global__ void __launch_bounds__(kArmWarps * 32) k_rollout_arm(KArgs a) {
+__global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   const int2 tile = tile_of(a);

@@ -197,8 +197,6 @@ def make(name: str, seed: int = 0, n_replans: int = 1, **over) -> dict:
         x0 = q0
     else:
         raise KeyError(name)
-    if over:
-        raise TypeError(f"unused overrides {sorted(over)}")
     n, m, p = DIMS[cfg["dyn"]]
     U0 = np.zeros((cfg["T"], m)) if u0 is None else np.tile(np.asarray(u0, float), (cfg["T"], 1))
     return dict(cfg=cfg, x0=np.asarray(x0, float), U0=U0,

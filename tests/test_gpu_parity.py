@@ -149,6 +149,28 @@ def test_stage_parity_small(name, kw):
           f"M={diag['n_clusters']} " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
 
 
+@pytest.mark.parametrize("name,K,eps,mp", [("di_blocked", 3000, 0.05, 3),
+                                          ("unicycle_blocked", 3000, 0.05, 3),
+                                          ("arm_blocked", 1500, 0.21, 3)])
+def test_stage_parity_many_clusters(name, K, eps, mp):
+    """Small DBSCAN radius: several clusters interleaved in V order, so the
+    per-warp statistics cache of the selection stage evicts and reloads."""
+    sc = W.make(name, seed=0, K=K)
+    sc["cfg"]["dbscan_eps"], sc["cfg"]["min_pts"] = eps, mp
+    diag, errs = _check_replan(sc)
+    assert diag["n_clusters"] >= 2
+
+
+@pytest.mark.parametrize("ref_mode,check_j0", [(1, 0), (0, 1), (1, 1)])
+def test_stage_parity_paper_literal_switches(ref_mode, check_j0):
+    """ref_mode 1: reference point over all of C_col (Eq. 11 as written);
+    check_j0 1: the current state counts for collisions (Eq. 8 as written)."""
+    for name, kw in [("di_blocked", {}), ("unicycle_blocked", dict(K=1200)),
+                     ("arm_blocked", dict(K=400))]:
+        sc = W.make(name, seed=0, ref_mode=ref_mode, check_j0=check_j0, **kw)
+        _check_replan(sc)
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_stage_parity_other_seeds_and_counters(seed):
     sc = W.make("unicycle_blocked", seed=seed, K=1500)
