@@ -272,6 +272,25 @@ def plain_mix_latency(pkg, n_each: int = 20) -> dict:
             "replans_per_s": 1.0 / mean_s, "rollout_steps_per_s": steps / mean_s}
 
 
+def shard_seeds(rank: int, n_per_rank: int) -> list:
+    """Instances are independent: rank r replans its own n_per_rank seeded
+    instances (weak scaling), with no exchange on the data path."""
+    return [rank * n_per_rank + i for i in range(n_per_rank)]
+
+
+def aggregate(tot_ms: float, units_per_rank: float, steps: int, world: int, dist=None):
+    """Whole-job rate: the units of all ranks over the slowest rank's time
+    (max-reduction of the timed region; the only collective)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([tot_ms], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    return world * units_per_rank * steps / (tot_ms / 1e3), tot_ms
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,6 +301,8 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=40)
+    ap.add_argument("--branches", type=int, default=4,
+                    help="concurrent branches of the batch (stage overlap)")
     ap.add_argument("--workload", default="unicycle", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served run (0: skip)")
@@ -323,7 +344,7 @@ def main() -> None:
     wl = WORKLOADS[args.workload]
     EPISODE = wl["episode"]
     N_INST = wl["n"]
-    seeds = [rank * N_INST + i for i in range(N_INST)]
+    seeds = shard_seeds(rank, N_INST)
     scenes = [W.make(wl["scene"], seed=s, n_replans=EPISODE + 8) for s in seeds]
     cfg0 = scenes[0]["cfg"]
     m = pkg.DIMS[cfg0["dyn"]][1]
@@ -357,7 +378,7 @@ def main() -> None:
         torch.cuda.synchronize()
 
     reset_episodes()
-    batch = pkg.Batch(planners, reqs, stream=stream, use_graph=True)
+    batch = pkg.Batch(planners, reqs, stream=stream, use_graph=True, n_branches=args.branches)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
@@ -385,14 +406,9 @@ def main() -> None:
             reset_episodes()
     clk = clocks.stop()
     step_ms = np.array(step_ms)
-    tot_ms = float(step_ms.sum())
+    value, tot_ms = aggregate(float(step_ms.sum()), units_per_step, args.steps, world, dist)
     if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
         dist.barrier()
-    units = world * units_per_step * args.steps
-    value = units / (tot_ms / 1e3)
     modes = {}
     for r in reqs:
         d = np.frombuffer(r["diag"].cpu().numpy().tobytes()[:32], dtype=np.int32)
@@ -443,7 +459,8 @@ def main() -> None:
             u_out=torch.zeros((sc["cfg"]["T"], m), dtype=torch.float32, device=dev)))
         e2e_req[-1]["x_next"] = e2e_req[-1]["x0"]
         e2e_pl.append(pl)
-    e2e_batch = pkg.Batch(e2e_pl, e2e_req, stream=stream, use_graph=True)
+    e2e_batch = pkg.Batch(e2e_pl, e2e_req, stream=stream, use_graph=True,
+                          n_branches=args.branches)
     host_obs = [torch.tensor(sc["obs"], dtype=torch.float32).pin_memory() for sc in scenes]
     host_u = [torch.zeros((sc["cfg"]["T"], m), dtype=torch.float32).pin_memory() for sc in scenes]
     h2d = sum(r["hist"].numel() * 4 for r in e2e_req)
@@ -487,7 +504,8 @@ def main() -> None:
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank"),
+        "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank",
+                       branches=args.branches),
         "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),

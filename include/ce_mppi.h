@@ -157,12 +157,16 @@ ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* req);
 /* Batches: n handles replanned together, one kernel launch per stage for all of
  * them (instances of different K, T and obstacle count).  The requests are
  * fixed at creation (use obs_step to replay recorded observation streams).
- * With use_graph != 0 the stage chain is captured once as a CUDA graph and
+ * With n_branches > 1 the instances are split (balanced by K*T) into that many
+ * branches whose stage chains run concurrently on streams of their own, so one
+ * branch's single-CTA stages overlap another's rollouts.  With use_graph != 0
+ * the whole batch (fork, branches, join) is captured once as a CUDA graph and
  * replayed by ce_mppi_batch_run.  stream is the cudaStream_t the batch runs on.
  * Every handle must have the same dynamics kind.  Results are bitwise those of
  * replanning each handle alone.  Errors: INVALID_ARG, NO_MEMORY, CUDA.        */
 ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_request* reqs,
-                                 int n, void* stream, int use_graph, ce_mppi_batch** out);
+                                 int n, void* stream, int use_graph, int n_branches,
+                                 ce_mppi_batch** out);
 /* Queue one replan of every instance of the batch; returns without waiting.  */
 ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
 /* Run one replan of the batch stage by stage (no graph) with CUDA events

@@ -99,7 +99,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_get_counter.argtypes = [vp, C.POINTER(u64)]
         L.ce_mppi_replan.argtypes = [vp, vp, vp, vp, i, vp, C.POINTER(Diag)]
         L.ce_mppi_replan_dev.argtypes = [vp, C.POINTER(Request)]
-        L.ce_mppi_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Request), i, vp, i,
+        L.ce_mppi_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Request), i, vp, i, i,
                                            C.POINTER(vp)]
         L.ce_mppi_batch_run.argtypes = [vp]
         L.ce_mppi_batch_profile.argtypes = [vp, C.POINTER(C.c_float)]
@@ -243,7 +243,7 @@ class Batch:
     captured CUDA graph).  requests: list of dicts of torch device tensors with
     keys x0, hist, radius and optional u_out, x_next, diag, obs_step."""
 
-    def __init__(self, planners, requests, stream=None, use_graph=True):
+    def __init__(self, planners, requests, stream=None, use_graph=True, n_branches=1):
         n = len(planners)
         self.planners = planners
         self.requests = requests  # keep tensors alive
@@ -257,7 +257,7 @@ class Batch:
                             _ptr(r.get("x_next")), _ptr(r.get("diag")))
         b = C.c_void_p()
         _check(lib().ce_mppi_batch_create(hs, rq, n, C.c_void_p(self.stream), int(use_graph),
-                                          C.byref(b)))
+                                          int(n_branches), C.byref(b)))
         self.b = b
 
     def run(self):

@@ -440,11 +440,63 @@ ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_
   return CE_MPPI_OK;
 }
 
+namespace {
+
+void free_batch(ce_mppi_batch* b) {
+  for (auto& br : b->branches) {
+    cudaFree(br.dtiles_roll);
+    cudaFree(br.dtiles_upd);
+    if (br.stream) cudaStreamDestroy(br.stream);
+    if (br.done) cudaEventDestroy(br.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->ddesc);
+  cudaFree(b->dreq);
+  cudaFree(b->dtiles_roll);
+  cudaFree(b->dtiles_upd);
+  delete b;
+}
+
+// Queue one replan of every instance: the branches fork from `s`, run their
+// chains concurrently on their own streams and join back into `s`.
+void run_branches(ce_mppi_batch* b, cudaStream_t s) {
+  if (b->branches.size() == 1) {
+    const auto& br = b->branches[0];
+    KArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.D = b->ddesc;
+    a.R = b->dreq;
+    a.n_inst = br.n;
+    run_chain(b->dyn, a, br.dtiles_roll, br.n_roll, br.dtiles_upd, br.n_upd, br.smem_roll,
+              br.max_cells, s);
+    return;
+  }
+  cudaEventRecord(b->fork, s);
+  for (auto& br : b->branches) {
+    cudaStreamWaitEvent(br.stream, b->fork, 0);
+    KArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.D = b->ddesc + br.off;
+    a.R = b->dreq + br.off;
+    a.n_inst = br.n;
+    run_chain(b->dyn, a, br.dtiles_roll, br.n_roll, br.dtiles_upd, br.n_upd, br.smem_roll,
+              br.max_cells, br.stream);
+    cudaEventRecord(br.done, br.stream);
+  }
+  for (auto& br : b->branches) cudaStreamWaitEvent(s, br.done, 0);
+}
+
+}  // namespace
+
 ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
-                                 void* stream, int use_graph, ce_mppi_batch** out) {
+                                 void* stream, int use_graph, int n_branches,
+                                 ce_mppi_batch** out) {
   if (!out) return fail(CE_MPPI_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!hs || !reqs || n < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "empty batch");
+  if (n_branches < 1 || n_branches > 64) return fail(CE_MPPI_ERR_INVALID_ARG, "n_branches in [1, 64]");
   const int dyn = hs[0] ? hs[0]->P.dyn : -1;
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle in batch");
@@ -454,72 +506,100 @@ ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_reques
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "a handle appears twice");
   }
+  n_branches = std::min(n_branches, n);
   ce_mppi_batch* b = new (std::nothrow) ce_mppi_batch();
   if (!b) return fail(CE_MPPI_ERR_NO_MEMORY, "host allocation failed");
   b->hs.assign(hs, hs + n);
   b->stream = static_cast<cudaStream_t>(stream);
   b->dyn = dyn;
-  std::vector<InstDesc> descs(n);
-  std::vector<Req> rq(n);
-  std::vector<int2> roll, upd;
-  for (int i = 0; i < n; ++i) {
-    ce_mppi_handle* h = hs[i];
-    unsigned long long c0 = 0;
-    cudaStreamSynchronize(h->stream);
-    cudaMemcpy(&c0, h->hdesc.counter, 8, cudaMemcpyDeviceToHost);
-    descs[i] = h->hdesc;
-    rq[i] = to_req(&reqs[i], c0);
-    tiles_of(h, i, roll, upd);
-    b->smem_roll = std::max(b->smem_roll, h->smem_roll);
-    b->max_cells = std::max(b->max_cells, h->ncells);
+  // balance the branches by rollout work (largest instances first)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (long long)hs[x]->P.K * hs[x]->P.T > (long long)hs[y]->P.K * hs[y]->P.T;
+  });
+  std::vector<std::vector<int>> members(n_branches);
+  std::vector<long long> load(n_branches, 0);
+  for (int i : order) {
+    const int bb = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    members[bb].push_back(i);
+    load[bb] += (long long)hs[i]->P.K * hs[i]->P.T;
+  }
+  std::vector<InstDesc> descs;
+  std::vector<Req> rq;
+  std::vector<int2> roll, upd;   // whole-batch tiles (stage-by-stage profile)
+  b->branches.resize(n_branches);
+  std::vector<std::vector<int2>> broll(n_branches), bupd(n_branches);
+  for (int bb = 0; bb < n_branches; ++bb) {
+    auto& br = b->branches[bb];
+    br.off = (int)descs.size();
+    br.n = (int)members[bb].size();
+    for (int li = 0; li < br.n; ++li) {
+      ce_mppi_handle* h = hs[members[bb][li]];
+      unsigned long long c0 = 0;
+      cudaStreamSynchronize(h->stream);
+      cudaMemcpy(&c0, h->hdesc.counter, 8, cudaMemcpyDeviceToHost);
+      descs.push_back(h->hdesc);
+      rq.push_back(to_req(&reqs[members[bb][li]], c0));
+      tiles_of(h, (int)descs.size() - 1, roll, upd);
+      tiles_of(h, li, broll[bb], bupd[bb]);
+      br.smem_roll = std::max(br.smem_roll, h->smem_roll);
+      br.max_cells = std::max(br.max_cells, h->ncells);
+      b->smem_roll = std::max(b->smem_roll, h->smem_roll);
+      b->max_cells = std::max(b->max_cells, h->ncells);
+    }
+    br.n_roll = (int)broll[bb].size();
+    br.n_upd = (int)bupd[bb].size();
   }
   b->n_roll = (int)roll.size();
   b->n_upd = (int)upd.size();
-  auto cleanup = [&]() {
-    cudaFree(b->ddesc); cudaFree(b->dreq); cudaFree(b->dtiles_roll); cudaFree(b->dtiles_upd);
-    delete b;
-  };
   cudaError_t e;
-  if ((e = cudaMalloc(&b->ddesc, sizeof(InstDesc) * n)) != cudaSuccess ||
-      (e = cudaMalloc(&b->dreq, sizeof(Req) * n)) != cudaSuccess ||
-      (e = cudaMalloc(&b->dtiles_roll, sizeof(int2) * roll.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->dtiles_upd, sizeof(int2) * upd.size())) != cudaSuccess) {
-    cleanup();
-    return fail(CE_MPPI_ERR_NO_MEMORY, "device allocation failed");
+  bool ok = (e = cudaMalloc(&b->ddesc, sizeof(InstDesc) * n)) == cudaSuccess &&
+            (e = cudaMalloc(&b->dreq, sizeof(Req) * n)) == cudaSuccess &&
+            (e = cudaMalloc(&b->dtiles_roll, sizeof(int2) * roll.size())) == cudaSuccess &&
+            (e = cudaMalloc(&b->dtiles_upd, sizeof(int2) * upd.size())) == cudaSuccess;
+  for (int bb = 0; ok && bb < n_branches; ++bb) {
+    auto& br = b->branches[bb];
+    ok = (e = cudaMalloc(&br.dtiles_roll, sizeof(int2) * broll[bb].size())) == cudaSuccess &&
+         (e = cudaMalloc(&br.dtiles_upd, sizeof(int2) * bupd[bb].size())) == cudaSuccess &&
+         (e = cudaMemcpy(br.dtiles_roll, broll[bb].data(), sizeof(int2) * broll[bb].size(),
+                         cudaMemcpyHostToDevice)) == cudaSuccess &&
+         (e = cudaMemcpy(br.dtiles_upd, bupd[bb].data(), sizeof(int2) * bupd[bb].size(),
+                         cudaMemcpyHostToDevice)) == cudaSuccess;
+    if (ok && n_branches > 1)
+      ok = (e = cudaStreamCreateWithFlags(&br.stream, cudaStreamNonBlocking)) == cudaSuccess &&
+           (e = cudaEventCreateWithFlags(&br.done, cudaEventDisableTiming)) == cudaSuccess;
   }
-  if ((e = cudaMemcpy(b->ddesc, descs.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->dreq, rq.data(), sizeof(Req) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->dtiles_roll, roll.data(), sizeof(int2) * roll.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->dtiles_upd, upd.data(), sizeof(int2) * upd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
-    cleanup();
-    return cuda_fail(e, "batch upload");
+  if (ok && n_branches > 1)
+    ok = (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) == cudaSuccess;
+  if (ok)
+    ok = (e = cudaMemcpy(b->ddesc, descs.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+         (e = cudaMemcpy(b->dreq, rq.data(), sizeof(Req) * n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+         (e = cudaMemcpy(b->dtiles_roll, roll.data(), sizeof(int2) * roll.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
+         (e = cudaMemcpy(b->dtiles_upd, upd.data(), sizeof(int2) * upd.size(), cudaMemcpyHostToDevice)) == cudaSuccess;
+  if (!ok) {
+    free_batch(b);
+    return cuda_fail(e, "batch set-up");
   }
   if (use_graph) {
-    KArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.D = b->ddesc;
-    a.R = b->dreq;
-    a.n_inst = n;
     // capture on a private non-blocking stream (the legacy default stream
     // cannot be captured); the graph is launched on the batch's stream.
     cudaStream_t cap;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
-      cleanup();
+      free_batch(b);
       return cuda_fail(e, "cudaStreamCreateWithFlags");
     }
     if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
       cudaStreamDestroy(cap);
-      cleanup();
+      free_batch(b);
       return cuda_fail(e, "cudaStreamBeginCapture");
     }
-    run_chain(dyn, a, b->dtiles_roll, b->n_roll, b->dtiles_upd, b->n_upd, b->smem_roll,
-              b->max_cells, cap);
+    run_branches(b, cap);
     e = cudaStreamEndCapture(cap, &b->graph);
     cudaStreamDestroy(cap);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) {
-      if (b->graph) cudaGraphDestroy(b->graph);
-      cleanup();
+      free_batch(b);
       return cuda_fail(e, "graph capture");
     }
   }
@@ -533,13 +613,7 @@ ce_status_t ce_mppi_batch_run(ce_mppi_batch* b) {
     CE_CUDA(cudaGraphLaunch(b->exec, b->stream));
     return CE_MPPI_OK;
   }
-  KArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.D = b->ddesc;
-  a.R = b->dreq;
-  a.n_inst = (int)b->hs.size();
-  run_chain(b->dyn, a, b->dtiles_roll, b->n_roll, b->dtiles_upd, b->n_upd, b->smem_roll,
-            b->max_cells, b->stream);
+  run_branches(b, b->stream);
   CE_CUDA(cudaGetLastError());
   return CE_MPPI_OK;
 }
@@ -582,13 +656,9 @@ ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms) {
 ce_status_t ce_mppi_batch_destroy(ce_mppi_batch* b) {
   if (!b) return CE_MPPI_OK;
   cudaStreamSynchronize(b->stream);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(b->ddesc);
-  cudaFree(b->dreq);
-  cudaFree(b->dtiles_roll);
-  cudaFree(b->dtiles_upd);
-  delete b;
+  for (auto& br : b->branches)
+    if (br.stream) cudaStreamSynchronize(br.stream);
+  free_batch(b);
   return CE_MPPI_OK;
 }
 

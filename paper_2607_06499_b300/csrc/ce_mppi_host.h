@@ -40,6 +40,17 @@ struct ce_mppi_batch {
   int n_roll = 0, n_upd = 0, smem_roll = 0, max_cells = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // concurrent branches: branch b owns descriptors/requests [off, off + n) of
+  // ddesc/dreq and its own tiles; the branches run on their own streams
+  struct Branch {
+    int off = 0, n = 0, n_roll = 0, n_upd = 0, smem_roll = 0, max_cells = 0;
+    int2* dtiles_roll = nullptr;
+    int2* dtiles_upd = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<Branch> branches;
+  cudaEvent_t fork = nullptr;
 };
 
 

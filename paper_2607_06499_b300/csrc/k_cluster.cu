@@ -589,6 +589,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       n_sparse += tot;
     }
     __syncthreads();
+    const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
     for (int is = wid; is < n_sparse; is += nwarp) {
       const int i = w.labels_tmp[is];
       const int ci = w.cell[i];
@@ -597,33 +598,46 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       for (int c = 0; c < p; ++c) za[c] = z[(size_t)c * ld + i];
       const int cx = ci % G, cy = (ci / G) % G, cz = p == 3 ? ci / (G * G) : 0;
       int count = 0;
-      const int zr = p == 3 ? R : 0;
-      for (int oz = -zr; oz <= zr && count < min_pts; ++oz)
-        for (int oy = -R; oy <= R && count < min_pts; ++oy)
-          for (int ox = -R; ox <= R && count < min_pts; ++ox) {
-            const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
-            if (nx < 0 || ny < 0 || nz < 0 || nx >= G || ny >= G || (p == 3 && nz >= G)) continue;
-            const int ob = map[(nz * G + ny) * G + nx];
-            if (ob < 0) continue;
-            float n2, f2;
-            box_dist2<p>(za, obox + ob, S, &n2, &f2);
-            if (n2 > near_no) continue;
-            if (f2 <= far_ok) {
-              count += ostart[ob + 1] - ostart[ob];
-              continue;
-            }
-            for (int pb0 = ostart[ob]; pb0 < ostart[ob + 1] && count < min_pts; pb0 += 32) {
-              const int pb = pb0 + lane;
-              bool hit = false;
-              if (pb < ostart[ob + 1]) {
-                float zb[3];
-#pragma unroll
-                for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pb];
-                hit = nb_pred_t<p>(za, zb, eps2);
-              }
-              count += __popc(__ballot_sync(FULL, hit));
+      // the lanes screen 32 neighbour cells at a time: boxes within eps count
+      // whole, boxes beyond eps are skipped, the rest are scanned by the warp
+      for (int of0 = 0; of0 < nofs && count < min_pts; of0 += 32) {
+        const int of = of0 + lane;
+        int whole = 0, ob = -1;
+        bool scan = false;
+        if (of < nofs) {
+          const int nx = cx + of % side - R, ny = cy + (of / side) % side - R;
+          const int nz = p == 3 ? cz + of / (side * side) - R : 0;
+          if (nx >= 0 && ny >= 0 && nz >= 0 && nx < G && ny < G && (p != 3 || nz < G)) {
+            ob = map[(nz * G + ny) * G + nx];
+            if (ob >= 0) {
+              float n2, f2;
+              box_dist2<p>(za, obox + ob, S, &n2, &f2);
+              if (f2 <= far_ok) whole = ostart[ob + 1] - ostart[ob];
+              else scan = n2 <= near_no;
             }
           }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) whole += __shfl_xor_sync(FULL, whole, o);
+        count += whole;
+        unsigned sm = __ballot_sync(FULL, scan);
+        while (sm && count < min_pts) {
+          const int src = __ffs(sm) - 1;
+          sm &= sm - 1;
+          const int obs = __shfl_sync(FULL, ob, src);
+          for (int pb0 = ostart[obs]; pb0 < ostart[obs + 1] && count < min_pts; pb0 += 32) {
+            const int pb = pb0 + lane;
+            bool hit = false;
+            if (pb < ostart[obs + 1]) {
+              float zb[3];
+#pragma unroll
+              for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pb];
+              hit = nb_pred_t<p>(za, zb, eps2);
+            }
+            count += __popc(__ballot_sync(FULL, hit));
+          }
+        }
+      }
       if (lane == 0) w.core[i] = count >= min_pts ? 1 : 0;
     }
   }

@@ -82,7 +82,7 @@ def test_null_arguments_rejected():
     L = pkg.lib()
     assert L.ce_mppi_create(None, None, None) == 1
     assert L.ce_mppi_replan(None, None, None, None, 0, None, None) == 1
-    assert L.ce_mppi_batch_create(None, None, 0, None, 0, None) == 1
+    assert L.ce_mppi_batch_create(None, None, 0, None, 0, 1, None) == 1
     assert L.ce_mppi_dbscan_dev(None, 4, 4, 5, 0.3, 3, None, None, None, 0, None) == 1
 
 

@@ -279,7 +279,7 @@ def test_replan_deterministic_and_batch_equals_single():
         u2, d2, _, _ = _run(sc)
         assert np.array_equal(u1, u2)                       # bitwise repeatable
         singles.append(u1)
-    for use_graph in (0, 1):
+    for use_graph, nb in ((0, 1), (1, 1), (0, 3), (1, 2)):
         pls, reqs = [], []
         for sc in scs:
             pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
@@ -289,7 +289,7 @@ def test_replan_deterministic_and_batch_equals_single():
                              radius=torch.tensor(sc["radius"], dtype=torch.float32, device="cuda"),
                              u_out=torch.zeros((sc["cfg"]["T"], 2), device="cuda")))
             pls.append(pl)
-        b = pkg.Batch(pls, reqs, use_graph=bool(use_graph))
+        b = pkg.Batch(pls, reqs, use_graph=bool(use_graph), n_branches=nb)
         b.run()
         torch.cuda.synchronize()
         for i, r in enumerate(reqs):
