@@ -80,9 +80,51 @@ def alu_peak_tflops(sm_count: int, mhz: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi SM clock / throttle sampling during the timed region."""
+    """SM clock and throttle reasons sampled every 10 ms through NVML during the
+    timed region (nvidia-smi every 200 ms where NVML is unavailable)."""
 
-    def __init__(self, index: int):
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"))
+
+    def __init__(self, index: int, bus_id: str = ""):
+        import threading
+        self.sm, self.reasons, self.max = [], set(), None
+        self.stop_ev = threading.Event()
+        self.p = None
+        self.thread = None
+        try:
+            import pynvml as nv
+            nv.nvmlInit()
+            try:
+                h = nv.nvmlDeviceGetHandleByPciBusId(bus_id) if bus_id else None
+            except nv.NVMLError:
+                h = None
+            if h is None:
+                h = nv.nvmlDeviceGetHandleByIndex(index)
+            self.max = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            masks = [(nm, getattr(nv, attr)) for nm, attr in self.REASONS]
+
+            def loop():
+                while not self.stop_ev.is_set():
+                    try:
+                        self.sm.append(float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)))
+                        r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                        for nm, mk in masks:
+                            if r & mk:
+                                self.reasons.add(nm)
+                    except nv.NVMLError:
+                        pass
+                    self.stop_ev.wait(0.01)
+
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            self.source = "nvml, 10 ms"
+            return
+        except Exception:
+            pass
+        self.source = "nvidia-smi, 200 ms"
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -95,14 +137,20 @@ class ClockSampler:
             self.p = None
 
     def stop(self) -> dict:
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join()
+            return {"sm_mhz": float(np.median(self.sm)) if self.sm else None,
+                    "sm_max_mhz": self.max, "reasons": sorted(self.reasons),
+                    "samples": len(self.sm), "source": self.source}
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"]}
         self.p.terminate()
         self.p.wait()
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
         sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        names = [nm for nm, _ in self.REASONS]
         for r in rows:
             try:
                 sm.append(float(r[0]))
@@ -113,7 +161,7 @@ class ClockSampler:
             except (ValueError, IndexError):
                 continue
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
 def cpu_baseline(scenes, u_init, max_threads: int, budget_s: float = 10.0) -> dict:
@@ -294,14 +342,14 @@ def aggregate(tot_ms: float, units_per_rank: float, steps: int, world: int, dist
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600,
+    ap.add_argument("--steps", type=int, default=2000,
                     help="timed steps (the 200-replan episodes restart every 200 steps)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=40)
-    ap.add_argument("--branches", type=int, default=4,
+    ap.add_argument("--branches", type=int, default=2,
                     help="concurrent branches of the batch (stage overlap)")
     ap.add_argument("--workload", default="unicycle", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -387,7 +435,12 @@ def main() -> None:
     assert args.steps >= 1
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local)
+    bus = ""
+    try:
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        pass
+    clocks = ClockSampler(local, bus)
     step_ms = []
     done = 0
     while done < args.steps:
@@ -521,7 +574,8 @@ def main() -> None:
                      "obstacle_tests_per_rollout": tests_per_rollout},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 6 * args.steps,
+        # six stage kernels per concurrent branch per step (the L2 flush is torch's)
+        "gpu_launches": 6 * min(args.branches, N_INST) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":

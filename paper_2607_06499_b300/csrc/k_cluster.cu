@@ -366,7 +366,10 @@ __device__ __forceinline__ void cell_boxes(int n, const DbWork& w, const int* ma
     uint32_t kk[3] = {0u, 0u, 0u}, idx = 0xffffffffu;
     if (pos < end) {
       const int i = w.sorted[pos];
-      if (!CORE || w.core[i]) {
+      const bool keep = !CORE || w.core[i];
+      // from here on, sorted marks the non-core points by their complement
+      if (CORE && !keep) w.sorted[pos] = ~i;
+      if (keep) {
         o = map[w.cell[i]];
         idx = (uint32_t)i;
 #pragma unroll
@@ -696,7 +699,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           if (ostart[Bc + 1] - ostart[Bc] < ostart[A + 1] - ostart[A]) { X = Bc; Y = A; }
           bool found = false;
           for (int px = ostart[X]; px < ostart[X + 1] && !found; ++px) {
-            if (!w.core[w.sorted[px]]) continue;
+            if (w.sorted[px] < 0) continue;
             float za[3];
 #pragma unroll
             for (int q = 0; q < p; ++q) za[q] = w.zs[(size_t)q * w.ld_s + px];
@@ -706,7 +709,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
             for (int py0 = ostart[Y]; py0 < ostart[Y + 1]; py0 += 32) {
               const int py = py0 + lane;
               bool hit = false;
-              if (py < ostart[Y + 1] && w.core[w.sorted[py]]) {
+              if (py < ostart[Y + 1] && w.sorted[py] >= 0) {
                 float zb[3];
 #pragma unroll
                 for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + py];
@@ -731,11 +734,10 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
     if (opar[o] >= 0 && opar[o] != o) atomicMin(&omin[opar[o]], omin[o]);
   __syncthreads();
   // 8. canonical ids (rank of each component minimum in point order), labels
-  //    of the core points, and the core / border point lists in index order
-  //    (the cell-ordered arrays are free now: sorted / zs take the core list,
-  //    cell the border list)
+  //    of the core points, and the list of the other points (into cell: a
+  //    chunk only overwrites entries of chunks already read)
   __shared__ unsigned long long wpack[33];
-  int M = 0, n_core = 0, n_border = 0;
+  int M = 0, n_border = 0;
   for (int i0 = 0; i0 < n; i0 += blockDim.x) {
     const int i = i0 + tid;
     const bool valid = i < n;
@@ -767,71 +769,73 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
     __syncthreads();
     const unsigned long long pre = wpack[wid], tot = wpack[32];
     const int msk = (1 << 21) - 1;
-    const int pf = (int)(pre & msk), pc = (int)((pre >> 21) & msk), pb = (int)(pre >> 42);
-    const int tf = (int)(tot & msk), tc = (int)((tot >> 21) & msk), tb = (int)(tot >> 42);
+    const int pf = (int)(pre & msk), pb = (int)(pre >> 42);
+    const int tf = (int)(tot & msk), tb = (int)(tot >> 42);
     const unsigned lt = (1u << lane) - 1u;
     if (first) ofill[rt] = M + pf + __popc(bf & lt);
     __syncthreads();   // canonical ids of this chunk's firsts are visible
-    if (isc) {
-      labels[i] = ofill[rt];
-      const int j = n_core + pc + __popc(bc & lt);
-      w.sorted[j] = i;
-      for (int q = 0; q < p; ++q) w.zs[(size_t)q * w.ld_s + j] = z[(size_t)q * ld + i];
-    }
+    if (isc) labels[i] = ofill[rt];
     if (isb) w.cell[n_border + pb + __popc(bb & lt)] = i;
     M += tf;
-    n_core += tc;
     n_border += tb;
     __syncthreads();
   }
   stamp(7);
-  // 9. border points: one warp per non-core point scans the core points in
-  //    ascending index, 32 at a time; the first neighbour found is the
-  //    lowest-index core neighbour (none: noise).
+  // 9. the other points: one warp per point finds its lowest-index core
+  //    neighbour among the core points of the cells within reach.  The lanes
+  //    screen the neighbour cells (core box within eps); the candidates are
+  //    visited in ascending order of a lower bound of their smallest core id
+  //    (the cell's own, or its component's for a root cell), and the visit
+  //    stops once that bound reaches the best id found.  No core neighbour:
+  //    noise.
   const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
   for (int ib = wid; ib < n_border; ib += nwarp) {
     const int a = w.cell[ib];
     float za[3];
     for (int q = 0; q < p; ++q) za[q] = z[(size_t)q * ld + a];
-    int lab = -1;
-    // a point with no core box within eps in its neighbourhood is noise
-    bool near_core = false;
-    {
-      int cc[3];
-      for (int q = 0; q < p; ++q) cc[q] = cell_coord(za[q], cell_inv, G);
-      for (int of0 = 0; of0 < nofs && !near_core; of0 += 32) {
-        const int of = of0 + lane;
-        bool nb = false;
-        if (of < nofs) {
-          const int bx = cc[0] + of % side - R, by = cc[1] + (of / side) % side - R;
-          const int bz = p == 3 ? cc[2] + of / (side * side) - R : 0;
-          if (bx >= 0 && by >= 0 && bz >= 0 && bx < G && by < G && (p != 3 || bz < G)) {
-            const int ob = map[(bz * G + by) * G + bx];
-            if (ob >= 0 && opar[ob] >= 0) {
-              float n2, f2;
-              box_dist2<p>(za, ocbox + ob, S, &n2, &f2);
-              nb = n2 <= near_no;
-            }
+    int cc[3];
+    for (int q = 0; q < p; ++q) cc[q] = cell_coord(za[q], cell_inv, G);
+    int best = 0x7fffffff;
+    for (int of0 = 0; of0 < nofs; of0 += 32) {
+      const int of = of0 + lane;
+      int ob = -1, lb = 0x7fffffff;
+      if (of < nofs) {
+        const int bx = cc[0] + of % side - R, by = cc[1] + (of / side) % side - R;
+        const int bz = p == 3 ? cc[2] + of / (side * side) - R : 0;
+        if (bx >= 0 && by >= 0 && bz >= 0 && bx < G && by < G && (p != 3 || bz < G)) {
+          ob = map[(bz * G + by) * G + bx];
+          if (ob >= 0 && opar[ob] >= 0) {
+            float n2, f2;
+            box_dist2<p>(za, ocbox + ob, S, &n2, &f2);
+            if (n2 <= near_no) lb = omin[ob];
           }
         }
-        near_core = __any_sync(FULL, nb);
+      }
+      for (int it = 0; it < 32; ++it) {
+        // candidate with the smallest bound (ties: lowest lane)
+        const int mlb = __reduce_min_sync(FULL, lb);
+        if (mlb >= best) break;
+        const int src = __ffs(__ballot_sync(FULL, lb == mlb)) - 1;
+        const int obs = __shfl_sync(FULL, ob, src);
+        if (lane == src) lb = 0x7fffffff;
+        const int e = ostart[obs + 1];
+        for (int pb0 = ostart[obs]; pb0 < e; pb0 += 32) {
+          const int pb = pb0 + lane;
+          int cand = 0x7fffffff;
+          if (pb < e) {
+            const int sid = w.sorted[pb];
+            if (sid >= 0 && sid < best) {
+              float zb[3];
+#pragma unroll
+              for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + pb];
+              if (nb_pred_t<p>(za, zb, eps2)) cand = sid;
+            }
+          }
+          best = min(best, __reduce_min_sync(FULL, cand));
+        }
       }
     }
-    for (int j0 = 0; near_core && j0 < n_core; j0 += 32) {
-      const int j = j0 + lane;
-      bool hit = false;
-      if (j < n_core) {
-        float zb[3];
-        for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + j];
-        hit = nb_pred_t<p>(za, zb, eps2);
-      }
-      const unsigned hm = __ballot_sync(FULL, hit);
-      if (hm) {
-        lab = labels[w.sorted[j0 + __ffs(hm) - 1]];
-        break;
-      }
-    }
-    if (lane == 0) labels[a] = lab;
+    if (lane == 0) labels[a] = best == 0x7fffffff ? -1 : labels[best];
   }
   __syncthreads();
   stamp(8);
