@@ -261,8 +261,10 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, A); return o; };
   const size_t o_ctr = take(8), o_ctl = take(sizeof(Ctl));
   const size_t o_U = take(sizeof(float) * T * m), o_Unew = take(sizeof(float) * T * m);
-  const size_t o_trk = take(track_bytes(T, nobs));
-  const size_t o_S = take(4 * Kp), o_w = take(4 * Kp);
+  // + 16: the packed 2-D table's header may round up 16 bytes past the rows'
+  const size_t o_trk = take(track_bytes(T, nobs) + 16);
+  const size_t o_S = take(4 * Kp), o_w = take(4 * Kp), o_Sv = take(4 * Kp),
+               o_cmin = take(4 * Kp), o_nzk = take(4 * kSparseMax), o_nze = take(4 * kSparseMax);
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
   const size_t eps_elems = P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
@@ -300,6 +302,10 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.tracks = reinterpret_cast<float4*>(b + o_trk);
   d.S = reinterpret_cast<float*>(b + o_S);
   d.w_k = reinterpret_cast<float*>(b + o_w);
+  d.Sv = reinterpret_cast<float*>(b + o_Sv);
+  d.cmin = reinterpret_cast<float*>(b + o_cmin);
+  d.nzk = reinterpret_cast<int*>(b + o_nzk);
+  d.nze = reinterpret_cast<float*>(b + o_nze);
   d.pN = reinterpret_cast<float*>(b + o_pN);
   d.z = reinterpret_cast<float*>(b + o_z);
   d.g = reinterpret_cast<float*>(b + o_g);
@@ -320,7 +326,9 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   tiles_of(h, 0, roll, upd);
   h->n_roll = (int)roll.size();
   h->n_upd = (int)upd.size();
-  h->smem_roll = (int)(track_bytes(T, nobs) + (size_t)T * m * 4);
+  h->smem_roll = P->dyn == CE_DYN_ARM6_KIN
+                     ? (int)(track_bytes(T, nobs) + (size_t)T * m * 4)
+                     : (int)((((size_t)T * m * 4 + 15) & ~(size_t)15) + kTrackSmem2D);
   auto cleanup = [&]() {
     cudaFree(h->dmem);
     cudaFree(h->ddesc);

@@ -22,11 +22,14 @@ constexpr int kMaxObs = 4096;           // obstacle bitmap in shared memory
 constexpr int kMaxT = 256;
 constexpr int kMaxSmemTracks = 200 * 1024;
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits (mbarrier, union-find)
+constexpr int kSparseMax = 256;         // nonzero update weights kept as a sorted list
 
 // Per-instance control block written by the stages of one replan.
 struct Ctl {
   int nV, nC, M, mode, sel, o_star, dynamic, status;
   float S_min, invZ;
+  float S_absmax_V, S_min_V, S_min_all;   // over V / over all K (written by the prune stage)
+  int nnz;                        // nonzero update weights listed (-1: more than kSparseMax)
   float pbar[3], v_obs[3], p0[3];
   unsigned int done;              // last-CTA ticket of the update stage
   int col_tests;                  // circle/sphere tests per rollout after reach culling
@@ -38,7 +41,9 @@ struct Ctl {
 // Layout of the scratch buffers (Kp = K rounded up to a multiple of 32):
 //   tracks float4 [(T+1)][track_stride]: 2-D (x, y, (r_o + r_robot)^2, index),
 //          arm (x, y, z, r_o + r_robot); then the (T+1) row counts
-//   S, w float [Kp]; hit, hitj, idxV, idxC, label, cell, sorted, parent int [Kp]
+//   S, w, Sv (S in V order), cmin (per-cluster least S) float [Kp];
+//   hit, hitj, idxV, idxC, label, cell, sorted, parent int [Kp]
+//   nzk int, nze float [kSparseMax]: nonzero update weights by ascending k
 //   pN, z, g, zs float [p][Kp] (SoA)
 //   eps    2-D: float [T*m][Kp] (k fastest); arm: float [Kp][T*m] (k slowest)
 struct InstDesc {
@@ -51,7 +56,8 @@ struct InstDesc {
   float* U;      // [T][m] nominal
   float* Unew;   // [T][m] updated nominal before the shift
   float4* tracks;
-  float *S, *w_k, *pN, *eps, *z, *g, *zs;
+  float *S, *w_k, *pN, *eps, *z, *g, *zs, *Sv, *cmin, *nze;
+  int* nzk;
   float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
   int TMp;       // T*m rounded up to a multiple of 4
   int *hit, *hitj, *idxV, *idxC, *label, *cell, *sorted, *parent;
@@ -108,6 +114,15 @@ __device__ __forceinline__ int2 tile_of(const KArgs& a) {
 // Row stride (in float4) of the obstacle track table: odd, so that lanes
 // reading different horizon rows hit different shared-memory banks.
 __host__ __device__ __forceinline__ int track_stride(int n_obs) { return n_obs | 1; }
+// 2-D robots use a packed table instead: row offsets off[0..T+1] (int,
+// padded to 16 bytes), then the kept entries of rows 0..T back to back
+// (row j = entries [off[j], off[j+1])).
+__host__ __device__ __forceinline__ size_t track_hdr_bytes(int T) {
+  return ((size_t)(T + 2) * 4 + 15) & ~(size_t)15;
+}
+// Shared memory the 2-D rollout kernel stages a packed table into; a larger
+// table is read from global memory (L1) instead.
+constexpr int kTrackSmem2D = 8 * 1024;
 // Bytes of the track table: (T+1) rows of track_stride float4, then the
 // (T+1) row counts (int), padded to 16 bytes.
 __host__ __device__ __forceinline__ size_t track_bytes(int T, int n_obs) {

@@ -56,24 +56,6 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return t;
 }
 
-__device__ __forceinline__ float block_max(float v, float* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    float t = lane < nw ? red[lane] : -INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(FULL, t, o));
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  const float r = red[32];
-  __syncthreads();
-  return r;
-}
-
 __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, float* p0) {
   if (d.dyn == CE_DYN_ARM6_KIN) {
     float q[6], O[7][3], R[9];
@@ -140,16 +122,24 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
   __syncthreads();
   const int nV = (int)(wpack[32] & 0xffffffffull), nC = (int)(wpack[32] >> 32);
   {
+    // also: S in V order, and max |S| over V, min S over V, min S over all K
+    // (the selection stage's fixed-point scale and softmin baselines)
+    float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
     int bv = (int)(wpack[wid] & 0xffffffffull), bc = (int)(wpack[wid] >> 32);
     for (int s0 = beg; s0 < end; s0 += 32) {
       const int k = s0 + lane;
       const int h = k < end ? d.hit[k] : -1;
+      const float Sk = k < end ? d.S[k] : INFINITY;
       const bool isV = k < end && h < 0, isC = h >= 0;
       const unsigned mv = __ballot_sync(0xffffffffu, isV), mc = __ballot_sync(0xffffffffu, isC);
+      amin = fminf(amin, Sk);
       if (isV) {
         const int pos = bv + __popc(mv & lt);
         d.idxV[pos] = k;
         d.vpos[k] = pos;
+        d.Sv[pos] = Sk;
+        vmax = fmaxf(vmax, fabsf(Sk));
+        vmin = fminf(vmin, Sk);
       }
       if (isC) {
         d.idxC[bc + __popc(mc & lt)] = k;
@@ -157,6 +147,27 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
       }
       bv += __popc(mv);
       bc += __popc(mc);
+    }
+    __shared__ float red3[3][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vmax = fmaxf(vmax, __shfl_xor_sync(FULL, vmax, o));
+      vmin = fminf(vmin, __shfl_xor_sync(FULL, vmin, o));
+      amin = fminf(amin, __shfl_xor_sync(FULL, amin, o));
+    }
+    if (lane == 0) { red3[0][wid] = vmax; red3[1][wid] = vmin; red3[2][wid] = amin; }
+    __syncthreads();
+    if (wid == 0) {
+      vmax = lane < nw ? red3[0][lane] : 0.f;
+      vmin = lane < nw ? red3[1][lane] : INFINITY;
+      amin = lane < nw ? red3[2][lane] : INFINITY;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        vmax = fmaxf(vmax, __shfl_xor_sync(FULL, vmax, o));
+        vmin = fminf(vmin, __shfl_xor_sync(FULL, vmin, o));
+        amin = fminf(amin, __shfl_xor_sync(FULL, amin, o));
+      }
+      if (lane == 0) { ctl->S_absmax_V = vmax; ctl->S_min_V = vmin; ctl->S_min_all = amin; }
     }
   }
   if (nC == 0 || nV == 0) {
@@ -899,11 +910,13 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
 
 // ========================================================================= select
 // Algorithm 1 [Cluster stats], [Selection], [Within-cluster weighting]:
-// per-cluster count, mean cost Sbar_c (Eq. 14) and mean direction vhat_c
-// (Eq. 16) by exact int64 fixed-point sums; c* by Eq. 14 (static) or Eq. 18
-// (dynamic, |v_o*| > threshold); then the softmin weights over the update set
-// (Eq. 19, or Eq. 6 over all K / over V in the fallbacks), normalised, with
-// the minimum subtracted before exp.
+// per-cluster count, mean cost Sbar_c (Eq. 14), mean direction vhat_c
+// (Eq. 16) and least cost, by exact int64 fixed-point sums (and min keys);
+// c* by Eq. 14 (static) or Eq. 18 (dynamic, |v_o*| > threshold); then the
+// softmin weights over the update set (Eq. 19, or Eq. 6 over all K / over V
+// in the fallbacks) with the set's least cost subtracted before exp.  The
+// weights are left unnormalised (the update multiplies by 1/Z); the nonzero
+// ones are also listed by ascending k when there are at most kSparseMax.
 constexpr int kWin = 512;   // clusters per statistics window
 constexpr int kSlots = 3;   // per-warp label cache of the cluster statistics
 
@@ -913,18 +926,21 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
   Ctl* ctl = d.ctl;
   __shared__ unsigned long long accS[kWin], accG[3][kWin];
   __shared__ int accN[kWin];
+  __shared__ unsigned int accM[kWin];
   __shared__ float red[33];
   __shared__ unsigned long long bestkey;
+  __shared__ int lk[kSparseMax];
+  __shared__ float le[kSparseMax];
+  __shared__ int lcount;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int K = d.K, Kp = d.Kp, p = d.p;
   const int mode0 = ctl->mode;
   const int nV = ctl->nV, M = ctl->M;
   int sel = -1, dynamic = 0;
+  if (tid == 0) lcount = 0;
   if (mode0 == CE_MODE_STATIC) {
     // fixed-point scales: S in [-Smax, Smax], g in [-1, 1], at most nV terms
-    float sm = 0.f;
-    for (int i = tid; i < nV; i += blockDim.x) sm = fmaxf(sm, fabsf(d.S[d.idxV[i]]));
-    sm = block_max(sm, red);
+    const float sm = ctl->S_absmax_V;
     const int lgN = 32 - __clz(nV + 1);
     int eS = 60 - lgN - (sm > 0.f ? ilogbf(sm) + 1 : 0);
     eS = max(-100, min(eS, 100));
@@ -938,21 +954,23 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
     // each warp owns a contiguous range of V and keeps per-lane partial sums
     // for up to kSlots labels (warp-uniform slot labels); a slot is reduced
     // across the warp and added to shared memory only when evicted or at the
-    // end -- exact int64 sums, so the result does not depend on the order.
+    // end -- exact int64 sums and min keys, so the result does not depend on
+    // the order.
     const int Lr = (((nV + nw - 1) / nw) + 31) & ~31;
     const int beg = min(nV, wid * Lr), end = min(nV, beg + Lr);
     for (int w0 = 0; w0 < M; w0 += kWin) {
       for (int c = tid; c < kWin; c += blockDim.x) {
-        accS[c] = 0ull; accN[c] = 0;
+        accS[c] = 0ull; accN[c] = 0; accM[c] = 0xffffffffu;
         accG[0][c] = accG[1][c] = accG[2][c] = 0ull;
       }
       __syncthreads();
       int cl[kSlots];
       long long aS[kSlots], aG[kSlots][3];
       int aN[kSlots];
+      uint32_t aM[kSlots];
 #pragma unroll
       for (int sl = 0; sl < kSlots; ++sl) {
-        cl[sl] = -1; aS[sl] = 0; aN[sl] = 0;
+        cl[sl] = -1; aS[sl] = 0; aN[sl] = 0; aM[sl] = 0xffffffffu;
         aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
       }
       auto flush = [&](int sl) {
@@ -966,6 +984,7 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
           g2 += __shfl_xor_sync(FULL, g2, o);
           nn += __shfl_xor_sync(FULL, nn, o);
         }
+        const uint32_t mk = __reduce_min_sync(FULL, aM[sl]);
         if (lane == 0 && cl[sl] >= 0) {
           const int c = cl[sl] - w0;
           atomicAdd(&accS[c], (unsigned long long)s);
@@ -973,18 +992,22 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
           atomicAdd(&accG[1][c], (unsigned long long)g1);
           atomicAdd(&accG[2][c], (unsigned long long)g2);
           atomicAdd(&accN[c], nn);
+          atomicMin(&accM[c], mk);
         }
-        cl[sl] = -1; aS[sl] = 0; aN[sl] = 0;
+        cl[sl] = -1; aS[sl] = 0; aN[sl] = 0; aM[sl] = 0xffffffffu;
         aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
       };
       for (int s0 = beg; s0 < end; s0 += 32) {
         const int i = s0 + lane;
         int L = -1;
         long long vS = 0, vG[3] = {0, 0, 0};
+        uint32_t vM = 0xffffffffu;
         if (i < end) {
           L = d.label[i];
           if (L >= w0 && L < w0 + kWin) {
-            vS = __float2ll_rn(ldexpf(d.S[d.idxV[i]], eS));
+            const float Si = d.Sv[i];
+            vS = __float2ll_rn(ldexpf(Si, eS));
+            vM = float_key(Si);
 #pragma unroll
             for (int q = 0; q < 3; ++q)
               if (q < p) vG[q] = __float2ll_rn(ldexpf(d.g[(size_t)q * Kp + i], eG));
@@ -1006,7 +1029,7 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
 #pragma unroll
           for (int sl = 0; sl < kSlots; ++sl)
             if (!done && L == cl[sl]) {
-              aS[sl] += vS; aN[sl] += 1;
+              aS[sl] += vS; aN[sl] += 1; aM[sl] = min(aM[sl], vM);
               aG[sl][0] += vG[0]; aG[sl][1] += vG[1]; aG[sl][2] += vG[2];
               done = true;
             }
@@ -1038,44 +1061,72 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
           const float iv = 1.0f / (sqrtf(nn) + d.norm_eps);
           crit = (v[0] * iv) * vh[0] + (v[1] * iv) * vh[1] + (v[2] * iv) * vh[2];
         }
+        d.cmin[w0 + c] = key_float(accM[c]);
         atomicMin(&bestkey, ((unsigned long long)float_key(crit) << 32) | (unsigned)(w0 + c));
       }
       __syncthreads();
     }
     sel = (int)(bestkey & 0xffffffffull);
   }
-  // update set (all K / V / the selected cluster), S_min over it, then one
-  // pass over all K writing e_k = exp(-(S_k - S_min)/lambda) (0 outside) and
-  // the normaliser Z; the update multiplies its sums by 1/Z.
+  // the update set (all K / V / the selected cluster) and its least cost
   const int mode = mode0 == CE_MODE_STATIC ? (dynamic ? CE_MODE_DYNAMIC : CE_MODE_STATIC) : mode0;
   const bool over_all = mode == CE_MODE_NOCOL || mode == CE_MODE_ALLCOL;
   const bool over_V = mode == CE_MODE_ALLNOISE;
-  auto member = [&](int k) {
-    if (over_all) return true;
-    const int v = d.vpos[k];
-    return v >= 0 && (over_V || d.label[v] == sel);
-  };
-  float smin = INFINITY;
-  for (int k = tid; k < K; k += blockDim.x)
-    if (member(k)) smin = fminf(smin, d.S[k]);
-  smin = -block_max(-smin, red);
+  const float smin = over_all ? ctl->S_min_all : over_V ? ctl->S_min_V : d.cmin[sel];
   const float il = d.inv_lambda;
   float z = 0.f, zc = 0.f;
-  for (int k = tid; k < K; k += blockDim.x) {
+  // e for one member; nonzero ones are appended to the list (warp-aggregated)
+  auto emit = [&](bool mem, int k, float Sk) {
     float e = 0.f;
-    if (member(k)) {
-      e = expf(-(d.S[k] - smin) * il);
+    if (mem) {
+      e = expf(-(Sk - smin) * il);
       kahan_add(z, zc, e);
+      d.w_k[k] = e;
     }
-    d.w_k[k] = e;
+    const bool nz = e != 0.f;
+    const unsigned b = __ballot_sync(FULL, nz);
+    if (b) {
+      int base = 0;
+      if (lane == __ffs(b) - 1) base = atomicAdd(&lcount, __popc(b));
+      base = __shfl_sync(FULL, base, __ffs(b) - 1) + __popc(b & ((1u << lane) - 1u));
+      if (nz && base < kSparseMax) { lk[base] = k; le[base] = e; }
+    }
+  };
+  if (over_all) {
+    for (int k0 = 0; k0 < K; k0 += blockDim.x) {
+      const int k = k0 + tid;
+      emit(k < K, k, k < K ? d.S[k] : 0.f);
+    }
+  } else {
+    for (int k = tid; k < K; k += blockDim.x) d.w_k[k] = 0.f;
+    __syncthreads();   // the zeros land before the members' weights
+    for (int i0 = 0; i0 < nV; i0 += blockDim.x) {
+      const int i = i0 + tid;
+      const bool mem = i < nV && (over_V || d.label[i] == sel);
+      emit(mem, mem ? d.idxV[i] : 0, mem ? d.Sv[i] : 0.f);
+    }
   }
-  const float Z = block_sum(z, red);
+  const float Z = block_sum(z, red);   // (its barriers also publish lcount and the list)
+  const int nl = lcount;
+  if (nl <= kSparseMax) {
+    // the list by ascending k (keys are distinct): rank by counting
+    int rk = 0, kk = 0;
+    float ee = 0.f;
+    if (tid < nl) {
+      kk = lk[tid];
+      ee = le[tid];
+      for (int j = 0; j < nl; ++j) rk += lk[j] < kk;
+    }
+    __syncthreads();
+    if (tid < nl) { d.nzk[rk] = kk; d.nze[rk] = ee; }
+  }
   if (tid == 0) {
     ctl->mode = mode;
     ctl->sel = sel;
     ctl->dynamic = dynamic;
     ctl->S_min = smin;
     ctl->invZ = 1.0f / Z;
+    ctl->nnz = nl <= kSparseMax ? nl : -1;
   }
 }
 
@@ -1150,17 +1201,57 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   const int c0 = cb * cper, k0 = kc * kch, k1 = min(K, k0 + kch);
   const float* __restrict__ w = d.w_k;
   const float* __restrict__ eps = d.eps;
-  if (!arm) {
+  const int nnz = d.ctl->nnz;
+  if (nnz >= 0) {
+    // few nonzero weights, listed by ascending k: the tiles of the first
+    // rollout chunk sum over the list, the others contribute zeros
+    if (!arm) {
+      const int c = c0 + wid;
+      if (c < TM) {
+        float s = 0.f, e = 0.f;
+        if (kc == 0) {
+          const float* col = eps + (size_t)c * d.eps_ld_c;
+          for (int j = lane; j < nnz; j += 32) kahan_add(s, e, d.nze[j] * col[d.nzk[j]]);
+          s = warp_sum(s);
+        }
+        if (lane == 0) d.upart[(size_t)kc * d.TMp + c] = s;
+      }
+    } else {
+      const int c = c0 + lane;
+      float s = 0.f, e = 0.f;
+      if (kc == 0 && c < TM)
+        for (int j = wid; j < nnz; j += kUpdateWarps)
+          kahan_add(s, e, d.nze[j] * eps[(size_t)d.nzk[j] * d.eps_ld_k + c]);
+      part[wid][lane] = s;
+      __syncthreads();
+      if (wid == 0 && c < TM) {
+        float t = 0.f;
+        for (int q = 0; q < kUpdateWarps; ++q) t += part[q][lane];
+        d.upart[(size_t)kc * d.TMp + c] = t;
+      }
+    }
+  } else if (!arm) {
     const int c = c0 + wid;
     if (c < TM) {
       const float* col = eps + (size_t)c * d.eps_ld_c;
       float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
       int k = k0 + lane;
+      // eps' is read only where the weight is nonzero: with the minimum
+      // subtracted, exp underflows to exactly 0 for most rollouts at small
+      // lambda, and their sectors are never fetched (adding 0 keeps the sums'
+      // bits as if they were).
       for (; k + 96 < k1; k += 128) {
+        float wk[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) kahan_add(s[u], e[u], w[k + 32 * u] * col[k + 32 * u]);
+        for (int u = 0; u < 4; ++u) wk[u] = w[k + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          kahan_add(s[u], e[u], wk[u] != 0.f ? wk[u] * col[k + 32 * u] : 0.f);
       }
-      for (; k < k1; k += 32) kahan_add(s[0], e[0], w[k] * col[k]);
+      for (; k < k1; k += 32) {
+        const float wk = w[k];
+        kahan_add(s[0], e[0], wk != 0.f ? wk * col[k] : 0.f);
+      }
       float t = (s[0] + s[1]) + (s[2] + s[3]);
       t = warp_sum(t);
       if (lane == 0) d.upart[(size_t)kc * d.TMp + c] = t;
@@ -1169,7 +1260,10 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
     const int c = c0 + lane;
     float s = 0.f, e = 0.f;
     if (c < TM)
-      for (int k = k0 + wid; k < k1; k += kUpdateWarps) kahan_add(s, e, w[k] * eps[(size_t)k * d.eps_ld_k + c]);
+      for (int k = k0 + wid; k < k1; k += kUpdateWarps) {
+        const float wk = w[k];   // warp-uniform: rows of zero weight are skipped
+        if (wk != 0.f) kahan_add(s, e, wk * eps[(size_t)k * d.eps_ld_k + c]);
+      }
     part[wid][lane] = s;
     __syncthreads();
     if (wid == 0 && c < TM) {

@@ -21,8 +21,10 @@ namespace cem {
 // v_0, r_j = dt^2 j (j-1)/2 |a|max), so an obstacle farther than
 // r_j + r_o + r_robot (+1 mm slack) from c_j cannot be hit at step j and is
 // left out.  This changes no collision result.  Entries are (x, y, (r_o +
-// r_robot)^2, obstacle index as int bits); the row counts follow the rows.
-// Arm: every row holds every obstacle as (x, y, z, r_o + r_robot).
+// r_robot)^2, obstacle index as int bits), packed row after row behind the
+// row offsets (a count pass, a scan of the row counts, a write pass).
+// Arm: every row holds every obstacle as (x, y, z, r_o + r_robot), rows of
+// track_stride entries, then the row counts.
 __global__ void k_tracks(KArgs a) {
   const int inst = blockIdx.x;
   const InstDesc& d = desc_of(a, inst);
@@ -59,46 +61,84 @@ __global__ void k_tracks(KArgs a) {
   const float m0 = fmaxf(fabsf(d.u_min[0]), fabsf(d.u_max[0]));
   const float m1 = fmaxf(fabsf(d.u_min[1]), fabsf(d.u_max[1]));
   const float amax = sqrtf(m0 * m0 + m1 * m1);
-  __shared__ int tests;
-  if (threadIdx.x == 0) tests = 0;
+  __shared__ int roff[kMaxT + 2];
+  // newest position, velocity and collision radius of the first obstacles
+  constexpr int kObsSmem = 1024;
+  __shared__ float4 opv[kObsSmem];
+  __shared__ float orr[kObsSmem];
+  auto obstacle = [&](int o, float4* pv, float* R) {
+    const float* newest = h + ((size_t)(H - 1) * n_obs + o) * 2;
+    const float* oldest = h + (size_t)o * 2;
+    *pv = make_float4(newest[0], newest[1], (newest[0] - oldest[0]) * inv,
+                      (newest[1] - oldest[1]) * inv);
+    *R = r.obs_radius[o] + d.robot_radius;
+  };
+  for (int o = threadIdx.x; o < min(n_obs, kObsSmem); o += blockDim.x) obstacle(o, &opv[o], &orr[o]);
   __syncthreads();
-  for (int j = wid; j <= T; j += nw) {
-    const float tj = (float)j * d.dt;
-    float cx = x0, cy = y0, rj;
-    if (d.dyn == CE_DYN_DOUBLE_INT_2D) {
-      cx = x0 + tj * vx0;
-      cy = y0 + tj * vy0;
-      rj = d.dt * d.dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
-    } else {
-      rj = tj * m0;
-    }
-    int cnt = 0;
-    for (int o0 = 0; o0 < n_obs; o0 += 32) {
-      const int o = o0 + lane;
-      bool keep = false;
-      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (o < n_obs) {
-        const float* newest = h + ((size_t)(H - 1) * n_obs + o) * 2;
-        const float* oldest = h + (size_t)o * 2;
-        const float ox = newest[0] + ((newest[0] - oldest[0]) * inv) * tj;
-        const float oy = newest[1] + ((newest[1] - oldest[1]) * inv) * tj;
-        const float R = r.obs_radius[o] + d.robot_radius;
-        const float reach = rj + R + 1e-3f * (1.0f + rj);
-        const float ddx = ox - cx, ddy = oy - cy;
-        keep = ddx * ddx + ddy * ddy <= reach * reach;
-        e = make_float4(ox, oy, R * R, __int_as_float(o));
+  int* off = reinterpret_cast<int*>(d.tracks);
+  float4* ent = reinterpret_cast<float4*>(reinterpret_cast<char*>(d.tracks) + track_hdr_bytes(T));
+  // pass 0 counts the kept entries of each row, pass 1 writes them
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = wid; j <= T; j += nw) {
+      const float tj = (float)j * d.dt;
+      float cx = x0, cy = y0, rj;
+      if (d.dyn == CE_DYN_DOUBLE_INT_2D) {
+        cx = x0 + tj * vx0;
+        cy = y0 + tj * vy0;
+        rj = d.dt * d.dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
+      } else {
+        rj = tj * m0;
       }
-      const unsigned b = __ballot_sync(0xffffffffu, keep);
-      if (keep) d.tracks[(size_t)j * ts + cnt + __popc(b & ((1u << lane) - 1u))] = e;
-      cnt += __popc(b);
+      int cnt = pass ? roff[j] : 0;
+      for (int o0 = 0; o0 < n_obs; o0 += 32) {
+        const int o = o0 + lane;
+        bool keep = false;
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (o < n_obs) {
+          float4 pv;
+          float R;
+          if (o < kObsSmem) {
+            pv = opv[o];
+            R = orr[o];
+          } else {
+            obstacle(o, &pv, &R);
+          }
+          const float ox = pv.x + pv.z * tj;
+          const float oy = pv.y + pv.w * tj;
+          const float reach = rj + R + 1e-3f * (1.0f + rj);
+          const float ddx = ox - cx, ddy = oy - cy;
+          keep = ddx * ddx + ddy * ddy <= reach * reach;
+          e = make_float4(ox, oy, R * R, __int_as_float(o));
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (pass && keep) ent[cnt + __popc(b & ((1u << lane) - 1u))] = e;
+        cnt += __popc(b);
+      }
+      if (!pass && lane == 0) roff[j] = cnt;
     }
-    if (lane == 0) {
-      counts[j] = cnt;
-      if (j >= 1) atomicAdd(&tests, cnt);
+    __syncthreads();
+    if (!pass && wid == 0) {
+      // exclusive scan of the T + 1 row counts, 32 at a time with a carry
+      int carry = 0;
+      for (int j0 = 0; j0 <= T; j0 += 32) {
+        const int j = j0 + lane;
+        const int v = j <= T ? roff[j] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (j <= T) roff[j] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+      }
+      if (lane == 0) roff[T + 1] = carry;
     }
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x == 0) d.ctl->col_tests = tests;
+  for (int j = threadIdx.x; j <= T + 1; j += blockDim.x) off[j] = roff[j];
+  // obstacle tests of a rollout at steps 1..T (row 0 only with check_j0)
+  if (threadIdx.x == 0) d.ctl->col_tests = roff[T + 1] - roff[1];
 }
 
 // Stage the instance's tracks and row counts (TMA bulk copy) and the nominal
@@ -130,23 +170,54 @@ __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float
 // (Eq. 21), cost Eq. 22-23 with Q = w[0..2], H = w[3..5].  Collision: first
 // horizon step j (1..T, plus 0 when check_j0) and lowest obstacle index with
 // |p_j - o_j|^2 < (r_o + r_robot)^2.
+// Shared memory of the 2-D kernel: the nominal, the row offsets of the packed
+// table, then an entry buffer of the rest of the launch's dynamic shared
+// memory (at least one row of the largest obstacle count).  A table that fits
+// arrives by one bulk copy; a larger one is staged in runs of whole rows,
+// each run by one bulk copy, the CTA advancing the horizon run by run.
 template <int DYN>
-__global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
+__global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
+  __shared__ int whole;
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
   const Req r = req_of(a, tile.x);
-  const int n_obs = r.n_obs, T = d.T, Kp = d.Kp, ts = track_stride(n_obs);
-  float4* trk = reinterpret_cast<float4*>(smem_raw);
-  const int* cnts = track_counts(trk, T, n_obs);
-  float* Us = reinterpret_cast<float*>(smem_raw + (n_obs > 0 ? track_bytes(T, n_obs) : 0));
-  if (!stage_tracks(d, n_obs, trk, Us, &bar)) return;
+  const int n_obs = r.n_obs, T = d.T, Kp = d.Kp;
+  const uint32_t us_bytes = ((uint32_t)(T * d.m) * 4u + 15u) & ~15u;
+  const uint32_t hdr = (uint32_t)track_hdr_bytes(T);
+  float* Us = reinterpret_cast<float*>(smem_raw);
+  const int* off = reinterpret_cast<const int*>(smem_raw + us_bytes);
+  const float4* buf = reinterpret_cast<const float4*>(smem_raw + us_bytes + hdr);
+  const float4* gent =
+      reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(d.tracks) + hdr);
+  uint32_t cap_b;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(cap_b));
+  const int cap_e = (int)((cap_b - us_bytes - hdr) / 16u);
+  uint32_t phase = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    const int tot = reinterpret_cast<const int*>(d.tracks)[T + 1];
+    const bool all = tot <= cap_e;
+    // everything at once, or the row offsets alone (the runs follow)
+    const uint32_t bytes = hdr + (all ? (uint32_t)tot * 16u : 0u);
+    mbar_expect_tx(&bar, bytes);
+    bulk_g2s(smem_raw + us_bytes, d.tracks, bytes, &bar);
+    whole = all;
+  }
+  for (int i = threadIdx.x; i < T * d.m; i += blockDim.x) Us[i] = d.U[i];
+  __syncthreads();
+  bool ok = mbar_wait(&bar, phase);
+  phase ^= 1u;
+  const bool all = whole != 0;
   const int k = tile.y * kRolloutThreads + threadIdx.x;
-  if (k >= d.K) return;
+  const bool act = k < d.K && ok;
   const unsigned long long ctr = *d.counter;
 
-  float s0 = r.x0[0], s1 = r.x0[1], s2 = r.x0[2], s3 = DYN == 0 ? r.x0[3] : 0.0f;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  if (act) {
+    s0 = r.x0[0]; s1 = r.x0[1]; s2 = r.x0[2]; s3 = DYN == 0 ? r.x0[3] : 0.0f;
+  }
   // parameters into registers (the output stores below may alias the descriptor)
   const float dt = d.dt;
   const float g0 = d.goal[0], g1 = d.goal[1], g2 = d.goal[2];
@@ -156,53 +227,77 @@ __global__ void __launch_bounds__(kRolloutThreads) k_rollout2d(KArgs a) {
   float* __restrict__ eps = d.eps;
   float S = 0.0f, Sc = 0.0f;
   int first = -1, first_j = -1;
-  if (d.check_j0 && n_obs > 0) {
-    const int c = cnts[0];
-    int h = n_obs;
-    for (int e = c - 1; e >= 0; --e) {
-      const float4 t = trk[e];
-      const float dx = s0 - t.x, dy = s1 - t.y;
-      h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
-    }
-    if (h < n_obs) { first = h; first_j = 0; }
-  }
   float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int j = 0; j < T; ++j) {
-    if ((j & 1) == 0) z4 = philox_normals(d, ctr, k, j >> 1);
-    const float z0 = (j & 1) ? z4.z : z4.x, z1 = (j & 1) ? z4.w : z4.y;
-    const float n0 = Us[2 * j], n1 = Us[2 * j + 1];
-    const float u0 = fminf(fmaxf(n0 + sg0 * z0, lo0), hi0);
-    const float u1 = fminf(fmaxf(n1 + sg1 * z1, lo1), hi1);
-    eps[(size_t)(2 * j) * Kp + k] = u0 - n0;
-    eps[(size_t)(2 * j + 1) * Kp + k] = u1 - n1;
-    if (DYN == 0) {
-      const float ex = s0 - g0, ey = s1 - g1;
-      kahan_add(S, Sc, w0 * (ex * ex + ey * ey) + w1 * (u0 * u0 + u1 * u1));
-      s0 += s2 * dt;
-      s1 += s3 * dt;
-      s2 += u0 * dt;
-      s3 += u1 * dt;
-    } else {
-      const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
-      kahan_add(S, Sc, w0 * ex * ex + w1 * ey * ey + w2 * et * et);
-      float sn, cs;
-      sincosf(s2, &sn, &cs);
-      s0 += u0 * cs * dt;
-      s1 += u0 * sn * dt;
-      s2 += u1 * dt;
+  int j = 0;
+  // runs of rows [ja, jb): step j tests row j + 1; row 0 only with check_j0
+  for (int ja = 0; ja <= T;) {
+    int jb = T + 1;
+    if (!all) {
+      jb = ja + 1;
+      while (jb <= T && off[jb + 1] - off[ja] <= cap_e) ++jb;
+      __syncthreads();   // the previous run's entries are no longer read
+      if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(off[jb] - off[ja]) * 16u;
+        mbar_expect_tx(&bar, bytes);
+        if (bytes > 0) bulk_g2s((void*)buf, gent + off[ja], bytes, &bar);
+      }
+      ok = mbar_wait(&bar, phase) && ok;
+      phase ^= 1u;
     }
-    if (first < 0 && n_obs > 0) {
-      const float4* tj = trk + (size_t)(j + 1) * ts;
-      const int c = cnts[j + 1];
+    const int base = all ? 0 : off[ja];
+    if (ja == 0 && d.check_j0 && act) {
       int h = n_obs;
-      for (int e = c - 1; e >= 0; --e) {   // descending: the lowest index wins
-        const float4 t = tj[e];
+      for (int e = off[1] - 1 - base; e >= off[0] - base; --e) {
+        const float4 t = buf[e];
         const float dx = s0 - t.x, dy = s1 - t.y;
         h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
       }
-      if (h < n_obs) { first = h; first_j = j + 1; }
+      if (h < n_obs) { first = h; first_j = 0; }
     }
+    int e_hi = off[j + 1] - base;   // end of row j + 1's entries is off[j + 2]
+    for (; act && j < jb - 1 && j < T; ++j) {
+      if ((j & 1) == 0) z4 = philox_normals(d, ctr, k, j >> 1);
+      const float z0 = (j & 1) ? z4.z : z4.x, z1 = (j & 1) ? z4.w : z4.y;
+      const float n0 = Us[2 * j], n1 = Us[2 * j + 1];
+      const float u0 = fminf(fmaxf(n0 + sg0 * z0, lo0), hi0);
+      const float u1 = fminf(fmaxf(n1 + sg1 * z1, lo1), hi1);
+      eps[(size_t)(2 * j) * Kp + k] = u0 - n0;
+      eps[(size_t)(2 * j + 1) * Kp + k] = u1 - n1;
+      if (DYN == 0) {
+        const float ex = s0 - g0, ey = s1 - g1;
+        kahan_add(S, Sc, w0 * (ex * ex + ey * ey) + w1 * (u0 * u0 + u1 * u1));
+        s0 += s2 * dt;
+        s1 += s3 * dt;
+        s2 += u0 * dt;
+        s3 += u1 * dt;
+      } else {
+        const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
+        kahan_add(S, Sc, w0 * ex * ex + w1 * ey * ey + w2 * et * et);
+        float sn, cs;
+        sincosf(s2, &sn, &cs);
+        s0 += u0 * cs * dt;
+        s1 += u0 * sn * dt;
+        s2 += u1 * dt;
+      }
+      const int e_lo = e_hi;
+      e_hi = off[j + 2] - base;
+      if (first < 0) {
+        int h = n_obs;
+        for (int e = e_hi - 1; e >= e_lo; --e) {   // descending: the lowest index wins
+          const float4 t = buf[e];
+          const float dx = s0 - t.x, dy = s1 - t.y;
+          h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
+        }
+        if (h < n_obs) { first = h; first_j = j + 1; }
+      }
+    }
+    ja = jb;
   }
+  if (!ok) {
+    if (threadIdx.x == 0) raise_status(d.ctl, CE_MPPI_ERR_TIMEOUT);
+    return;
+  }
+  if (!act) return;
   if (DYN == 0) {
     const float ex = s0 - g0, ey = s1 - g1;
     kahan_add(S, Sc, w2 * (ex * ex + ey * ey));

@@ -179,6 +179,25 @@ def test_stage_parity_other_seeds_and_counters(seed):
     _check_replan(sc, counter=(1 << 40) + seed)
 
 
+@pytest.mark.parametrize("check_j0", [0, 1])
+def test_stage_parity_track_table_in_runs(check_j0):
+    """250 small static discs within 1.5 m of the start: the packed track table
+    holds more entries than the 2-D rollout kernel's shared-memory buffer (8 KB,
+    512 entries), so it is staged in runs of whole rows."""
+    sc = W.make("di_static", seed=0, check_j0=check_j0)
+    rng = np.random.default_rng(5)
+    n_extra = 250
+    ang = rng.uniform(0.0, 2.0 * np.pi, n_extra)
+    rad = rng.uniform(0.3, 1.5, n_extra)
+    c = np.array([0.5, 0.5]) + np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1)
+    extra = np.broadcast_to(c, (sc["obs"].shape[0], n_extra, 2))
+    sc["obs"] = np.concatenate([sc["obs"], extra], axis=1)
+    sc["radius"] = np.concatenate([sc["radius"], np.full(n_extra, 0.02)])
+    diag, errs = _check_replan(sc)
+    assert diag["col_tests"] > 3 * 512 and diag["n_col"] > 0
+    print("PARITY track runs", diag["col_tests"], errs)
+
+
 def test_stage_parity_full_size_unicycle():
     """The benchmark's workload: unicycle, K=16384, T=50, 50 (+1) moving discs."""
     sc = W.make("unicycle_blocked", seed=0)
