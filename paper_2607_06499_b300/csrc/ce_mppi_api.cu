@@ -405,6 +405,7 @@ ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* q) {
   a.r0 = to_req(q, 0);
   a.r0.obs_step = 0;  // a single replan reads obs_hist as given
   a.n_inst = 1;
+  a.n_conc = 1;
   run_chain(h->P.dyn, a, h->dtiles, h->n_roll, h->dtiles + h->n_roll, h->n_upd, h->smem_roll,
             h->ncells, h->stream);
   CE_CUDA(cudaGetLastError());
@@ -477,6 +478,7 @@ void run_branches(ce_mppi_batch* b, cudaStream_t s) {
     a.D = b->ddesc;
     a.R = b->dreq;
     a.n_inst = br.n;
+    a.n_conc = (int)b->hs.size();
     run_chain(b->dyn, a, br.dtiles_roll, br.n_roll, br.dtiles_upd, br.n_upd, br.smem_roll,
               br.max_cells, s);
     return;
@@ -489,6 +491,7 @@ void run_branches(ce_mppi_batch* b, cudaStream_t s) {
     a.D = b->ddesc + br.off;
     a.R = b->dreq + br.off;
     a.n_inst = br.n;
+    a.n_conc = (int)b->hs.size();
     run_chain(b->dyn, a, br.dtiles_roll, br.n_roll, br.dtiles_upd, br.n_upd, br.smem_roll,
               br.max_cells, br.stream);
     cudaEventRecord(br.done, br.stream);
@@ -635,6 +638,7 @@ ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms) {
   a.D = b->ddesc;
   a.R = b->dreq;
   a.n_inst = (int)b->hs.size();
+  a.n_conc = a.n_inst;
   cudaStream_t s = b->stream;
   cudaEventRecord(ev[0], s);
   launch_tracks(a, s);

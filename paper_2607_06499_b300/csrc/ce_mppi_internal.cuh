@@ -23,6 +23,7 @@ constexpr int kMaxT = 256;
 constexpr int kMaxSmemTracks = 200 * 1024;
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits (mbarrier, union-find)
 constexpr int kSparseMax = 256;         // nonzero update weights kept as a sorted list
+constexpr int kPruneRanges = 256;       // fixed rollout ranges of the pbar sums
 
 // Per-instance control block written by the stages of one replan.
 struct Ctl {
@@ -94,6 +95,7 @@ struct KArgs {
   const int* tprefix;
   int n_inst;
   int n_tiles;
+  int n_conc;   // instances whose per-instance stages run at the same time (sizes clusters)
 };
 
 __device__ __forceinline__ const InstDesc& desc_of(const KArgs& a, int i) {

@@ -253,6 +253,7 @@ struct ce_mppi_server {
     a.slot = reinterpret_cast<const int*>(f.d_in);
     a.R = reinterpret_cast<const Req*>(f.d_in + align16(sizeof(int) * (3 * (size_t)n + 2)));
     a.n_inst = n;
+    a.n_conc = n;
     const int* d_pre_roll = reinterpret_cast<const int*>(f.d_in) + n;
     run_chain(f.dyn, a, nullptr, n_roll, nullptr, n_upd, smem, cells, f.stream, d_pre_roll,
               d_pre_roll + n + 1);

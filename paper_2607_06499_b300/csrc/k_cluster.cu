@@ -6,7 +6,11 @@
 // K alone (thread t takes elements t, t + blockDim, ...; fixed shuffle trees),
 // and per-cluster sums use exact int64 fixed-point atomics, so a replan gives
 // the same bits alone and inside any batch.
+#include <cooperative_groups.h>
+
 #include "ce_mppi_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cem {
 
@@ -73,37 +77,61 @@ __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, fl
 // Eq. 9-10 (stable ballot/prefix-sum compaction of V and C_col), the closest
 // hit obstacle o* and the reference point pbar (Eq. 11), the features z
 // (Eq. 12-13) and g (Eq. 15) of V, and the velocity estimate of o* (Eq. 17).
+// One thread-block cluster of CL CTAs per instance (CL = 1 .. 8, chosen at
+// launch); the K rollouts are split into CL * 32 contiguous warp ranges, each
+// read three times, coalesced: pass 1 counts V / C_col and marks the
+// obstacles hit first; the CTAs then exchange their counts and marks through
+// distributed shared memory (o* follows from the marks); pass 2 writes V,
+// C_col, each k's position in V and S in V order, and sums the terminal
+// positions for pbar; the CTAs exchange those partial sums (added in rank
+// order: deterministic); pass 3 writes the features.
 __global__ void __maxnreg__(64) k_prune(KArgs a) {
-  const int inst = blockIdx.x;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int inst = blockIdx.x / CL;
   const InstDesc& d = desc_of(a, inst);
   const Req r = req_of(a, inst);
   Ctl* ctl = d.ctl;
   __shared__ unsigned hitmask[kMaxObs / 32];
   __shared__ unsigned long long best;
   __shared__ float p0s[3];
+  __shared__ unsigned long long wpack[33];
+  __shared__ float red[3][33];
+  __shared__ float vpart[4][kPruneRanges];   // per range: count, sum x, y, z
+  __shared__ unsigned long long cbase;   // V / C_col counts of the lower ranks
+  __shared__ unsigned long long tall;    // V / C_col counts of the instance
   const int K = d.K, Kp = d.Kp, p = d.p, n_obs = r.n_obs, tid = threadIdx.x;
-  for (int i = tid; i < (n_obs + 31) / 32; i += blockDim.x) hitmask[i] = 0u;
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int nmw = (n_obs + 31) / 32;
+  const int* __restrict__ hit = d.hit;
+  const float* __restrict__ pN = d.pN;
+  for (int i = tid; i < nmw; i += blockDim.x) hitmask[i] = 0u;
   if (tid == 0) {
     best = ~0ull;
     task_pos0(d, r.x0, p0s);
   }
   __syncthreads();
-  // stable two-pass compaction: each warp owns a contiguous range of k; pass 1
-  // counts (and marks the obstacles hit first), warp 0 scans the warp counts,
-  // pass 2 writes V, C_col and the position of each k in V (-1 if colliding)
-  __shared__ unsigned long long wpack[33];
-  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const int L = (((K + nw - 1) / nw) + 31) & ~31;
-  const int beg = min(K, wid * L), end = min(K, beg + L);
+  // kPruneRanges contiguous ranges of Lv rollouts; a warp owns m consecutive
+  // ranges.  The pbar sums are reduced per range and the ranges added in
+  // order, so the result does not depend on CL.
+  const int Lv = (((K + kPruneRanges - 1) / kPruneRanges) + 31) & ~31;
+  const int m_r = kPruneRanges / (CL * nw);
+  const int L = m_r * Lv;
+  const int beg = min(K, (rank * nw + wid) * L), end = min(K, beg + L);
   const unsigned lt = (1u << lane) - 1u;
+  // ---- pass 1
   {
     unsigned long long cnt = 0;
+#pragma unroll 4
     for (int s0 = beg; s0 < end; s0 += 32) {
       const int k = s0 + lane;
-      const int h = k < end ? d.hit[k] : -1;
-      if (h >= 0) atomicOr(&hitmask[h >> 5], 1u << (h & 31));
-      cnt += __popc(__ballot_sync(0xffffffffu, k < end && h < 0)) |
-             ((unsigned long long)__popc(__ballot_sync(0xffffffffu, h >= 0)) << 32);
+      const int h = k < end ? __ldg(hit + k) : -1;
+      // one shared-memory OR per distinct mask word in the warp
+      const unsigned grp = __match_any_sync(FULL, h >= 0 ? (h >> 5) : -1);
+      const unsigned bits = __reduce_or_sync(grp, h >= 0 ? 1u << (h & 31) : 0u);
+      if (h >= 0 && lane == __ffs(grp) - 1) atomicOr(&hitmask[h >> 5], bits);
+      cnt += __popc(__ballot_sync(FULL, k < end && h < 0)) |
+             ((unsigned long long)__popc(__ballot_sync(FULL, h >= 0)) << 32);
     }
     if (lane == 0) wpack[wid] = cnt;
   }
@@ -113,25 +141,79 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
     unsigned long long x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      const unsigned long long y = __shfl_up_sync(FULL, x, o);
       if (lane >= o) x += y;
     }
     wpack[lane] = x - v;
     if (lane == 31) wpack[32] = x;
   }
+  cluster.sync();   // counts and marks of every CTA of the instance are final
+  // totals, the lower ranks' counts, and the union of the marks (the ranks'
+  // wpack and hitmask are not written again)
+  if (wid == 0) {
+    unsigned long long t = 0ull, lo = 0ull;
+    if (lane < CL) {
+      t = cluster.map_shared_rank(wpack, lane)[32];
+      lo = lane < rank ? t : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_xor_sync(FULL, t, o);
+      lo += __shfl_xor_sync(FULL, lo, o);
+    }
+    if (lane == 0) {
+      tall = t;
+      cbase = lo;
+    }
+  }
+  __shared__ unsigned allmask[kMaxObs / 32];
+  for (int i = tid; i < nmw; i += blockDim.x) {
+    unsigned m = 0u;
+    for (int q = 0; q < CL; ++q) m |= cluster.map_shared_rank(hitmask, q)[i];
+    allmask[i] = m;
+  }
   __syncthreads();
-  const int nV = (int)(wpack[32] & 0xffffffffull), nC = (int)(wpack[32] >> 32);
   {
-    // also: S in V order, and max |S| over V, min S over V, min S over all K
-    // (the selection stage's fixed-point scale and softmin baselines)
-    float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
-    int bv = (int)(wpack[wid] & 0xffffffffull), bc = (int)(wpack[wid] >> 32);
-    for (int s0 = beg; s0 < end; s0 += 32) {
+    // o*: least clearance |p(x_0) - o_t| - r_o among obstacles hit first by
+    // some rollout; ties to the lowest index (packed key, atomicMin)
+    const float* hn = hist_of(r, d) + (size_t)(d.H - 1) * n_obs * p;   // newest observation
+    for (int o = tid; o < n_obs; o += blockDim.x) {
+      if (!((allmask[o >> 5] >> (o & 31)) & 1u)) continue;
+      const float dx = p0s[0] - hn[o * p], dy = p0s[1] - hn[o * p + 1];
+      const float dz = p == 3 ? p0s[2] - hn[o * p + 2] : 0.f;
+      const float clear = sqrtf(dx * dx + dy * dy + dz * dz) - r.obs_radius[o];
+      atomicMin(&best, ((unsigned long long)float_key(clear) << 32) | (unsigned)o);
+    }
+  }
+  __syncthreads();
+  const int nV = (int)(tall & 0xffffffffull), nC = (int)(tall >> 32);
+  const int o_star = nC > 0 ? (int)(best & 0xffffffffull) : -1;
+  // ---- pass 2: lists, S in V order, S extremes; pbar sums over the colliding
+  // rollouts whose first hit is o* (ref_mode 0) or over all of them (ref_mode 1)
+  float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
+  float cntp = 0.f, acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
+  {
+    int bv = (int)(wpack[wid] & 0xffffffffull) + (int)(cbase & 0xffffffffull);
+    int bc = (int)(wpack[wid] >> 32) + (int)(cbase >> 32);
+    const int v0 = (rank * nw + wid) * m_r;   // first range of this warp
+    auto flush = [&](int v) {
+      const float c4[4] = {warp_sum(cntp), warp_sum(acc[0]), warp_sum(acc[1]), warp_sum(acc[2])};
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vpart[q][v] = c4[q];
+      cntp = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] = cmp[c] = 0.f;
+    };
+    for (int j = 0; j < m_r; ++j) {
+    const int rb = min(K, beg + j * Lv), re = min(K, rb + Lv);
+#pragma unroll 2
+    for (int s0 = rb; s0 < re; s0 += 32) {
       const int k = s0 + lane;
-      const int h = k < end ? d.hit[k] : -1;
-      const float Sk = k < end ? d.S[k] : INFINITY;
+      const int h = k < end ? __ldg(hit + k) : -1;
+      const float Sk = k < end ? __ldg(d.S + k) : INFINITY;
       const bool isV = k < end && h < 0, isC = h >= 0;
-      const unsigned mv = __ballot_sync(0xffffffffu, isV), mc = __ballot_sync(0xffffffffu, isC);
+      const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
       amin = fminf(amin, Sk);
       if (isV) {
         const int pos = bv + __popc(mv & lt);
@@ -144,110 +226,133 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
       if (isC) {
         d.idxC[bc + __popc(mc & lt)] = k;
         d.vpos[k] = -1;
+        if (d.ref_mode != 0 || h == o_star) {
+          cntp += 1.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (c < p) kahan_add(acc[c], cmp[c], __ldg(pN + (size_t)c * Kp + k));
+        }
       }
       bv += __popc(mv);
       bc += __popc(mc);
     }
-    __shared__ float red3[3][32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      vmax = fmaxf(vmax, __shfl_xor_sync(FULL, vmax, o));
-      vmin = fminf(vmin, __shfl_xor_sync(FULL, vmin, o));
-      amin = fminf(amin, __shfl_xor_sync(FULL, amin, o));
-    }
-    if (lane == 0) { red3[0][wid] = vmax; red3[1][wid] = vmin; red3[2][wid] = amin; }
-    __syncthreads();
-    if (wid == 0) {
-      vmax = lane < nw ? red3[0][lane] : 0.f;
-      vmin = lane < nw ? red3[1][lane] : INFINITY;
-      amin = lane < nw ? red3[2][lane] : INFINITY;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        vmax = fmaxf(vmax, __shfl_xor_sync(FULL, vmax, o));
-        vmin = fminf(vmin, __shfl_xor_sync(FULL, vmin, o));
-        amin = fminf(amin, __shfl_xor_sync(FULL, amin, o));
-      }
-      if (lane == 0) { ctl->S_absmax_V = vmax; ctl->S_min_V = vmin; ctl->S_min_all = amin; }
+    flush(v0 + j);
     }
   }
+  // block extremes of S (order-free), then the instance's values: extremes
+  // over the ranks, and the range partials of pbar added in range order
+  {
+    float v3[3] = {vmax, vmin, amin};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v3[0] = fmaxf(v3[0], __shfl_xor_sync(FULL, v3[0], o));
+      v3[1] = fminf(v3[1], __shfl_xor_sync(FULL, v3[1], o));
+      v3[2] = fminf(v3[2], __shfl_xor_sync(FULL, v3[2], o));
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) red[q][wid] = v3[q];
+    __syncthreads();
+    if (wid == 0) {
+      float t[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) t[q] = red[q][lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        t[0] = fmaxf(t[0], __shfl_xor_sync(FULL, t[0], o));
+        t[1] = fminf(t[1], __shfl_xor_sync(FULL, t[1], o));
+        t[2] = fminf(t[2], __shfl_xor_sync(FULL, t[2], o));
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red[q][32] = t[q];
+    }
+  }
+  cluster.sync();   // every rank's extremes and range partials are final
+  __shared__ float tv[7];
+  if (wid == 0) {
+    // lane l adds ranges 8l .. 8l+7 (owned by rank 8l / (32 m_r)), then a
+    // fixed tree over the lanes
+    constexpr int per = kPruneRanges / 32;
+    const int own = 32 * m_r;   // ranges per rank
+    const float* vp = cluster.map_shared_rank(&vpart[0][0], (per * lane) / own);
+    float c4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < per; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c4[q] += vp[q * kPruneRanges + per * lane + j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c4[q] = warp_sum(c4[q]);
+    float e3[3] = {0.f, INFINITY, INFINITY};
+    if (lane < CL) {
+      const float* rr = cluster.map_shared_rank(&red[0][0], lane);
+      e3[0] = rr[0 * 33 + 32];
+      e3[1] = rr[1 * 33 + 32];
+      e3[2] = rr[2 * 33 + 32];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e3[0] = fmaxf(e3[0], __shfl_xor_sync(FULL, e3[0], o));
+      e3[1] = fminf(e3[1], __shfl_xor_sync(FULL, e3[1], o));
+      e3[2] = fminf(e3[2], __shfl_xor_sync(FULL, e3[2], o));
+    }
+    if (lane == 0) {
+      tv[0] = e3[0]; tv[1] = e3[1]; tv[2] = e3[2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tv[3 + q] = c4[q];
+    }
+  }
+  cluster.sync();   // no distributed shared memory access after this point
+  if (tid == 0 && rank == 0) {
+    ctl->S_absmax_V = tv[0];
+    ctl->S_min_V = tv[1];
+    ctl->S_min_all = tv[2];
+  }
   if (nC == 0 || nV == 0) {
-    if (tid == 0) {
+    if (tid == 0 && rank == 0) {
       ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = -1;
       ctl->dynamic = 0; ctl->mode = nC == 0 ? CE_MODE_NOCOL : CE_MODE_ALLCOL;
       for (int i = 0; i < 3; ++i) { ctl->pbar[i] = 0.f; ctl->v_obs[i] = 0.f; ctl->p0[i] = p0s[i]; }
     }
     return;
   }
-  // o*: least clearance |p(x_0) - o_t| - r_o among obstacles hit first by some
-  // rollout; ties to the lowest index (packed key, atomicMin).
-  const float* hn = hist_of(r, d) + (size_t)(d.H - 1) * n_obs * p;   // newest observation
-  for (int o = tid; o < n_obs; o += blockDim.x) {
-    if (!((hitmask[o >> 5] >> (o & 31)) & 1u)) continue;
-    const float dx = p0s[0] - hn[o * p], dy = p0s[1] - hn[o * p + 1];
-    const float dz = p == 3 ? p0s[2] - hn[o * p + 2] : 0.f;
-    const float clear = sqrtf(dx * dx + dy * dy + dz * dz) - r.obs_radius[o];
-    atomicMin(&best, ((unsigned long long)float_key(clear) << 32) | (unsigned)o);
-  }
-  __syncthreads();
-  const int o_star = (int)(best & 0xffffffffull);
-  // pbar: mean terminal position of the colliding rollouts whose first hit is
-  // o* (ref_mode 0) or of all colliding rollouts (ref_mode 1).
-  float acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
-  int cnt = 0;
-  for (int i = tid; i < nC; i += blockDim.x) {
-    const int k = d.idxC[i];
-    if (d.ref_mode == 0 && d.hit[k] != o_star) continue;
-    ++cnt;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (c < p) kahan_add(acc[c], cmp[c], d.pN[(size_t)c * Kp + k]);
-  }
-  // one block reduction of (count, sum x, sum y, sum z)
-  __shared__ float red4[4][33];
-  {
-    float v4[4] = {(float)cnt, acc[0], acc[1], acc[2]};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      v4[q] = warp_sum(v4[q]);
-      if (lane == 0) red4[q][wid] = v4[q];
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float t = warp_sum(lane < nw ? red4[q][lane] : 0.f);
-        if (lane == 0) red4[q][32] = t;
-      }
-    }
-    __syncthreads();
-  }
-  const float ncnt = red4[0][32];
+  const float ncnt = tv[3];
   float pbar[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) pbar[c] = c < p ? red4[1 + c][32] / ncnt : 0.f;
-  // features of V
+  for (int c = 0; c < 3; ++c) pbar[c] = c < p ? tv[4 + c] / ncnt : 0.f;
+  // ---- pass 3: features of V (positions as in pass 2)
   const float ne = d.norm_eps;
-  for (int i = tid; i < nV; i += blockDim.x) {
-    const int k = d.idxV[i];
-    float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
+  {
+    int bv = (int)(wpack[wid] & 0xffffffffull) + (int)(cbase & 0xffffffffull);
+#pragma unroll 2
+    for (int s0 = beg; s0 < end; s0 += 32) {
+      const int k = s0 + lane;
+      const bool isV = k < end && __ldg(hit + k) < 0;
+      const unsigned mv = __ballot_sync(FULL, isV);
+      if (isV) {
+        const int i = bv + __popc(mv & lt);
+        float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (c >= p) continue;
-      const float pk = d.pN[(size_t)c * Kp + k];
-      dv[c] = pk - pbar[c];
-      ev[c] = pk - p0s[c];
-      nd += dv[c] * dv[c];
-      nn += ev[c] * ev[c];
-    }
-    const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
+        for (int c = 0; c < 3; ++c) {
+          if (c >= p) continue;
+          const float pk = __ldg(pN + (size_t)c * Kp + k);
+          dv[c] = pk - pbar[c];
+          ev[c] = pk - p0s[c];
+          nd += dv[c] * dv[c];
+          nn += ev[c] * ev[c];
+        }
+        const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (c >= p) continue;
-      d.z[(size_t)c * Kp + i] = dv[c] * izd;
-      d.g[(size_t)c * Kp + i] = ev[c] * izn;
+        for (int c = 0; c < 3; ++c) {
+          if (c >= p) continue;
+          d.z[(size_t)c * Kp + i] = dv[c] * izd;
+          d.g[(size_t)c * Kp + i] = ev[c] * izn;
+        }
+      }
+      bv += __popc(mv);
     }
   }
-  if (tid == 0) {
+  if (tid == 0 && rank == 0) {
     const float* h = hist_of(r, d);
     const int H = d.H;
     const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
@@ -997,23 +1102,34 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
         cl[sl] = -1; aS[sl] = 0; aN[sl] = 0; aM[sl] = 0xffffffffu;
         aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
       };
+      // the loads of the next 32 positions are issued before this step's work
+      int nL = -1;
+      float nS = 0.f, nG[3] = {0.f, 0.f, 0.f};
+      auto fetch = [&](int i) {
+        nL = -1;
+        if (i < end) {
+          nL = __ldg(d.label + i);
+          nS = __ldg(d.Sv + i);
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            if (q < p) nG[q] = __ldg(d.g + (size_t)q * Kp + i);
+        }
+      };
+      fetch(beg + lane);
       for (int s0 = beg; s0 < end; s0 += 32) {
-        const int i = s0 + lane;
-        int L = -1;
+        int L = nL;
+        const float Si = nS, Gi[3] = {nG[0], nG[1], nG[2]};
+        fetch(s0 + 32 + lane);
         long long vS = 0, vG[3] = {0, 0, 0};
         uint32_t vM = 0xffffffffu;
-        if (i < end) {
-          L = d.label[i];
-          if (L >= w0 && L < w0 + kWin) {
-            const float Si = d.Sv[i];
-            vS = __float2ll_rn(ldexpf(Si, eS));
-            vM = float_key(Si);
+        if (L >= w0 && L < w0 + kWin) {
+          vS = __float2ll_rn(ldexpf(Si, eS));
+          vM = float_key(Si);
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-              if (q < p) vG[q] = __float2ll_rn(ldexpf(d.g[(size_t)q * Kp + i], eG));
-          } else {
-            L = -1;
-          }
+          for (int q = 0; q < 3; ++q)
+            if (q < p) vG[q] = __float2ll_rn(ldexpf(Gi[q], eG));
+        } else {
+          L = -1;
         }
         // accumulate the lanes whose label is cached; while some are not, flush
         // the slots and load up to kSlots of the missing labels (each round
@@ -1093,17 +1209,19 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
     }
   };
   if (over_all) {
+#pragma unroll 4
     for (int k0 = 0; k0 < K; k0 += blockDim.x) {
       const int k = k0 + tid;
-      emit(k < K, k, k < K ? d.S[k] : 0.f);
+      emit(k < K, k, k < K ? __ldg(d.S + k) : 0.f);
     }
   } else {
     for (int k = tid; k < K; k += blockDim.x) d.w_k[k] = 0.f;
     __syncthreads();   // the zeros land before the members' weights
+#pragma unroll 4
     for (int i0 = 0; i0 < nV; i0 += blockDim.x) {
       const int i = i0 + tid;
-      const bool mem = i < nV && (over_V || d.label[i] == sel);
-      emit(mem, mem ? d.idxV[i] : 0, mem ? d.Sv[i] : 0.f);
+      const bool mem = i < nV && (over_V || __ldg(d.label + i) == sel);
+      emit(mem, mem ? __ldg(d.idxV + i) : 0, mem ? __ldg(d.Sv + i) : 0.f);
     }
   }
   const float Z = block_sum(z, red);   // (its barriers also publish lcount and the list)
@@ -1294,11 +1412,74 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
 }
 
 // ========================================================================= launchers
-void launch_prune(const KArgs& a, cudaStream_t s) { k_prune<<<a.n_inst, kBlock, 0, s>>>(a); }
+// Cluster sizes of a per-instance kernel: the largest of 8, 4, 2 CTAs of which
+// the device can hold n_conc clusters at once (queried once per kernel and
+// size; clusters must fit in one GPC), else 1.
+struct ClusterFit {
+  int max_active[4] = {0, 0, 0, 0};   // clusters of 1, 2, 4, 8 CTAs
+};
+
+template <typename... Args>
+static ClusterFit query_fit(void (*kern)(Args...), int threads, size_t smem) {
+  ClusterFit f;
+  for (int i = 1; i < 4; ++i) {
+    const int cl = 1 << i;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    f.max_active[i] = n;
+  }
+  return f;
+}
+
+static int cluster_ctas(const ClusterFit& f, int n_conc) {
+  for (int i = 3; i >= 1; --i)
+    if (f.max_active[i] >= n_conc) return 1 << i;
+  return 1;
+}
+
+static ClusterFit g_fit_prune;
+
+template <typename... Args>
+static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int threads, size_t smem,
+                             cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_inst * cl));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+void launch_prune(const KArgs& a, cudaStream_t s) {
+  const int cl = cluster_ctas(g_fit_prune, a.n_conc > 0 ? a.n_conc : a.n_inst);
+  launch_clustered(k_prune, cl, a.n_inst, kBlock, 0, s, a);
+}
 
 static size_t dbscan_smem(int nc) { return dbscan_smem_bytes(nc); }
 
 void configure_cluster() {
+  g_fit_prune = query_fit(k_prune, kBlock, 0);
   cudaFuncSetAttribute(k_dbscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)dbscan_smem(kMaxCells));
   cudaFuncSetAttribute(k_dbscan_standalone, cudaFuncAttributeMaxDynamicSharedMemorySize,

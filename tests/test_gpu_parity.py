@@ -318,6 +318,46 @@ def test_replan_deterministic_and_batch_equals_single():
             pl.close()
 
 
+def test_batch_size_independent_bits():
+    """The per-instance stages run as thread-block clusters of 8, 4, 2 or 1
+    CTAs depending on the batch size; every replan gives the same bits in
+    batches of 1, 20 (4 CTAs), 40 (2) and 80 (1) instances."""
+    scs = [W.make("batch_instance", seed=s) for s in range(80)]
+
+    def run(sub):
+        pls, reqs = [], []
+        for sc in sub:
+            pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+            pl.set_nominal(np.tile([1.0, 0.0], (sc["cfg"]["T"], 1)))
+            reqs.append(dict(x0=torch.tensor(sc["x0"], dtype=torch.float32, device="cuda"),
+                             hist=torch.tensor(W.history(sc, 0), dtype=torch.float32, device="cuda"),
+                             radius=torch.tensor(sc["radius"], dtype=torch.float32, device="cuda"),
+                             u_out=torch.zeros((sc["cfg"]["T"], 2), device="cuda"),
+                             diag=torch.zeros(128, dtype=torch.uint8, device="cuda")))
+            pls.append(pl)
+        b = pkg.Batch(pls, reqs, use_graph=False, n_branches=1)
+        b.run()
+        torch.cuda.synchronize()
+        out = [(r["u_out"].cpu().numpy(), r["diag"].cpu().numpy()) for r in reqs]
+        b.close()
+        for pl in pls:
+            pl.close()
+        return out
+
+    full = run(scs)
+    modes = {int(np.frombuffer(dg.tobytes()[:4], np.int32)[0]) for _, dg in full}
+    assert len(modes) >= 2
+    for n in (40, 20):
+        part = run(scs[:n])
+        for i in range(n):
+            assert np.array_equal(part[i][0], full[i][0]), (n, i)
+            assert np.array_equal(part[i][1], full[i][1]), (n, i)
+    for i in (0, 7, 33, 79):
+        one = run(scs[i:i + 1])
+        assert np.array_equal(one[0][0], full[i][0]), i
+        assert np.array_equal(one[0][1][:72], full[i][1][:72]), i
+
+
 def test_closed_loop_episode_on_device():
     """Device-resident closed loop: recorded observations advance per replan
     (obs_step) and x_next aliases x0, all inside one captured graph."""
