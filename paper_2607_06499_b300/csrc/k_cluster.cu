@@ -450,17 +450,18 @@ __device__ __forceinline__ void box_dist2(const float* za, const uint32_t* bb, i
 }
 
 // Per-cell boxes (and, for core points, the smallest point id) over the
-// positions [0, n) in cell order.  Warp w takes a contiguous range of
+// positions [pb, pe) in cell order, merged by atomics into box / opar / omin
+// (which may be another CTA's shared memory).  Warp w takes a contiguous range of
 // positions, 32 at a time; a step whose lanes all fall in one cell is reduced
 // across the warp and merged into a running accumulator that is written
 // (shared-memory atomics) only when the cell changes, so a cell of thousands of
 // points costs a handful of atomics; mixed steps reduce per cell group.
 template <int p, bool CORE>
-__device__ __forceinline__ void cell_boxes(int n, const DbWork& w, const int* map, uint32_t* box,
-                                           int S, int* opar, int* omin) {
+__device__ __forceinline__ void cell_boxes(int pb, int pe, const DbWork& w, const int* map,
+                                           uint32_t* box, int S, int* opar, int* omin) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int L = (((n + nwarp - 1) / nwarp) + 31) & ~31;
-  const int beg = wid * L, end = min(n, beg + L);
+  const int L = (((pe - pb + nwarp - 1) / nwarp) + 31) & ~31;
+  const int beg = min(pe, pb + wid * L), end = min(pe, beg + L);
   int run = -1;
   uint32_t rlo[3], rhi[3], rmn = 0xffffffffu;
   auto flush = [&]() {
@@ -543,45 +544,68 @@ __device__ __forceinline__ void cell_boxes(int n, const DbWork& w, const int* ma
   flush();
 }
 
-// Shared memory of dbscan_block: map[nc] (cell -> occupied-cell id), then per
-// occupied cell: ostart[kMaxOcc + 1], ocell, ofill, opar, omin (kMaxOcc each),
-// obox[6][kMaxOcc] (all points) and ocbox[6][kMaxOcc] (core points) as keys.
+// Shared memory of dbscan_block: map[nc] (cell -> occupied-cell id), lcnt[nc]
+// (this CTA's points per cell), then per occupied cell: ostart[kMaxOcc + 1],
+// ocell, ofill, opar, omin (kMaxOcc each), obox[6][kMaxOcc] (all points) and
+// ocbox[6][kMaxOcc] (core points) as keys.
 __host__ __device__ __forceinline__ size_t dbscan_smem_bytes(int nc) {
-  return ((size_t)nc + 1 + 17 * (size_t)kMaxOcc) * 4;
+  return (2 * (size_t)nc + 1 + 17 * (size_t)kMaxOcc) * 4;
 }
 
+// One thread-block cluster of CL CTAs (CL = 1 .. 8) per point set.  CTA r owns
+// the index slice [i0, i1) and the cell-order position slice [pb, pe) of n.
+// The cell-level tables (occupied cells, offsets, boxes, union-find parents,
+// component minima) are computed identically in every CTA or merged into
+// rank 0's shared memory (distributed shared memory atomics) and copied back;
+// the union-find runs on rank 0's parents.  Phases, separated by cluster
+// barriers: 1 cells and per-CTA counts; 2 occupied cells and offsets; 3
+// scatter into cell order, cell boxes; 4 core flags; 5 core boxes; 6 union of
+// cells; 7 components; 8 canonical ids and core labels; 9 border points.
 template <int p>
 __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld, int n,
                                              float eps2, float cell_inv, int G, int R, int min_pts,
                                              DbWork w, int* labels, int* M_out, int* status,
                                              int* smem, long long* cyc) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
   const int nc = p == 3 ? G * G * G : G * G;
   const float far_ok = eps2 * 0.9999f;              // whole box within eps
   const float near_no = eps2 * 1.0001f + 1e-12f;    // whole box beyond eps
   const int S = kMaxOcc;
   int* map = smem;                  // [nc]
-  int* ostart = map + nc;           // [S + 1]
+  int* lcnt = map + nc;             // [nc]
+  int* ostart = lcnt + nc;          // [S + 1]
   int* ocell = ostart + S + 1;      // [S]
   int* ofill = ocell + S;           // [S] scatter cursor, later canonical id of a root
   int* opar = ofill + S;            // [S] union-find parent (-1: no core point)
   int* omin = opar + S;             // [S] smallest core id of the cell / component
   uint32_t* obox = reinterpret_cast<uint32_t*>(omin + S);   // [6][S]
   uint32_t* ocbox = obox + 6 * S;                           // [6][S]
+  // rank 0's tables (this CTA's own when CL == 1)
+  int* opar0 = cluster.map_shared_rank(opar, 0);
+  int* omin0 = cluster.map_shared_rank(omin, 0);
+  uint32_t* obox0 = cluster.map_shared_rank(obox, 0);
+  uint32_t* ocbox0 = cluster.map_shared_rank(ocbox, 0);
   __shared__ int wsum[33];
-  __shared__ int bad, n_occ_s;
+  __shared__ int bad, n_occ_s, n_root_s;
   auto stamp = [&](int k) {
-    if (cyc && tid == 0) cyc[k] = clock64();
+    if (cyc && tid == 0 && rank == 0) cyc[k] = clock64();
   };
+  // slices: index [i0, i1) and cell-order position [pb, pe) (32-aligned)
+  const int chunk = (((n + CL - 1) / CL) + 31) & ~31;
+  const int i0 = min(n, rank * chunk), i1 = min(n, i0 + chunk);
+  const int pb = i0, pe = i1;
   stamp(0);
   if (tid == 0) bad = 0;
-  for (int c = tid; c < nc; c += blockDim.x) map[c] = 0;
+  for (int c = tid; c < nc; c += blockDim.x) lcnt[c] = 0;
   __syncthreads();
-  // 1. cell of each point; per-cell counts (one atomic per cell per warp)
-  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-    const int i = i0 + tid;
+  // 1. cell of each point of the slice; per-cell counts (one atomic per cell
+  //    per warp)
+  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+    const int i = b0 + tid;
     int ci = -1;
-    if (i < n) {
+    if (i < i1) {
       int mul = 1;
       ci = 0;
       for (int c = 0; c < p; ++c) {
@@ -593,12 +617,21 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       w.cell[i] = ci;
     }
     const unsigned peers = __match_any_sync(FULL, ci);
-    if (ci >= 0 && lane == __ffs(peers) - 1) atomicAdd(&map[ci], __popc(peers));
+    if (ci >= 0 && lane == __ffs(peers) - 1) atomicAdd(&lcnt[ci], __popc(peers));
+  }
+  cluster.sync();   // (1) every CTA's counts
+  stamp(1);
+  // 2. counts of the whole set per cell; occupied cells in cell order: id,
+  //    offsets, reset of the per-cell summaries; map becomes cell -> occupied
+  //    id.  Identical in every CTA.
+  int anybad = 0;
+  for (int q = 0; q < CL; ++q) anybad |= *cluster.map_shared_rank(&bad, q);
+  for (int c = tid; c < nc; c += blockDim.x) {
+    int t = 0;
+    for (int q = 0; q < CL; ++q) t += cluster.map_shared_rank(lcnt, q)[c];
+    map[c] = t;
   }
   __syncthreads();
-  stamp(1);
-  // 2. occupied cells in cell order: id, offsets (prefix of counts), reset of
-  //    the per-cell summaries; map becomes cell -> occupied id
   {
     int base = 0, off = 0;
     for (int c0 = 0; c0 < nc; c0 += blockDim.x) {
@@ -659,17 +692,24 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   }
   __syncthreads();
   const int n_occ = n_occ_s;
-  if (bad || n_occ > S) {
-    for (int i = tid; i < n; i += blockDim.x) labels[i] = -1;
-    if (tid == 0) { *M_out = 0; atomicCAS(status, 0, CE_MPPI_ERR_INVALID_ARG); }
+  if (anybad || n_occ > S) {
+    for (int i = i0 + tid; i < i1; i += blockDim.x) labels[i] = -1;
+    if (tid == 0 && rank == 0) { *M_out = 0; atomicCAS(status, 0, CE_MPPI_ERR_INVALID_ARG); }
+    cluster.sync();   // no CTA leaves while another reads its counts
     return;
   }
+  // this CTA's write cursor in each occupied cell: after the lower ranks' points
+  for (int o = tid; o < n_occ; o += blockDim.x) {
+    int lo = 0;
+    for (int q = 0; q < rank; ++q) lo += cluster.map_shared_rank(lcnt, q)[ocell[o]];
+    ofill[o] = ostart[o] + lo;
+  }
+  __syncthreads();
   stamp(2);
-  // 3. scatter into cell order (one cursor atomic per cell per warp), then the
-  //    bounding box of all points of each cell
-  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-    const int i = i0 + tid;
-    const int o = i < n ? map[w.cell[i]] : -1;
+  // 3. scatter the slice into cell order (one cursor atomic per cell per warp)
+  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+    const int i = b0 + tid;
+    const int o = i < i1 ? map[w.cell[i]] : -1;
     const unsigned peers = __match_any_sync(FULL, o);
     const int leader = __ffs(peers) - 1;
     int base = 0;
@@ -682,21 +722,29 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       for (int q = 0; q < p; ++q) w.zs[(size_t)q * w.ld_s + pos] = z[(size_t)q * ld + i];
     }
   }
-  __syncthreads();
-  cell_boxes<p, false>(n, w, map, obox, S, opar, omin);
+  cluster.sync();   // (2) the cell order is complete; no more reads of lcnt
+  //    bounding boxes of all points of each cell: the position slice of each
+  //    CTA merged into rank 0, then copied back
+  cell_boxes<p, false>(pb, pe, w, map, obox0, S, nullptr, nullptr);
+  cluster.sync();   // (3)
+  if (rank != 0)
+    for (int e = tid; e < 6 * n_occ; e += blockDim.x) {
+      const int q = e / n_occ, o = e - q * n_occ;
+      obox[q * S + o] = obox0[q * S + o];
+    }
   __syncthreads();
   stamp(3);
-  // 4. core flags.  A cell with >= min_pts points is all core.  The points of
-  //    the other cells are listed, then one warp per listed point counts its
-  //    neighbours cell by cell: a box entirely within eps counts whole, a box
-  //    entirely beyond eps is skipped, other cells are scanned 32 points per
-  //    step; the count stops at min_pts.
+  // 4. core flags of the slice.  A cell with >= min_pts points is all core.
+  //    The points of the other cells are listed, then one warp per listed
+  //    point counts its neighbours cell by cell: a box entirely within eps
+  //    counts whole, a box entirely beyond eps is skipped, other cells are
+  //    scanned 32 points per step; the count stops at min_pts.
   {
     int n_sparse = 0;
-    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-      const int i = i0 + tid;
+    for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+      const int i = b0 + tid;
       bool sparse = false;
-      if (i < n) {
+      if (i < i1) {
         const int oi = map[w.cell[i]];
         const bool dense = (ostart[oi + 1] - ostart[oi]) >= min_pts;
         w.core[i] = dense ? 1 : 0;
@@ -704,13 +752,13 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       }
       int tot;
       const int rk = block_scan_flag(sparse, wsum, &tot);
-      if (sparse) w.labels_tmp[n_sparse + rk] = i;
+      if (sparse) w.labels_tmp[i0 + n_sparse + rk] = i;
       n_sparse += tot;
     }
     __syncthreads();
     const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
     for (int is = wid; is < n_sparse; is += nwarp) {
-      const int i = w.labels_tmp[is];
+      const int i = w.labels_tmp[i0 + is];
       const int ci = w.cell[i];
       float za[3];
 #pragma unroll
@@ -745,12 +793,12 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           sm &= sm - 1;
           const int obs = __shfl_sync(FULL, ob, src);
           for (int pb0 = ostart[obs]; pb0 < ostart[obs + 1] && count < min_pts; pb0 += 32) {
-            const int pb = pb0 + lane;
+            const int pp = pb0 + lane;
             bool hit = false;
-            if (pb < ostart[obs + 1]) {
+            if (pp < ostart[obs + 1]) {
               float zb[3];
 #pragma unroll
-              for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pb];
+              for (int c = 0; c < p; ++c) zb[c] = w.zs[(size_t)c * w.ld_s + pp];
               hit = nb_pred_t<p>(za, zb, eps2);
             }
             count += __popc(__ballot_sync(FULL, hit));
@@ -760,20 +808,29 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       if (lane == 0) w.core[i] = count >= min_pts ? 1 : 0;
     }
   }
-  __syncthreads();
+  cluster.sync();   // (4) core flags of every slice
   stamp(4);
-  // 5. per-cell core summary: parent, smallest core id, bounding box of the
-  //    core points
-  cell_boxes<p, true>(n, w, map, ocbox, S, opar, omin);
+  // 5. per-cell core summary (parent, smallest core id, box of the core
+  //    points) merged into rank 0, then copied back
+  cell_boxes<p, true>(pb, pe, w, map, ocbox0, S, opar0, omin0);
+  cluster.sync();   // (5)
+  if (rank != 0)
+    for (int e = tid; e < 8 * n_occ; e += blockDim.x) {
+      const int q = e / n_occ, o = e - q * n_occ;
+      if (q < 6) ocbox[q * S + o] = ocbox0[q * S + o];
+      else if (q == 6) opar[o] = opar0[o];
+      else omin[o] = omin0[o];
+    }
   __syncthreads();
   stamp(5);
-  // 6. cell-level union, one warp per occupied cell A with core points: the
-  //    lanes screen the neighbour offsets in parallel (B > A with core points,
-  //    core boxes within eps, not yet joined) and the warp searches each
-  //    surviving pair for a core pair within eps.
+  // 6. cell-level union over rank 0's parents, one warp per occupied cell A
+  //    with core points (cells dealt round the cluster's warps): the lanes
+  //    screen the neighbour offsets in parallel (B > A with core points, core
+  //    boxes within eps, not yet joined) and the warp searches each surviving
+  //    pair for a core pair within eps (non-core positions hold ~index).
   {
     const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
-    for (int A = wid; A < n_occ; A += nwarp) {
+    for (int A = rank * nwarp + wid; A < n_occ; A += CL * nwarp) {
       if (opar[A] < 0) continue;
       const int cA = ocell[A];
       const int ax = cA % G, ay = (cA / G) % G, az = p == 3 ? cA / (G * G) : 0;
@@ -807,7 +864,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           cm &= cm - 1;
           const int Bc = __shfl_sync(FULL, B, src);
           int joined = 0;
-          if (lane == 0) joined = cfind(opar, A) == cfind(opar, Bc);
+          if (lane == 0) joined = cfind(opar0, A) == cfind(opar0, Bc);
           if (__shfl_sync(FULL, joined, 0)) continue;   // warp-uniform decision
           // one point of the smaller cell at a time (warp-uniform); the lanes
           // test 32 points of the other cell per step
@@ -834,68 +891,77 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
               if (__any_sync(FULL, hit)) { found = true; break; }
             }
           }
-          if (found && lane == 0 && !cunion(opar, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
+          if (found && lane == 0 && !cunion(opar0, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
           __syncwarp();
         }
       }
     }
   }
-  __syncthreads();
+  cluster.sync();   // (6)
   stamp(6);
-  // 7. components: compress to the root; component minimum core id
-  for (int o = tid; o < n_occ; o += blockDim.x)
-    if (opar[o] >= 0) opar[o] = cfind(opar, o);
-  __syncthreads();
-  for (int o = tid; o < n_occ; o += blockDim.x)
-    if (opar[o] >= 0 && opar[o] != o) atomicMin(&omin[opar[o]], omin[o]);
-  __syncthreads();
-  // 8. canonical ids (rank of each component minimum in point order), labels
-  //    of the core points, and the list of the other points (into cell: a
-  //    chunk only overwrites entries of chunks already read)
-  __shared__ unsigned long long wpack[33];
-  int M = 0, n_border = 0;
-  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-    const int i = i0 + tid;
-    const bool valid = i < n;
-    const bool isc = valid && w.core[i], isb = valid && !w.core[i];
-    int rt = -1;
-    bool first = false;
-    if (isc) {
-      rt = opar[map[w.cell[i]]];
-      first = omin[rt] == i;
-    }
-    const unsigned bf = __ballot_sync(FULL, first), bc = __ballot_sync(FULL, isc),
-                   bb = __ballot_sync(FULL, isb);
-    // per-warp counts packed 21 bits apart; warp 0 scans the 32 warps
-    if (lane == 0)
-      wpack[wid] = (unsigned long long)__popc(bf) | ((unsigned long long)__popc(bc) << 21) |
-                   ((unsigned long long)__popc(bb) << 42);
+  // 7. components (rank 0): compress to the root; component minimum core id;
+  //    then every CTA copies parents and minima
+  if (rank == 0) {
+    for (int o = tid; o < n_occ; o += blockDim.x)
+      if (opar[o] >= 0) opar[o] = cfind(opar, o);
     __syncthreads();
-    if (wid == 0) {
-      const unsigned long long v = lane < nwarp ? wpack[lane] : 0ull;
-      unsigned long long x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-      }
-      wpack[lane] = x - v;                 // exclusive prefix of warp `lane`
-      if (lane == 31) wpack[32] = x;       // chunk totals
-    }
-    __syncthreads();
-    const unsigned long long pre = wpack[wid], tot = wpack[32];
-    const int msk = (1 << 21) - 1;
-    const int pf = (int)(pre & msk), pb = (int)(pre >> 42);
-    const int tf = (int)(tot & msk), tb = (int)(tot >> 42);
-    const unsigned lt = (1u << lane) - 1u;
-    if (first) ofill[rt] = M + pf + __popc(bf & lt);
-    __syncthreads();   // canonical ids of this chunk's firsts are visible
-    if (isc) labels[i] = ofill[rt];
-    if (isb) w.cell[n_border + pb + __popc(bb & lt)] = i;
-    M += tf;
-    n_border += tb;
-    __syncthreads();
+    for (int o = tid; o < n_occ; o += blockDim.x)
+      if (opar[o] >= 0 && opar[o] != o) atomicMin(&omin[opar[o]], omin[o]);
   }
+  cluster.sync();   // (7)
+  if (rank != 0)
+    for (int e = tid; e < 2 * n_occ; e += blockDim.x) {
+      if (e < n_occ) opar[e] = opar0[e];
+      else omin[e - n_occ] = omin0[e - n_occ];
+    }
+  __syncthreads();
+  // 8. canonical ids: a component's id is the rank of its smallest core index
+  //    among the components' (computed identically in every CTA from the
+  //    roots), then the labels of the slice's core points and the list of its
+  //    other points (into cell: a chunk only overwrites entries already read)
+  {
+    if (tid == 0) n_root_s = 0;
+    __syncthreads();
+    for (int o = tid; o < n_occ; o += blockDim.x)
+      if (opar[o] == o) ocell[atomicAdd(&n_root_s, 1)] = o;   // ocell is free now
+    __syncthreads();
+    const int nr = n_root_s;
+    for (int t = tid; t < nr; t += blockDim.x) {
+      const int ro = ocell[t], key = omin[ro];
+      int id = 0;
+      for (int u = 0; u < nr; ++u) id += omin[ocell[u]] < key;
+      ofill[ro] = id;
+    }
+    __syncthreads();
+    int n_border = 0;
+    for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+      const int i = b0 + tid;
+      const bool valid = i < i1;
+      const bool isc = valid && w.core[i], isb = valid && !w.core[i];
+      if (isc) labels[i] = ofill[opar[map[w.cell[i]]]];
+      const int rk_tot = __syncthreads_count(isb);   // (also orders the cell reads first)
+      const unsigned bb = __ballot_sync(FULL, isb);
+      if (lane == 0) wsum[wid] = __popc(bb);
+      __syncthreads();
+      if (wid == 0) {
+        const int v = lane < nwarp ? wsum[lane] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(FULL, x, o);
+          if (lane >= o) x += y;
+        }
+        wsum[lane] = x - v;
+      }
+      __syncthreads();
+      if (isb) w.cell[i0 + n_border + wsum[wid] + __popc(bb & ((1u << lane) - 1u))] = i;
+      n_border += rk_tot;
+      __syncthreads();
+    }
+    if (tid == 0) wsum[32] = n_border;
+    if (tid == 0 && rank == 0) *M_out = nr;
+  }
+  cluster.sync();   // (8) core labels of every slice; no distributed shared memory after
   stamp(7);
   // 9. the other points: one warp per point finds its lowest-index core
   //    neighbour among the core points of the cells within reach.  The lanes
@@ -904,9 +970,10 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    (the cell's own, or its component's for a root cell), and the visit
   //    stops once that bound reaches the best id found.  No core neighbour:
   //    noise.
+  const int n_border = wsum[32];
   const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
   for (int ib = wid; ib < n_border; ib += nwarp) {
-    const int a = w.cell[ib];
+    const int a = w.cell[i0 + ib];
     float za[3];
     for (int q = 0; q < p; ++q) za[q] = z[(size_t)q * ld + a];
     int cc[3];
@@ -936,14 +1003,14 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
         if (lane == src) lb = 0x7fffffff;
         const int e = ostart[obs + 1];
         for (int pb0 = ostart[obs]; pb0 < e; pb0 += 32) {
-          const int pb = pb0 + lane;
+          const int pp = pb0 + lane;
           int cand = 0x7fffffff;
-          if (pb < e) {
-            const int sid = w.sorted[pb];
+          if (pp < e) {
+            const int sid = w.sorted[pp];
             if (sid >= 0 && sid < best) {
               float zb[3];
 #pragma unroll
-              for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + pb];
+              for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + pp];
               if (nb_pred_t<p>(za, zb, eps2)) cand = sid;
             }
           }
@@ -953,9 +1020,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
     }
     if (lane == 0) labels[a] = best == 0x7fffffff ? -1 : labels[best];
   }
-  __syncthreads();
   stamp(8);
-  if (tid == 0) *M_out = M;
 }
 
 __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
@@ -970,13 +1035,16 @@ __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
   return w;
 }
 
+// One cluster per instance; rank 0 publishes the cluster count and the mode.
 __global__ void __maxnreg__(64) k_dbscan(KArgs a) {
   extern __shared__ int smem_i[];
-  const int inst = blockIdx.x;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int inst = blockIdx.x / CL;
   const InstDesc& d = desc_of(a, inst);
   Ctl* ctl = d.ctl;
   const int mode = ctl->mode;
-  if (mode != CE_MODE_STATIC) return;   // fallback replans skip clustering
+  if (mode != CE_MODE_STATIC) return;   // fallback replans skip clustering (whole cluster)
   const int nV = ctl->nV;
   const DbWork w = db_work_of(d);
   __shared__ int M;
@@ -987,7 +1055,7 @@ __global__ void __maxnreg__(64) k_dbscan(KArgs a) {
     dbscan_block<2>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
                     &ctl->status, smem_i, ctl->dbcyc);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && cluster.block_rank() == 0) {
     ctl->M = M;
     if (M == 0) ctl->mode = CE_MODE_ALLNOISE;
   }
@@ -998,19 +1066,21 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
                                                               int R, int min_pts, int* labels,
                                                               int* n_clusters, DbWork w) {
   extern __shared__ int smem_i[];
+  cg::cluster_group cluster = cg::this_cluster();
   __shared__ int M;
   __shared__ int status;
   w.labels_tmp = labels;
   if (threadIdx.x == 0) status = 0;
-  __syncthreads();
+  cluster.sync();   // rank 0's status is cleared before any CTA may raise it
+  int* st0 = cluster.map_shared_rank(&status, 0);
   if (p == 3)
-    dbscan_block<3>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, &status, smem_i,
+    dbscan_block<3>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i,
                     nullptr);
   else
-    dbscan_block<2>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, &status, smem_i,
+    dbscan_block<2>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i,
                     nullptr);
-  __syncthreads();
-  if (threadIdx.x == 0) *n_clusters = status ? -status : M;
+  cluster.sync();   // every CTA's status updates have landed
+  if (threadIdx.x == 0 && cluster.block_rank() == 0) *n_clusters = status ? -status : M;
 }
 
 // ========================================================================= select
@@ -1452,6 +1522,12 @@ static int cluster_ctas(const ClusterFit& f, int n_conc) {
 }
 
 static ClusterFit g_fit_prune;
+// DBSCAN: the fit depends on the shared memory of the launch (by grid size)
+static ClusterFit g_fit_db[2];   // small grids (<= 1024 cells), large grids
+static size_t dbscan_smem(int nc);
+static const ClusterFit& fit_dbscan(size_t smem) {
+  return smem <= dbscan_smem(1024) ? g_fit_db[0] : g_fit_db[1];
+}
 
 template <typename... Args>
 static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int threads, size_t smem,
@@ -1484,10 +1560,14 @@ void configure_cluster() {
                        (int)dbscan_smem(kMaxCells));
   cudaFuncSetAttribute(k_dbscan_standalone, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)dbscan_smem(kMaxCells));
+  g_fit_db[0] = query_fit(k_dbscan, kBlock, dbscan_smem(1024));
+  g_fit_db[1] = query_fit(k_dbscan, kBlock, dbscan_smem(kMaxCells));
 }
 
 void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s) {
-  k_dbscan<<<a.n_inst, kBlock, dbscan_smem(max_cells), s>>>(a);
+  const size_t smem = dbscan_smem(max_cells);
+  const int cl = cluster_ctas(fit_dbscan(smem), a.n_conc > 0 ? a.n_conc : a.n_inst);
+  launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, a);
 }
 
 void launch_select(const KArgs& a, cudaStream_t s) { k_select<<<a.n_inst, kBlock, 0, s>>>(a); }
@@ -1509,9 +1589,10 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
   w.zs = reinterpret_cast<float*>(b); b += sizeof(float) * 3 * ldn;
   w.ld_s = ldn;
   w.bbox = reinterpret_cast<float*>(b);
-  (void)nc;
-  k_dbscan_standalone<<<1, kBlock, dbscan_smem(nc), s>>>(z, n, ld, p, eps2, cell_inv, G, R,
-                                                          min_pts, labels, n_clusters, w);
+  const size_t smem = dbscan_smem(nc);
+  const int cl = cluster_ctas(fit_dbscan(smem), 1);
+  launch_clustered(k_dbscan_standalone, cl, 1, kBlock, smem, s, z, n, ld, p, eps2, cell_inv, G, R,
+                   min_pts, labels, n_clusters, w);
 }
 
 size_t dbscan_ws_bytes(int n) {
