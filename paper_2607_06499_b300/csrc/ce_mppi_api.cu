@@ -264,7 +264,8 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   // + 16: the packed 2-D table's header may round up 16 bytes past the rows'
   const size_t o_trk = take(track_bytes(T, nobs) + 16);
   const size_t o_S = take(4 * Kp), o_w = take(4 * Kp), o_Sv = take(4 * Kp),
-               o_cmin = take(4 * Kp), o_nzk = take(4 * kSparseMax), o_nze = take(4 * kSparseMax);
+               o_cmin = take(4 * Kp), o_nzk = take(4 * kSparseMax), o_nze = take(4 * kSparseMax),
+               o_zpart = take(4 * kPruneRanges);
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
   const size_t eps_elems = P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
@@ -306,6 +307,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.cmin = reinterpret_cast<float*>(b + o_cmin);
   d.nzk = reinterpret_cast<int*>(b + o_nzk);
   d.nze = reinterpret_cast<float*>(b + o_nze);
+  d.zpart = reinterpret_cast<float*>(b + o_zpart);
   d.pN = reinterpret_cast<float*>(b + o_pN);
   d.z = reinterpret_cast<float*>(b + o_z);
   d.g = reinterpret_cast<float*>(b + o_g);

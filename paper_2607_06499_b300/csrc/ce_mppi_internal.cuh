@@ -58,6 +58,7 @@ struct InstDesc {
   float* Unew;   // [T][m] updated nominal before the shift
   float4* tracks;
   float *S, *w_k, *pN, *eps, *z, *g, *zs, *Sv, *cmin, *nze;
+  float* zpart;  // [kPruneRanges] range partials of the softmin normaliser
   int* nzk;
   float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
   int TMp;       // T*m rounded up to a multiple of 4

@@ -43,23 +43,6 @@ __device__ __forceinline__ int block_scan_flag(bool f, int* wsum, int* total) {
   return r;
 }
 
-// Deterministic block sum (warp trees, then warp 0 over the warp partials).
-__device__ __forceinline__ float block_sum(float v, float* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  float t = 0.0f;
-  if (wid == 0) {
-    t = warp_sum(lane < nw ? red[lane] : 0.0f);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  t = red[32];
-  __syncthreads();
-  return t;
-}
-
 __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, float* p0) {
   if (d.dyn == CE_DYN_ARM6_KIN) {
     float q[6], O[7][3], R[9];
@@ -1093,10 +1076,17 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
 // weights are left unnormalised (the update multiplies by 1/Z); the nonzero
 // ones are also listed by ascending k when there are at most kSparseMax.
 constexpr int kWin = 512;   // clusters per statistics window
-constexpr int kSlots = 3;   // per-warp label cache of the cluster statistics
+constexpr int kSlots = 2;   // per-warp label cache of the cluster statistics
 
+// One thread-block cluster of CL CTAs per instance.  The statistics of a
+// window of clusters are merged into rank 0's shared memory (distributed
+// shared memory atomics: exact, order-free); rank 0 evaluates the criterion.
+// The weights pass splits its domain into kPruneRanges fixed ranges whose
+// normaliser partials are added in range order, so Z does not depend on CL.
 __global__ void __maxnreg__(64) k_select(KArgs a) {
-  const int inst = blockIdx.x;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int inst = blockIdx.x / CL;
   const InstDesc& d = desc_of(a, inst);
   Ctl* ctl = d.ctl;
   __shared__ unsigned long long accS[kWin], accG[3][kWin];
@@ -1128,17 +1118,18 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
     if (tid == 0) bestkey = ~0ull;
     // each warp owns a contiguous range of V and keeps per-lane partial sums
     // for up to kSlots labels (warp-uniform slot labels); a slot is reduced
-    // across the warp and added to shared memory only when evicted or at the
-    // end -- exact int64 sums and min keys, so the result does not depend on
-    // the order.
-    const int Lr = (((nV + nw - 1) / nw) + 31) & ~31;
-    const int beg = min(nV, wid * Lr), end = min(nV, beg + Lr);
+    // across the warp and added to rank 0's accumulators only when evicted or
+    // at the end -- exact int64 sums and min keys, so the result does not
+    // depend on the order.
+    const int Lr = (((nV + CL * nw - 1) / (CL * nw)) + 31) & ~31;
+    const int beg = min(nV, (rank * nw + wid) * Lr), end = min(nV, beg + Lr);
     for (int w0 = 0; w0 < M; w0 += kWin) {
-      for (int c = tid; c < kWin; c += blockDim.x) {
-        accS[c] = 0ull; accN[c] = 0; accM[c] = 0xffffffffu;
-        accG[0][c] = accG[1][c] = accG[2][c] = 0ull;
-      }
-      __syncthreads();
+      if (rank == 0)
+        for (int c = tid; c < kWin; c += blockDim.x) {
+          accS[c] = 0ull; accN[c] = 0; accM[c] = 0xffffffffu;
+          accG[0][c] = accG[1][c] = accG[2][c] = 0ull;
+        }
+      cluster.sync();   // rank 0's accumulators are clear
       int cl[kSlots];
       long long aS[kSlots], aG[kSlots][3];
       int aN[kSlots];
@@ -1162,12 +1153,12 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
         const uint32_t mk = __reduce_min_sync(FULL, aM[sl]);
         if (lane == 0 && cl[sl] >= 0) {
           const int c = cl[sl] - w0;
-          atomicAdd(&accS[c], (unsigned long long)s);
-          atomicAdd(&accG[0][c], (unsigned long long)g0);
-          atomicAdd(&accG[1][c], (unsigned long long)g1);
-          atomicAdd(&accG[2][c], (unsigned long long)g2);
-          atomicAdd(&accN[c], nn);
-          atomicMin(&accM[c], mk);
+          atomicAdd(cluster.map_shared_rank(&accS[c], 0), (unsigned long long)s);
+          atomicAdd(cluster.map_shared_rank(&accG[0][c], 0), (unsigned long long)g0);
+          atomicAdd(cluster.map_shared_rank(&accG[1][c], 0), (unsigned long long)g1);
+          atomicAdd(cluster.map_shared_rank(&accG[2][c], 0), (unsigned long long)g2);
+          atomicAdd(cluster.map_shared_rank(&accN[c], 0), nn);
+          atomicMin(cluster.map_shared_rank(&accM[c], 0), mk);
         }
         cl[sl] = -1; aS[sl] = 0; aN[sl] = 0; aM[sl] = 0xffffffffu;
         aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
@@ -1231,28 +1222,30 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
       }
 #pragma unroll
       for (int sl = 0; sl < kSlots; ++sl) flush(sl);
-      __syncthreads();
-      for (int c = tid; c < kWin && w0 + c < M; c += blockDim.x) {
-        const float n = (float)accN[c];
-        float crit;
-        if (!dynamic) {
-          crit = ldexpf(__ll2float_rn((long long)accS[c]), -eS) / n;
-        } else {
-          float v[3], nn = 0.f;
+      cluster.sync();   // the window's statistics are complete in rank 0
+      if (rank == 0)
+        for (int c = tid; c < kWin && w0 + c < M; c += blockDim.x) {
+          const float n = (float)accN[c];
+          float crit;
+          if (!dynamic) {
+            crit = ldexpf(__ll2float_rn((long long)accS[c]), -eS) / n;
+          } else {
+            float v[3], nn = 0.f;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            v[q] = q < p ? ldexpf(__ll2float_rn((long long)accG[q][c]), -eG) / n : 0.f;
-            nn += v[q] * v[q];
+            for (int q = 0; q < 3; ++q) {
+              v[q] = q < p ? ldexpf(__ll2float_rn((long long)accG[q][c]), -eG) / n : 0.f;
+              nn += v[q] * v[q];
+            }
+            const float iv = 1.0f / (sqrtf(nn) + d.norm_eps);
+            crit = (v[0] * iv) * vh[0] + (v[1] * iv) * vh[1] + (v[2] * iv) * vh[2];
           }
-          const float iv = 1.0f / (sqrtf(nn) + d.norm_eps);
-          crit = (v[0] * iv) * vh[0] + (v[1] * iv) * vh[1] + (v[2] * iv) * vh[2];
+          d.cmin[w0 + c] = key_float(accM[c]);
+          atomicMin(&bestkey, ((unsigned long long)float_key(crit) << 32) | (unsigned)(w0 + c));
         }
-        d.cmin[w0 + c] = key_float(accM[c]);
-        atomicMin(&bestkey, ((unsigned long long)float_key(crit) << 32) | (unsigned)(w0 + c));
-      }
       __syncthreads();
     }
-    sel = (int)(bestkey & 0xffffffffull);
+    cluster.sync();   // rank 0's choice and the cluster minima are final
+    sel = (int)(*cluster.map_shared_rank(&bestkey, 0) & 0xffffffffull);
   }
   // the update set (all K / V / the selected cluster) and its least cost
   const int mode = mode0 == CE_MODE_STATIC ? (dynamic ? CE_MODE_DYNAMIC : CE_MODE_STATIC) : mode0;
@@ -1260,44 +1253,70 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
   const bool over_V = mode == CE_MODE_ALLNOISE;
   const float smin = over_all ? ctl->S_min_all : over_V ? ctl->S_min_V : d.cmin[sel];
   const float il = d.inv_lambda;
-  float z = 0.f, zc = 0.f;
-  // e for one member; nonzero ones are appended to the list (warp-aggregated)
-  auto emit = [&](bool mem, int k, float Sk) {
-    float e = 0.f;
-    if (mem) {
-      e = expf(-(Sk - smin) * il);
-      kahan_add(z, zc, e);
-      d.w_k[k] = e;
-    }
-    const bool nz = e != 0.f;
-    const unsigned b = __ballot_sync(FULL, nz);
-    if (b) {
-      int base = 0;
-      if (lane == __ffs(b) - 1) base = atomicAdd(&lcount, __popc(b));
-      base = __shfl_sync(FULL, base, __ffs(b) - 1) + __popc(b & ((1u << lane) - 1u));
-      if (nz && base < kSparseMax) { lk[base] = k; le[base] = e; }
-    }
-  };
-  if (over_all) {
-#pragma unroll 4
-    for (int k0 = 0; k0 < K; k0 += blockDim.x) {
-      const int k = k0 + tid;
-      emit(k < K, k, k < K ? __ldg(d.S + k) : 0.f);
-    }
-  } else {
-    for (int k = tid; k < K; k += blockDim.x) d.w_k[k] = 0.f;
-    __syncthreads();   // the zeros land before the members' weights
-#pragma unroll 4
-    for (int i0 = 0; i0 < nV; i0 += blockDim.x) {
-      const int i = i0 + tid;
-      const bool mem = i < nV && (over_V || __ldg(d.label + i) == sel);
-      emit(mem, mem ? __ldg(d.idxV + i) : 0, mem ? __ldg(d.Sv + i) : 0.f);
-    }
+  // weights: the domain (K, or V) in kPruneRanges fixed ranges, m_z per warp
+  const int dom = over_all ? K : nV;
+  const int Lz = (((dom + kPruneRanges - 1) / kPruneRanges) + 31) & ~31;
+  const int m_z = kPruneRanges / (CL * nw);
+  const int v0 = (rank * nw + wid) * m_z;
+  if (!over_all) {
+    const int chunk = (((K + CL - 1) / CL) + 31) & ~31;
+    const int kb = min(K, rank * chunk), ke = min(K, kb + chunk);
+    for (int k = kb + tid; k < ke; k += blockDim.x) d.w_k[k] = 0.f;
   }
-  const float Z = block_sum(z, red);   // (its barriers also publish lcount and the list)
+  cluster.sync();   // the zeros land before the members' weights
+  for (int j = 0; j < m_z; ++j) {
+    const int rb = min(dom, (v0 + j) * Lz), re = min(dom, rb + Lz);
+    float z = 0.f, zc = 0.f;
+#pragma unroll 2
+    for (int s0 = rb; s0 < re; s0 += 32) {
+      const int i = s0 + lane;
+      bool mem = false;
+      int k = 0;
+      float Sk = 0.f;
+      if (i < re) {
+        if (over_all) {
+          mem = true; k = i; Sk = __ldg(d.S + i);
+        } else {
+          mem = over_V || __ldg(d.label + i) == sel;
+          if (mem) { k = __ldg(d.idxV + i); Sk = __ldg(d.Sv + i); }
+        }
+      }
+      float e = 0.f;
+      if (mem) {
+        e = expf(-(Sk - smin) * il);
+        kahan_add(z, zc, e);
+        d.w_k[k] = e;
+      }
+      // nonzero weights into rank 0's list (warp-aggregated)
+      const bool nz = e != 0.f;
+      const unsigned b = __ballot_sync(FULL, nz);
+      if (b) {
+        int base = 0;
+        if (lane == __ffs(b) - 1) base = atomicAdd(cluster.map_shared_rank(&lcount, 0), __popc(b));
+        base = __shfl_sync(FULL, base, __ffs(b) - 1) + __popc(b & ((1u << lane) - 1u));
+        if (nz && base < kSparseMax) {
+          *cluster.map_shared_rank(&lk[base], 0) = k;
+          *cluster.map_shared_rank(&le[base], 0) = e;
+        }
+      }
+    }
+    z = warp_sum(z);
+    if (lane == 0) d.zpart[v0 + j] = z;
+  }
+  cluster.sync();   // the list and the range partials are complete
+  if (rank != 0) return;
+  // rank 0: Z in range order, the list by ascending k, the control block
+  if (wid == 0) {
+    constexpr int per = kPruneRanges / 32;
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < per; ++j) t += __ldcg(d.zpart + per * lane + j);
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
   const int nl = lcount;
   if (nl <= kSparseMax) {
-    // the list by ascending k (keys are distinct): rank by counting
+    // rank by counting (keys are distinct)
     int rk = 0, kk = 0;
     float ee = 0.f;
     if (tid < nl) {
@@ -1305,15 +1324,15 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
       ee = le[tid];
       for (int j = 0; j < nl; ++j) rk += lk[j] < kk;
     }
-    __syncthreads();
     if (tid < nl) { d.nzk[rk] = kk; d.nze[rk] = ee; }
   }
+  __syncthreads();
   if (tid == 0) {
     ctl->mode = mode;
     ctl->sel = sel;
     ctl->dynamic = dynamic;
     ctl->S_min = smin;
-    ctl->invZ = 1.0f / Z;
+    ctl->invZ = 1.0f / red[32];
     ctl->nnz = nl <= kSparseMax ? nl : -1;
   }
 }
@@ -1521,7 +1540,7 @@ static int cluster_ctas(const ClusterFit& f, int n_conc) {
   return 1;
 }
 
-static ClusterFit g_fit_prune;
+static ClusterFit g_fit_prune, g_fit_select;
 // DBSCAN: the fit depends on the shared memory of the launch (by grid size)
 static ClusterFit g_fit_db[2];   // small grids (<= 1024 cells), large grids
 static size_t dbscan_smem(int nc);
@@ -1556,6 +1575,7 @@ static size_t dbscan_smem(int nc) { return dbscan_smem_bytes(nc); }
 
 void configure_cluster() {
   g_fit_prune = query_fit(k_prune, kBlock, 0);
+  g_fit_select = query_fit(k_select, kBlock, 0);
   cudaFuncSetAttribute(k_dbscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)dbscan_smem(kMaxCells));
   cudaFuncSetAttribute(k_dbscan_standalone, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1570,7 +1590,10 @@ void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s) {
   launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, a);
 }
 
-void launch_select(const KArgs& a, cudaStream_t s) { k_select<<<a.n_inst, kBlock, 0, s>>>(a); }
+void launch_select(const KArgs& a, cudaStream_t s) {
+  const int cl = cluster_ctas(g_fit_select, a.n_conc > 0 ? a.n_conc : a.n_inst);
+  launch_clustered(k_select, cl, a.n_inst, kBlock, 0, s, a);
+}
 
 void launch_update(const KArgs& a, cudaStream_t s) {
   k_update<<<a.n_tiles, kUpdateWarps * 32, 0, s>>>(a);
