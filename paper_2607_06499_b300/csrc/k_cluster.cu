@@ -188,10 +188,11 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] = cmp[c] = 0.f;
     };
-    for (int j = 0; j < m_r; ++j) {
-    const int rb = min(K, beg + j * Lv), re = min(K, rb + Lv);
-#pragma unroll 2
-    for (int s0 = rb; s0 < re; s0 += 32) {
+    // one loop over the warp's ranges (loads of consecutive steps overlap);
+    // each range's sums are flushed at its end
+    int jr = 0;
+#pragma unroll 4
+    for (int s0 = beg; s0 < end; s0 += 32) {
       const int k = s0 + lane;
       const int h = k < end ? __ldg(hit + k) : -1;
       const float Sk = k < end ? __ldg(d.S + k) : INFINITY;
@@ -218,9 +219,9 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
       }
       bv += __popc(mv);
       bc += __popc(mc);
+      if (s0 + 32 - beg == (jr + 1) * Lv) flush(v0 + jr++);
     }
-    flush(v0 + j);
-    }
+    for (; jr < m_r; ++jr) flush(v0 + jr);   // a range cut by K, and ranges past it
   }
   // block extremes of S (order-free), then the instance's values: extremes
   // over the ranks, and the range partials of pbar added in range order
@@ -1264,16 +1265,17 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
     for (int k = kb + tid; k < ke; k += blockDim.x) d.w_k[k] = 0.f;
   }
   cluster.sync();   // the zeros land before the members' weights
-  for (int j = 0; j < m_z; ++j) {
-    const int rb = min(dom, (v0 + j) * Lz), re = min(dom, rb + Lz);
+  {
+    const int zb = min(dom, v0 * Lz), ze = min(dom, zb + m_z * Lz);
+    int jr = 0;
     float z = 0.f, zc = 0.f;
-#pragma unroll 2
-    for (int s0 = rb; s0 < re; s0 += 32) {
+#pragma unroll 4
+    for (int s0 = zb; s0 < ze; s0 += 32) {
       const int i = s0 + lane;
       bool mem = false;
       int k = 0;
       float Sk = 0.f;
-      if (i < re) {
+      if (i < ze) {
         if (over_all) {
           mem = true; k = i; Sk = __ldg(d.S + i);
         } else {
@@ -1299,9 +1301,18 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
           *cluster.map_shared_rank(&le[base], 0) = e;
         }
       }
+      if (s0 + 32 - zb == (jr + 1) * Lz) {
+        const float t = warp_sum(z);
+        if (lane == 0) d.zpart[v0 + jr] = t;
+        ++jr;
+        z = zc = 0.f;
+      }
     }
-    z = warp_sum(z);
-    if (lane == 0) d.zpart[v0 + j] = z;
+    for (; jr < m_z; ++jr) {   // a range cut by the domain's end, and ranges past it
+      const float t = warp_sum(z);
+      if (lane == 0) d.zpart[v0 + jr] = t;
+      z = zc = 0.f;
+    }
   }
   cluster.sync();   // the list and the range partials are complete
   if (rank != 0) return;
@@ -1562,7 +1573,7 @@ static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int thre
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = cl > 1 ? 1 : 0;   // one CTA per instance: a plain launch
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
