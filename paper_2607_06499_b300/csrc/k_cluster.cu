@@ -368,6 +368,19 @@ struct DbWork {
   float* bbox;   // [ncells][6] core bounding box (min xyz, max xyz)
 };
 
+// The 125 neighbour-cell offsets of a 3-D point (reach R = 2 cells), nearest
+// first: by the least possible distance between points of the two cells, so
+// that core counting meets min_pts early.  Entry = (dx+2) | (dy+2) << 3 |
+// (dz+2) << 6.
+__device__ const unsigned short kNbOrder3[125] = {
+    146, 82, 138, 145, 147, 154, 210, 74, 81, 83, 90, 137, 139, 153, 155, 202, 209, 211, 218, 73,
+    75, 89, 91, 201, 203, 217, 219, 18, 130, 144, 148, 162, 274, 10, 17, 19, 26, 66, 80, 84,
+    98, 129, 131, 136, 140, 152, 156, 161, 163, 194, 208, 212, 226, 266, 273, 275, 282, 9, 11, 25,
+    27, 65, 67, 72, 76, 88, 92, 97, 99, 193, 195, 200, 204, 216, 220, 225, 227, 265, 267, 281,
+    283, 2, 16, 20, 34, 128, 132, 160, 164, 258, 272, 276, 290, 1, 3, 8, 12, 24, 28, 33,
+    35, 64, 68, 96, 100, 192, 196, 224, 228, 257, 259, 264, 268, 280, 284, 289, 291, 0, 4, 32,
+    36, 256, 260, 288, 292};
+
 template <int p>
 __device__ __forceinline__ bool nb_pred_t(const float* za, const float* zb, float eps2) {
   const float dx = __fsub_rn(za[0], zb[0]);
@@ -756,8 +769,17 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
         int whole = 0, ob = -1;
         bool scan = false;
         if (of < nofs) {
-          const int nx = cx + of % side - R, ny = cy + (of / side) % side - R;
-          const int nz = p == 3 ? cz + of / (side * side) - R : 0;
+          int nx, ny, nz = 0;
+          if (p == 3 && R == 2) {   // nearest cells first
+            const int code = __ldg(&kNbOrder3[of]);
+            nx = cx + (code & 7) - 2;
+            ny = cy + ((code >> 3) & 7) - 2;
+            nz = cz + (code >> 6) - 2;
+          } else {
+            nx = cx + of % side - R;
+            ny = cy + (of / side) % side - R;
+            if (p == 3) nz = cz + of / (side * side) - R;
+          }
           if (nx >= 0 && ny >= 0 && nz >= 0 && nx < G && ny < G && (p != 3 || nz < G)) {
             ob = map[(nz * G + ny) * G + nx];
             if (ob >= 0) {
@@ -811,9 +833,12 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    with core points (cells dealt round the cluster's warps): the lanes
   //    screen the neighbour offsets in parallel (B > A with core points, core
   //    boxes within eps, not yet joined) and the warp searches each surviving
-  //    pair for a core pair within eps (non-core positions hold ~index).
-  {
-    const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
+  //    pair for a core pair within eps (non-core positions hold ~index).  In
+  //    2-D, two rounds: touching cells (offsets within 1) first, then the
+  //    cells two apart, most of which are joined by then and need no search.
+  const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
+  for (int ring = p == 3 ? R : 1; ring <= R; ++ring) {   // (3-D: one round)
+    if (ring > 1) cluster.sync();   // the touching cells' unions are done
     for (int A = rank * nwarp + wid; A < n_occ; A += CL * nwarp) {
       if (opar[A] < 0) continue;
       const int cA = ocell[A];
@@ -828,7 +853,9 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           const int ox = of % side - R, oy = (of / side) % side - R;
           const int oz = p == 3 ? of / (side * side) - R : 0;
           const int bx = ax + ox, by = ay + oy, bz = az + oz;
-          if (bx >= 0 && by >= 0 && bz >= 0 && bx < G && by < G && (p != 3 || bz < G)) {
+          const int cheb = max(max(abs(ox), abs(oy)), abs(oz));
+          const bool in_ring = p == 3 || (ring < R ? cheb <= ring : cheb >= ring);
+          if (in_ring && bx >= 0 && by >= 0 && bz >= 0 && bx < G && by < G && (p != 3 || bz < G)) {
             B = map[(bz * G + by) * G + bx];
             if (B > A && opar[B] >= 0) {
               float s2 = 0.f;
@@ -850,29 +877,48 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           int joined = 0;
           if (lane == 0) joined = cfind(opar0, A) == cfind(opar0, Bc);
           if (__shfl_sync(FULL, joined, 0)) continue;   // warp-uniform decision
-          // one point of the smaller cell at a time (warp-uniform); the lanes
-          // test 32 points of the other cell per step
+          // the smaller cell's core points within eps of the other cell's core
+          // box are found 32 at a time (lane-parallel screening); each of them
+          // in turn (warp-uniform) is tested against 32 points of the other
+          // cell per step
           int X = A, Y = Bc;
           if (ostart[Bc + 1] - ostart[Bc] < ostart[A + 1] - ostart[A]) { X = Bc; Y = A; }
           bool found = false;
-          for (int px = ostart[X]; px < ostart[X + 1] && !found; ++px) {
-            if (w.sorted[px] < 0) continue;
-            float za[3];
+          for (int px0 = ostart[X]; px0 < ostart[X + 1] && !found; px0 += 32) {
+            const int pxl = px0 + lane;
+            bool cnd = false;
+            float zx[3] = {0.f, 0.f, 0.f};
+            if (pxl < ostart[X + 1] && w.sorted[pxl] >= 0) {
 #pragma unroll
-            for (int q = 0; q < p; ++q) za[q] = w.zs[(size_t)q * w.ld_s + px];
-            float n2, f2;
-            box_dist2<p>(za, ocbox + Y, S, &n2, &f2);
-            if (n2 > near_no) continue;
-            for (int py0 = ostart[Y]; py0 < ostart[Y + 1]; py0 += 32) {
-              const int py = py0 + lane;
-              bool hit = false;
-              if (py < ostart[Y + 1] && w.sorted[py] >= 0) {
-                float zb[3];
+              for (int q = 0; q < p; ++q) zx[q] = w.zs[(size_t)q * w.ld_s + pxl];
+              float n2, f2;
+              box_dist2<p>(zx, ocbox + Y, S, &n2, &f2);
+              cnd = n2 <= near_no;
+            }
+            unsigned cb = __ballot_sync(FULL, cnd);
+            // a long search stops once other warps have joined the two cells
+            if (cb && px0 > ostart[X]) {
+              int jn = 0;
+              if (lane == 0) jn = cfind(opar0, A) == cfind(opar0, Bc);
+              if (__shfl_sync(FULL, jn, 0)) break;
+            }
+            while (cb && !found) {
+              const int src = __ffs(cb) - 1;
+              cb &= cb - 1;
+              float za[3];
 #pragma unroll
-                for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + py];
-                hit = nb_pred_t<p>(za, zb, eps2);
+              for (int q = 0; q < p; ++q) za[q] = __shfl_sync(FULL, zx[q], src);
+              for (int py0 = ostart[Y]; py0 < ostart[Y + 1]; py0 += 32) {
+                const int py = py0 + lane;
+                bool hit = false;
+                if (py < ostart[Y + 1] && w.sorted[py] >= 0) {
+                  float zb[3];
+#pragma unroll
+                  for (int q = 0; q < p; ++q) zb[q] = w.zs[(size_t)q * w.ld_s + py];
+                  hit = nb_pred_t<p>(za, zb, eps2);
+                }
+                if (__any_sync(FULL, hit)) { found = true; break; }
               }
-              if (__any_sync(FULL, hit)) { found = true; break; }
             }
           }
           if (found && lane == 0 && !cunion(opar0, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
@@ -955,7 +1001,6 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    stops once that bound reaches the best id found.  No core neighbour:
   //    noise.
   const int n_border = wsum[32];
-  const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
   for (int ib = wid; ib < n_border; ib += nwarp) {
     const int a = w.cell[i0 + ib];
     float za[3];

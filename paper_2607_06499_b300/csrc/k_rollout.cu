@@ -515,7 +515,7 @@ __global__ void k_normals(unsigned long long seed, unsigned long long counter, i
 // ------------------------------------------------------------------ launchers
 int rollout_threads(int dyn) { return dyn == CE_DYN_ARM6_KIN ? kArmWarps * 32 : kRolloutThreads; }
 
-void launch_tracks(const KArgs& a, cudaStream_t s) { k_tracks<<<a.n_inst, 256, 0, s>>>(a); }
+void launch_tracks(const KArgs& a, cudaStream_t s) { k_tracks<<<a.n_inst, 1024, 0, s>>>(a); }
 
 void configure_rollout() {
   cudaFuncSetAttribute(k_rollout2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
