@@ -56,6 +56,10 @@ WORKLOADS = {
 METRIC = "CE-MPPI replan throughput (rollout-steps/s)"
 UNIT = "rollout-steps/s"
 STAGES = ("tracks", "rollout", "prune", "dbscan", "select", "update")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout
+# launch over the workload's instances, from one ncu capture of the current
+# kernel on this workload; issue-slot use of the same capture.
+ROLLOUT_NCU = {"unicycle": {"traffic": 62.76e6, "issue_active": 0.735}}
 EPISODE = 200   # closed-loop replans per episode
 
 
@@ -568,7 +572,9 @@ def main() -> None:
         "modes_last_step": modes,
         "roofline": {"kernel": "k_rollout_arm" if cfg0["dyn"] == pkg.DYN_ARM else "k_rollout2d<unicycle>",
                      "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": ROLLOUT_NCU.get(args.workload, {}).get("traffic"),
+                     "issue_active_ncu": ROLLOUT_NCU.get(args.workload, {}).get("issue_active"),
                      "peak_kind": f"FP32 lanes x 2 x max SM clock ({pk_kind} clock)",
                      "flops_per_rollout": flops_per_rollout,
                      "obstacle_tests_per_rollout": tests_per_rollout},
