@@ -138,9 +138,11 @@ void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const 
   a.tprefix = pre_roll;
   a.n_tiles = n_roll;
   launch_rollout(dyn, a, smem_roll, s);
-  launch_prune(a, s);
-  launch_dbscan(a, max_cells, s);
-  launch_select(a, s);
+  if (!launch_post(a, max_cells, s)) {
+    launch_prune(a, s);
+    launch_dbscan(a, max_cells, s);
+    launch_select(a, s);
+  }
   a.tiles = tupd;
   a.tprefix = pre_upd;
   a.n_tiles = n_upd;

@@ -31,6 +31,7 @@ struct Ctl {
   float S_min, invZ;
   float S_absmax_V, S_min_V, S_min_all;   // over V / over all K (written by the prune stage)
   int nnz;                        // nonzero update weights listed (-1: more than kSparseMax)
+  int updated;                    // the update was applied by the fused per-instance kernel
   float pbar[3], v_obs[3], p0[3];
   unsigned int done;              // last-CTA ticket of the update stage
   int col_tests;                  // circle/sphere tests per rollout after reach culling
@@ -318,6 +319,9 @@ void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s);
 void launch_prune(const KArgs& a, cudaStream_t s);
 void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s);
 void launch_select(const KArgs& a, cudaStream_t s);
+// prune + DBSCAN + selection (+ the update with few nonzero weights) as one
+// clustered launch; false when the shared memory does not allow it
+bool launch_post(const KArgs& a, int max_cells, cudaStream_t s);
 void launch_update(const KArgs& a, cudaStream_t s);
 void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
                    unsigned int* out, cudaStream_t s);

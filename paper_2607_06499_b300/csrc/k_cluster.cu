@@ -6,6 +6,7 @@
 // K alone (thread t takes elements t, t + blockDim, ...; fixed shuffle trees),
 // and per-cluster sums use exact int64 fixed-point atomics, so a replan gives
 // the same bits alone and inside any batch.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "ce_mppi_internal.cuh"
@@ -68,7 +69,7 @@ __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, fl
 // C_col, each k's position in V and S in V order, and sums the terminal
 // positions for pbar; the CTAs exchange those partial sums (added in rank
 // order: deterministic); pass 3 writes the features.
-__global__ void __maxnreg__(64) k_prune(KArgs a) {
+__device__ __forceinline__ void prune_stage(const KArgs& a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int inst = blockIdx.x / CL;
@@ -351,6 +352,8 @@ __global__ void __maxnreg__(64) k_prune(KArgs a) {
     }
   }
 }
+
+__global__ void __maxnreg__(64) k_prune(KArgs a) { prune_stage(a); }
 
 // ========================================================================= DBSCAN
 // Grid-binned DBSCAN over n points z ([p][ld], coordinates in [-1, 1]).  The
@@ -1065,8 +1068,7 @@ __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
 }
 
 // One cluster per instance; rank 0 publishes the cluster count and the mode.
-__global__ void __maxnreg__(64) k_dbscan(KArgs a) {
-  extern __shared__ int smem_i[];
+__device__ __forceinline__ void dbscan_stage(const KArgs& a, int* smem_i) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int inst = blockIdx.x / CL;
@@ -1088,6 +1090,11 @@ __global__ void __maxnreg__(64) k_dbscan(KArgs a) {
     ctl->M = M;
     if (M == 0) ctl->mode = CE_MODE_ALLNOISE;
   }
+}
+
+__global__ void __maxnreg__(64) k_dbscan(KArgs a) {
+  extern __shared__ int smem_i[];
+  dbscan_stage(a, smem_i);
 }
 
 __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int ld, int p,
@@ -1129,19 +1136,32 @@ constexpr int kSlots = 2;   // per-warp label cache of the cluster statistics
 // shared memory atomics: exact, order-free); rank 0 evaluates the criterion.
 // The weights pass splits its domain into kPruneRanges fixed ranges whose
 // normaliser partials are added in range order, so Z does not depend on CL.
-__global__ void __maxnreg__(64) k_select(KArgs a) {
+struct SelSmem {
+  unsigned long long accS[kWin], accG[3][kWin];
+  int accN[kWin];
+  unsigned int accM[kWin];
+  int lk[kSparseMax];
+  float le[kSparseMax];
+};
+
+// fused: called after the DBSCAN stage in the same kernel; with few nonzero
+// weights rank 0 then also applies the update and finalizes the replan.
+__device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const InstDesc& d, int inst);
+
+__device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool fused) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int inst = blockIdx.x / CL;
   const InstDesc& d = desc_of(a, inst);
   Ctl* ctl = d.ctl;
-  __shared__ unsigned long long accS[kWin], accG[3][kWin];
-  __shared__ int accN[kWin];
-  __shared__ unsigned int accM[kWin];
+  unsigned long long* accS = sm.accS;
+  unsigned long long (*accG)[kWin] = sm.accG;
+  int* accN = sm.accN;
+  unsigned int* accM = sm.accM;
+  int* lk = sm.lk;
+  float* le = sm.le;
   __shared__ float red[33];
   __shared__ unsigned long long bestkey;
-  __shared__ int lk[kSparseMax];
-  __shared__ float le[kSparseMax];
   __shared__ int lcount;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int K = d.K, Kp = d.Kp, p = d.p;
@@ -1391,9 +1411,34 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
     ctl->invZ = 1.0f / red[32];
     ctl->nnz = nl <= kSparseMax ? nl : -1;
   }
+  if (fused && nl <= kSparseMax) {
+    __syncthreads();
+    update_sparse_finalize(a, d, inst);
+  }
+}
+
+__global__ void __maxnreg__(64) k_select(KArgs a) {
+  __shared__ SelSmem sm;
+  select_stage(a, sm, false);
+}
+
+// ========================================================================= fused
+// Prune, DBSCAN and selection of one instance in one cluster launch: the
+// stages follow each other at cluster barriers instead of kernel boundaries,
+// each instance at its own pace.  The selection's accumulators reuse the
+// DBSCAN tables' shared memory.
+__global__ void __maxnreg__(64) k_post(KArgs a) {
+  extern __shared__ __align__(16) int smem_post[];
+  cg::cluster_group cluster = cg::this_cluster();
+  prune_stage(a);
+  cluster.sync();   // lists, features and the control block of the instance
+  dbscan_stage(a, smem_post);
+  cluster.sync();   // labels, cluster count and mode; DBSCAN tables no longer read
+  select_stage(a, *reinterpret_cast<SelSmem*>(smem_post), true);
 }
 
 // ========================================================================= update
+__device__ void finalize(const InstDesc& d, const Req& r);
 // Eq. 20 / Eq. 7: U_new[c] = U[c] + sum_k w_k eps'[c][k] (Kahan, fixed order),
 // then, in the last CTA of the instance, the outputs, the receding-horizon
 // shift of the nominal, x_next = f(x0, u_0), the diagnostics and the counter.
@@ -1449,11 +1494,35 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
 // Arm layout eps[Kp][T*m]: tile = (32 columns, 512 rollouts), lanes over the
 // columns, warps over k.  Each tile writes its partial sums; the last tile of
 // the instance adds them in chunk order (deterministic) and finalizes.
+// The fused per-instance kernel's update when at most kSparseMax weights are
+// nonzero (rank 0 of the cluster, all columns): U_new[c] = U[c] + (1/Z) sum_j
+// w_j eps'[c][k_j] over the list in ascending k (Kahan), then finalize.
+__device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const InstDesc& d,
+                                                       int inst) {
+  Ctl* ctl = d.ctl;
+  const int TM = d.T * d.m, nnz = ctl->nnz;
+  const bool arm = d.dyn == CE_DYN_ARM6_KIN;
+  const float iz = ctl->invZ;
+  for (int c = threadIdx.x; c < TM; c += blockDim.x) {
+    float s = 0.f, e = 0.f;
+    for (int j = 0; j < nnz; ++j) {
+      const int k = d.nzk[j];
+      const float x = arm ? d.eps[(size_t)k * d.eps_ld_k + c] : d.eps[(size_t)c * d.eps_ld_c + k];
+      kahan_add(s, e, d.nze[j] * x);
+    }
+    d.Unew[c] = d.U[c] + s * iz;
+  }
+  __syncthreads();
+  finalize(d, req_of(a, inst));
+  if (threadIdx.x == 0) ctl->updated = 1;
+}
+
 __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   __shared__ float part[kUpdateWarps][32];
   __shared__ int last;
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
+  if (d.ctl->updated) return;   // done by the fused per-instance kernel
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int K = d.K, TM = d.T * d.m;
   const bool arm = d.dyn == CE_DYN_ARM6_KIN;
@@ -1567,7 +1636,7 @@ struct ClusterFit {
 template <typename... Args>
 static ClusterFit query_fit(void (*kern)(Args...), int threads, size_t smem) {
   ClusterFit f;
-  for (int i = 1; i < 4; ++i) {
+  for (int i = 0; i < 4; ++i) {
     const int cl = 1 << i;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cl);
@@ -1629,6 +1698,19 @@ void launch_prune(const KArgs& a, cudaStream_t s) {
 
 static size_t dbscan_smem(int nc) { return dbscan_smem_bytes(nc); }
 
+static ClusterFit g_fit_post[2];
+static size_t post_smem(int nc) { return std::max(dbscan_smem(nc), sizeof(SelSmem)); }
+
+bool launch_post(const KArgs& a, int max_cells, cudaStream_t s) {
+  const size_t smem = post_smem(max_cells);
+  if (smem > post_smem(kMaxCells)) return false;
+  const ClusterFit& f = smem <= post_smem(1024) ? g_fit_post[0] : g_fit_post[1];
+  if (f.max_active[0] == 0) return false;   // (the launch would not fit)
+  const int cl = cluster_ctas(f, a.n_conc > 0 ? a.n_conc : a.n_inst);
+  launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, a);
+  return true;
+}
+
 void configure_cluster() {
   g_fit_prune = query_fit(k_prune, kBlock, 0);
   g_fit_select = query_fit(k_select, kBlock, 0);
@@ -1638,6 +1720,10 @@ void configure_cluster() {
                        (int)dbscan_smem(kMaxCells));
   g_fit_db[0] = query_fit(k_dbscan, kBlock, dbscan_smem(1024));
   g_fit_db[1] = query_fit(k_dbscan, kBlock, dbscan_smem(kMaxCells));
+  cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)post_smem(kMaxCells));
+  g_fit_post[0] = query_fit(k_post, kBlock, post_smem(1024));
+  g_fit_post[1] = query_fit(k_post, kBlock, post_smem(kMaxCells));
 }
 
 void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s) {

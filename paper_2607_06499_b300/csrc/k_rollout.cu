@@ -38,6 +38,7 @@ __global__ void k_tracks(KArgs a) {
   if (threadIdx.x == 0) {   // a new replan: clear the control block's flags
     d.ctl->status = 0;
     d.ctl->done = 0u;
+    d.ctl->updated = 0;
   }
   if (d.dyn == CE_DYN_ARM6_KIN) {
     const int total = (T + 1) * n_obs;
