@@ -256,14 +256,16 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
       if (h < n_obs) { first = h; first_j = 0; }
     }
     int e_hi = off[j + 1] - base;   // end of row j + 1's entries is off[j + 2]
-    for (; act && j < jb - 1 && j < T; ++j) {
-      if ((j & 1) == 0) z4 = philox_normals(d, ctr, k, j >> 1);
-      const float z0 = (j & 1) ? z4.z : z4.x, z1 = (j & 1) ? z4.w : z4.y;
-      const float n0 = Us[2 * j], n1 = Us[2 * j + 1];
+    const int jend = act ? min(jb - 1, T) : j;
+    float* ep = eps + (size_t)(2 * j) * Kp + k;   // eps' of step j (advances 2 Kp a step)
+    // one horizon step with normals (z0, z1)
+    auto step = [&](int jj, float z0, float z1) {
+      const float n0 = Us[2 * jj], n1 = Us[2 * jj + 1];
       const float u0 = fminf(fmaxf(n0 + sg0 * z0, lo0), hi0);
       const float u1 = fminf(fmaxf(n1 + sg1 * z1, lo1), hi1);
-      eps[(size_t)(2 * j) * Kp + k] = u0 - n0;
-      eps[(size_t)(2 * j + 1) * Kp + k] = u1 - n1;
+      ep[0] = u0 - n0;
+      ep[Kp] = u1 - n1;
+      ep += 2 * (size_t)Kp;
       if (DYN == 0) {
         const float ex = s0 - g0, ey = s1 - g1;
         kahan_add(S, Sc, w0 * (ex * ex + ey * ey) + w1 * (u0 * u0 + u1 * u1));
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
         s2 += u1 * dt;
       }
       const int e_lo = e_hi;
-      e_hi = off[j + 2] - base;
+      e_hi = off[jj + 2] - base;
       if (first < 0) {
         int h = n_obs;
         for (int e = e_hi - 1; e >= e_lo; --e) {   // descending: the lowest index wins
@@ -293,8 +295,25 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
           const float dx = s0 - t.x, dy = s1 - t.y;
           h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
         }
-        if (h < n_obs) { first = h; first_j = j + 1; }
+        if (h < n_obs) { first = h; first_j = jj + 1; }
       }
+    };
+    // normals 2j, 2j+1 of step j are elements (2j) % 4, (2j) % 4 + 1 of
+    // Philox block j / 2: two steps per block
+    if (j < jend && (j & 1)) {   // a run that starts on an odd step
+      z4 = philox_normals(d, ctr, k, j >> 1);
+      step(j, z4.z, z4.w);
+      ++j;
+    }
+    for (; j + 1 < jend; j += 2) {
+      z4 = philox_normals(d, ctr, k, j >> 1);
+      step(j, z4.x, z4.y);
+      step(j + 1, z4.z, z4.w);
+    }
+    if (j < jend) {
+      z4 = philox_normals(d, ctr, k, j >> 1);
+      step(j, z4.x, z4.y);
+      ++j;
     }
     ja = jb;
   }
