@@ -174,7 +174,9 @@ __device__ __forceinline__ float4 normals4(uint4 w) {
   const float s23 = 1.1920928955078125e-7f;  // 2^-23
   const float u1a = ((float)(w.x >> 9) + 0.5f) * s23, u2a = ((float)(w.y >> 9) + 0.5f) * s23;
   const float u1b = ((float)(w.z >> 9) + 0.5f) * s23, u2b = ((float)(w.w >> 9) + 0.5f) * s23;
-  const float ra = sqrtf(-2.0f * logf(u1a)), rb = sqrtf(-2.0f * logf(u1b));
+  // sqrt(x) as x * rsqrt(x) (x >= 2^-23 > 0 here; rsqrtf is within 2 ulp)
+  const float xa = -2.0f * logf(u1a), xb = -2.0f * logf(u1b);
+  const float ra = xa * rsqrtf(xa), rb = xb * rsqrtf(xb);
   float sa, ca, sb, cb;
   sincospif(2.0f * u2a, &sa, &ca);
   sincospif(2.0f * u2b, &sb, &cb);

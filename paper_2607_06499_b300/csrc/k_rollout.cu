@@ -282,8 +282,9 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
         // sequence in the kernel's innermost loop)
         float sn, cs;
         __sincosf(s2, &sn, &cs);
-        s0 += u0 * cs * dt;
-        s1 += u0 * sn * dt;
+        const float vdt = u0 * dt;
+        s0 += vdt * cs;
+        s1 += vdt * sn;
         s2 += u1 * dt;
       }
       const int e_lo = e_hi;
