@@ -359,6 +359,8 @@ def main() -> None:
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served run (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--noise-regen", type=int, default=0, choices=[0, 1],
+                    help="1: perturbations not stored, drawn again by the update")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -397,7 +399,8 @@ def main() -> None:
     EPISODE = wl["episode"]
     N_INST = wl["n"]
     seeds = shard_seeds(rank, N_INST)
-    scenes = [W.make(wl["scene"], seed=s, n_replans=EPISODE + 8) for s in seeds]
+    scenes = [W.make(wl["scene"], seed=s, n_replans=EPISODE + 8, noise_regen=args.noise_regen)
+              for s in seeds]
     cfg0 = scenes[0]["cfg"]
     m = pkg.DIMS[cfg0["dyn"]][1]
     p_dim = pkg.DIMS[cfg0["dyn"]][2]
@@ -562,7 +565,7 @@ def main() -> None:
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank",
-                       branches=args.branches),
+                       branches=args.branches, noise_regen=args.noise_regen),
         "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),

@@ -89,6 +89,10 @@ typedef struct {
   int ref_mode;          /* 0: colliding rollouts whose first hit is the closest   */
                          /*    hit obstacle (the method overview); 1: all of C_col */
   int check_j0;          /* 1: the current state x_0 also counts for collisions    */
+  int noise_regen;       /* 0: the rollouts store eps' (K*T*m floats) for the      */
+                         /*    update; 1: nothing is stored, the update draws the  */
+                         /*    same Philox numbers again for the rollouts of       */
+                         /*    nonzero weight (less memory; peek of EPS refused)   */
 } ce_mppi_params;
 
 /* Per-replan diagnostics. */

@@ -39,7 +39,7 @@ class Params(C.Structure):
         ("u_max", C.c_float * 6), ("goal", C.c_float * 16), ("w", C.c_float * 8),
         ("n_obs_max", C.c_int), ("hist_len", C.c_int), ("robot_radius", C.c_float),
         ("norm_eps", C.c_float), ("v_static_thresh", C.c_float), ("seed", C.c_ulonglong),
-        ("ref_mode", C.c_int), ("check_j0", C.c_int),
+        ("ref_mode", C.c_int), ("check_j0", C.c_int), ("noise_regen", C.c_int),
     ]
 
 
@@ -154,6 +154,7 @@ def make_params(cfg: dict, n_obs_max: int) -> Params:
     P.robot_radius, P.norm_eps = cfg["robot_radius"], cfg["norm_eps"]
     P.v_static_thresh, P.seed = cfg["v_static_thresh"], cfg["seed"]
     P.ref_mode, P.check_j0 = cfg.get("ref_mode", 0), cfg.get("check_j0", 0)
+    P.noise_regen = cfg.get("noise_regen", 0)
     return P
 
 

@@ -98,6 +98,8 @@ ce_status_t validate(const ce_mppi_params* P) {
     return fail(CE_MPPI_ERR_INVALID_ARG, "v_static_thresh must be >= 0");
   if (P->ref_mode < 0 || P->ref_mode > 1) return fail(CE_MPPI_ERR_INVALID_ARG, "ref_mode must be 0 or 1");
   if (P->check_j0 < 0 || P->check_j0 > 1) return fail(CE_MPPI_ERR_INVALID_ARG, "check_j0 must be 0 or 1");
+  if (P->noise_regen < 0 || P->noise_regen > 1)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "noise_regen must be 0 or 1");
   int n, m, p;
   dims_of(P->dyn, &n, &m, &p);
   for (int i = 0; i < m; ++i) {
@@ -158,7 +160,8 @@ bool same_layout(const ce_mppi_handle* h, const ce_mppi_params* P) {
   dims_of(P->dyn, &n, &m, &p);
   dbscan_grid(P->dbscan_eps, p, &ci, &G, &R, &nc);
   return P->dyn == h->P.dyn && P->K == h->P.K && P->T == h->P.T &&
-         P->n_obs_max == h->P.n_obs_max && P->hist_len == h->P.hist_len && nc == h->ncells;
+         P->n_obs_max == h->P.n_obs_max && P->hist_len == h->P.hist_len && nc == h->ncells &&
+         P->noise_regen == h->P.noise_regen;
 }
 
 ce_status_t handle_retarget(ce_mppi_handle* h, const ce_mppi_params* P) {
@@ -211,7 +214,7 @@ void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h)
   dbscan_grid(P->dbscan_eps, h->p, &ci, &G, &R, &nc);
   d.dyn = P->dyn; d.K = K; d.Kp = Kp; d.T = P->T; d.m = h->m; d.n = h->n; d.p = h->p;
   d.n_obs_max = P->n_obs_max; d.H = P->hist_len; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
-  d.check_j0 = P->check_j0; d.G = G; d.R = R;
+  d.check_j0 = P->check_j0; d.G = G; d.R = R; d.regen = P->noise_regen;
   d.eps_ld_c = P->dyn == CE_DYN_ARM6_KIN ? 1 : Kp;
   d.eps_ld_k = P->dyn == CE_DYN_ARM6_KIN ? h->TMp : 1;
   d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;
@@ -270,7 +273,8 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
                o_zpart = take(4 * kPruneRanges);
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
-  const size_t eps_elems = P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
+  const size_t eps_elems = P->noise_regen ? 0
+                          : P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
   const size_t o_eps = take(4 * eps_elems);
   size_t o_int[9];
   for (int i = 0; i < 9; ++i) o_int[i] = take(4 * Kp);
@@ -314,7 +318,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.z = reinterpret_cast<float*>(b + o_z);
   d.g = reinterpret_cast<float*>(b + o_g);
   d.zs = reinterpret_cast<float*>(b + o_zs);
-  d.eps = reinterpret_cast<float*>(b + o_eps);
+  d.eps = P->noise_regen ? nullptr : reinterpret_cast<float*>(b + o_eps);
   int** ints[9] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent,
                    &d.vpos};
   for (int i = 0; i < 9; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
@@ -720,6 +724,7 @@ ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* dst, size_t bytes) 
     return CE_MPPI_OK;
   }
   if (which == CE_BUF_EPS) {
+    if (!d.eps) return fail(CE_MPPI_ERR_INVALID_ARG, "peek: eps' is not stored (noise_regen)");
     if (want(4 * K * TM) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
     float* o = static_cast<float*>(dst);
     if (h->P.dyn == CE_DYN_ARM6_KIN) {

@@ -50,6 +50,7 @@ struct Ctl {
 //   eps    2-D: float [T*m][Kp] (k fastest); arm: float [Kp][T*m] (k slowest)
 struct InstDesc {
   int dyn, K, Kp, T, m, n, p, n_obs_max, H, min_pts, ref_mode, check_j0;
+  int regen;                      // eps' is not stored: the update draws it again
   int G, R, eps_ld_c, eps_ld_k;   // DBSCAN grid size/reach; eps strides (column, rollout)
   float dt, obs_dt, inv_lambda, eps2, cell_inv, robot_radius, norm_eps, v_static_thresh;
   float sigma[6], u_min[6], u_max[6], goal[16], w[8];
@@ -187,6 +188,25 @@ __device__ __forceinline__ float4 philox_normals(const InstDesc& d, unsigned lon
                                                  int k, int b) {
   const uint4 c = make_uint4((uint32_t)k, (uint32_t)b, (uint32_t)ctr, (uint32_t)(ctr >> 32));
   return normals4(philox10(c, make_uint2(d.seed_lo, d.seed_hi)));
+}
+
+// The sampled control clip(u + sigma z) of Eq. 3 (the rollouts and the
+// regenerating update share this one expression, so both round alike).
+__device__ __forceinline__ float sampled_control(float nom, float sg, float z, float lo,
+                                                 float hi) {
+  return fminf(fmaxf(nom + sg * z, lo), hi);
+}
+
+// eps' of rollout k, column c (step c / m, input c % m) drawn again: normal
+// c of rollout k is element c % 4 of Philox block c / 4 for every robot.
+__device__ __forceinline__ float eps_regen(const InstDesc& d, unsigned long long ctr, int k,
+                                           int c) {
+  const float4 z4 = philox_normals(d, ctr, k, c >> 2);
+  const int e = c & 3;
+  const float z = e == 0 ? z4.x : e == 1 ? z4.y : e == 2 ? z4.z : z4.w;
+  const int q = c % d.m;
+  const float nom = d.U[c];
+  return sampled_control(nom, d.sigma[q], z, d.u_min[q], d.u_max[q]) - nom;
 }
 
 // ---------------------------------------------------------------- TMA bulk copy

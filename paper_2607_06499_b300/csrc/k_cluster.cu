@@ -1503,11 +1503,14 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
   const int TM = d.T * d.m, nnz = ctl->nnz;
   const bool arm = d.dyn == CE_DYN_ARM6_KIN;
   const float iz = ctl->invZ;
+  const unsigned long long ctr = *d.counter;
   for (int c = threadIdx.x; c < TM; c += blockDim.x) {
     float s = 0.f, e = 0.f;
     for (int j = 0; j < nnz; ++j) {
       const int k = d.nzk[j];
-      const float x = arm ? d.eps[(size_t)k * d.eps_ld_k + c] : d.eps[(size_t)c * d.eps_ld_c + k];
+      const float x = d.regen ? eps_regen(d, ctr, k, c)
+                      : arm   ? d.eps[(size_t)k * d.eps_ld_k + c]
+                              : d.eps[(size_t)c * d.eps_ld_c + k];
       kahan_add(s, e, d.nze[j] * x);
     }
     d.Unew[c] = d.U[c] + s * iz;
@@ -1534,6 +1537,7 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   const float* __restrict__ w = d.w_k;
   const float* __restrict__ eps = d.eps;
   const int nnz = d.ctl->nnz;
+  const unsigned long long ctr = *d.counter;   // this replan's (finalize advances it)
   if (nnz >= 0) {
     // few nonzero weights, listed by ascending k: the tiles of the first
     // rollout chunk sum over the list, the others contribute zeros
@@ -1542,8 +1546,11 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
       if (c < TM) {
         float s = 0.f, e = 0.f;
         if (kc == 0) {
-          const float* col = eps + (size_t)c * d.eps_ld_c;
-          for (int j = lane; j < nnz; j += 32) kahan_add(s, e, d.nze[j] * col[d.nzk[j]]);
+          const float* col = d.regen ? nullptr : eps + (size_t)c * d.eps_ld_c;
+          for (int j = lane; j < nnz; j += 32) {
+            const int k = d.nzk[j];
+            kahan_add(s, e, d.nze[j] * (col ? col[k] : eps_regen(d, ctr, k, c)));
+          }
           s = warp_sum(s);
         }
         if (lane == 0) d.upart[(size_t)kc * d.TMp + c] = s;
@@ -1552,8 +1559,11 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
       const int c = c0 + lane;
       float s = 0.f, e = 0.f;
       if (kc == 0 && c < TM)
-        for (int j = wid; j < nnz; j += kUpdateWarps)
-          kahan_add(s, e, d.nze[j] * eps[(size_t)d.nzk[j] * d.eps_ld_k + c]);
+        for (int j = wid; j < nnz; j += kUpdateWarps) {
+          const int k = d.nzk[j];
+          kahan_add(s, e, d.nze[j] * (d.regen ? eps_regen(d, ctr, k, c)
+                                               : eps[(size_t)k * d.eps_ld_k + c]));
+        }
       part[wid][lane] = s;
       __syncthreads();
       if (wid == 0 && c < TM) {
@@ -1572,17 +1582,19 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
       // subtracted, exp underflows to exactly 0 for most rollouts at small
       // lambda, and their sectors are never fetched (adding 0 keeps the sums'
       // bits as if they were).
+      // eps' stored, or drawn again (same order of the sums either way)
+      auto val = [&](int kk) { return d.regen ? eps_regen(d, ctr, kk, c) : col[kk]; };
       for (; k + 96 < k1; k += 128) {
         float wk[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) wk[u] = w[k + 32 * u];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          kahan_add(s[u], e[u], wk[u] != 0.f ? wk[u] * col[k + 32 * u] : 0.f);
+          kahan_add(s[u], e[u], wk[u] != 0.f ? wk[u] * val(k + 32 * u) : 0.f);
       }
       for (; k < k1; k += 32) {
         const float wk = w[k];
-        kahan_add(s[0], e[0], wk != 0.f ? wk * col[k] : 0.f);
+        kahan_add(s[0], e[0], wk != 0.f ? wk * val(k) : 0.f);
       }
       float t = (s[0] + s[1]) + (s[2] + s[3]);
       t = warp_sum(t);
@@ -1594,7 +1606,8 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
     if (c < TM)
       for (int k = k0 + wid; k < k1; k += kUpdateWarps) {
         const float wk = w[k];   // warp-uniform: rows of zero weight are skipped
-        if (wk != 0.f) kahan_add(s, e, wk * eps[(size_t)k * d.eps_ld_k + c]);
+        if (wk != 0.f)
+          kahan_add(s, e, wk * (d.regen ? eps_regen(d, ctr, k, c) : eps[(size_t)k * d.eps_ld_k + c]));
       }
     part[wid][lane] = s;
     __syncthreads();

@@ -257,15 +257,18 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
     }
     int e_hi = off[j + 1] - base;   // end of row j + 1's entries is off[j + 2]
     const int jend = act ? min(jb - 1, T) : j;
-    float* ep = eps + (size_t)(2 * j) * Kp + k;   // eps' of step j (advances 2 Kp a step)
+    const bool store = !d.regen;
+    float* ep = store ? eps + (size_t)(2 * j) * Kp + k : nullptr;   // eps' of step j (advances 2 Kp a step)
     // one horizon step with normals (z0, z1)
     auto step = [&](int jj, float z0, float z1) {
       const float n0 = Us[2 * jj], n1 = Us[2 * jj + 1];
-      const float u0 = fminf(fmaxf(n0 + sg0 * z0, lo0), hi0);
-      const float u1 = fminf(fmaxf(n1 + sg1 * z1, lo1), hi1);
-      ep[0] = u0 - n0;
-      ep[Kp] = u1 - n1;
-      ep += 2 * (size_t)Kp;
+      const float u0 = sampled_control(n0, sg0, z0, lo0, hi0);
+      const float u1 = sampled_control(n1, sg1, z1, lo1, hi1);
+      if (store) {
+        ep[0] = u0 - n0;
+        ep[Kp] = u1 - n1;
+        ep += 2 * (size_t)Kp;
+      }
       if (DYN == 0) {
         const float ex = s0 - g0, ey = s1 - g1;
         kahan_add(S, Sc, w0 * (ex * ex + ey * ey) + w1 * (u0 * u0 + u1 * u1));
@@ -452,8 +455,8 @@ __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
       for (int i = 0; i < 6; ++i) {
         const float z = off == 0 ? zz[i] : zz[i + 2];
         const float nom = Us[j * 6 + i];
-        u[i] = fminf(fmaxf(nom + d.sigma[i] * z, d.u_min[i]), d.u_max[i]);
-        d.eps[(size_t)k * d.eps_ld_k + n0 + i] = u[i] - nom;
+        u[i] = sampled_control(nom, d.sigma[i], z, d.u_min[i], d.u_max[i]);
+        if (!d.regen) d.eps[(size_t)k * d.eps_ld_k + n0 + i] = u[i] - nom;
       }
     } else {
 #pragma unroll

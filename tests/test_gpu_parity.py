@@ -394,3 +394,37 @@ def test_host_replan_rejects_too_many_obstacles():
     with pytest.raises(pkg.CeError):
         pl.replan(sc["x0"], W.history(sc, 0), sc["radius"])
     pl.close()
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("unicycle_blocked", dict(K=2000)),                 # few nonzero weights: listed
+    ("unicycle_blocked", dict(K=2000, lam=1e4)),        # all weights nonzero: dense tiles
+    ("arm_blocked", dict(K=1000)),
+    ("arm_blocked", dict(K=1000, lam=1e4)),
+    ("di_blocked", dict(K=4099, T=17, lam=50.0)),
+])
+def test_noise_regen_same_bits(name, kw):
+    """noise_regen = 1 stores no perturbations; the update draws the same
+    Philox numbers again and gives the same bits as the stored ones."""
+    outs = []
+    kw = dict(kw)
+    lam = kw.pop("lam", None)
+    for regen in (0, 1):
+        sc = W.make(name, seed=0, noise_regen=regen, **kw)
+        cfg = sc["cfg"]
+        if lam is not None:
+            cfg["lambda"] = lam
+        pl = pkg.Planner(cfg, n_obs_max=max(1, sc["radius"].shape[0]))
+        pl.set_nominal(sc["U0"])
+        us = []
+        for r in range(3):   # successive replans: counters and shifted nominals
+            u, diag = pl.replan(sc["x0"], W.history(sc, r), sc["radius"])
+            assert diag["status"] == 0
+            us.append((u, diag["mode"], diag["n_clusters"], diag["sel_label"]))
+        if regen:
+            with pytest.raises(RuntimeError):
+                pl.peek("EPS")
+        pl.close()
+        outs.append(us)
+    for a, b in zip(*outs):
+        assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
