@@ -47,6 +47,12 @@ WORKLOADS = {
                             dyn="arm", K=4096, T=32, n_obs=20, episodes=N_EPISODES,
                             dbscan_eps=0.2, min_pts=16, lam=1.0, sigma=[0.3] * 6,
                             l2="flushed between timed steps (256 MB write)")),
+    "arm12": dict(scene="arm12", n=N_EPISODES, episode=500, u_init=None,
+                  config=dict(workload="ce-mppi replan, 12-D arm (joint accelerations) closed loop, "
+                                       "moving spheres",
+                              dyn="arm12", K=4096, T=32, n_obs=20, episodes=N_EPISODES,
+                              dbscan_eps=0.2, min_pts=16, lam=1.0, sigma=[1.0] * 6,
+                              l2="flushed between timed steps (256 MB write)")),
     "batch": dict(scene="batch_instance", n=256, episode=50, u_init=(1.0, 0.0),
                   config=dict(workload="ce-mppi replan, 256 uneven unicycle instances",
                               dyn="unicycle", K="log-uniform [512, 16384]", T="[20, 60]",
@@ -492,7 +498,7 @@ def main() -> None:
     tests = np.array(tests, dtype=np.float64).reshape(args.profile_steps, N_INST).mean(0)
     Ks = np.array([sc["cfg"]["K"] for sc in scenes], dtype=np.float64)
     Ts = np.array([sc["cfg"]["T"] for sc in scenes], dtype=np.float64)
-    if cfg0["dyn"] == pkg.DYN_ARM:
+    if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12):
         # per step: FK (6 DH transforms ~ 6*40) + 24 sphere centres (3*3*24)
         # + pose cost (~60); per sphere test 8 (3 sub, mul, 2 fma x2, compare)
         flops_roll = Ks * (Ts * (240 + 216 + 60) + 24 * 8 * tests)
@@ -573,7 +579,7 @@ def main() -> None:
         "plain": plain,
         "stage_ms": stage_ms,
         "modes_last_step": modes,
-        "roofline": {"kernel": "k_rollout_arm" if cfg0["dyn"] == pkg.DYN_ARM else "k_rollout2d<unicycle>",
+        "roofline": {"kernel": "k_rollout_arm" if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12) else "k_rollout2d<unicycle>",
                      "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": ROLLOUT_NCU.get(args.workload, {}).get("traffic"),

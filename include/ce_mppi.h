@@ -45,7 +45,9 @@ extern "C" {
 typedef enum {
   CE_DYN_DOUBLE_INT_2D = 0, /* p += v dt; v += a dt                        */
   CE_DYN_UNICYCLE = 1,      /* Sec. III-A, Eq. 21                          */
-  CE_DYN_ARM6_KIN = 2       /* q += qdot dt, UR5e-like standard DH chain   */
+  CE_DYN_ARM6_KIN = 2,      /* q += qdot dt, UR5e-like standard DH chain   */
+  CE_DYN_ARM12_DI = 3       /* 12-D (q, qdot), joint accelerations: q += qdot dt, */
+                            /* qdot += u dt (the UR5e state of Sec. III-C) */
 } ce_dyn_t;
 
 typedef enum {

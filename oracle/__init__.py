@@ -23,7 +23,7 @@ _HDR = os.path.join(_HERE, "ce_mppi_oracle.h")
 _LIB = os.path.join(_HERE, "libce_mppi_oracle.so")
 
 MODE_NOCOL, MODE_ALLCOL, MODE_ALLNOISE, MODE_STATIC, MODE_DYNAMIC = range(5)
-DIMS = {0: (4, 2, 2), 1: (3, 2, 2), 2: (6, 6, 3)}  # dyn -> (n, m, p)
+DIMS = {0: (4, 2, 2), 1: (3, 2, 2), 2: (6, 6, 3), 3: (12, 6, 3)}  # dyn -> (n, m, p)
 
 
 def build(force: bool = False) -> str:

@@ -71,9 +71,12 @@ void philox10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 // (exactly representable in FP32 as well, so both precisions see one value).
 double unit23(uint32_t w) { return ((double)(w >> 9) + 0.5) / 8388608.0; }
 
-int dim_n(int dyn) { return dyn == ORC_DI ? 4 : (dyn == ORC_UNICYCLE ? 3 : 6); }
-int dim_m(int dyn) { return dyn == ORC_ARM ? 6 : 2; }
-int dim_p(int dyn) { return dyn == ORC_ARM ? 3 : 2; }
+bool is_arm(int dyn) { return dyn == ORC_ARM || dyn == ORC_ARM12; }
+int dim_n(int dyn) {
+  return dyn == ORC_DI ? 4 : dyn == ORC_UNICYCLE ? 3 : dyn == ORC_ARM ? 6 : 12;
+}
+int dim_m(int dyn) { return is_arm(dyn) ? 6 : 2; }
+int dim_p(int dyn) { return is_arm(dyn) ? 3 : 2; }
 
 double clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -228,6 +231,9 @@ void orc_tracks(const orc_params* P, const double* hist, int n_obs, double* trac
 // x_{t+1} = f(x_t, u_t).  Double integrator: explicit Euler on (p, v) with
 // acceleration input.  Unicycle: Eq. 21 (heading advanced after the position,
 // from the old heading).  Arm: joint-velocity integrator q' = q + u dt.
+// 12-D arm (joint positions and velocities, the UR5e state of Sec. III-C):
+// explicit Euler with joint-acceleration input, q' = q + qdot dt,
+// qdot' = qdot + u dt.
 void orc_step(const orc_params* P, const double* x, const double* u, double* xn) {
   const double dt = P->dt;
   if (P->dyn == ORC_DI) {
@@ -239,14 +245,19 @@ void orc_step(const orc_params* P, const double* x, const double* u, double* xn)
     xn[0] = x[0] + u[0] * std::cos(x[2]) * dt;
     xn[1] = x[1] + u[0] * std::sin(x[2]) * dt;
     xn[2] = x[2] + u[1] * dt;
-  } else {
+  } else if (P->dyn == ORC_ARM) {
     for (int i = 0; i < 6; ++i) xn[i] = x[i] + u[i] * dt;
+  } else {
+    for (int i = 0; i < 6; ++i) {
+      xn[i] = x[i] + x[6 + i] * dt;
+      xn[6 + i] = x[6 + i] + u[i] * dt;
+    }
   }
 }
 
 // Task-space position p(x): planar position, or the arm's end-effector.
 void orc_task_pos(const orc_params* P, const double* x, double* pos) {
-  if (P->dyn == ORC_ARM) {
+  if (is_arm(P->dyn)) {
     double O[21], R[9];
     orc_arm_fk(x, O, R);
     for (int i = 0; i < 3; ++i) pos[i] = O[18 + i];
@@ -284,7 +295,7 @@ void orc_arm_fk(const double* q, double* O, double* R) {
 // Collision geometry: the planar robot is one disc; the arm carries four
 // spheres per link at fractions 0, 1/3, 2/3, 1 of the segment O_{i-1} -> O_i.
 int orc_robot_points(const orc_params* P, const double* x, double* centres) {
-  if (P->dyn != ORC_ARM) {
+  if (!is_arm(P->dyn)) {
     centres[0] = x[0];
     centres[1] = x[1];
     centres[2] = 0.0;
@@ -313,7 +324,7 @@ void orc_rollouts(const orc_params* P, const double* x0, const double* U,
   std::vector<double> nz((size_t)T * m);
   for (int k = 0; k < K; ++k) {
     orc_normals(P->seed, P->counter, k, T * m, nz.data());
-    double x[6], xn[6], u[6];
+    double x[12], xn[12], u[6];
     for (int i = 0; i < n; ++i) x[i] = x0[i];
     if (traj)
       for (int i = 0; i < n; ++i) traj[((size_t)k * (T + 1)) * n + i] = x[i];

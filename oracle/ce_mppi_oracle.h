@@ -31,12 +31,12 @@
 extern "C" {
 #endif
 
-enum { ORC_DI = 0, ORC_UNICYCLE = 1, ORC_ARM = 2 };
+enum { ORC_DI = 0, ORC_UNICYCLE = 1, ORC_ARM = 2, ORC_ARM12 = 3 };
 enum { ORC_MODE_NOCOL = 0, ORC_MODE_ALLCOL = 1, ORC_MODE_ALLNOISE = 2,
        ORC_MODE_STATIC = 3, ORC_MODE_DYNAMIC = 4 };
 
 typedef struct {
-  int dyn;             /* ORC_DI / ORC_UNICYCLE / ORC_ARM                     */
+  int dyn;             /* ORC_DI / ORC_UNICYCLE / ORC_ARM / ORC_ARM12         */
   int K, T;            /* rollouts, horizon N                                 */
   double dt;           /* model time step                                     */
   double obs_dt;       /* spacing of obstacle observations (Delta t, Eq. 17)  */

@@ -18,8 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcemppi.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "ce_mppi.h")
 
-DYN_DI, DYN_UNICYCLE, DYN_ARM = 0, 1, 2
-DIMS = {DYN_DI: (4, 2, 2), DYN_UNICYCLE: (3, 2, 2), DYN_ARM: (6, 6, 3)}  # (n, m, p)
+DYN_DI, DYN_UNICYCLE, DYN_ARM, DYN_ARM12 = 0, 1, 2, 3
+DIMS = {DYN_DI: (4, 2, 2), DYN_UNICYCLE: (3, 2, 2), DYN_ARM: (6, 6, 3),
+        DYN_ARM12: (12, 6, 3)}  # (n, m, p)
 MODES = {0: "nocol", 1: "allcol", 2: "allnoise", 3: "static", 4: "dynamic"}
 BUF = dict(S=0, HIT=1, PN=2, EPS=3, IDXV=4, IDXC=5, Z=6, G=7, LABEL=8, W=9, HITJ=10, DBCYC=11)
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NO_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY"}

@@ -37,9 +37,9 @@ ce_status_t cuda_fail(cudaError_t e, const char* what) {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 void dims_of(int dyn, int* n, int* m, int* p) {
-  *n = dyn == CE_DYN_DOUBLE_INT_2D ? 4 : (dyn == CE_DYN_UNICYCLE ? 3 : 6);
-  *m = dyn == CE_DYN_ARM6_KIN ? 6 : 2;
-  *p = dyn == CE_DYN_ARM6_KIN ? 3 : 2;
+  *n = dyn == CE_DYN_DOUBLE_INT_2D ? 4 : dyn == CE_DYN_UNICYCLE ? 3 : dyn == CE_DYN_ARM6_KIN ? 6 : 12;
+  *m = is_arm(dyn) ? 6 : 2;
+  *p = is_arm(dyn) ? 3 : 2;
 }
 
 bool finite(float v) { return std::isfinite(v); }
@@ -76,7 +76,7 @@ namespace {
 
 ce_status_t validate(const ce_mppi_params* P) {
   if (!P) return fail(CE_MPPI_ERR_INVALID_ARG, "params is NULL");
-  if (P->dyn < 0 || P->dyn > 2) return fail(CE_MPPI_ERR_INVALID_ARG, "dyn must be 0, 1 or 2");
+  if (P->dyn < 0 || P->dyn > 3) return fail(CE_MPPI_ERR_INVALID_ARG, "dyn must be 0, 1, 2 or 3");
   if (P->K < 1 || P->K > (1 << 20)) return fail(CE_MPPI_ERR_INVALID_ARG, "K must be in [1, 2^20]");
   if (P->T < 1 || P->T > kMaxT) return fail(CE_MPPI_ERR_INVALID_ARG, "T must be in [1, 256]");
   if (!(P->dt > 0) || !finite(P->dt)) return fail(CE_MPPI_ERR_INVALID_ARG, "dt must be > 0");
@@ -181,11 +181,11 @@ ce_status_t handle_retarget(ce_mppi_handle* h, const ce_mppi_params* P) {
 namespace {
 
 void tiles_of(const ce_mppi_handle* h, int inst, std::vector<int2>& roll, std::vector<int2>& upd) {
-  const int per = h->P.dyn == CE_DYN_ARM6_KIN ? kArmWarps : kRolloutThreads;
+  const int per = is_arm(h->P.dyn) ? kArmWarps : kRolloutThreads;
   for (int t = 0; t * per < h->P.K; ++t) roll.push_back(make_int2(inst, t));
   // update tiles: (column block, rollout chunk) enumerated as kc * ncb + cb
   const int TM = h->P.T * h->m;
-  const bool arm = h->P.dyn == CE_DYN_ARM6_KIN;
+  const bool arm = is_arm(h->P.dyn);
   const int cper = arm ? 32 : kUpdateWarps, kch = arm ? kUpdChunkArm : kUpdChunk2D;
   const int ncb = (TM + cper - 1) / cper, nkc = (h->P.K + kch - 1) / kch;
   for (int t = 0; t < ncb * nkc; ++t) upd.push_back(make_int2(inst, t));
@@ -215,8 +215,8 @@ void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h)
   d.dyn = P->dyn; d.K = K; d.Kp = Kp; d.T = P->T; d.m = h->m; d.n = h->n; d.p = h->p;
   d.n_obs_max = P->n_obs_max; d.H = P->hist_len; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
   d.check_j0 = P->check_j0; d.G = G; d.R = R; d.regen = P->noise_regen;
-  d.eps_ld_c = P->dyn == CE_DYN_ARM6_KIN ? 1 : Kp;
-  d.eps_ld_k = P->dyn == CE_DYN_ARM6_KIN ? h->TMp : 1;
+  d.eps_ld_c = is_arm(P->dyn) ? 1 : Kp;
+  d.eps_ld_k = is_arm(P->dyn) ? h->TMp : 1;
   d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;
   d.eps2 = eps_squared(P->dbscan_eps); d.cell_inv = ci; d.robot_radius = P->robot_radius;
   d.norm_eps = P->norm_eps; d.v_static_thresh = P->v_static_thresh;
@@ -274,7 +274,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
   const size_t eps_elems = P->noise_regen ? 0
-                          : P->dyn == CE_DYN_ARM6_KIN ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
+                          : is_arm(P->dyn) ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
   const size_t o_eps = take(4 * eps_elems);
   size_t o_int[9];
   for (int i = 0; i < 9; ++i) o_int[i] = take(4 * Kp);
@@ -334,7 +334,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   tiles_of(h, 0, roll, upd);
   h->n_roll = (int)roll.size();
   h->n_upd = (int)upd.size();
-  h->smem_roll = P->dyn == CE_DYN_ARM6_KIN
+  h->smem_roll = is_arm(P->dyn)
                      ? (int)(track_bytes(T, nobs) + (size_t)T * m * 4)
                      : (int)((((size_t)T * m * 4 + 15) & ~(size_t)15) + kTrackSmem2D);
   auto cleanup = [&]() {
@@ -727,7 +727,7 @@ ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* dst, size_t bytes) 
     if (!d.eps) return fail(CE_MPPI_ERR_INVALID_ARG, "peek: eps' is not stored (noise_regen)");
     if (want(4 * K * TM) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
     float* o = static_cast<float*>(dst);
-    if (h->P.dyn == CE_DYN_ARM6_KIN) {
+    if (is_arm(h->P.dyn)) {
       CE_CUDA(cudaMemcpy2D(o, 4 * TM, d.eps, 4 * (size_t)h->TMp, 4 * TM, K, cudaMemcpyDeviceToHost));
     } else {
       std::vector<float> tmp(TM * K);

@@ -118,6 +118,11 @@ __device__ __forceinline__ int2 tile_of(const KArgs& a) {
 
 // Row stride (in float4) of the obstacle track table: odd, so that lanes
 // reading different horizon rows hit different shared-memory banks.
+// The two arm models share the kinematics, cost, collision and kernels.
+__host__ __device__ __forceinline__ bool is_arm(int dyn) {
+  return dyn == CE_DYN_ARM6_KIN || dyn == CE_DYN_ARM12_DI;
+}
+
 __host__ __device__ __forceinline__ int track_stride(int n_obs) { return n_obs | 1; }
 // 2-D robots use a packed table instead: row offsets off[0..T+1] (int,
 // padded to 16 bytes), then the kept entries of rows 0..T back to back

@@ -202,10 +202,10 @@ struct ce_mppi_server {
       Session& s = sessions[f.members[i]];
       ce_mppi_handle* h = s.h;
       slots[i] = f.members[i];
-      const int per = dyn == CE_DYN_ARM6_KIN ? kArmWarps : kRolloutThreads;
+      const int per = is_arm(dyn) ? kArmWarps : kRolloutThreads;
       const int TM = h->P.T * h->m;
-      const int cper = dyn == CE_DYN_ARM6_KIN ? 32 : kUpdateWarps;
-      const int kch = dyn == CE_DYN_ARM6_KIN ? kUpdChunkArm : kUpdChunk2D;
+      const int cper = is_arm(dyn) ? 32 : kUpdateWarps;
+      const int kch = is_arm(dyn) ? kUpdChunkArm : kUpdChunk2D;
       pre_roll[i + 1] = pre_roll[i] + (h->P.K + per - 1) / per;
       pre_upd[i + 1] = pre_upd[i] + ((TM + cper - 1) / cper) * ((h->P.K + kch - 1) / kch);
       std::memcpy(f.h_in + ioff, s.in.data(), sizeof(float) * s.in.size());

@@ -45,7 +45,7 @@ __device__ __forceinline__ int block_scan_flag(bool f, int* wsum, int* total) {
 }
 
 __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, float* p0) {
-  if (d.dyn == CE_DYN_ARM6_KIN) {
+  if (is_arm(d.dyn)) {
     float q[6], O[7][3], R[9];
     for (int i = 0; i < 6; ++i) q[i] = x0[i];
     arm_fk(q, O, R);
@@ -1457,7 +1457,7 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
   }
   if (threadIdx.x == 0) {
     if (r.x_next) {
-      float x[6], u[6];
+      float x[12], u[6];
       for (int i = 0; i < d.n; ++i) x[i] = r.x0[i];
       for (int i = 0; i < m; ++i) u[i] = __ldcg(d.Unew + i);
       const float dt = d.dt;
@@ -1467,8 +1467,10 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
         float sn, cs;
         sincosf(x[2], &sn, &cs);
         x[0] += u[0] * cs * dt; x[1] += u[0] * sn * dt; x[2] += u[1] * dt;
-      } else {
+      } else if (d.dyn == CE_DYN_ARM6_KIN) {
         for (int i = 0; i < 6; ++i) x[i] += u[i] * dt;
+      } else {
+        for (int i = 0; i < 6; ++i) { x[i] += x[6 + i] * dt; x[6 + i] += u[i] * dt; }
       }
       for (int i = 0; i < d.n; ++i) r.x_next[i] = x[i];
     }
@@ -1501,7 +1503,7 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
                                                        int inst) {
   Ctl* ctl = d.ctl;
   const int TM = d.T * d.m, nnz = ctl->nnz;
-  const bool arm = d.dyn == CE_DYN_ARM6_KIN;
+  const bool arm = is_arm(d.dyn);
   const float iz = ctl->invZ;
   const unsigned long long ctr = *d.counter;
   for (int c = threadIdx.x; c < TM; c += blockDim.x) {
@@ -1528,7 +1530,7 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   if (d.ctl->updated) return;   // done by the fused per-instance kernel
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int K = d.K, TM = d.T * d.m;
-  const bool arm = d.dyn == CE_DYN_ARM6_KIN;
+  const bool arm = is_arm(d.dyn);
   const int kch = arm ? kUpdChunkArm : kUpdChunk2D;
   const int cper = arm ? 32 : kUpdateWarps;
   const int ncb = (TM + cper - 1) / cper;
@@ -1538,6 +1540,7 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   const float* __restrict__ eps = d.eps;
   const int nnz = d.ctl->nnz;
   const unsigned long long ctr = *d.counter;   // this replan's (finalize advances it)
+  const bool regen = d.regen;
   if (nnz >= 0) {
     // few nonzero weights, listed by ascending k: the tiles of the first
     // rollout chunk sum over the list, the others contribute zeros
@@ -1583,18 +1586,31 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
       // lambda, and their sectors are never fetched (adding 0 keeps the sums'
       // bits as if they were).
       // eps' stored, or drawn again (same order of the sums either way)
-      auto val = [&](int kk) { return d.regen ? eps_regen(d, ctr, kk, c) : col[kk]; };
-      for (; k + 96 < k1; k += 128) {
-        float wk[4];
+      if (!regen) {
+        for (; k + 96 < k1; k += 128) {
+          float wk[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) wk[u] = w[k + 32 * u];
+          for (int u = 0; u < 4; ++u) wk[u] = w[k + 32 * u];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          kahan_add(s[u], e[u], wk[u] != 0.f ? wk[u] * val(k + 32 * u) : 0.f);
-      }
-      for (; k < k1; k += 32) {
-        const float wk = w[k];
-        kahan_add(s[0], e[0], wk != 0.f ? wk * val(k) : 0.f);
+          for (int u = 0; u < 4; ++u)
+            kahan_add(s[u], e[u], wk[u] != 0.f ? wk[u] * col[k + 32 * u] : 0.f);
+        }
+        for (; k < k1; k += 32) {
+          const float wk = w[k];
+          kahan_add(s[0], e[0], wk != 0.f ? wk * col[k] : 0.f);
+        }
+      } else {
+        for (; k + 96 < k1; k += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float wk = w[k + 32 * u];
+            kahan_add(s[u], e[u], wk != 0.f ? wk * eps_regen(d, ctr, k + 32 * u, c) : 0.f);
+          }
+        }
+        for (; k < k1; k += 32) {
+          const float wk = w[k];
+          kahan_add(s[0], e[0], wk != 0.f ? wk * eps_regen(d, ctr, k, c) : 0.f);
+        }
       }
       float t = (s[0] + s[1]) + (s[2] + s[3]);
       t = warp_sum(t);
@@ -1603,11 +1619,15 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   } else {
     const int c = c0 + lane;
     float s = 0.f, e = 0.f;
-    if (c < TM)
+    if (c < TM && !regen)
       for (int k = k0 + wid; k < k1; k += kUpdateWarps) {
         const float wk = w[k];   // warp-uniform: rows of zero weight are skipped
-        if (wk != 0.f)
-          kahan_add(s, e, wk * (d.regen ? eps_regen(d, ctr, k, c) : eps[(size_t)k * d.eps_ld_k + c]));
+        if (wk != 0.f) kahan_add(s, e, wk * eps[(size_t)k * d.eps_ld_k + c]);
+      }
+    else if (c < TM)
+      for (int k = k0 + wid; k < k1; k += kUpdateWarps) {
+        const float wk = w[k];
+        if (wk != 0.f) kahan_add(s, e, wk * eps_regen(d, ctr, k, c));
       }
     part[wid][lane] = s;
     __syncthreads();

@@ -40,7 +40,7 @@ __global__ void k_tracks(KArgs a) {
     d.ctl->done = 0u;
     d.ctl->updated = 0;
   }
-  if (d.dyn == CE_DYN_ARM6_KIN) {
+  if (is_arm(d.dyn)) {
     const int total = (T + 1) * n_obs;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int j = e / n_obs, o = e - j * n_obs;
@@ -413,6 +413,7 @@ __device__ __forceinline__ float arm_cost(const InstDesc& d, const float O[7][3]
          (collide ? d.w[2] : 0.0f);
 }
 
+template <bool ACC>   // ACC: 12-D state with joint-acceleration input
 __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
@@ -429,9 +430,13 @@ __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
   const unsigned long long ctr = *d.counter;
   const float dt = d.dt;
 
-  float q[6];
+  constexpr bool acc = ACC;
+  float q[6], qd[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) q[i] = r.x0[i];
+  for (int i = 0; i < 6; ++i) {
+    q[i] = r.x0[i];
+    qd[i] = acc ? r.x0[6 + i] : 0.0f;
+  }
   float O[7][3], R[9];
   // the shared initial state: its cost term (and optional collision test)
   arm_fk(q, O, R);
@@ -462,20 +467,30 @@ __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
 #pragma unroll
       for (int i = 0; i < 6; ++i) u[i] = 0.0f;
     }
-    // inclusive warp prefix sum of u: displacement up to and including step j
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      float v = u[i];
+    // inclusive warp prefix sums.  Velocity input: q_{j+1} = q + dt sum_{i<=j} u_i.
+    // Acceleration input: qdot_j = qdot + dt sum_{i<j} u_i, then
+    // q_{j+1} = q + dt sum_{i<=j} qdot_i.
+    auto scan = [&](float v) {
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const float y = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += y;
       }
-      u[i] = v;
-    }
+      return v;
+    };
+    const int last = min(31, T - 1 - base);
     float qj[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) qj[i] = q[i] + u[i] * dt;
+    for (int i = 0; i < 6; ++i) {
+      const float su = scan(u[i]);
+      if (!acc) {
+        qj[i] = q[i] + su * dt;
+      } else {
+        const float vj = act ? qd[i] + (su - u[i]) * dt : 0.0f;
+        qj[i] = q[i] + scan(vj) * dt;
+        qd[i] = qd[i] + __shfl_sync(0xffffffffu, su, last) * dt;   // the next chunk's start
+      }
+    }
     int hit_here = n_obs;
     float cost = 0.0f;
     if (act) {
@@ -492,7 +507,6 @@ __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
       first_j = base + l + 1;
     }
     // carry the chunk's final state to the next chunk
-    const int last = min(31, T - 1 - base);
 #pragma unroll
     for (int i = 0; i < 6; ++i) q[i] = __shfl_sync(0xffffffffu, qj[i], last);
   }
@@ -537,7 +551,7 @@ __global__ void k_normals(unsigned long long seed, unsigned long long counter, i
 }
 
 // ------------------------------------------------------------------ launchers
-int rollout_threads(int dyn) { return dyn == CE_DYN_ARM6_KIN ? kArmWarps * 32 : kRolloutThreads; }
+int rollout_threads(int dyn) { return is_arm(dyn) ? kArmWarps * 32 : kRolloutThreads; }
 
 void launch_tracks(const KArgs& a, cudaStream_t s) { k_tracks<<<a.n_inst, 1024, 0, s>>>(a); }
 
@@ -546,7 +560,9 @@ void configure_rollout() {
                        kMaxSmemTracks + 8192);
   cudaFuncSetAttribute(k_rollout2d<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kMaxSmemTracks + 8192);
-  cudaFuncSetAttribute(k_rollout_arm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_rollout_arm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kMaxSmemTracks + 8192);
+  cudaFuncSetAttribute(k_rollout_arm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kMaxSmemTracks + 8192);
 }
 
@@ -555,8 +571,10 @@ void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s) {
     k_rollout2d<0><<<a.n_tiles, kRolloutThreads, smem_bytes, s>>>(a);
   else if (dyn == CE_DYN_UNICYCLE)
     k_rollout2d<1><<<a.n_tiles, kRolloutThreads, smem_bytes, s>>>(a);
+  else if (dyn == CE_DYN_ARM6_KIN)
+    k_rollout_arm<false><<<a.n_tiles, kArmWarps * 32, smem_bytes, s>>>(a);
   else
-    k_rollout_arm<<<a.n_tiles, kArmWarps * 32, smem_bytes, s>>>(a);
+    k_rollout_arm<true><<<a.n_tiles, kArmWarps * 32, smem_bytes, s>>>(a);
 }
 
 void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,

@@ -31,8 +31,9 @@ import math
 
 import numpy as np
 
-DYN_DI, DYN_UNICYCLE, DYN_ARM = 0, 1, 2
-DIMS = {DYN_DI: (4, 2, 2), DYN_UNICYCLE: (3, 2, 2), DYN_ARM: (6, 6, 3)}  # (n, m, p)
+DYN_DI, DYN_UNICYCLE, DYN_ARM, DYN_ARM12 = 0, 1, 2, 3
+DIMS = {DYN_DI: (4, 2, 2), DYN_UNICYCLE: (3, 2, 2), DYN_ARM: (6, 6, 3),
+        DYN_ARM12: (12, 6, 3)}  # (n, m, p)
 
 # Start pose of the arm (base turned to face +x) and the positions of its
 # seven DH frame origins there, in metres; obstacles are kept clear of them.
@@ -166,10 +167,17 @@ def make(name: str, seed: int = 0, n_replans: int = 1, **over) -> dict:
                        n_replans + cfg["hist_len"] - 1, cfg["obs_dt"], static=True)
         x0 = np.array([0.0, 0.0, 0.0])
         u0 = (0.6, 0.0)  # already driving forward at 0.6 m/s
-    elif name in ("arm", "arm_blocked", "arm_paper"):
+    elif name in ("arm", "arm_blocked", "arm_paper", "arm12", "arm12_blocked"):
         q0 = np.array(ARM_Q0)
         q_goal = q0 + rng.uniform(-1.0, 1.0, size=6)
-        if name in ("arm", "arm_blocked"):
+        if name in ("arm12", "arm12_blocked"):
+            # 12-D state (q, qdot) with joint-acceleration input, config-3 sizes
+            cfg = base_params(DYN_ARM12, over.pop("K", 4096), over.pop("T", 32), 0.02, lam=1.0,
+                              sigma=[1.0] * 6, u_min=[-3.0] * 6, u_max=[3.0] * 6,
+                              goal=(), w=(10, 3, 1000), eps=0.2, min_pts=16, seed=seed,
+                              robot_radius=0.06, **over)
+            n_obs, speed_hi = 20, 0.3
+        elif name in ("arm", "arm_blocked"):
             cfg = base_params(DYN_ARM, over.pop("K", 4096), over.pop("T", 32), 0.02, lam=1.0,
                               sigma=[0.3] * 6, u_min=[-1.0] * 6, u_max=[1.0] * 6,
                               goal=(), w=(10, 3, 1000), eps=0.2, min_pts=16, seed=seed,
@@ -184,7 +192,7 @@ def make(name: str, seed: int = 0, n_replans: int = 1, **over) -> dict:
         cfg["goal_q"] = [float(v) for v in q_goal]
         field = [(0.2, 1.4), (-0.6, 0.6), (0.0, 1.2)]
         centres, radius = _place_discs(rng, n_obs, field, 0.05, 0.15, _ARM_Q0_JOINTS, 0.2)
-        if name != "arm":
+        if name not in ("arm", "arm12"):
             # one static sphere just beside the end effector, 0.03 m clear of it
             ee = np.array(_ARM_Q0_JOINTS[6])
             centres = np.vstack([centres, ee + np.array([0.0, 0.0, -0.17])])
@@ -192,9 +200,9 @@ def make(name: str, seed: int = 0, n_replans: int = 1, **over) -> dict:
         obs, _ = _move(rng, centres, radius, field, 0.0, speed_hi,
                        n_replans + cfg["hist_len"] - 1, cfg["obs_dt"],
                        static=(speed_hi == 0.0))
-        if name == "arm_blocked":
+        if name in ("arm_blocked", "arm12_blocked"):
             obs[:, -1, :] = obs[0, -1, :]
-        x0 = q0
+        x0 = q0 if cfg["dyn"] == DYN_ARM else np.concatenate([q0, np.zeros(6)])
     else:
         raise KeyError(name)
     n, m, p = DIMS[cfg["dyn"]]

@@ -141,6 +141,7 @@ def _check_replan(sc, counter=0, report=None):
     ("di_static", {}), ("di_blocked", {}), ("unicycle_paper", {}), ("arm_paper", {}),
     ("unicycle_blocked", dict(K=2000)), ("arm_blocked", dict(K=1000)),
     ("unicycle", dict(K=777, T=23)), ("di_blocked", dict(K=4099, T=17)),
+    ("arm12_blocked", dict(K=1000)), ("arm12", dict(K=333, T=45)),
 ])
 def test_stage_parity_small(name, kw):
     sc = W.make(name, seed=0, **kw)
@@ -210,6 +211,13 @@ def test_stage_parity_full_size_arm():
     sc = W.make("arm_blocked", seed=0)
     diag, errs = _check_replan(sc)
     print("PARITY full arm_blocked", diag["mode"], errs)
+
+
+def test_stage_parity_full_size_arm12():
+    """The 12-D arm (joint positions and velocities, acceleration input)."""
+    sc = W.make("arm12_blocked", seed=0)
+    diag, errs = _check_replan(sc)
+    print("PARITY full arm12_blocked", diag["mode"], errs)
 
 
 def test_philox_words_bit_exact():
@@ -402,6 +410,7 @@ def test_host_replan_rejects_too_many_obstacles():
     ("arm_blocked", dict(K=1000)),
     ("arm_blocked", dict(K=1000, lam=1e4)),
     ("di_blocked", dict(K=4099, T=17, lam=50.0)),
+    ("arm12_blocked", dict(K=700, lam=1e4)),
 ])
 def test_noise_regen_same_bits(name, kw):
     """noise_regen = 1 stores no perturbations; the update draws the same

@@ -465,3 +465,43 @@ def test_replan_invariants(name):
     # the update is a convex combination of feasible controls
     lo, hi = np.array(cfg["u_min"]), np.array(cfg["u_max"])
     assert np.all(r["U_new"] >= lo - 1e-12) and np.all(r["U_new"] <= hi + 1e-12)
+
+
+# ----------------------------------------------------------------- 12-D arm
+def test_arm12_double_integrator_closed_form():
+    # explicit Euler with acceleration input: q_N = q_0 + N dt qdot_0 +
+    # dt^2 sum_j (N-1-j) a_j, qdot_N = qdot_0 + dt sum_j a_j, per joint
+    sc = _cfg("arm12", K=8, T=9)
+    P = oracle.make_params(sc["cfg"])
+    rng = np.random.default_rng(12)
+    x0 = np.concatenate([rng.uniform(-1, 1, 6), rng.uniform(-0.5, 0.5, 6)])
+    U = rng.uniform(-1, 1, size=(9, 6))
+    far = np.full((10, 1, 3), 50.0)
+    r = oracle.rollouts(P, x0, U, far, np.array([0.1]), want_traj=True)
+    dt, N = P.dt, P.T
+    a = U[None] + r["eps"]
+    jw = (N - 1 - np.arange(N))[None, :, None]
+    qN = x0[None, :6] + N * dt * x0[None, 6:] + dt * dt * np.sum(jw * a, axis=1)
+    vN = x0[None, 6:] + dt * np.sum(a, axis=1)
+    np.testing.assert_allclose(r["traj"][:, -1, :6], qN, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r["traj"][:, -1, 6:], vN, rtol=1e-12, atol=1e-12)
+    # the terminal task position is the end effector of q_N
+    for k in range(8):
+        O, _ = oracle.arm_fk(qN[k])
+        np.testing.assert_allclose(r["pN"][k], O[6], atol=1e-12)
+
+
+def test_arm12_at_rest_matches_the_velocity_arm():
+    # zero velocity, zero input, no noise: both arm models hold q_0, so the
+    # costs (Eq. 24 on q) are equal, (T+1) l(q_0)
+    sc6, sc12 = _cfg("arm", K=2, T=6), _cfg("arm12", K=2, T=6)
+    P6 = _params(sc6["cfg"], sigma=[0.0] * 6)
+    P12 = _params(sc12["cfg"], sigma=[0.0] * 6)
+    P12.goal[:] = P6.goal[:]
+    q0 = np.random.default_rng(6).uniform(-2, 2, 6)
+    far = np.full((7, 1, 3), 50.0)
+    r6 = oracle.rollouts(P6, q0, np.zeros((6, 6)), far, np.array([0.1]))
+    r12 = oracle.rollouts(P12, np.concatenate([q0, np.zeros(6)]), np.zeros((6, 6)), far,
+                          np.array([0.1]))
+    np.testing.assert_allclose(r12["S"], r6["S"], rtol=1e-14)
+    np.testing.assert_allclose(r12["pN"], r6["pN"], atol=1e-14)
