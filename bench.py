@@ -365,6 +365,8 @@ def main() -> None:
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served run (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
+                    help="1: two halves of the episodes software-pipelined in one graph")
     ap.add_argument("--noise-regen", type=int, default=0, choices=[0, 1],
                     help="1: perturbations not stored, drawn again by the update")
     args = ap.parse_args()
@@ -441,10 +443,49 @@ def main() -> None:
     reset_episodes()
     batch = pkg.Batch(planners, reqs, stream=stream, use_graph=True, n_branches=args.branches)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # Software pipeline of two halves A, B of the episodes (independent
+    # instances): one graph replay = [B clustering + update (replan s-1) |
+    # A tracks + rollouts (s)], then [A clustering + update (s) | B tracks +
+    # rollouts (s)] -- one replan of every episode per replay, each half's
+    # latency-bound stages over the other half's rollouts.
+    pipe = None
+    if args.pipeline and N_INST >= 2:
+        half = N_INST // 2
+        bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False)
+        bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False)
+        side = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph):
+            main = torch.cuda.current_stream()
+            side.wait_stream(main)
+            bB.run_part(1, main)
+            bA.run_part(0, side)
+            main.wait_stream(side)
+            side.wait_stream(main)
+            bA.run_part(1, main)
+            bB.run_part(0, side)
+            main.wait_stream(side)
+        torch.cuda.synchronize()
+        pipe = (bA, bB, graph)
 
-    for _ in range(args.warmup):
-        batch.run()
+    def prologue():
+        """(pipelined) B's first tracks + rollouts, untimed"""
+        if pipe:
+            pipe[1].run_part(0, stream)
+
+    def step():
+        if pipe:
+            pipe[2].replay()
+        else:
+            batch.run()
+
     reset_episodes()
+    prologue()
+    for _ in range(args.warmup):
+        step()
+    reset_episodes()
+    prologue()
     assert args.steps >= 1
     if dist:
         dist.barrier()
@@ -463,13 +504,14 @@ def main() -> None:
         for i in range(n):
             flush.fill_(float(i))
             ev[i][0].record(stream)
-            batch.run()
+            step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         step_ms += [a.elapsed_time(b) for a, b in ev]
         done += n
         if done < args.steps:
             reset_episodes()
+            prologue()
     clk = clocks.stop()
     step_ms = np.array(step_ms)
     value, tot_ms = aggregate(float(step_ms.sum()), units_per_step, args.steps, world, dist)
@@ -571,7 +613,8 @@ def main() -> None:
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank",
-                       branches=args.branches, noise_regen=args.noise_regen),
+                       branches=0 if pipe else args.branches, pipeline=args.pipeline,
+                       noise_regen=args.noise_regen),
         "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),
@@ -589,8 +632,10 @@ def main() -> None:
                      "obstacle_tests_per_rollout": tests_per_rollout},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        # six stage kernels per concurrent branch per step (the L2 flush is torch's)
-        "gpu_launches": 6 * min(args.branches, N_INST) * args.steps,
+        # four kernels per replan chain (tracks, rollouts, the fused clustering
+        # kernel, update): per step two half chains (pipelined) or one chain per
+        # branch (the L2 flush is torch's)
+        "gpu_launches": 4 * (2 if pipe else min(args.branches, N_INST)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":
@@ -602,7 +647,7 @@ def main() -> None:
         line["cpu_baseline"] = cpu_baseline(scenes, u_init, max_threads=16)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for obj in [batch, e2e_batch] + planners + e2e_pl + plain_pl:
+    for obj in [batch, e2e_batch] + (list(pipe[:2]) if pipe else []) + planners + e2e_pl + plain_pl:
         obj.close()
     if dist:
         dist.destroy_process_group()

@@ -175,6 +175,17 @@ ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_reques
                                  ce_mppi_batch** out);
 /* Queue one replan of every instance of the batch; returns without waiting.  */
 ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
+/* Queue one half of a replan of every instance, without a graph, on stream (a
+ * cudaStream_t; NULL: the batch's stream): part 0 = obstacle tracks and the
+ * rollouts (Algorithm 1 [Rollouts]); part 1 = pruning, reference point,
+ * features, DBSCAN, selection, weights and the update with its shift.  Part 1
+ * must follow part 0 of the same replan in stream order, and part 0 of the
+ * next replan must follow part 1.  Between the two, the instances' state is
+ * held on the device, so the halves of two batches of independent instances
+ * can be interleaved (one batch's rollouts over the other's clustering), for
+ * example on two streams inside the caller's own CUDA graph.  The results are
+ * bitwise those of ce_mppi_batch_run.  Errors: INVALID_ARG, CUDA.            */
+ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream);
 /* Run one replan of the batch stage by stage (no graph) with CUDA events
  * between the stage launches, wait for it, and write the device time of each
  * stage in milliseconds to stage_ms[6]: tracks, rollouts, prune + reference

@@ -71,7 +71,7 @@ class Request(C.Structure):
 EXPORTS = (
     "ce_mppi_create", "ce_mppi_destroy", "ce_mppi_set_nominal", "ce_mppi_get_nominal",
     "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_replan_dev",
-    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_profile",
+    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
     "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
     "ce_mppi_dbscan_dev", "ce_mppi_dbscan_noalloc_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
@@ -103,6 +103,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Request), i, vp, i, i,
                                            C.POINTER(vp)]
         L.ce_mppi_batch_run.argtypes = [vp]
+        L.ce_mppi_batch_run_part.argtypes = [vp, i, vp]
         L.ce_mppi_batch_profile.argtypes = [vp, C.POINTER(C.c_float)]
         L.ce_mppi_batch_destroy.argtypes = [vp]
         L.ce_mppi_peek.argtypes = [vp, i, vp, C.c_size_t]
@@ -264,6 +265,11 @@ class Batch:
 
     def run(self):
         _check(lib().ce_mppi_batch_run(self.b))
+
+    def run_part(self, part: int, stream=None):
+        """Half a replan (0: tracks + rollouts, 1: clustering + update) on stream."""
+        s = 0 if stream is None else _stream_ptr(stream)
+        _check(lib().ce_mppi_batch_run_part(self.b, int(part), C.c_void_p(s)))
 
     STAGES = ("tracks", "rollout", "prune", "dbscan", "select", "update")
 

@@ -637,6 +637,35 @@ ce_status_t ce_mppi_batch_run(ce_mppi_batch* b) {
   return CE_MPPI_OK;
 }
 
+ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
+  if (!b) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL batch");
+  if (part != 0 && part != 1) return fail(CE_MPPI_ERR_INVALID_ARG, "part must be 0 or 1");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->stream;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.D = b->ddesc;
+  a.R = b->dreq;
+  a.n_inst = (int)b->hs.size();
+  a.n_conc = a.n_inst;
+  if (part == 0) {
+    launch_tracks(a, s);
+    a.tiles = b->dtiles_roll;
+    a.n_tiles = b->n_roll;
+    launch_rollout(b->dyn, a, b->smem_roll, s);
+  } else {
+    if (!launch_post(a, b->max_cells, s)) {
+      launch_prune(a, s);
+      launch_dbscan(a, b->max_cells, s);
+      launch_select(a, s);
+    }
+    a.tiles = b->dtiles_upd;
+    a.n_tiles = b->n_upd;
+    launch_update(a, s);
+  }
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
 ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms) {
   if (!b || !stage_ms) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
   cudaEvent_t ev[7];

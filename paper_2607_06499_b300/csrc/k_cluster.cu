@@ -548,8 +548,10 @@ __device__ __forceinline__ void cell_boxes(int pb, int pe, const DbWork& w, cons
 // (this CTA's points per cell), then per occupied cell: ostart[kMaxOcc + 1],
 // ocell, ofill, opar, omin (kMaxOcc each), obox[6][kMaxOcc] (all points) and
 // ocbox[6][kMaxOcc] (core points) as keys.
+// (the per-occupied-cell tables hold min(kMaxOcc, nc) entries)
+__host__ __device__ __forceinline__ int dbscan_occ_cap(int nc) { return nc < kMaxOcc ? nc : kMaxOcc; }
 __host__ __device__ __forceinline__ size_t dbscan_smem_bytes(int nc) {
-  return (2 * (size_t)nc + 1 + 17 * (size_t)kMaxOcc) * 4;
+  return (2 * (size_t)nc + 1 + 17 * (size_t)dbscan_occ_cap(nc)) * 4;
 }
 
 // One thread-block cluster of CL CTAs (CL = 1 .. 8) per point set.  CTA r owns
@@ -572,7 +574,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   const int nc = p == 3 ? G * G * G : G * G;
   const float far_ok = eps2 * 0.9999f;              // whole box within eps
   const float near_no = eps2 * 1.0001f + 1e-12f;    // whole box beyond eps
-  const int S = kMaxOcc;
+  const int S = dbscan_occ_cap(nc);
   int* map = smem;                  // [nc]
   int* lcnt = map + nc;             // [nc]
   int* ostart = lcnt + nc;          // [S + 1]
@@ -1700,11 +1702,10 @@ static int cluster_ctas(const ClusterFit& f, int n_conc) {
 
 static ClusterFit g_fit_prune, g_fit_select;
 // DBSCAN: the fit depends on the shared memory of the launch (by grid size)
-static ClusterFit g_fit_db[2];   // small grids (<= 1024 cells), large grids
+constexpr int kFitCells[3] = {256, 1024, kMaxCells};   // grid-size classes
+static ClusterFit g_fit_db[3];
 static size_t dbscan_smem(int nc);
-static const ClusterFit& fit_dbscan(size_t smem) {
-  return smem <= dbscan_smem(1024) ? g_fit_db[0] : g_fit_db[1];
-}
+static int fit_class(int nc) { return nc <= kFitCells[0] ? 0 : nc <= kFitCells[1] ? 1 : 2; }
 
 template <typename... Args>
 static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int threads, size_t smem,
@@ -1731,13 +1732,14 @@ void launch_prune(const KArgs& a, cudaStream_t s) {
 
 static size_t dbscan_smem(int nc) { return dbscan_smem_bytes(nc); }
 
-static ClusterFit g_fit_post[2];
+static ClusterFit g_fit_post[3];
 static size_t post_smem(int nc) { return std::max(dbscan_smem(nc), sizeof(SelSmem)); }
 
 bool launch_post(const KArgs& a, int max_cells, cudaStream_t s) {
-  const size_t smem = post_smem(max_cells);
-  if (smem > post_smem(kMaxCells)) return false;
-  const ClusterFit& f = smem <= post_smem(1024) ? g_fit_post[0] : g_fit_post[1];
+  if (max_cells > kMaxCells) return false;
+  const int fc = fit_class(max_cells);
+  const size_t smem = post_smem(kFitCells[fc]);   // the class's size (a fit was queried for it)
+  const ClusterFit& f = g_fit_post[fc];
   if (f.max_active[0] == 0) return false;   // (the launch would not fit)
   const int cl = cluster_ctas(f, a.n_conc > 0 ? a.n_conc : a.n_inst);
   launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, a);
@@ -1751,17 +1753,16 @@ void configure_cluster() {
                        (int)dbscan_smem(kMaxCells));
   cudaFuncSetAttribute(k_dbscan_standalone, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)dbscan_smem(kMaxCells));
-  g_fit_db[0] = query_fit(k_dbscan, kBlock, dbscan_smem(1024));
-  g_fit_db[1] = query_fit(k_dbscan, kBlock, dbscan_smem(kMaxCells));
+  for (int c = 0; c < 3; ++c) g_fit_db[c] = query_fit(k_dbscan, kBlock, dbscan_smem(kFitCells[c]));
   cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)post_smem(kMaxCells));
-  g_fit_post[0] = query_fit(k_post, kBlock, post_smem(1024));
-  g_fit_post[1] = query_fit(k_post, kBlock, post_smem(kMaxCells));
+  for (int c = 0; c < 3; ++c) g_fit_post[c] = query_fit(k_post, kBlock, post_smem(kFitCells[c]));
 }
 
 void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s) {
-  const size_t smem = dbscan_smem(max_cells);
-  const int cl = cluster_ctas(fit_dbscan(smem), a.n_conc > 0 ? a.n_conc : a.n_inst);
+  const int fc = fit_class(max_cells);
+  const size_t smem = dbscan_smem(kFitCells[fc]);
+  const int cl = cluster_ctas(g_fit_db[fc], a.n_conc > 0 ? a.n_conc : a.n_inst);
   launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, a);
 }
 
@@ -1787,8 +1788,9 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
   w.zs = reinterpret_cast<float*>(b); b += sizeof(float) * 3 * ldn;
   w.ld_s = ldn;
   w.bbox = reinterpret_cast<float*>(b);
-  const size_t smem = dbscan_smem(nc);
-  const int cl = cluster_ctas(fit_dbscan(smem), 1);
+  const int fc = fit_class(nc);
+  const size_t smem = dbscan_smem(kFitCells[fc]);
+  const int cl = cluster_ctas(g_fit_db[fc], 1);
   launch_clustered(k_dbscan_standalone, cl, 1, kBlock, smem, s, z, n, ld, p, eps2, cell_inv, G, R,
                    min_pts, labels, n_clusters, w);
 }

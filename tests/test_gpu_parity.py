@@ -437,3 +437,60 @@ def test_noise_regen_same_bits(name, kw):
         outs.append(us)
     for a, b in zip(*outs):
         assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+
+
+def test_batch_run_in_two_parts_same_bits():
+    """Half replans (tracks + rollouts, then clustering + update) of two
+    batches interleaved on two streams give the bits of whole replans."""
+    scs = [W.make("unicycle_blocked", seed=s, K=3000, n_replans=4) for s in range(4)]
+
+    def setup():
+        pls, reqs = [], []
+        for sc in scs:
+            pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+            pl.set_nominal(sc["U0"])
+            n_obs = sc["radius"].shape[0]
+            rq = dict(x0=torch.tensor(sc["x0"], dtype=torch.float32, device="cuda"),
+                      hist=torch.tensor(sc["obs"], dtype=torch.float32, device="cuda").contiguous(),
+                      radius=torch.tensor(sc["radius"], dtype=torch.float32, device="cuda"),
+                      u_out=torch.zeros((sc["cfg"]["T"], 2), device="cuda"), obs_step=n_obs * 2)
+            rq["x_next"] = rq["x0"]
+            pls.append(pl)
+            reqs.append(rq)
+        return pls, reqs
+
+    pls, reqs = setup()
+    whole = pkg.Batch(pls, reqs, use_graph=False)
+    ref = []
+    for _ in range(3):
+        whole.run()
+        torch.cuda.synchronize()
+        ref.append([(r["u_out"].cpu().numpy().copy(), r["x0"].cpu().numpy().copy()) for r in reqs])
+    whole.close()
+    for pl in pls:
+        pl.close()
+
+    pls, reqs = setup()
+    bA = pkg.Batch(pls[:2], reqs[:2], use_graph=False)
+    bB = pkg.Batch(pls[2:], reqs[2:], use_graph=False)
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    bB.run_part(0, main)
+    got = []
+    for s in range(3):
+        side.wait_stream(main)
+        bB.run_part(1, main)
+        bA.run_part(0, side)
+        main.wait_stream(side)
+        side.wait_stream(main)
+        bA.run_part(1, main)
+        if s < 2:
+            bB.run_part(0, side)
+        main.wait_stream(side)
+        torch.cuda.synchronize()
+        got.append([(r["u_out"].cpu().numpy().copy(), r["x0"].cpu().numpy().copy()) for r in reqs])
+    for s in range(3):
+        for i in range(4):
+            assert np.array_equal(got[s][i][0], ref[s][i][0]), (s, i)
+            assert np.array_equal(got[s][i][1], ref[s][i][1]), (s, i)
+    for obj in [bA, bB] + pls:
+        obj.close()
