@@ -632,10 +632,11 @@ def main() -> None:
                      "obstacle_tests_per_rollout": tests_per_rollout},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        # four kernels per replan chain (tracks, rollouts, the fused clustering
-        # kernel, update): per step two half chains (pipelined) or one chain per
-        # branch (the L2 flush is torch's)
-        "gpu_launches": 4 * (2 if pipe else min(args.branches, N_INST)) * args.steps,
+        # kernels per replan chain: tracks, rollouts, the fused clustering +
+        # update kernel (+ the tiled update for the arms); per step two half
+        # chains (pipelined) or one chain per branch (the L2 flush is torch's)
+        "gpu_launches": (4 if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12) else 3)
+                        * (2 if pipe else min(args.branches, N_INST)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":

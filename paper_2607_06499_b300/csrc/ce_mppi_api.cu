@@ -140,7 +140,13 @@ void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const 
   a.tprefix = pre_roll;
   a.n_tiles = n_roll;
   launch_rollout(dyn, a, smem_roll, s);
-  if (!launch_post(a, max_cells, s)) {
+  // The fused kernel applies the update; a dense one (many nonzero weights,
+  // usual for the arms' small costs) only for 2-D robots -- for the arms the
+  // tiled update kernel follows, which then skips sparse replans already done.
+  a.post_dense = !is_arm(dyn);
+  const bool fused = launch_post(a, max_cells, s);
+  if (fused && a.post_dense) return;
+  if (!fused) {
     launch_prune(a, s);
     launch_dbscan(a, max_cells, s);
     launch_select(a, s);
@@ -270,7 +276,8 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   const size_t o_trk = take(track_bytes(T, nobs) + 16);
   const size_t o_S = take(4 * Kp), o_w = take(4 * Kp), o_Sv = take(4 * Kp),
                o_cmin = take(4 * Kp), o_nzk = take(4 * kSparseMax), o_nze = take(4 * kSparseMax),
-               o_zpart = take(4 * kPruneRanges);
+               o_zpart = take(4 * kPruneRanges),
+               o_rpart = take(4 * (size_t)kPruneRanges * h->TMp);
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
   const size_t eps_elems = P->noise_regen ? 0
@@ -314,6 +321,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.nzk = reinterpret_cast<int*>(b + o_nzk);
   d.nze = reinterpret_cast<float*>(b + o_nze);
   d.zpart = reinterpret_cast<float*>(b + o_zpart);
+  d.rpart = reinterpret_cast<float*>(b + o_rpart);
   d.pN = reinterpret_cast<float*>(b + o_pN);
   d.z = reinterpret_cast<float*>(b + o_z);
   d.g = reinterpret_cast<float*>(b + o_g);
@@ -653,14 +661,18 @@ ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
     a.n_tiles = b->n_roll;
     launch_rollout(b->dyn, a, b->smem_roll, s);
   } else {
-    if (!launch_post(a, b->max_cells, s)) {
+    a.post_dense = !is_arm(b->dyn);   // (as in a whole replan's chain)
+    const bool fused = launch_post(a, b->max_cells, s);
+    if (!fused) {
       launch_prune(a, s);
       launch_dbscan(a, b->max_cells, s);
       launch_select(a, s);
     }
-    a.tiles = b->dtiles_upd;
-    a.n_tiles = b->n_upd;
-    launch_update(a, s);
+    if (!fused || !a.post_dense) {
+      a.tiles = b->dtiles_upd;
+      a.n_tiles = b->n_upd;
+      launch_update(a, s);
+    }
   }
   CE_CUDA(cudaGetLastError());
   return CE_MPPI_OK;

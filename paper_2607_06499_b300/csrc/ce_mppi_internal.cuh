@@ -32,6 +32,7 @@ struct Ctl {
   float S_absmax_V, S_min_V, S_min_all;   // over V / over all K (written by the prune stage)
   int nnz;                        // nonzero update weights listed (-1: more than kSparseMax)
   int updated;                    // the update was applied by the fused per-instance kernel
+  int nnz_all;                    // nonzero weights of the replan (all CTAs of the instance)
   float pbar[3], v_obs[3], p0[3];
   unsigned int done;              // last-CTA ticket of the update stage
   int col_tests;                  // circle/sphere tests per rollout after reach culling
@@ -61,6 +62,7 @@ struct InstDesc {
   float4* tracks;
   float *S, *w_k, *pN, *eps, *z, *g, *zs, *Sv, *cmin, *nze;
   float* zpart;  // [kPruneRanges] range partials of the softmin normaliser
+  float* rpart;  // [kPruneRanges][TMp] range partials of the dense update (fused kernel)
   int* nzk;
   float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
   int TMp;       // T*m rounded up to a multiple of 4
@@ -99,6 +101,7 @@ struct KArgs {
   int n_inst;
   int n_tiles;
   int n_conc;   // instances whose per-instance stages run at the same time (sizes clusters)
+  int post_dense;   // the fused kernel also applies a dense update (else k_update follows)
 };
 
 __device__ __forceinline__ const InstDesc& desc_of(const KArgs& a, int i) {

@@ -1149,6 +1149,7 @@ struct SelSmem {
 // fused: called after the DBSCAN stage in the same kernel; with few nonzero
 // weights rank 0 then also applies the update and finalizes the replan.
 __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const InstDesc& d, int inst);
+__device__ void finalize(const InstDesc& d, const Req& r);
 
 __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool fused) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -1164,13 +1165,13 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   float* le = sm.le;
   __shared__ float red[33];
   __shared__ unsigned long long bestkey;
-  __shared__ int lcount;
+  __shared__ int lcount, lnz;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int K = d.K, Kp = d.Kp, p = d.p;
   const int mode0 = ctl->mode;
   const int nV = ctl->nV, M = ctl->M;
   int sel = -1, dynamic = 0;
-  if (tid == 0) lcount = 0;
+  if (tid == 0) { lcount = 0; lnz = 0; }
   if (mode0 == CE_MODE_STATIC) {
     // fixed-point scales: S in [-Smax, Smax], g in [-1, 1], at most nV terms
     const float sm = ctl->S_absmax_V;
@@ -1361,7 +1362,10 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
       const unsigned b = __ballot_sync(FULL, nz);
       if (b) {
         int base = 0;
-        if (lane == __ffs(b) - 1) base = atomicAdd(cluster.map_shared_rank(&lcount, 0), __popc(b));
+        if (lane == __ffs(b) - 1) {
+          base = atomicAdd(cluster.map_shared_rank(&lcount, 0), __popc(b));
+          atomicAdd(&lnz, __popc(b));
+        }
         base = __shfl_sync(FULL, base, __ffs(b) - 1) + __popc(b & ((1u << lane) - 1u));
         if (nz && base < kSparseMax) {
           *cluster.map_shared_rank(&lk[base], 0) = k;
@@ -1381,7 +1385,77 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
       z = zc = 0.f;
     }
   }
-  cluster.sync();   // the list and the range partials are complete
+  __syncthreads();
+  if (tid == 0 && lnz) atomicAdd(&ctl->nnz_all, lnz);
+  cluster.sync();   // the list, the range partials and the nonzero count are complete
+  if (fused && a.post_dense && __ldcg(&ctl->nnz_all) > kSparseMax) {
+    // dense update by every CTA: per fixed rollout range and column, the
+    // weighted eps' sum (Kahan, lanes in k order, fixed trees), into rpart;
+    // rank 0 adds the ranges in order below
+    const int TM = d.T * d.m, TMp = d.TMp;
+    const bool arm = is_arm(d.dyn), regen = d.regen;
+    const unsigned long long ctr = *d.counter;
+    const int Lk = (((K + kPruneRanges - 1) / kPruneRanges) + 31) & ~31;
+    const int m_k = kPruneRanges / (CL * nw);
+    for (int j = 0; j < m_k; ++j) {
+      const int v = (rank * nw + wid) * m_k + j;
+      const int kb = min(K, v * Lk), ke = min(K, kb + Lk);
+      auto val = [&](int k, int c) {
+        return regen ? eps_regen(d, ctr, k, c)
+                     : d.eps[arm ? (size_t)k * d.eps_ld_k + c : (size_t)c * d.eps_ld_c + k];
+      };
+      if (!arm) {
+        // lanes over k, four columns at a time (independent loads in flight)
+        for (int c0 = 0; c0 < TM; c0 += 4) {
+          float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int k = kb + lane; k < ke; k += 32) {
+            const float wk = d.w_k[k];
+            float x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = (wk != 0.f && c0 + q < TM) ? val(k, c0 + q) : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk * x[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float t = warp_sum(s[q]);
+            if (lane == 0 && c0 + q < TM) d.rpart[(size_t)v * TMp + c0 + q] = t;
+          }
+        }
+      } else {
+        // lanes over columns, up to six 32-column chunks per pass (one row of
+        // eps' per k), k in steps of two: 12 independent loads in flight
+        constexpr int kCh = 6;
+        for (int cp = 0; cp < TM; cp += 32 * kCh) {
+          float s[kCh], e[kCh];
+#pragma unroll
+          for (int q = 0; q < kCh; ++q) s[q] = e[q] = 0.f;
+          for (int k = kb; k < ke; k += 2) {
+            float wk[2], x[2][kCh];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              wk[u] = k + u < ke ? d.w_k[k + u] : 0.f;
+#pragma unroll
+              for (int q = 0; q < kCh; ++q) {
+                const int c = cp + q * 32 + lane;
+                x[u][q] = (wk[u] != 0.f && c < TM) ? val(k + u, c) : 0.f;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+              for (int q = 0; q < kCh; ++q) kahan_add(s[q], e[q], wk[u] * x[u][q]);
+          }
+#pragma unroll
+          for (int q = 0; q < kCh; ++q) {
+            const int c = cp + q * 32 + lane;
+            if (c < TM) d.rpart[(size_t)v * TMp + c] = s[q];
+          }
+        }
+      }
+    }
+    cluster.sync();   // every range's partials are written
+  }
   if (rank != 0) return;
   // rank 0: Z in range order, the list by ascending k, the control block
   if (wid == 0) {
@@ -1413,9 +1487,22 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
     ctl->invZ = 1.0f / red[32];
     ctl->nnz = nl <= kSparseMax ? nl : -1;
   }
-  if (fused && nl <= kSparseMax) {
+  if (fused) {
     __syncthreads();
-    update_sparse_finalize(a, d, inst);
+    if (nl <= kSparseMax) {
+      update_sparse_finalize(a, d, inst);
+    } else if (a.post_dense) {
+      const int TM = d.T * d.m, TMp = d.TMp;
+      const float iz = 1.0f / red[32];
+      for (int c = tid; c < TM; c += blockDim.x) {
+        float t = 0.f;
+        for (int v = 0; v < kPruneRanges; ++v) t += __ldcg(d.rpart + (size_t)v * TMp + c);
+        d.Unew[c] = d.U[c] + t * iz;
+      }
+      __syncthreads();
+      finalize(d, req_of(a, inst));
+      if (tid == 0) ctl->updated = 1;
+    }
   }
 }
 

@@ -39,6 +39,7 @@ __global__ void k_tracks(KArgs a) {
     d.ctl->status = 0;
     d.ctl->done = 0u;
     d.ctl->updated = 0;
+    d.ctl->nnz_all = 0;
   }
   if (is_arm(d.dyn)) {
     const int total = (T + 1) * n_obs;
