@@ -1519,10 +1519,16 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
 __global__ void __maxnreg__(64) k_post(KArgs a) {
   extern __shared__ __align__(16) int smem_post[];
   cg::cluster_group cluster = cg::this_cluster();
+  // stage clock stamps of rank 0 (diagnostics): start, after prune, after DBSCAN
+  long long* cyc = desc_of(a, blockIdx.x / cluster.num_blocks()).ctl->dbcyc;
+  const bool st = threadIdx.x == 0 && cluster.block_rank() == 0;
+  if (st) cyc[9] = clock64();
   prune_stage(a);
   cluster.sync();   // lists, features and the control block of the instance
+  if (st) cyc[10] = clock64();
   dbscan_stage(a, smem_post);
   cluster.sync();   // labels, cluster count and mode; DBSCAN tables no longer read
+  if (st) cyc[11] = clock64();
   select_stage(a, *reinterpret_cast<SelSmem*>(smem_post), true);
 }
 
