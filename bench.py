@@ -536,6 +536,27 @@ def main() -> None:
             tests.append(int(np.frombuffer(r["diag"].cpu().numpy().tobytes()[72:76], np.int32)[0]))
     stage_ms = {s: float(np.mean(v)) for s, v in prof.items()}
     roll_ms = stage_ms["rollout"]
+    # the fused clustering kernel as the chain runs it: whole-batch half
+    # replans, events around part 1 (prune + DBSCAN + selection + update)
+    reset_episodes()
+    post = []
+    for i in range(args.profile_steps):
+        flush.fill_(float(i))
+        batch.run_part(0, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run_part(1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        post.append(e0.elapsed_time(e1))
+    post_ms = float(np.mean(post))
+    # algorithmic bytes of the clustering stages per rollout (read + written,
+    # each array once): prune reads hit, S, p(x_T), writes V/C_col lists, V
+    # positions, S in V order, z, g; DBSCAN reads z, writes cells, cell order,
+    # coordinates in cell order, labels; selection reads labels, S, g, writes w
+    pd = p_dim
+    post_bytes = float(Ks.sum()) * (4 * (1 + 1 + pd) + 4 * 4 + 8 * pd + 4 * pd
+                                    + 4 * (3 + pd) + 4 * (2 + pd + 1))
     # per instance: obstacle tests per rollout (after culling) from diag
     tests = np.array(tests, dtype=np.float64).reshape(args.profile_steps, N_INST).mean(0)
     Ks = np.array([sc["cfg"]["K"] for sc in scenes], dtype=np.float64)
@@ -641,6 +662,13 @@ def main() -> None:
                      "peak_kind": f"FP32 lanes x 2 x max SM clock ({pk_kind} clock)",
                      "flops_per_rollout": flops_per_rollout,
                      "obstacle_tests_per_rollout": tests_per_rollout},
+        "roofline_post": {"kernel": "k_post (prune + DBSCAN + selection + update)",
+                          "bound": "hbm", "achieved": post_bytes / (post_ms * 1e-3) / 1e9,
+                          "peak": pk.get("hbm_gbs", 6400.0), "unit": "GB/s",
+                          "frac": post_bytes / (post_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6400.0),
+                          "ms_per_launch": post_ms, "algorithmic_bytes": post_bytes,
+                          "note": "latency-bound (dependent L2 accesses between cluster "
+                                  "barriers), far below the bandwidth bound"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         # kernels per replan chain: tracks, rollouts, the fused clustering +
