@@ -555,7 +555,7 @@ def main() -> None:
     # positions, S in V order, z, g; DBSCAN reads z, writes cells, cell order,
     # coordinates in cell order, labels; selection reads labels, S, g, writes w
     pd = p_dim
-    post_bytes = float(Ks.sum()) * (4 * (1 + 1 + pd) + 4 * 4 + 8 * pd + 4 * pd
+    post_bytes = float(sum(sc["cfg"]["K"] for sc in scenes)) * (4 * (1 + 1 + pd) + 4 * 4 + 8 * pd + 4 * pd
                                     + 4 * (3 + pd) + 4 * (2 + pd + 1))
     # per instance: obstacle tests per rollout (after culling) from diag
     tests = np.array(tests, dtype=np.float64).reshape(args.profile_steps, N_INST).mean(0)
