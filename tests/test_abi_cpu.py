@@ -49,7 +49,8 @@ def _params(**kw):
     (dict(sigma=[-1.0, 0.5]), "sigma"), (dict(u_min=[3.0, -2.0]), "u_min"),
     (dict(n_obs_max=100000), "n_obs_max"), (dict(hist_len=0), "hist_len"),
     (dict(norm_eps=0.0), "norm_eps"), (dict(ref_mode=3), "ref_mode"),
-    (dict(n_obs_max=4000, T=100), "shared memory"),
+    (dict(n_obs_max=4000, T=100), "shared memory"), (dict(noise_regen=2), "noise_regen"),
+    (dict(check_j0=-1), "check_j0"), (dict(dyn=4), "dyn"),
 ])
 def test_invalid_parameters_rejected_before_launch(kw, msg):
     P = _params(**kw)
@@ -106,3 +107,20 @@ def test_binding_structs_match_the_header(tmp_path):
             pkg.Params.seed.offset, pkg.Diag.counter.offset, pkg.Diag.col_tests.offset,
             pkg.Request.obs_step.offset]
     assert got == want
+
+
+def test_batch_run_part_rejects_bad_arguments():
+    L = pkg.lib()
+    assert L.ce_mppi_batch_run_part(None, 0, None) == 1
+    assert "NULL" in L.ce_mppi_last_error().decode()
+
+
+def test_twelve_d_arm_dims_and_parameters_accepted_by_validation():
+    # dyn 3 passes the host-side checks up to the device allocation (no GPU
+    # here: creation then fails with a CUDA or memory status, not INVALID_ARG)
+    sc = W.make("arm12", seed=0, K=64)
+    assert pkg.DIMS[sc["cfg"]["dyn"]] == (12, 6, 3)
+    P = pkg.make_params(sc["cfg"], 20)
+    h = C.c_void_p()
+    st = pkg.lib().ce_mppi_create(C.byref(P), None, C.byref(h))
+    assert st != 1, pkg.lib().ce_mppi_last_error().decode()
