@@ -65,7 +65,8 @@ typedef enum {
   CE_MODE_ALLCOL = 1,   /* every rollout collides: standard MPPI over all K         */
   CE_MODE_ALLNOISE = 2, /* DBSCAN found no cluster: standard MPPI over V            */
   CE_MODE_STATIC = 3,   /* cluster of least mean cost (Eq. 14)                      */
-  CE_MODE_DYNAMIC = 4   /* cluster most opposite to the obstacle motion (Eq. 18)    */
+  CE_MODE_DYNAMIC = 4,  /* cluster most opposite to the obstacle motion (Eq. 18)    */
+  CE_MODE_MPPI = 5      /* standard MPPI requested (mppi_only): Eq. 6-7 over all K  */
 } ce_mode_t;
 
 typedef struct {
@@ -81,7 +82,9 @@ typedef struct {
   float u_min[6], u_max[6]; /* input box, u_min <= u_max                           */
   float goal[16];        /* 2-D: goal state (n entries); arm: p_g[3], R_g[9]        */
   float w[8];            /* cost weights: DI (pos, ctrl, terminal);                */
-                         /* unicycle Q[3], H[3] (Eq. 22-23); arm (w_p, w_R, w_c)    */
+                         /* unicycle Q[3], H[3] (Eq. 22-23); arm (w_p, w_R, w_c);   */
+                         /* 2-D robots: w[7] is added once to S of a colliding    */
+                         /* rollout (I_col of Eq. 8; 0 for CE-MPPI, which prunes) */
   int n_obs_max;         /* largest obstacle count a replan may pass, >= 0         */
   int hist_len;          /* H, observations per replan, >= 1                       */
   float robot_radius;    /* 2-D robot disc radius / arm link-sphere radius (m)     */
@@ -91,6 +94,8 @@ typedef struct {
   int ref_mode;          /* 0: colliding rollouts whose first hit is the closest   */
                          /*    hit obstacle (the method overview); 1: all of C_col */
   int check_j0;          /* 1: the current state x_0 also counts for collisions    */
+  int mppi_only;         /* 1: standard MPPI (Eq. 6-7 over all K), no pruning or   */
+                         /*    clustering (the paper's comparison baseline)        */
   int noise_regen;       /* 0: the rollouts store eps' (K*T*m floats) for the      */
                          /*    update; 1: nothing is stored, the update draws the  */
                          /*    same Philox numbers again for the rollouts of       */

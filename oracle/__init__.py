@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("goal", C.c_double * 16), ("w", C.c_double * 8),
         ("hist_len", C.c_int), ("robot_radius", C.c_double), ("norm_eps", C.c_double),
         ("v_static_thresh", C.c_double), ("seed", C.c_uint64), ("counter", C.c_uint64),
-        ("ref_mode", C.c_int), ("check_j0", C.c_int),
+        ("ref_mode", C.c_int), ("check_j0", C.c_int), ("mppi_only", C.c_int),
     ]
 
 
@@ -85,6 +85,7 @@ def make_params(cfg: dict, counter: int = 0) -> Params:
     P.counter = counter
     P.ref_mode = cfg.get("ref_mode", 0)
     P.check_j0 = cfg.get("check_j0", 0)
+    P.mppi_only = cfg.get("mppi_only", 0)
     return P
 
 

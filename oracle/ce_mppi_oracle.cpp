@@ -351,6 +351,9 @@ void orc_rollouts(const orc_params* P, const double* x0, const double* U,
       if (o >= 0 && first_o < 0) { first_o = o; first_j = j + 1; }
     }
     cost += terminal_cost(P, x, tracks + (size_t)T * n_obs * p, radius, n_obs);
+    // 2-D robots: w[7] I_col(tau) (Eq. 8), a collision penalty for standard
+    // MPPI (zero by default: CE-MPPI prunes colliding rollouts instead)
+    if (!is_arm(P->dyn) && first_o >= 0) cost += P->w[7];
     if (S) S[k] = cost;
     if (col) col[k] = first_o >= 0 ? 1 : 0;
     if (hit) hit[k] = first_o;
@@ -600,8 +603,8 @@ void orc_replan(const orc_params* P, const double* x0, const double* U,
   dg.o_star = -1;
   dg.sel_label = -1;
   std::vector<int> members;
-  if (nC == 0 || nV == 0) {
-    dg.mode = nC == 0 ? ORC_MODE_NOCOL : ORC_MODE_ALLCOL;
+  if (P->mppi_only || nC == 0 || nV == 0) {
+    dg.mode = P->mppi_only ? ORC_MODE_MPPI : nC == 0 ? ORC_MODE_NOCOL : ORC_MODE_ALLCOL;
     for (int k = 0; k < K; ++k) members.push_back(k);
   } else {
     dg.o_star = orc_reference_point(P, x0, tracks.data(), radius, n_obs, idxC.data(), nC,

@@ -33,7 +33,7 @@ extern "C" {
 
 enum { ORC_DI = 0, ORC_UNICYCLE = 1, ORC_ARM = 2, ORC_ARM12 = 3 };
 enum { ORC_MODE_NOCOL = 0, ORC_MODE_ALLCOL = 1, ORC_MODE_ALLNOISE = 2,
-       ORC_MODE_STATIC = 3, ORC_MODE_DYNAMIC = 4 };
+       ORC_MODE_STATIC = 3, ORC_MODE_DYNAMIC = 4, ORC_MODE_MPPI = 5 };
 
 typedef struct {
   int dyn;             /* ORC_DI / ORC_UNICYCLE / ORC_ARM / ORC_ARM12         */
@@ -54,6 +54,7 @@ typedef struct {
   uint64_t counter;    /* replan counter (upper Philox counter words)         */
   int ref_mode;        /* 0: colliding rollouts whose first hit is o*; 1: all */
   int check_j0;        /* 1: also test x_0 for collision                      */
+  int mppi_only;       /* 1: standard MPPI (Eq. 6-7 over all K), no clustering */
 } orc_params;
 
 typedef struct {

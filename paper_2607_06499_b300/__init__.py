@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ce_mppi.h")
 DYN_DI, DYN_UNICYCLE, DYN_ARM, DYN_ARM12 = 0, 1, 2, 3
 DIMS = {DYN_DI: (4, 2, 2), DYN_UNICYCLE: (3, 2, 2), DYN_ARM: (6, 6, 3),
         DYN_ARM12: (12, 6, 3)}  # (n, m, p)
-MODES = {0: "nocol", 1: "allcol", 2: "allnoise", 3: "static", 4: "dynamic"}
+MODES = {0: "nocol", 1: "allcol", 2: "allnoise", 3: "static", 4: "dynamic", 5: "mppi"}
 BUF = dict(S=0, HIT=1, PN=2, EPS=3, IDXV=4, IDXC=5, Z=6, G=7, LABEL=8, W=9, HITJ=10, DBCYC=11)
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NO_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY"}
 
@@ -40,7 +40,8 @@ class Params(C.Structure):
         ("u_max", C.c_float * 6), ("goal", C.c_float * 16), ("w", C.c_float * 8),
         ("n_obs_max", C.c_int), ("hist_len", C.c_int), ("robot_radius", C.c_float),
         ("norm_eps", C.c_float), ("v_static_thresh", C.c_float), ("seed", C.c_ulonglong),
-        ("ref_mode", C.c_int), ("check_j0", C.c_int), ("noise_regen", C.c_int),
+        ("ref_mode", C.c_int), ("check_j0", C.c_int), ("mppi_only", C.c_int),
+        ("noise_regen", C.c_int),
     ]
 
 
@@ -156,6 +157,7 @@ def make_params(cfg: dict, n_obs_max: int) -> Params:
     P.robot_radius, P.norm_eps = cfg["robot_radius"], cfg["norm_eps"]
     P.v_static_thresh, P.seed = cfg["v_static_thresh"], cfg["seed"]
     P.ref_mode, P.check_j0 = cfg.get("ref_mode", 0), cfg.get("check_j0", 0)
+    P.mppi_only = cfg.get("mppi_only", 0)
     P.noise_regen = cfg.get("noise_regen", 0)
     return P
 

@@ -98,6 +98,8 @@ ce_status_t validate(const ce_mppi_params* P) {
     return fail(CE_MPPI_ERR_INVALID_ARG, "v_static_thresh must be >= 0");
   if (P->ref_mode < 0 || P->ref_mode > 1) return fail(CE_MPPI_ERR_INVALID_ARG, "ref_mode must be 0 or 1");
   if (P->check_j0 < 0 || P->check_j0 > 1) return fail(CE_MPPI_ERR_INVALID_ARG, "check_j0 must be 0 or 1");
+  if (P->mppi_only < 0 || P->mppi_only > 1)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "mppi_only must be 0 or 1");
   if (P->noise_regen < 0 || P->noise_regen > 1)
     return fail(CE_MPPI_ERR_INVALID_ARG, "noise_regen must be 0 or 1");
   int n, m, p;
@@ -221,6 +223,7 @@ void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h)
   d.dyn = P->dyn; d.K = K; d.Kp = Kp; d.T = P->T; d.m = h->m; d.n = h->n; d.p = h->p;
   d.n_obs_max = P->n_obs_max; d.H = P->hist_len; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
   d.check_j0 = P->check_j0; d.G = G; d.R = R; d.regen = P->noise_regen;
+  d.mppi_only = P->mppi_only;
   d.eps_ld_c = is_arm(P->dyn) ? 1 : Kp;
   d.eps_ld_k = is_arm(P->dyn) ? h->TMp : 1;
   d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;

@@ -52,6 +52,7 @@ struct Ctl {
 struct InstDesc {
   int dyn, K, Kp, T, m, n, p, n_obs_max, H, min_pts, ref_mode, check_j0;
   int regen;                      // eps' is not stored: the update draws it again
+  int mppi_only;                  // standard MPPI: no pruning or clustering
   int G, R, eps_ld_c, eps_ld_k;   // DBSCAN grid size/reach; eps strides (column, rollout)
   float dt, obs_dt, inv_lambda, eps2, cell_inv, robot_radius, norm_eps, v_static_thresh;
   float sigma[6], u_min[6], u_max[6], goal[16], w[8];

@@ -293,10 +293,11 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
     ctl->S_min_V = tv[1];
     ctl->S_min_all = tv[2];
   }
-  if (nC == 0 || nV == 0) {
+  if (nC == 0 || nV == 0 || d.mppi_only) {
     if (tid == 0 && rank == 0) {
       ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = -1;
-      ctl->dynamic = 0; ctl->mode = nC == 0 ? CE_MODE_NOCOL : CE_MODE_ALLCOL;
+      ctl->dynamic = 0;
+      ctl->mode = d.mppi_only ? CE_MODE_MPPI : nC == 0 ? CE_MODE_NOCOL : CE_MODE_ALLCOL;
       for (int i = 0; i < 3; ++i) { ctl->pbar[i] = 0.f; ctl->v_obs[i] = 0.f; ctl->p0[i] = p0s[i]; }
     }
     return;
@@ -1318,7 +1319,7 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   }
   // the update set (all K / V / the selected cluster) and its least cost
   const int mode = mode0 == CE_MODE_STATIC ? (dynamic ? CE_MODE_DYNAMIC : CE_MODE_STATIC) : mode0;
-  const bool over_all = mode == CE_MODE_NOCOL || mode == CE_MODE_ALLCOL;
+  const bool over_all = mode == CE_MODE_NOCOL || mode == CE_MODE_ALLCOL || mode == CE_MODE_MPPI;
   const bool over_V = mode == CE_MODE_ALLNOISE;
   const float smin = over_all ? ctl->S_min_all : over_V ? ctl->S_min_V : d.cmin[sel];
   const float il = d.inv_lambda;

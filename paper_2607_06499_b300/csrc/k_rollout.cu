@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
     const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
     kahan_add(S, Sc, w3 * ex * ex + w4 * ey * ey + w5 * et * et);
   }
+  if (first >= 0) kahan_add(S, Sc, d.w[7]);   // collision penalty (0 for CE-MPPI)
   d.S[k] = S;
   d.hit[k] = first;
   d.hitj[k] = first_j;

@@ -51,7 +51,8 @@ def base_params(dyn: int, K: int, T: int, dt: float, *, lam: float, sigma, u_min
                 goal, w, eps: float, min_pts: int, seed: int, hist_len: int = 5,
                 robot_radius: float = 0.0, obs_dt: float | None = None,
                 norm_eps: float = 1e-6, v_static_thresh: float = 0.05,
-                ref_mode: int = 0, check_j0: int = 0, noise_regen: int = 0) -> dict:
+                ref_mode: int = 0, check_j0: int = 0, noise_regen: int = 0,
+                mppi_only: int = 0) -> dict:
     """A parameter set with the fields both the library and the oracle take."""
     return dict(dyn=dyn, K=int(K), T=int(T), dt=float(dt),
                 obs_dt=float(dt if obs_dt is None else obs_dt), **{"lambda": float(lam)},
@@ -61,7 +62,8 @@ def base_params(dyn: int, K: int, T: int, dt: float, *, lam: float, sigma, u_min
                 w=[float(x) for x in w], hist_len=int(hist_len),
                 robot_radius=float(robot_radius), norm_eps=float(norm_eps),
                 v_static_thresh=float(v_static_thresh), seed=int(seed),
-                ref_mode=int(ref_mode), check_j0=int(check_j0), noise_regen=int(noise_regen))
+                ref_mode=int(ref_mode), check_j0=int(check_j0), noise_regen=int(noise_regen),
+                mppi_only=int(mppi_only))
 
 
 def _place_discs(rng, n, field, r_lo, r_hi, keep_out, margin):

@@ -81,7 +81,10 @@ def _check_replan(sc, counter=0, report=None):
     eps_g = out["EPS"].astype(np.float64)
     pN_g = out["PN"].T.astype(np.float64)
     errs = dict(S=errS, pN=errP, eps=errE)
-    if nC == 0 or nV == 0:
+    if cfg.get("mppi_only", 0):
+        assert diag["mode"] == 5          # standard MPPI over all K
+        members = np.arange(K, dtype=np.int32)
+    elif nC == 0 or nV == 0:
         assert diag["mode"] == (0 if nC == 0 else 1)
         members = np.arange(K, dtype=np.int32)
     else:
@@ -160,6 +163,16 @@ def test_stage_parity_many_clusters(name, K, eps, mp):
     sc["cfg"]["dbscan_eps"], sc["cfg"]["min_pts"] = eps, mp
     diag, errs = _check_replan(sc)
     assert diag["n_clusters"] >= 2
+
+
+@pytest.mark.parametrize("name,K", [("unicycle_blocked", 2000), ("di_blocked", 3000)])
+def test_stage_parity_standard_mppi_with_collision_penalty(name, K):
+    """The comparison baseline: standard MPPI (Eq. 6-7 over all K) with a
+    collision penalty w[7] I_col(tau) in S."""
+    sc = W.make(name, seed=0, K=K, mppi_only=1)
+    sc["cfg"]["w"] = list(sc["cfg"]["w"]) + [0.0] * (7 - len(sc["cfg"]["w"])) + [1000.0]
+    diag, errs = _check_replan(sc)
+    assert diag["n_col"] > 0
 
 
 @pytest.mark.parametrize("ref_mode,check_j0", [(1, 0), (0, 1), (1, 1)])
@@ -494,3 +507,14 @@ def test_batch_run_in_two_parts_same_bits():
             assert np.array_equal(got[s][i][1], ref[s][i][1]), (s, i)
     for obj in [bA, bB] + pls:
         obj.close()
+
+
+def test_task_level_scenarios_run():
+    """Short closed-loop runs of both methods on both scenes (a smoke test of
+    the task-level runner: counts are in range, the robots move)."""
+    from paper_2607_06499_b300 import scenarios as SC
+    for kind in ("static", "crossing"):
+        for mppi in (False, True):
+            r = SC.run(kind, mppi, episodes=4, steps=60)
+            assert r["episodes"] == 4
+            assert 0 <= r["collided"] <= 4 and 0 <= r["reached"] <= 4

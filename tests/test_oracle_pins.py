@@ -505,3 +505,52 @@ def test_arm12_at_rest_matches_the_velocity_arm():
                           np.array([0.1]))
     np.testing.assert_allclose(r12["S"], r6["S"], rtol=1e-14)
     np.testing.assert_allclose(r12["pN"], r6["pN"], atol=1e-14)
+
+
+
+# ------------------------------------------------------- standard MPPI baseline
+def test_collision_penalty_added_once_to_colliding_rollouts():
+    sc = _cfg("di_blocked", K=64, T=30)
+    P0 = oracle.make_params(sc["cfg"])
+    P1 = oracle.make_params(sc["cfg"])
+    P1.w[7] = 123.5
+    hist = W.history(sc, 0)
+    trk = oracle.tracks(P0, hist)
+    r0 = oracle.rollouts(P0, sc["x0"], sc["U0"], trk, sc["radius"])
+    r1 = oracle.rollouts(P1, sc["x0"], sc["U0"], trk, sc["radius"])
+    assert r0["col"].sum() > 0 and (1 - r0["col"]).sum() > 0
+    np.testing.assert_array_equal(r1["col"], r0["col"])
+    np.testing.assert_allclose(r1["S"] - r0["S"], 123.5 * r0["col"], rtol=0, atol=1e-9)
+
+
+def test_standard_mppi_replan_is_the_softmin_over_all_rollouts():
+    sc = _cfg("di_blocked", K=96, T=30, mppi_only=1)
+    P = oracle.make_params(sc["cfg"])
+    out = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
+    assert out["diag"]["mode"] == 5 and out["diag"]["n_col"] > 0
+    # Eq. 6-7 written out: weights softmin(S / lambda) over all K
+    w = np.exp(-(out["S"] - out["S"].min()) / P.lam)
+    w /= w.sum()
+    np.testing.assert_allclose(out["w"], w, rtol=1e-12, atol=1e-15)
+    U_ref = sc["U0"] + np.einsum("k,kjd->jd", w, out["eps"])
+    np.testing.assert_allclose(out["U_new"], U_ref, rtol=1e-12, atol=1e-13)
+
+
+# --------------------------------------------------------- task-level scenes
+def test_scenario_scenes_and_evaluation():
+    from paper_2607_06499_b300 import scenarios as SC
+    s = SC.scene("static", 0, 60)
+    assert s["obs"].shape == (65, 3, 2) and np.allclose(s["obs"][0], s["obs"][-1])
+    c = SC.scene("crossing", 1, 50)
+    v = (c["obs"][1:, 0] - c["obs"][:-1, 0]) / c["dt"]
+    assert np.allclose(v[:, 0], 0.0) and np.all(v[:, 1] > 0.4)
+    # a straight path through the wall collides; a detour above it reaches
+    steps = 60
+    xs = np.linspace(0.0, 4.0, steps + 1)
+    straight = np.stack([xs, np.zeros_like(xs), np.zeros_like(xs)], 1)[:, None, :]
+    r = SC.evaluate([s], straight)
+    assert r["collided"] == 1 and r["reached"] == 0
+    detour = straight.copy()
+    detour[:, 0, 1] = 1.5 * np.sin(np.pi * xs / 4.0)
+    r = SC.evaluate([s], detour)
+    assert r["collided"] == 0 and r["reached"] == 1 and r["time_to_goal_median_s"] > 0
