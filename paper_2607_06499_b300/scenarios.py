@@ -1,8 +1,8 @@
 """Closed-loop task-level runs: CE-MPPI against standard MPPI.
 
 Two synthetic unicycle scenes in the spirit of the paper's evaluation
-(Sec. III-B): a static obstacle group placed across the straight path to the
-goal (Scenario 1), and an obstacle crossing the robot's path (Scenario 2).
+(Sec. III-B): a static obstacle on the straight path to the goal (Scenario 1),
+and an obstacle crossing the robot's path (Scenario 2).
 Many seeded episodes of each method run as one device-resident batch: every
 replan's first control moves the robot through the planner's own model step
 (`x_next` aliases `x0`), the obstacles follow recorded streams, and after the
@@ -34,9 +34,10 @@ def scene(kind: str, seed: int, n_steps: int) -> dict:
     n_rows = n_steps + H
     dt = 0.03
     if kind == "static":
-        # three discs across the path at x ~ 2, a wall about 1.4 m wide
-        c = np.array([[2.0, -0.45], [2.0, 0.0], [2.0, 0.45]]) + rng.uniform(-0.05, 0.05, (3, 2))
-        r = np.full(3, 0.25)
+        # one disc on the straight path (within 2 cm of it): the rollouts split
+        # to both sides, and their weighted average points at the disc
+        c = np.array([[2.0, rng.uniform(-0.02, 0.02)]])
+        r = np.array([0.35])
         obs = np.repeat(c[None], n_rows, axis=0)
     elif kind == "crossing":
         # one disc crossing the path from below, meeting the robot near x = 2

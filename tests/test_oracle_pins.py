@@ -540,7 +540,7 @@ def test_standard_mppi_replan_is_the_softmin_over_all_rollouts():
 def test_scenario_scenes_and_evaluation():
     from paper_2607_06499_b300 import scenarios as SC
     s = SC.scene("static", 0, 60)
-    assert s["obs"].shape == (65, 3, 2) and np.allclose(s["obs"][0], s["obs"][-1])
+    assert s["obs"].shape == (65, 1, 2) and np.allclose(s["obs"][0], s["obs"][-1])
     c = SC.scene("crossing", 1, 50)
     v = (c["obs"][1:, 0] - c["obs"][:-1, 0]) / c["dt"]
     assert np.allclose(v[:, 0], 0.0) and np.all(v[:, 1] > 0.4)
