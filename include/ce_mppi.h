@@ -165,12 +165,14 @@ ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_
  * diag->status.  Errors: INVALID_ARG, CUDA.                                   */
 ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* req);
 
-/* Batches: n handles replanned together, one kernel launch per stage for all of
- * them (instances of different K, T and obstacle count).  The requests are
- * fixed at creation (use obs_step to replay recorded observation streams).
- * With n_branches > 1 the instances are split (balanced by K*T) into that many
- * branches whose stage chains run concurrently on streams of their own, so one
- * branch's single-CTA stages overlap another's rollouts.  With use_graph != 0
+/* Batches: n handles replanned together by one replan chain for all of them
+ * (instances of different K, T and obstacle count): the track kernel, the
+ * rollout kernel, and one kernel running pruning, DBSCAN, selection and the
+ * update as a thread-block cluster per instance (plus the tiled update kernel
+ * for the arms).  The requests are fixed at creation (use obs_step to replay
+ * recorded observation streams).  With n_branches > 1 the instances are split
+ * (balanced by K*T) into that many branches whose chains run concurrently on
+ * streams of their own.  With use_graph != 0
  * the whole batch (fork, branches, join) is captured once as a CUDA graph and
  * replayed by ce_mppi_batch_run.  stream is the cudaStream_t the batch runs on.
  * Every handle must have the same dynamics kind.  Results are bitwise those of

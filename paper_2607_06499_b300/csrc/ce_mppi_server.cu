@@ -5,8 +5,8 @@
 // device.  Replan requests are staged on the host as they arrive; a worker
 // thread forms a batch from every queued session of one dynamics kind as soon
 // as one of its in-flight slots (a non-blocking stream with its own staging
-// buffers) is free, copies the batch's inputs in one transfer, runs the six
-// stages once for the whole batch (instances addressed through the session
+// buffers) is free, copies the batch's inputs in one transfer, runs the replan
+// chain once for the whole batch (instances addressed through the session
 // slot table), and copies the results back in one transfer.  Batches on
 // different slots overlap on the device, so requests that arrive while others
 // run are picked up by the next free slot without waiting for them.  A session
