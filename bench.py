@@ -359,8 +359,8 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=40)
-    ap.add_argument("--branches", type=int, default=2,
-                    help="concurrent branches of the batch (stage overlap)")
+    ap.add_argument("--branches", type=int, default=0,
+                    help="concurrent branches of the batch (0: autotuned)")
     ap.add_argument("--workload", default="unicycle", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served run (0: skip)")
@@ -451,8 +451,8 @@ def main() -> None:
     pipe = None
     if args.pipeline and N_INST >= 2:
         half = N_INST // 2
-        bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False)
-        bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False)
+        bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False, n_branches=0)
+        bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False, n_branches=0)
         side = torch.cuda.Stream()
         graph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
@@ -645,8 +645,8 @@ def main() -> None:
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank",
-                       branches=0 if pipe else args.branches, pipeline=args.pipeline,
-                       noise_regen=args.noise_regen),
+                       pipeline=args.pipeline, noise_regen=args.noise_regen,
+                       batch_config=(pipe[0].config() if pipe else batch.config())),
         "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),
@@ -675,7 +675,7 @@ def main() -> None:
         # update kernel (+ the tiled update for the arms); per step two half
         # chains (pipelined) or one chain per branch (the L2 flush is torch's)
         "gpu_launches": (4 if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12) else 3)
-                        * (2 if pipe else min(args.branches, N_INST)) * args.steps,
+                        * (2 if pipe else batch.config()["n_branches"]) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":

@@ -172,14 +172,23 @@ ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* req);
  * for the arms).  The requests are fixed at creation (use obs_step to replay
  * recorded observation streams).  With n_branches > 1 the instances are split
  * (balanced by K*T) into that many branches whose chains run concurrently on
- * streams of their own.  With use_graph != 0
- * the whole batch (fork, branches, join) is captured once as a CUDA graph and
- * replayed by ce_mppi_batch_run.  stream is the cudaStream_t the batch runs on.
- * Every handle must have the same dynamics kind.  Results are bitwise those of
- * replanning each handle alone.  Errors: INVALID_ARG, NO_MEMORY, CUDA.        */
+ * streams of their own.  n_branches = 0 autotunes: the branch count (1, 2,
+ * 4, 8) and the CTAs per instance of the clustering kernel (1, 2, 4, 8) are
+ * chosen by timing the batch itself (a warm-up and three replans per
+ * candidate; the planners' nominals, counters and the requests' x0 are
+ * restored after each, u_out / x_next / diag receive the trial results) and
+ * cached per (dynamics, log2 largest K, largest T / 16, log2 n).  With
+ * use_graph != 0 the whole batch (fork, branches, join) is captured once as a
+ * CUDA graph and replayed by ce_mppi_batch_run.  stream is the cudaStream_t
+ * the batch runs on.  Every handle must have the same dynamics kind.  Results
+ * are bitwise those of replanning each handle alone.  Errors: INVALID_ARG,
+ * NO_MEMORY, CUDA.                                                            */
 ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_request* reqs,
                                  int n, void* stream, int use_graph, int n_branches,
                                  ce_mppi_batch** out);
+/* The batch's branch count and clustering-kernel CTAs per instance (0: chosen
+ * per launch from the occupancy of the device).  Errors: INVALID_ARG.        */
+ce_status_t ce_mppi_batch_config(const ce_mppi_batch* b, int* n_branches, int* post_ctas);
 /* Queue one replan of every instance of the batch; returns without waiting.  */
 ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
 /* Queue one half of a replan of every instance, without a graph, on stream (a

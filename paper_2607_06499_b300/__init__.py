@@ -72,7 +72,7 @@ class Request(C.Structure):
 EXPORTS = (
     "ce_mppi_create", "ce_mppi_destroy", "ce_mppi_set_nominal", "ce_mppi_get_nominal",
     "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_replan_dev",
-    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_profile",
+    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_config", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
     "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
     "ce_mppi_dbscan_dev", "ce_mppi_dbscan_noalloc_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
@@ -105,6 +105,7 @@ def lib() -> C.CDLL:
                                            C.POINTER(vp)]
         L.ce_mppi_batch_run.argtypes = [vp]
         L.ce_mppi_batch_run_part.argtypes = [vp, i, vp]
+        L.ce_mppi_batch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
         L.ce_mppi_batch_profile.argtypes = [vp, C.POINTER(C.c_float)]
         L.ce_mppi_batch_destroy.argtypes = [vp]
         L.ce_mppi_peek.argtypes = [vp, i, vp, C.c_size_t]
@@ -267,6 +268,13 @@ class Batch:
 
     def run(self):
         _check(lib().ce_mppi_batch_run(self.b))
+
+    def config(self) -> dict:
+        """Branch count and clustering-kernel CTAs per instance (autotuned with
+        n_branches=0; 0 CTAs: chosen per launch from the device occupancy)."""
+        nb, pc = C.c_int(), C.c_int()
+        _check(lib().ce_mppi_batch_config(self.b, C.byref(nb), C.byref(pc)))
+        return dict(n_branches=nb.value, post_ctas=pc.value)
 
     def run_part(self, part: int, stream=None):
         """Half a replan (0: tracks + rollouts, 1: clustering + update) on stream."""

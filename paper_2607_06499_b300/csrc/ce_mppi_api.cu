@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -498,6 +500,7 @@ void run_branches(ce_mppi_batch* b, cudaStream_t s) {
     a.R = b->dreq;
     a.n_inst = br.n;
     a.n_conc = (int)b->hs.size();
+    a.post_ctas = b->post_ctas;
     run_chain(b->dyn, a, br.dtiles_roll, br.n_roll, br.dtiles_upd, br.n_upd, br.smem_roll,
               br.max_cells, s);
     return;
@@ -511,6 +514,7 @@ void run_branches(ce_mppi_batch* b, cudaStream_t s) {
     a.R = b->dreq + br.off;
     a.n_inst = br.n;
     a.n_conc = (int)b->hs.size();
+    a.post_ctas = b->post_ctas;
     run_chain(b->dyn, a, br.dtiles_roll, br.n_roll, br.dtiles_upd, br.n_upd, br.smem_roll,
               br.max_cells, br.stream);
     cudaEventRecord(br.done, br.stream);
@@ -520,13 +524,153 @@ void run_branches(ce_mppi_batch* b, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+ce_status_t batch_create_with(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
+                              void* stream, int use_graph, int n_branches, int post_ctas,
+                              ce_mppi_batch** out);
+ce_status_t batch_autotune(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
+                           void* stream, int* n_branches, int* post_ctas);
+}  // namespace
+
 ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
                                  void* stream, int use_graph, int n_branches,
                                  ce_mppi_batch** out) {
   if (!out) return fail(CE_MPPI_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!hs || !reqs || n < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "empty batch");
-  if (n_branches < 1 || n_branches > 64) return fail(CE_MPPI_ERR_INVALID_ARG, "n_branches in [1, 64]");
+  if (n_branches < 0 || n_branches > 64) return fail(CE_MPPI_ERR_INVALID_ARG, "n_branches in [0, 64]");
+  int post_ctas = 0;
+  if (n_branches == 0) {
+    ce_status_t st = batch_autotune(hs, reqs, n, stream, &n_branches, &post_ctas);
+    if (st != CE_MPPI_OK) return st;
+  }
+  return batch_create_with(hs, reqs, n, stream, use_graph, n_branches, post_ctas, out);
+}
+
+ce_status_t ce_mppi_batch_config(const ce_mppi_batch* b, int* n_branches, int* post_ctas) {
+  if (!b || !n_branches || !post_ctas) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  *n_branches = (int)b->branches.size();
+  *post_ctas = b->post_ctas;
+  return CE_MPPI_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The batch autotuner: the branch count and the fused kernel's CTAs per
+// instance, chosen by timing the batch itself (one warm-up and three timed
+// replans per candidate, every planner's nominal, counter and state restored
+// after each) and cached per shape: (dynamics, log2 of the largest K, largest
+// T / 16, log2 of the instance count).
+struct TuneKey {
+  int dyn, lk, lt, ln;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dyn, lk, lt, ln) < std::tie(o.dyn, o.lk, o.lt, o.ln);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+int ceil_log2(long long v) {
+  int l = 0;
+  while ((1ll << l) < v) ++l;
+  return l;
+}
+
+ce_status_t batch_autotune(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
+                           void* stream, int* n_branches, int* post_ctas) {
+  int maxK = 0, maxT = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle in batch");
+    maxK = std::max(maxK, hs[i]->P.K);
+    maxT = std::max(maxT, hs[i]->P.T);
+  }
+  const TuneKey key{hs[0]->P.dyn, ceil_log2(maxK), (maxT + 15) / 16, ceil_log2(n)};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *n_branches = it->second.first;
+      *post_ctas = it->second.second;
+      return CE_MPPI_OK;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // device copies of the state a replan changes: nominal, counter, x0 (x_next
+  // may alias it)
+  size_t bytes = 0;
+  std::vector<size_t> offU(n), offX(n);
+  for (int i = 0; i < n; ++i) {
+    offU[i] = bytes;
+    bytes += align_up(4 * (size_t)hs[i]->P.T * hs[i]->m + 8, 16);
+    offX[i] = bytes;
+    bytes += align_up(4 * (size_t)hs[i]->n, 16);
+  }
+  char* save = nullptr;
+  cudaError_t e = cudaMalloc(&save, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune scratch");
+  auto copy_state = [&](bool to_save) {
+    for (int i = 0; i < n; ++i) {
+      const InstDesc& d = hs[i]->hdesc;
+      const size_t ub = 4 * (size_t)hs[i]->P.T * hs[i]->m;
+      char* su = save + offU[i];
+      char* sx = save + offX[i];
+      float* x0 = const_cast<float*>(reqs[i].x0);
+      if (to_save) {
+        cudaMemcpyAsync(su, d.U, ub, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(su + ub, d.counter, 8, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(sx, x0, 4 * (size_t)hs[i]->n, cudaMemcpyDeviceToDevice, s);
+      } else {
+        cudaMemcpyAsync(d.U, su, ub, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(d.counter, su + ub, 8, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(x0, sx, 4 * (size_t)hs[i]->n, cudaMemcpyDeviceToDevice, s);
+      }
+    }
+  };
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  float best_ms = 1e30f;
+  int best_nb = 1, best_cl = 0;
+  const int nbs[4] = {1, 2, 4, 8}, cls[4] = {1, 2, 4, 8};
+  for (int a = 0; a < 4; ++a) {
+    if (nbs[a] > n) break;
+    for (int c = 0; c < 4; ++c) {
+      ce_mppi_batch* b = nullptr;
+      if (batch_create_with(hs, reqs, n, stream, 0, nbs[a], cls[c], &b) != CE_MPPI_OK) continue;
+      copy_state(true);
+      run_branches(b, s);   // warm-up
+      cudaEventRecord(ev[0], s);
+      for (int r = 0; r < 3; ++r) run_branches(b, s);
+      cudaEventRecord(ev[1], s);
+      copy_state(false);
+      float ms = 0.f;
+      e = cudaEventSynchronize(ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      free_batch(b);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (ms < best_ms) { best_ms = ms; best_nb = nbs[a]; best_cl = cls[c]; }
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cudaStreamSynchronize(s);
+  cudaFree(save);
+  *n_branches = best_nb;
+  *post_ctas = best_cl;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {best_nb, best_cl};
+  return CE_MPPI_OK;
+}
+
+ce_status_t batch_create_with(ce_mppi_handle* const* hs, const ce_mppi_request* reqs, int n,
+                              void* stream, int use_graph, int n_branches, int post_ctas,
+                              ce_mppi_batch** out) {
+  *out = nullptr;
   const int dyn = hs[0] ? hs[0]->P.dyn : -1;
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle in batch");
@@ -542,6 +686,7 @@ ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_reques
   b->hs.assign(hs, hs + n);
   b->stream = static_cast<cudaStream_t>(stream);
   b->dyn = dyn;
+  b->post_ctas = post_ctas;
   // balance the branches by rollout work (largest instances first)
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -637,6 +782,10 @@ ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_reques
   return CE_MPPI_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 ce_status_t ce_mppi_batch_run(ce_mppi_batch* b) {
   if (!b) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL batch");
   if (b->exec) {
@@ -658,6 +807,7 @@ ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
   a.R = b->dreq;
   a.n_inst = (int)b->hs.size();
   a.n_conc = a.n_inst;
+  a.post_ctas = b->post_ctas;
   if (part == 0) {
     launch_tracks(a, s);
     a.tiles = b->dtiles_roll;

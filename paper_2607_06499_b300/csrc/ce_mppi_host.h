@@ -51,6 +51,7 @@ struct ce_mppi_batch {
   };
   std::vector<Branch> branches;
   cudaEvent_t fork = nullptr;
+  int post_ctas = 0;   // CTAs per instance of the fused kernel (0: occupancy fit)
 };
 
 

@@ -103,6 +103,7 @@ struct KArgs {
   int n_tiles;
   int n_conc;   // instances whose per-instance stages run at the same time (sizes clusters)
   int post_dense;   // the fused kernel also applies a dense update (else k_update follows)
+  int post_ctas;    // CTAs per instance of the fused kernel (0: from the occupancy fit)
 };
 
 __device__ __forceinline__ const InstDesc& desc_of(const KArgs& a, int i) {

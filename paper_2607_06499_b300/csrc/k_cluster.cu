@@ -1835,7 +1835,7 @@ bool launch_post(const KArgs& a, int max_cells, cudaStream_t s) {
   const size_t smem = post_smem(kFitCells[fc]);   // the class's size (a fit was queried for it)
   const ClusterFit& f = g_fit_post[fc];
   if (f.max_active[0] == 0) return false;   // (the launch would not fit)
-  const int cl = cluster_ctas(f, a.n_conc > 0 ? a.n_conc : a.n_inst);
+  const int cl = a.post_ctas > 0 ? a.post_ctas : cluster_ctas(f, a.n_conc > 0 ? a.n_conc : a.n_inst);
   launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, a);
   return true;
 }

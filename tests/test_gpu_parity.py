@@ -319,7 +319,7 @@ def test_replan_deterministic_and_batch_equals_single():
         u2, d2, _, _ = _run(sc)
         assert np.array_equal(u1, u2)                       # bitwise repeatable
         singles.append(u1)
-    for use_graph, nb in ((0, 1), (1, 1), (0, 3), (1, 2)):
+    for use_graph, nb in ((0, 1), (1, 1), (0, 3), (1, 2), (1, 0)):   # (nb 0: autotuned)
         pls, reqs = [], []
         for sc in scs:
             pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
@@ -330,6 +330,8 @@ def test_replan_deterministic_and_batch_equals_single():
                              u_out=torch.zeros((sc["cfg"]["T"], 2), device="cuda")))
             pls.append(pl)
         b = pkg.Batch(pls, reqs, use_graph=bool(use_graph), n_branches=nb)
+        cfg_b = b.config()
+        assert cfg_b["n_branches"] >= 1 and cfg_b["post_ctas"] in (0, 1, 2, 4, 8)
         b.run()
         torch.cuda.synchronize()
         for i, r in enumerate(reqs):
