@@ -91,7 +91,7 @@ def alu_peak_tflops(sm_count: int, mhz: float) -> float:
 
 class ClockSampler:
     """SM clock and throttle reasons sampled every 10 ms through NVML during the
-    timed region (nvidia-smi every 200 ms where NVML is unavailable)."""
+    timed region (nvidia-smi every 50 ms where NVML is unavailable)."""
 
     REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
                ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
@@ -134,14 +134,14 @@ class ClockSampler:
             return
         except Exception:
             pass
-        self.source = "nvidia-smi, 200 ms"
+        self.source = "nvidia-smi, 50 ms"
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -451,8 +451,11 @@ def main() -> None:
     pipe = None
     if args.pipeline and N_INST >= 2:
         half = N_INST // 2
-        bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False, n_branches=0)
-        bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False, n_branches=0)
+        # (not autotuned: the tuner times whole replans, and the halves run
+        # beside each other's rollouts, where the occupancy-chosen cluster
+        # size measures better)
+        bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False)
+        bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False)
         side = torch.cuda.Stream()
         graph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
