@@ -352,7 +352,7 @@ def aggregate(tot_ms: float, units_per_rank: float, steps: int, world: int, dist
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000,
+    ap.add_argument("--steps", type=int, default=4000,
                     help="timed steps (the 200-replan episodes restart every 200 steps)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
