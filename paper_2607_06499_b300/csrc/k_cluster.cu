@@ -1241,9 +1241,10 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
         if (i < end) {
           nL = __ldg(d.label + i);
           nS = __ldg(d.Sv + i);
+          if (dynamic)   // (directions only enter the dynamic criterion)
 #pragma unroll
-          for (int q = 0; q < 3; ++q)
-            if (q < p) nG[q] = __ldg(d.g + (size_t)q * Kp + i);
+            for (int q = 0; q < 3; ++q)
+              if (q < p) nG[q] = __ldg(d.g + (size_t)q * Kp + i);
         }
       };
       fetch(beg + lane);
