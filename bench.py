@@ -367,8 +367,9 @@ def main() -> None:
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
                     help="1: two halves of the episodes software-pipelined in one graph")
-    ap.add_argument("--noise-regen", type=int, default=0, choices=[0, 1],
-                    help="1: perturbations not stored, drawn again by the update")
+    ap.add_argument("--noise-regen", type=int, default=-1, choices=[-1, 0, 1],
+                    help="1: perturbations not stored, drawn again by the update; "
+                         "-1: 1 for 2-D robots (few nonzero weights), 0 for the arms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -404,6 +405,8 @@ def main() -> None:
     props = torch.cuda.get_device_properties(dev)
 
     wl = WORKLOADS[args.workload]
+    if args.noise_regen < 0:
+        args.noise_regen = 0 if args.workload in ("arm", "arm12") else 1
     EPISODE = wl["episode"]
     N_INST = wl["n"]
     seeds = shard_seeds(rank, N_INST)
