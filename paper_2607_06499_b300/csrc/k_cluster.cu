@@ -1132,11 +1132,13 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
 // weights are left unnormalised (the update multiplies by 1/Z); the nonzero
 // ones are also listed by ascending k when there are at most kSparseMax.
 constexpr int kWin = 512;   // clusters per statistics window
+constexpr int kUpdProdMax = 2048;   // products staged per pass of the listed update
 constexpr int kSlots = 2;   // per-warp label cache of the cluster statistics
 
-// One thread-block cluster of CL CTAs per instance.  The statistics of a
-// window of clusters are merged into rank 0's shared memory (distributed
-// shared memory atomics: exact, order-free); rank 0 evaluates the criterion.
+// One thread-block cluster of CL CTAs per instance.  Each CTA sums the
+// statistics of a window of clusters over its slice of V in its own shared
+// memory; rank 0 adds the CTAs' sums through distributed shared memory (exact
+// integers: order-free) and evaluates the criterion.
 // The weights pass splits its domain into kPruneRanges fixed ranges whose
 // normaliser partials are added in range order, so Z does not depend on CL.
 struct SelSmem {
@@ -1194,12 +1196,13 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
     const int Lr = (((nV + CL * nw - 1) / (CL * nw)) + 31) & ~31;
     const int beg = min(nV, (rank * nw + wid) * Lr), end = min(nV, beg + Lr);
     for (int w0 = 0; w0 < M; w0 += kWin) {
-      if (rank == 0)
-        for (int c = tid; c < kWin; c += blockDim.x) {
-          accS[c] = 0ull; accN[c] = 0; accM[c] = 0xffffffffu;
-          accG[0][c] = accG[1][c] = accG[2][c] = 0ull;
-        }
-      cluster.sync();   // rank 0's accumulators are clear
+      // each CTA accumulates its slice of V in its own shared memory; rank 0
+      // adds the CTAs' sums after the window (exact integers: order-free)
+      for (int c = tid; c < kWin; c += blockDim.x) {
+        accS[c] = 0ull; accN[c] = 0; accM[c] = 0xffffffffu;
+        accG[0][c] = accG[1][c] = accG[2][c] = 0ull;
+      }
+      __syncthreads();
       int cl[kSlots];
       long long aS[kSlots], aG[kSlots][3];
       int aN[kSlots];
@@ -1223,12 +1226,12 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
         const uint32_t mk = __reduce_min_sync(FULL, aM[sl]);
         if (lane == 0 && cl[sl] >= 0) {
           const int c = cl[sl] - w0;
-          atomicAdd(cluster.map_shared_rank(&accS[c], 0), (unsigned long long)s);
-          atomicAdd(cluster.map_shared_rank(&accG[0][c], 0), (unsigned long long)g0);
-          atomicAdd(cluster.map_shared_rank(&accG[1][c], 0), (unsigned long long)g1);
-          atomicAdd(cluster.map_shared_rank(&accG[2][c], 0), (unsigned long long)g2);
-          atomicAdd(cluster.map_shared_rank(&accN[c], 0), nn);
-          atomicMin(cluster.map_shared_rank(&accM[c], 0), mk);
+          atomicAdd(&accS[c], (unsigned long long)s);
+          atomicAdd(&accG[0][c], (unsigned long long)g0);
+          atomicAdd(&accG[1][c], (unsigned long long)g1);
+          atomicAdd(&accG[2][c], (unsigned long long)g2);
+          atomicAdd(&accN[c], nn);
+          atomicMin(&accM[c], mk);
         }
         cl[sl] = -1; aS[sl] = 0; aN[sl] = 0; aM[sl] = 0xffffffffu;
         aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
@@ -1293,30 +1296,39 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
       }
 #pragma unroll
       for (int sl = 0; sl < kSlots; ++sl) flush(sl);
-      cluster.sync();   // the window's statistics are complete in rank 0
+      cluster.sync();   // every CTA's sums of the window are final
       if (rank == 0)
         for (int c = tid; c < kWin && w0 + c < M; c += blockDim.x) {
-          const float n = (float)accN[c];
+          unsigned long long tS = 0ull, tG[3] = {0ull, 0ull, 0ull};
+          int tN = 0;
+          unsigned int tM = 0xffffffffu;
+          for (int q = 0; q < CL; ++q) {
+            tS += *cluster.map_shared_rank(&accS[c], q);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) tG[e] += *cluster.map_shared_rank(&accG[e][c], q);
+            tN += *cluster.map_shared_rank(&accN[c], q);
+            tM = min(tM, *cluster.map_shared_rank(&accM[c], q));
+          }
+          const float n = (float)tN;
           float crit;
           if (!dynamic) {
-            crit = ldexpf(__ll2float_rn((long long)accS[c]), -eS) / n;
+            crit = ldexpf(__ll2float_rn((long long)tS), -eS) / n;
           } else {
             float v[3], nn = 0.f;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              v[q] = q < p ? ldexpf(__ll2float_rn((long long)accG[q][c]), -eG) / n : 0.f;
+              v[q] = q < p ? ldexpf(__ll2float_rn((long long)tG[q]), -eG) / n : 0.f;
               nn += v[q] * v[q];
             }
             const float iv = 1.0f / (sqrtf(nn) + d.norm_eps);
             crit = (v[0] * iv) * vh[0] + (v[1] * iv) * vh[1] + (v[2] * iv) * vh[2];
           }
-          d.cmin[w0 + c] = key_float(accM[c]);
+          d.cmin[w0 + c] = key_float(tM);
           atomicMin(&bestkey, ((unsigned long long)float_key(crit) << 32) | (unsigned)(w0 + c));
         }
-      __syncthreads();
+      cluster.sync();   // rank 0 has read every CTA's sums (they may be cleared)
     }
-    cluster.sync();   // rank 0's choice and the cluster minima are final
-    sel = (int)(*cluster.map_shared_rank(&bestkey, 0) & 0xffffffffull);
+    sel = (int)(*cluster.map_shared_rank(&bestkey, 0) & 0xffffffffull);   // (final since the last window)
   }
   // the update set (all K / V / the selected cluster) and its least cost
   const int mode = mode0 == CE_MODE_STATIC ? (dynamic ? CE_MODE_DYNAMIC : CE_MODE_STATIC) : mode0;
@@ -1603,16 +1615,41 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
   const bool arm = is_arm(d.dyn);
   const float iz = ctl->invZ;
   const unsigned long long ctr = *d.counter;
-  for (int c = threadIdx.x; c < TM; c += blockDim.x) {
-    float s = 0.f, e = 0.f;
-    for (int j = 0; j < nnz; ++j) {
-      const int k = d.nzk[j];
-      const float x = d.regen ? eps_regen(d, ctr, k, c)
-                      : arm   ? d.eps[(size_t)k * d.eps_ld_k + c]
-                              : d.eps[(size_t)c * d.eps_ld_c + k];
-      kahan_add(s, e, d.nze[j] * x);
+  // the products w_j eps'_j[c] of JB list entries at a time are formed by all
+  // threads at once (independent loads or Philox draws), then each column's
+  // thread adds them in list order (Kahan)
+  __shared__ float prod[kUpdProdMax];
+  const int JB = max(1, min(kUpdProdMax / max(TM, 1), (int)blockDim.x / max(TM, 1)));
+  float s = 0.f, e = 0.f;   // column threadIdx.x (one pass) 
+  const bool one_pass = TM <= (int)blockDim.x && TM * JB <= kUpdProdMax;
+  if (one_pass) {
+    for (int j0 = 0; j0 < nnz; j0 += JB) {
+      const int jn = min(JB, nnz - j0);
+      for (int t = threadIdx.x; t < jn * TM; t += blockDim.x) {
+        const int jj = t / TM, c = t - jj * TM, k = d.nzk[j0 + jj];
+        const float x = d.regen ? eps_regen(d, ctr, k, c)
+                        : arm   ? d.eps[(size_t)k * d.eps_ld_k + c]
+                                : d.eps[(size_t)c * d.eps_ld_c + k];
+        prod[t] = d.nze[j0 + jj] * x;
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < TM)
+        for (int jj = 0; jj < jn; ++jj) kahan_add(s, e, prod[jj * TM + threadIdx.x]);
+      __syncthreads();
     }
-    d.Unew[c] = d.U[c] + s * iz;
+    if ((int)threadIdx.x < TM) d.Unew[threadIdx.x] = d.U[threadIdx.x] + s * iz;
+  } else {
+    for (int c = threadIdx.x; c < TM; c += blockDim.x) {
+      float sc = 0.f, ec = 0.f;
+      for (int j = 0; j < nnz; ++j) {
+        const int k = d.nzk[j];
+        const float x = d.regen ? eps_regen(d, ctr, k, c)
+                        : arm   ? d.eps[(size_t)k * d.eps_ld_k + c]
+                                : d.eps[(size_t)c * d.eps_ld_c + k];
+        kahan_add(sc, ec, d.nze[j] * x);
+      }
+      d.Unew[c] = d.U[c] + sc * iz;
+    }
   }
   __syncthreads();
   finalize(d, req_of(a, inst));
