@@ -232,7 +232,8 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
-def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: float = 200.0) -> dict:
+def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: float = 200.0,
+              max_batch: int = 1024, n_streams: int = 3) -> dict:
     """The served request loop: controller sessions arrive as a Poisson process
     (rate_hz), 70 % unicycle (K in {1024, 4096, 16384}, T=50, 50 discs) and 30 %
     arm (K in {2048, 4096}, T=32, 20 spheres); each asks for a replan every 20 ms
@@ -249,7 +250,7 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
     x0s = {k: np.stack([t["x0"] for t in v]).astype(np.float32) for k, v in tmpl.items()}
     H = 5
     srv = pkg.Server(mem_budget_bytes=int(budget_gb * (1 << 30)), max_sessions=4096,
-                     max_batch=1024, n_streams=3)
+                     max_batch=max_batch, n_streams=n_streams)
     active = {}   # sid -> [kind, template, t_start, t_end, next_due, K, T]
     rejected = opened = 0
     submitted = {"unicycle": 0, "arm": 0}
@@ -301,7 +302,8 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
             "superseded": st["superseded"], "replans_per_s": st["replans"] / elapsed,
             "rollout_steps_per_s": steps_sub * frac_served / elapsed,
             "p50_ms": 1e3 * st["p50_latency_s"], "p99_ms": 1e3 * st["p99_latency_s"],
-            "mean_batch": st["mean_batch"], "budget_gb": budget_gb, "arrival_rate_hz": rate_hz}
+            "mean_batch": st["mean_batch"], "budget_gb": budget_gb, "arrival_rate_hz": rate_hz,
+            "max_batch": max_batch, "n_streams": n_streams}
 
 
 def plain_mix_latency(pkg, n_each: int = 20) -> dict:
@@ -687,6 +689,12 @@ def main() -> None:
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":
         line["served"] = run_serve(pkg, args.serve_seconds, args.serve_budget_gb)
         line["served"]["plain_mix"] = plain_mix_latency(pkg)
+        # the plain form under the same offered load: the same server with one
+        # instance per launch chain and one stream (a session's queued request
+        # is still replaced by its newer one, which bounds the queue)
+        line["served"]["plain_same_load"] = run_serve(pkg, min(args.serve_seconds, 5.0),
+                                                      args.serve_budget_gb, max_batch=1,
+                                                      n_streams=1)
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
