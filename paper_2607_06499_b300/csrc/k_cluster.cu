@@ -153,7 +153,9 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
   __shared__ unsigned allmask[kMaxObs / 32];
   for (int i = tid; i < nmw; i += blockDim.x) {
     unsigned m = 0u;
-    for (int q = 0; q < CL; ++q) m |= cluster.map_shared_rank(hitmask, q)[i];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)   // (loads of all ranks in flight together)
+      if (q < CL) m |= cluster.map_shared_rank(hitmask, q)[i];
     allmask[i] = m;
   }
   __syncthreads();
@@ -628,10 +630,14 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    offsets, reset of the per-cell summaries; map becomes cell -> occupied
   //    id.  Identical in every CTA.
   int anybad = 0;
-  for (int q = 0; q < CL; ++q) anybad |= *cluster.map_shared_rank(&bad, q);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q < CL) anybad |= *cluster.map_shared_rank(&bad, q);
   for (int c = tid; c < nc; c += blockDim.x) {
     int t = 0;
-    for (int q = 0; q < CL; ++q) t += cluster.map_shared_rank(lcnt, q)[c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < CL) t += cluster.map_shared_rank(lcnt, q)[c];
     map[c] = t;
   }
   __syncthreads();
@@ -704,7 +710,10 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   // this CTA's write cursor in each occupied cell: after the lower ranks' points
   for (int o = tid; o < n_occ; o += blockDim.x) {
     int lo = 0;
-    for (int q = 0; q < rank; ++q) lo += cluster.map_shared_rank(lcnt, q)[ocell[o]];
+    const int co = ocell[o];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < rank) lo += cluster.map_shared_rank(lcnt, q)[co];
     ofill[o] = ostart[o] + lo;
   }
   __syncthreads();
@@ -1302,12 +1311,15 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
           unsigned long long tS = 0ull, tG[3] = {0ull, 0ull, 0ull};
           int tN = 0;
           unsigned int tM = 0xffffffffu;
-          for (int q = 0; q < CL; ++q) {
-            tS += *cluster.map_shared_rank(&accS[c], q);
 #pragma unroll
-            for (int e = 0; e < 3; ++e) tG[e] += *cluster.map_shared_rank(&accG[e][c], q);
-            tN += *cluster.map_shared_rank(&accN[c], q);
-            tM = min(tM, *cluster.map_shared_rank(&accM[c], q));
+          for (int q = 0; q < 8; ++q) {
+            if (q < CL) {   // (loads of all ranks in flight together)
+              tS += *cluster.map_shared_rank(&accS[c], q);
+#pragma unroll
+              for (int e = 0; e < 3; ++e) tG[e] += *cluster.map_shared_rank(&accG[e][c], q);
+              tN += *cluster.map_shared_rank(&accN[c], q);
+              tM = min(tM, *cluster.map_shared_rank(&accM[c], q));
+            }
           }
           const float n = (float)tN;
           float crit;
