@@ -163,6 +163,13 @@ struct ce_mppi_server {
 
   // Take queued sessions of one dynamics kind into flight f (under the lock).
   bool form(Flight& f) {
+    // a session closed while queued leaves its id behind (its planner may
+    // already be pooled or its slot reused): drop such entries first
+    while (!queue.empty()) {
+      const Session& s = sessions[queue.front()];
+      if (s.open && s.queued && s.h) break;
+      queue.pop_front();
+    }
     if (queue.empty()) return false;
     const int dyn = sessions[queue.front()].h->P.dyn;
     std::deque<int> rest;

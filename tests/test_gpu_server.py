@@ -77,3 +77,28 @@ def test_server_replaces_a_queued_request():
     else:                               # t1 had already been launched
         assert r2[1]["counter"] == r1[1]["counter"] + 1
     srv.close()
+
+
+def test_server_sessions_closed_while_queued():
+    """Sessions closed while their requests wait in the queue, under one
+    instance per launch and one stream (the queue stays long): the stale queue
+    entries are dropped, slots and pooled planners are reused, and the
+    surviving sessions' replans still equal their replans alone."""
+    sc = W.make("unicycle", seed=2, K=16384, n_replans=8)
+    srv = pkg.Server(mem_budget_bytes=8 << 30, max_sessions=16, max_batch=1, n_streams=1)
+    keep = srv.open(sc["cfg"], sc["radius"].shape[0])
+    alone = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+    for rnd in range(6):
+        churn = [srv.open(sc["cfg"], sc["radius"].shape[0]) for _ in range(6)]
+        for s in churn:
+            srv.submit(s, sc["x0"], W.history(sc, rnd), sc["radius"], want_result=False)
+        tk = srv.submit(keep, sc["x0"], W.history(sc, rnd), sc["radius"])
+        for s in churn[::-1]:   # most of these are still queued
+            srv.close_session(s)
+        u, diag, _ = _wait(srv, tk, keep)
+        u_ref, _ = alone.replan(sc["x0"], W.history(sc, rnd), sc["radius"])
+        assert diag["status"] == 0 and diag["counter"] == rnd
+        assert np.array_equal(u, u_ref), rnd
+    assert srv.stats()["sessions_open"] == 1
+    srv.close()
+    alone.close()
