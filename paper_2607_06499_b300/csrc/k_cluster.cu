@@ -44,6 +44,16 @@ __device__ __forceinline__ int block_scan_flag(bool f, int* wsum, int* total) {
   return r;
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async), and the wait for all
+// of this thread's copies.
+__device__ __forceinline__ void async_copy4(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, float* p0) {
   if (is_arm(d.dyn)) {
     float q[6], O[7][3], R[9];
@@ -69,7 +79,7 @@ __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, fl
 // C_col, each k's position in V and S in V order, and sums the terminal
 // positions for pbar; the CTAs exchange those partial sums (added in rank
 // order: deterministic); pass 3 writes the features.
-__device__ __forceinline__ void prune_stage(const KArgs& a) {
+__device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int inst = blockIdx.x / CL;
@@ -89,6 +99,14 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
   const int nmw = (n_obs + 31) / 32;
   const int* __restrict__ hit = d.hit;
   const float* __restrict__ pN = d.pN;
+  const float* __restrict__ Sg = d.S;
+  int* idxV = d.idxV;
+  int* idxC = d.idxC;
+  int* vpos = d.vpos;
+  float* Sv = d.Sv;
+  float* zf = d.z;
+  float* gf = d.g;
+  const int ref_mode = d.ref_mode;
   for (int i = tid; i < nmw; i += blockDim.x) hitmask[i] = 0u;
   if (tid == 0) {
     best = ~0ull;
@@ -103,19 +121,43 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
   const int L = m_r * Lv;
   const int beg = min(K, (rank * nw + wid) * L), end = min(K, beg + L);
   const unsigned lt = (1u << lane) - 1u;
+  // The warp's rollouts are taken kPG steps of 32 at a time, the inputs of a
+  // group (first hit, S, p(x_T)) loaded together.  A warp whose range is one
+  // group keeps them in registers for all three passes.
+  constexpr int kPG = 2;
+  const bool one_group = end - beg <= 32 * kPG;
+  int hc[kPG];
+  float sc[kPG], pc[kPG][3];
+  auto load_group = [&](int g0, bool want_s, bool want_p) {
+#pragma unroll
+    for (int u = 0; u < kPG; ++u) {
+      const int k = g0 + 32 * u + lane;
+      const bool in = k < end;
+      hc[u] = in ? __ldg(hit + k) : -1;
+      sc[u] = in && want_s ? __ldg(Sg + k) : INFINITY;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        pc[u][c] = in && want_p && c < p ? __ldg(pN + (size_t)c * Kp + k) : 0.f;
+    }
+  };
   // ---- pass 1
   {
     unsigned long long cnt = 0;
-#pragma unroll 4
-    for (int s0 = beg; s0 < end; s0 += 32) {
+    for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
+    load_group(g0, one_group, one_group);
+#pragma unroll
+    for (int u = 0; u < kPG; ++u) {
+      const int s0 = g0 + 32 * u;
+      if (s0 >= end) break;
       const int k = s0 + lane;
-      const int h = k < end ? __ldg(hit + k) : -1;
+      const int h = hc[u];
       // one shared-memory OR per distinct mask word in the warp
       const unsigned grp = __match_any_sync(FULL, h >= 0 ? (h >> 5) : -1);
       const unsigned bits = __reduce_or_sync(grp, h >= 0 ? 1u << (h & 31) : 0u);
       if (h >= 0 && lane == __ffs(grp) - 1) atomicOr(&hitmask[h >> 5], bits);
       cnt += __popc(__ballot_sync(FULL, k < end && h < 0)) |
              ((unsigned long long)__popc(__ballot_sync(FULL, h >= 0)) << 32);
+    }
     }
     if (lane == 0) wpack[wid] = cnt;
   }
@@ -174,6 +216,17 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
   __syncthreads();
   const int nV = (int)(tall & 0xffffffffull), nC = (int)(tall >> 32);
   const int o_star = nC > 0 ? (int)(best & 0xffffffffull) : -1;
+  // newest and oldest observation of o* for its velocity (Eq. 17): copied
+  // into shared memory now (asynchronously, no registers held), used at the end
+  __shared__ float vo_obs[2][3];
+  // (only on the clustering path, which waits for them before its end)
+  if (tid == 0 && rank == 0 && o_star >= 0 && nV > 0 && !d.mppi_only) {
+    const float* h = hist_of(r, d);
+    for (int c = 0; c < p; ++c) {
+      async_copy4(&vo_obs[0][c], h + ((size_t)(d.H - 1) * n_obs + o_star) * p + c);
+      async_copy4(&vo_obs[1][c], h + (size_t)o_star * p + c);
+    }
+  }
   // ---- pass 2: lists, S in V order, S extremes; pbar sums over the colliding
   // rollouts whose first hit is o* (ref_mode 0) or over all of them (ref_mode 1)
   float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
@@ -194,35 +247,40 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
     // one loop over the warp's ranges (loads of consecutive steps overlap);
     // each range's sums are flushed at its end
     int jr = 0;
-#pragma unroll 4
-    for (int s0 = beg; s0 < end; s0 += 32) {
+    for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
+    if (!one_group) load_group(g0, true, true);
+#pragma unroll
+    for (int u = 0; u < kPG; ++u) {
+      const int s0 = g0 + 32 * u;
+      if (s0 >= end) break;
       const int k = s0 + lane;
-      const int h = k < end ? __ldg(hit + k) : -1;
-      const float Sk = k < end ? __ldg(d.S + k) : INFINITY;
+      const int h = hc[u];
+      const float Sk = sc[u];
       const bool isV = k < end && h < 0, isC = h >= 0;
       const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
       amin = fminf(amin, Sk);
       if (isV) {
         const int pos = bv + __popc(mv & lt);
-        d.idxV[pos] = k;
-        d.vpos[k] = pos;
-        d.Sv[pos] = Sk;
+        idxV[pos] = k;
+        vpos[k] = pos;
+        Sv[pos] = Sk;
         vmax = fmaxf(vmax, fabsf(Sk));
         vmin = fminf(vmin, Sk);
       }
       if (isC) {
-        d.idxC[bc + __popc(mc & lt)] = k;
-        d.vpos[k] = -1;
-        if (d.ref_mode != 0 || h == o_star) {
+        idxC[bc + __popc(mc & lt)] = k;
+        vpos[k] = -1;
+        if (ref_mode != 0 || h == o_star) {
           cntp += 1.f;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            if (c < p) kahan_add(acc[c], cmp[c], __ldg(pN + (size_t)c * Kp + k));
+            if (c < p) kahan_add(acc[c], cmp[c], pc[u][c]);
         }
       }
       bv += __popc(mv);
       bc += __popc(mc);
       if (s0 + 32 - beg == (jr + 1) * Lv) flush(v0 + jr++);
+    }
     }
     for (; jr < m_r; ++jr) flush(v0 + jr);   // a range cut by K, and ranges past it
   }
@@ -257,19 +315,19 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
   }
   cluster.sync();   // every rank's extremes and range partials are final
   __shared__ float tv[7];
-  if (wid == 0) {
-    // lane l adds ranges 8l .. 8l+7 (owned by rank 8l / (32 m_r)), then a
-    // fixed tree over the lanes
+  if (wid < 4) {
+    // warp q takes partial q (count, sum x, y, z): lane l adds ranges
+    // 8l .. 8l+7 (owned by rank 8l / (32 m_r)), then a fixed tree over the
+    // lanes
     constexpr int per = kPruneRanges / 32;
     const int own = 32 * m_r;   // ranges per rank
-    const float* vp = cluster.map_shared_rank(&vpart[0][0], (per * lane) / own);
-    float c4[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* vp = cluster.map_shared_rank(&vpart[wid][0], (per * lane) / own);
+    float c1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < per; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) c4[q] += vp[q * kPruneRanges + per * lane + j];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) c4[q] = warp_sum(c4[q]);
+    for (int j = 0; j < per; ++j) c1 += vp[per * lane + j];
+    c1 = warp_sum(c1);
+    if (lane == 0) tv[3 + wid] = c1;
+  } else if (wid == 4) {
     float e3[3] = {0.f, INFINITY, INFINITY};
     if (lane < CL) {
       const float* rr = cluster.map_shared_rank(&red[0][0], lane);
@@ -283,13 +341,13 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
       e3[1] = fminf(e3[1], __shfl_xor_sync(FULL, e3[1], o));
       e3[2] = fminf(e3[2], __shfl_xor_sync(FULL, e3[2], o));
     }
-    if (lane == 0) {
-      tv[0] = e3[0]; tv[1] = e3[1]; tv[2] = e3[2];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) tv[3 + q] = c4[q];
-    }
+    if (lane == 0) { tv[0] = e3[0]; tv[1] = e3[1]; tv[2] = e3[2]; }
   }
-  cluster.sync();   // no distributed shared memory access after this point
+  // no distributed shared memory access after this point; inside the fused
+  // kernel the caller's cluster barrier after this stage keeps every CTA
+  // (and its shared memory) alive until all reads are done
+  if (fused) __syncthreads();
+  else cluster.sync();
   if (tid == 0 && rank == 0) {
     ctl->S_absmax_V = tv[0];
     ctl->S_min_V = tv[1];
@@ -312,10 +370,14 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
   const float ne = d.norm_eps;
   {
     int bv = (int)(wpack[wid] & 0xffffffffull) + (int)(cbase & 0xffffffffull);
-#pragma unroll 2
-    for (int s0 = beg; s0 < end; s0 += 32) {
+    for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
+    if (!one_group) load_group(g0, false, true);
+#pragma unroll
+    for (int u = 0; u < kPG; ++u) {
+      const int s0 = g0 + 32 * u;
+      if (s0 >= end) break;
       const int k = s0 + lane;
-      const bool isV = k < end && __ldg(hit + k) < 0;
+      const bool isV = k < end && hc[u] < 0;
       const unsigned mv = __ballot_sync(FULL, isV);
       if (isV) {
         const int i = bv + __popc(mv & lt);
@@ -323,7 +385,7 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (c >= p) continue;
-          const float pk = __ldg(pN + (size_t)c * Kp + k);
+          const float pk = pc[u][c];
           dv[c] = pk - pbar[c];
           ev[c] = pk - p0s[c];
           nd += dv[c] * dv[c];
@@ -333,30 +395,30 @@ __device__ __forceinline__ void prune_stage(const KArgs& a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (c >= p) continue;
-          d.z[(size_t)c * Kp + i] = dv[c] * izd;
-          d.g[(size_t)c * Kp + i] = ev[c] * izn;
+          zf[(size_t)c * Kp + i] = dv[c] * izd;
+          gf[(size_t)c * Kp + i] = ev[c] * izn;
         }
       }
       bv += __popc(mv);
     }
+    }
   }
   if (tid == 0 && rank == 0) {
-    const float* h = hist_of(r, d);
     const int H = d.H;
     const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
+    async_wait_all();   // this thread's copies of o*'s observations
     ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = o_star;
     ctl->dynamic = 0; ctl->mode = CE_MODE_STATIC;
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       ctl->pbar[c] = c < p ? pbar[c] : 0.f;
       ctl->p0[c] = p0s[c];
-      ctl->v_obs[c] = c < p ? (h[((size_t)(H - 1) * n_obs + o_star) * p + c] -
-                               h[(size_t)o_star * p + c]) * inv
-                            : 0.f;
+      ctl->v_obs[c] = c < p ? (vo_obs[0][c] - vo_obs[1][c]) * inv : 0.f;
     }
   }
 }
 
-__global__ void __maxnreg__(64) k_prune(KArgs a) { prune_stage(a); }
+__global__ void __maxnreg__(64) k_prune(KArgs a) { prune_stage(a, false); }
 
 // ========================================================================= DBSCAN
 // Grid-binned DBSCAN over n points z ([p][ld], coordinates in [-1, 1]).  The
@@ -851,6 +913,8 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    pair for a core pair within eps (non-core positions hold ~index).  In
   //    2-D, two rounds: touching cells (offsets within 1) first, then the
   //    cells two apart, most of which are joined by then and need no search.
+  //    (Spreading one cell's candidates over several warps measured slower:
+  //    the concurrent unions contend on rank 0's parents.)
   const int side = 2 * R + 1, nofs = p == 3 ? side * side * side : side * side;
   for (int ring = p == 3 ? R : 1; ring <= R; ++ring) {   // (3-D: one round)
     if (ring > 1) cluster.sync();   // the touching cells' unions are done
@@ -1549,7 +1613,7 @@ __global__ void __maxnreg__(64) k_post(KArgs a) {
   long long* cyc = desc_of(a, blockIdx.x / cluster.num_blocks()).ctl->dbcyc;
   const bool st = threadIdx.x == 0 && cluster.block_rank() == 0;
   if (st) cyc[9] = clock64();
-  prune_stage(a);
+  prune_stage(a, true);
   cluster.sync();   // lists, features and the control block of the instance
   if (st) cyc[10] = clock64();
   dbscan_stage(a, smem_post);
