@@ -306,6 +306,45 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
             "max_batch": max_batch, "n_streams": n_streams}
 
 
+STAMP_PHASES = ("cells and per-CTA counts", "occupied cells, offsets, cursors",
+                "scatter into cell order, cell boxes", "core flags", "core boxes",
+                "cell unions", "components, ids, core labels", "border points")
+
+
+def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
+    """SM clock stamps that the fused clustering kernel leaves per instance
+    (thread 0 of rank 0 of its cluster): kernel start, end of the prune stage,
+    the DBSCAN phases, end of the DBSCAN stage.  Mean and max cycles over the
+    replans of n_steps steps (each step synchronised and the stamps read back;
+    a replan that clustered contributes its DBSCAN phases); the episodes are
+    restarted every `episode` steps, as in the timed loop."""
+    import torch
+    prune, dbs, phases = [], [], []
+    last = [None] * len(planners)
+    for s in range(n_steps):
+        if s and s % episode == 0:
+            restart()
+        replay()
+        torch.cuda.synchronize()
+        for i, pl in enumerate(planners):
+            c = pl.peek("DBCYC")
+            if last[i] is not None and c[9] == last[i][9]:
+                continue   # this instance did not replan in the step
+            last[i] = c.copy()
+            prune.append(c[10] - c[9])
+            if c[0] > c[10] and c[11] > c[8]:   # clustered in this replan
+                phases.append(np.diff(c[0:9]))
+                dbs.append(c[11] - c[10])
+    out = {"replans": len(prune), "clustered": len(dbs),
+           "prune": [int(np.mean(prune)), int(np.max(prune))] if prune else None,
+           "dbscan": [int(np.mean(dbs)), int(np.max(dbs))] if dbs else None}
+    if phases:
+        ph = np.array(phases)
+        out["dbscan_phases"] = {n: [int(ph[:, k].mean()), int(ph[:, k].max())]
+                                for k, n in enumerate(STAMP_PHASES)}
+    return out
+
+
 def plain_mix_latency(pkg, n_each: int = 20) -> dict:
     """Plain form on the served mix: each replan alone through the blocking
     host-buffer call (launch chain + stream sync per replan)."""
@@ -369,6 +408,12 @@ def main() -> None:
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
                     help="1: two halves of the episodes software-pipelined in one graph")
+    ap.add_argument("--pipe-post-ctas", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="clustering-kernel CTAs per instance in the pipelined halves "
+                         "(0: from the occupancy, as if each half ran alone)")
+    ap.add_argument("--stamps", type=int, default=0,
+                    help="pipelined steps over which to read the clustering kernel's stage "
+                         "clock stamps (0: off)")
     ap.add_argument("--noise-regen", type=int, default=-1, choices=[-1, 0, 1],
                     help="1: perturbations not stored, drawn again by the update; "
                          "-1: 1 for 2-D robots (few nonzero weights), 0 for the arms")
@@ -461,6 +506,8 @@ def main() -> None:
         # size measures better)
         bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False)
         bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False)
+        bA.set_post_ctas(args.pipe_post_ctas)
+        bB.set_post_ctas(args.pipe_post_ctas)
         side = torch.cuda.Stream()
         graph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
@@ -558,6 +605,14 @@ def main() -> None:
         torch.cuda.synchronize()
         post.append(e0.elapsed_time(e1))
     post_ms = float(np.mean(post))
+    stamps = None
+    if args.stamps > 0:
+        def restart():
+            reset_episodes()
+            prologue()
+
+        restart()
+        stamps = stage_stamps(planners, step, restart, args.stamps, EPISODE)
     # algorithmic bytes of the clustering stages per rollout (read + written,
     # each array once): prune reads hit, S, p(x_T), writes V/C_col lists, V
     # positions, S in V order, z, g; DBSCAN reads z, writes cells, cell order,
@@ -653,7 +708,8 @@ def main() -> None:
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank",
-                       pipeline=args.pipeline, noise_regen=args.noise_regen,
+                       pipeline=args.pipeline, pipe_post_ctas=args.pipe_post_ctas,
+                       noise_regen=args.noise_regen,
                        batch_config=(pipe[0].config() if pipe else batch.config())),
         "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -686,6 +742,8 @@ def main() -> None:
                         * (2 if pipe else batch.config()["n_branches"]) * args.steps,
         "clocks": clk,
     }
+    if stamps is not None:
+        line["post_stamps_cycles"] = stamps
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":
         line["served"] = run_serve(pkg, args.serve_seconds, args.serve_budget_gb)
         line["served"]["plain_mix"] = plain_mix_latency(pkg)

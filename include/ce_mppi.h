@@ -189,6 +189,16 @@ ce_status_t ce_mppi_batch_create(ce_mppi_handle* const* hs, const ce_mppi_reques
 /* The batch's branch count and clustering-kernel CTAs per instance (0: chosen
  * per launch from the occupancy of the device).  Errors: INVALID_ARG.        */
 ce_status_t ce_mppi_batch_config(const ce_mppi_batch* b, int* n_branches, int* post_ctas);
+/* Set the clustering-kernel CTAs per instance of the batch's later launches
+ * made without a graph (ce_mppi_batch_run_part; ce_mppi_batch_run of a batch
+ * created with use_graph = 0): 1, 2, 4 or 8 CTAs (one thread-block cluster
+ * per instance), or 0 to choose per launch from the occupancy of the device
+ * as if the batch ran alone.  A batch whose clustering runs beside other work
+ * (the halves of a software pipeline) may give the SMs to that work with
+ * fewer CTAs.  The results do not depend on it (the stage sums run in an
+ * order fixed by K alone).  Errors: INVALID_ARG (NULL batch, another value,
+ * or a batch that replays a captured graph, whose launches are fixed).      */
+ce_status_t ce_mppi_batch_set_post_ctas(ce_mppi_batch* b, int post_ctas);
 /* Queue one replan of every instance of the batch; returns without waiting.  */
 ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
 /* Queue one half of a replan of every instance, without a graph, on stream (a

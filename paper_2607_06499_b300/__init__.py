@@ -72,7 +72,8 @@ class Request(C.Structure):
 EXPORTS = (
     "ce_mppi_create", "ce_mppi_destroy", "ce_mppi_set_nominal", "ce_mppi_get_nominal",
     "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_replan_dev",
-    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_config", "ce_mppi_batch_profile",
+    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_config",
+    "ce_mppi_batch_set_post_ctas", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
     "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
     "ce_mppi_dbscan_dev", "ce_mppi_dbscan_noalloc_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
@@ -106,6 +107,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_batch_run.argtypes = [vp]
         L.ce_mppi_batch_run_part.argtypes = [vp, i, vp]
         L.ce_mppi_batch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
+        L.ce_mppi_batch_set_post_ctas.argtypes = [vp, i]
         L.ce_mppi_batch_profile.argtypes = [vp, C.POINTER(C.c_float)]
         L.ce_mppi_batch_destroy.argtypes = [vp]
         L.ce_mppi_peek.argtypes = [vp, i, vp, C.c_size_t]
@@ -275,6 +277,11 @@ class Batch:
         nb, pc = C.c_int(), C.c_int()
         _check(lib().ce_mppi_batch_config(self.b, C.byref(nb), C.byref(pc)))
         return dict(n_branches=nb.value, post_ctas=pc.value)
+
+    def set_post_ctas(self, n: int):
+        """Clustering-kernel CTAs per instance of later launches without a
+        graph (0: from the device occupancy, as if the batch ran alone)."""
+        _check(lib().ce_mppi_batch_set_post_ctas(self.b, int(n)))
 
     def run_part(self, part: int, stream=None):
         """Half a replan (0: tracks + rollouts, 1: clustering + update) on stream."""

@@ -554,6 +554,15 @@ ce_status_t ce_mppi_batch_config(const ce_mppi_batch* b, int* n_branches, int* p
   return CE_MPPI_OK;
 }
 
+ce_status_t ce_mppi_batch_set_post_ctas(ce_mppi_batch* b, int post_ctas) {
+  if (!b) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL batch");
+  if (post_ctas != 0 && post_ctas != 1 && post_ctas != 2 && post_ctas != 4 && post_ctas != 8)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "post_ctas must be 0, 1, 2, 4 or 8");
+  if (b->exec) return fail(CE_MPPI_ERR_INVALID_ARG, "the batch replays a captured graph");
+  b->post_ctas = post_ctas;
+  return CE_MPPI_OK;
+}
+
 }  // extern "C"
 
 namespace {

@@ -454,9 +454,11 @@ def test_noise_regen_same_bits(name, kw):
         assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
 
 
-def test_batch_run_in_two_parts_same_bits():
+@pytest.mark.parametrize("ctas", [(0, 0), (4, 1), (2, 8)])
+def test_batch_run_in_two_parts_same_bits(ctas):
     """Half replans (tracks + rollouts, then clustering + update) of two
-    batches interleaved on two streams give the bits of whole replans."""
+    batches interleaved on two streams give the bits of whole replans, with
+    any clustering-kernel CTAs per instance in either half."""
     scs = [W.make("unicycle_blocked", seed=s, K=3000, n_replans=4) for s in range(4)]
 
     def setup():
@@ -488,6 +490,8 @@ def test_batch_run_in_two_parts_same_bits():
     pls, reqs = setup()
     bA = pkg.Batch(pls[:2], reqs[:2], use_graph=False)
     bB = pkg.Batch(pls[2:], reqs[2:], use_graph=False)
+    bA.set_post_ctas(ctas[0])
+    bB.set_post_ctas(ctas[1])
     main, side = torch.cuda.current_stream(), torch.cuda.Stream()
     bB.run_part(0, main)
     got = []
@@ -507,8 +511,24 @@ def test_batch_run_in_two_parts_same_bits():
         for i in range(4):
             assert np.array_equal(got[s][i][0], ref[s][i][0]), (s, i)
             assert np.array_equal(got[s][i][1], ref[s][i][1]), (s, i)
+    with pytest.raises(Exception):
+        bA.set_post_ctas(3)
     for obj in [bA, bB] + pls:
         obj.close()
+
+
+def test_set_post_ctas_rejected_for_a_graph_batch():
+    sc = W.make("unicycle", seed=0, K=1024)
+    pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+    rq = dict(x0=torch.tensor(sc["x0"], dtype=torch.float32, device="cuda"),
+              hist=torch.tensor(sc["obs"][:sc["cfg"]["hist_len"]], dtype=torch.float32,
+                                device="cuda").contiguous(),
+              radius=torch.tensor(sc["radius"], dtype=torch.float32, device="cuda"))
+    b = pkg.Batch([pl], [rq], use_graph=True)
+    with pytest.raises(Exception):
+        b.set_post_ctas(2)
+    b.close()
+    pl.close()
 
 
 def test_task_level_scenarios_run():
