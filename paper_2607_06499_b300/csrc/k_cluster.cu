@@ -144,20 +144,20 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
   {
     unsigned long long cnt = 0;
     for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
-    load_group(g0, one_group, one_group);
+      load_group(g0, one_group, one_group);
 #pragma unroll
-    for (int u = 0; u < kPG; ++u) {
-      const int s0 = g0 + 32 * u;
-      if (s0 >= end) break;
-      const int k = s0 + lane;
-      const int h = hc[u];
-      // one shared-memory OR per distinct mask word in the warp
-      const unsigned grp = __match_any_sync(FULL, h >= 0 ? (h >> 5) : -1);
-      const unsigned bits = __reduce_or_sync(grp, h >= 0 ? 1u << (h & 31) : 0u);
-      if (h >= 0 && lane == __ffs(grp) - 1) atomicOr(&hitmask[h >> 5], bits);
-      cnt += __popc(__ballot_sync(FULL, k < end && h < 0)) |
-             ((unsigned long long)__popc(__ballot_sync(FULL, h >= 0)) << 32);
-    }
+      for (int u = 0; u < kPG; ++u) {
+        const int s0 = g0 + 32 * u;
+        if (s0 >= end) break;
+        const int k = s0 + lane;
+        const int h = hc[u];
+        // one shared-memory OR per distinct mask word in the warp
+        const unsigned grp = __match_any_sync(FULL, h >= 0 ? (h >> 5) : -1);
+        const unsigned bits = __reduce_or_sync(grp, h >= 0 ? 1u << (h & 31) : 0u);
+        if (h >= 0 && lane == __ffs(grp) - 1) atomicOr(&hitmask[h >> 5], bits);
+        cnt += __popc(__ballot_sync(FULL, k < end && h < 0)) |
+               ((unsigned long long)__popc(__ballot_sync(FULL, h >= 0)) << 32);
+      }
     }
     if (lane == 0) wpack[wid] = cnt;
   }
@@ -248,39 +248,39 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
     // each range's sums are flushed at its end
     int jr = 0;
     for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
-    if (!one_group) load_group(g0, true, true);
+      if (!one_group) load_group(g0, true, true);
 #pragma unroll
-    for (int u = 0; u < kPG; ++u) {
-      const int s0 = g0 + 32 * u;
-      if (s0 >= end) break;
-      const int k = s0 + lane;
-      const int h = hc[u];
-      const float Sk = sc[u];
-      const bool isV = k < end && h < 0, isC = h >= 0;
-      const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
-      amin = fminf(amin, Sk);
-      if (isV) {
-        const int pos = bv + __popc(mv & lt);
-        idxV[pos] = k;
-        vpos[k] = pos;
-        Sv[pos] = Sk;
-        vmax = fmaxf(vmax, fabsf(Sk));
-        vmin = fminf(vmin, Sk);
-      }
-      if (isC) {
-        idxC[bc + __popc(mc & lt)] = k;
-        vpos[k] = -1;
-        if (ref_mode != 0 || h == o_star) {
-          cntp += 1.f;
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (c < p) kahan_add(acc[c], cmp[c], pc[u][c]);
+      for (int u = 0; u < kPG; ++u) {
+        const int s0 = g0 + 32 * u;
+        if (s0 >= end) break;
+        const int k = s0 + lane;
+        const int h = hc[u];
+        const float Sk = sc[u];
+        const bool isV = k < end && h < 0, isC = h >= 0;
+        const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
+        amin = fminf(amin, Sk);
+        if (isV) {
+          const int pos = bv + __popc(mv & lt);
+          idxV[pos] = k;
+          vpos[k] = pos;
+          Sv[pos] = Sk;
+          vmax = fmaxf(vmax, fabsf(Sk));
+          vmin = fminf(vmin, Sk);
         }
+        if (isC) {
+          idxC[bc + __popc(mc & lt)] = k;
+          vpos[k] = -1;
+          if (ref_mode != 0 || h == o_star) {
+            cntp += 1.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              if (c < p) kahan_add(acc[c], cmp[c], pc[u][c]);
+          }
+        }
+        bv += __popc(mv);
+        bc += __popc(mc);
+        if (s0 + 32 - beg == (jr + 1) * Lv) flush(v0 + jr++);
       }
-      bv += __popc(mv);
-      bc += __popc(mc);
-      if (s0 + 32 - beg == (jr + 1) * Lv) flush(v0 + jr++);
-    }
     }
     for (; jr < m_r; ++jr) flush(v0 + jr);   // a range cut by K, and ranges past it
   }
@@ -371,36 +371,36 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
   {
     int bv = (int)(wpack[wid] & 0xffffffffull) + (int)(cbase & 0xffffffffull);
     for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
-    if (!one_group) load_group(g0, false, true);
+      if (!one_group) load_group(g0, false, true);
 #pragma unroll
-    for (int u = 0; u < kPG; ++u) {
-      const int s0 = g0 + 32 * u;
-      if (s0 >= end) break;
-      const int k = s0 + lane;
-      const bool isV = k < end && hc[u] < 0;
-      const unsigned mv = __ballot_sync(FULL, isV);
-      if (isV) {
-        const int i = bv + __popc(mv & lt);
-        float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
+      for (int u = 0; u < kPG; ++u) {
+        const int s0 = g0 + 32 * u;
+        if (s0 >= end) break;
+        const int k = s0 + lane;
+        const bool isV = k < end && hc[u] < 0;
+        const unsigned mv = __ballot_sync(FULL, isV);
+        if (isV) {
+          const int i = bv + __popc(mv & lt);
+          float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (c >= p) continue;
-          const float pk = pc[u][c];
-          dv[c] = pk - pbar[c];
-          ev[c] = pk - p0s[c];
-          nd += dv[c] * dv[c];
-          nn += ev[c] * ev[c];
+          for (int c = 0; c < 3; ++c) {
+            if (c >= p) continue;
+            const float pk = pc[u][c];
+            dv[c] = pk - pbar[c];
+            ev[c] = pk - p0s[c];
+            nd += dv[c] * dv[c];
+            nn += ev[c] * ev[c];
+          }
+          const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (c >= p) continue;
+            zf[(size_t)c * Kp + i] = dv[c] * izd;
+            gf[(size_t)c * Kp + i] = ev[c] * izn;
+          }
         }
-        const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (c >= p) continue;
-          zf[(size_t)c * Kp + i] = dv[c] * izd;
-          gf[(size_t)c * Kp + i] = ev[c] * izn;
-        }
+        bv += __popc(mv);
       }
-      bv += __popc(mv);
-    }
     }
   }
   if (tid == 0 && rank == 0) {
