@@ -180,7 +180,13 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 
 // Four standard normals from one Philox block: Box-Muller on the 23-bit
 // uniforms ((w >> 9) + 1/2) 2^-23 of the pairs (w0, w1) and (w2, w3); each
-// uniform is exact in FP32 (24 significant bits).
+// uniform is exact in FP32 (24 significant bits).  The radius keeps the
+// full-accuracy logarithm (near u1 = 1 an approximate one's absolute error
+// would dominate the tiny -ln u1).  The angle 2 pi u2 is taken in [-pi, pi)
+// (u2 - 1 for u2 >= 1/2 is exact) and its sine and cosine come from the
+// special-function unit: absolute error <= 2^-21.41 there, plus <= pi 2^-24
+// from rounding the angle, so a normal is within r (2^-21.41 + pi 2^-24)
+// <= 3.2e-6 of exact for the largest radius r = sqrt(-2 ln 2^-24) = 5.77.
 __device__ __forceinline__ float4 normals4(uint4 w) {
   const float s23 = 1.1920928955078125e-7f;  // 2^-23
   const float u1a = ((float)(w.x >> 9) + 0.5f) * s23, u2a = ((float)(w.y >> 9) + 0.5f) * s23;
@@ -188,9 +194,12 @@ __device__ __forceinline__ float4 normals4(uint4 w) {
   // sqrt(x) as x * rsqrt(x) (x >= 2^-23 > 0 here; rsqrtf is within 2 ulp)
   const float xa = -2.0f * logf(u1a), xb = -2.0f * logf(u1b);
   const float ra = xa * rsqrtf(xa), rb = xb * rsqrtf(xb);
+  const float two_pi = 6.2831853071795865f;
+  const float ta = two_pi * (u2a >= 0.5f ? u2a - 1.0f : u2a);
+  const float tb = two_pi * (u2b >= 0.5f ? u2b - 1.0f : u2b);
   float sa, ca, sb, cb;
-  sincospif(2.0f * u2a, &sa, &ca);
-  sincospif(2.0f * u2b, &sb, &cb);
+  __sincosf(ta, &sa, &ca);
+  __sincosf(tb, &sb, &cb);
   return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
 }
 

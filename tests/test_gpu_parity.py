@@ -67,9 +67,13 @@ def _check_replan(sc, counter=0, report=None):
     errS = _rel(out["S"][clear], ref["S"][clear], 1.0)
     errP = _rel(out["PN"].T[clear], ref["pN"][clear], 1.0)
     # eps' = u - U with u = U + eps' held in FP32: its rounding scales with
-    # |U| + |eps'| (the magnitude of the applied control), floored at 1e-3 sigma
+    # |U| + |eps'| (the magnitude of the applied control); the normal behind it
+    # carries an absolute error up to 4.6e-6 (the Box-Muller angle's sine and
+    # cosine from the special-function unit, 2^-21.41 + pi 2^-24, times the
+    # radius <= 5.77, plus a few ulp of the radius), i.e. sigma * 4.6e-6, so
+    # the scale is floored at 0.05 sigma (4.6e-6 / 1e-4)
     sig = np.array(cfg["sigma"])[None, None, :]
-    scaleE = np.maximum(np.abs(sc["U0"])[None] + np.abs(ref["eps"]), 1e-3 * sig)
+    scaleE = np.maximum(np.abs(sc["U0"])[None] + np.abs(ref["eps"]), 0.05 * sig)
     errE = float(np.max(np.abs(out["EPS"] - ref["eps"]) / scaleE))
     assert errS < RTOL and errP < RTOL and errE < RTOL, (errS, errP, errE)
     # ---- pruning (bit-exact on the GPU's flags)
@@ -255,8 +259,12 @@ def test_normals_close_to_fp64():
     torch.cuda.synchronize()
     g = out.cpu().numpy().reshape(K, n).astype(np.float64)
     ref = np.stack([oracle.normals(99, 4, k, n) for k in range(K)])
+    # the angle's sine and cosine come from the special-function unit
+    # (absolute error <= 2^-21.41 on [-pi, pi], plus pi 2^-24 from rounding the
+    # angle), scaled by the radius (<= 5.77 for 23-bit uniforms): <= 3.2e-6,
+    # plus a few ulp of the radius itself
     err = np.abs(g - ref) / np.maximum(np.abs(ref), 1.0)
-    assert err.max() < 2e-6, err.max()
+    assert err.max() < 6e-6, err.max()
 
 
 def _features(rng, n, p, eps):
