@@ -187,10 +187,17 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 // special-function unit: absolute error <= 2^-21.41 there, plus <= pi 2^-24
 // from rounding the angle, so a normal is within r (2^-21.41 + pi 2^-24)
 // <= 3.2e-6 of exact for the largest radius r = sqrt(-2 ln 2^-24) = 5.77.
+// The uniform ((w >> 9) + 1/2) 2^-23 formed without an int-to-float
+// conversion: 1 + (w >> 9) 2^-23 from the exponent bits of 1.0, minus
+// (1 - 2^-24); the difference is exact (both operands lie in [1/2, 2]), so the
+// value is the same float (checked for all 2^23 inputs).
+__device__ __forceinline__ float unit23(uint32_t w) {
+  return __uint_as_float((w >> 9) | 0x3f800000u) - 0.99999994039535522f;
+}
+
 __device__ __forceinline__ float4 normals4(uint4 w) {
-  const float s23 = 1.1920928955078125e-7f;  // 2^-23
-  const float u1a = ((float)(w.x >> 9) + 0.5f) * s23, u2a = ((float)(w.y >> 9) + 0.5f) * s23;
-  const float u1b = ((float)(w.z >> 9) + 0.5f) * s23, u2b = ((float)(w.w >> 9) + 0.5f) * s23;
+  const float u1a = unit23(w.x), u2a = unit23(w.y);
+  const float u1b = unit23(w.z), u2b = unit23(w.w);
   // sqrt(x) as x * rsqrt(x) (x >= 2^-23 > 0 here; rsqrtf is within 2 ulp)
   const float xa = -2.0f * logf(u1a), xb = -2.0f * logf(u1b);
   const float ra = xa * rsqrtf(xa), rb = xb * rsqrtf(xb);
