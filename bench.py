@@ -65,7 +65,7 @@ STAGES = ("tracks", "rollout", "prune", "dbscan", "select", "update")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout
 # launch over the workload's instances, from one ncu capture of the current
 # kernel on this workload; issue-slot use of the same capture.
-ROLLOUT_NCU = {"unicycle": {"traffic": 0.696e6, "issue_active": 0.745}}
+ROLLOUT_NCU = {"unicycle": {"traffic": 0.694e6, "issue_active": 0.746}}
 EPISODE = 200   # closed-loop replans per episode
 
 
