@@ -307,7 +307,10 @@ ce_status_t ce_mppi_philox_dev(unsigned long long seed, unsigned long long count
 /* The first n standard normals of rollouts k < K: out[k][n]: normal i is
  * element i % 4 of block i / 4; Box-Muller on the uniforms ((w >> 9) + 1/2)
  * 2^-23 of the word pairs (w0,w1) and (w2,w3): r = sqrt(-2 ln u1),
- * (r cos 2 pi u2, r sin 2 pi u2).                                            */
+ * (r cos 2 pi u2, r sin 2 pi u2).  FP32: the logarithm at full accuracy, the
+ * sine and cosine from the special-function unit, so each normal is within
+ * ~5e-6 of exact (absolute; the largest radius is 5.77).  These are the
+ * normals the rollouts draw.                                                 */
 ce_status_t ce_mppi_normals_dev(unsigned long long seed, unsigned long long counter, int K,
                                 int n, float* out, void* stream);
 /* DBSCAN (Sec. II-B2) of n points z stored as [p][ld] (SoA, p = 2 or 3):
