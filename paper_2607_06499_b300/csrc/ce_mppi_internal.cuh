@@ -235,6 +235,24 @@ __device__ __forceinline__ float eps_regen(const InstDesc& d, unsigned long long
   return sampled_control(nom, d.sigma[q], z, d.u_min[q], d.u_max[q]) - nom;
 }
 
+// eps' of rollout k, columns 4b .. 4b+3 (those below TM) from one Philox
+// block: column by column the values eps_regen gives (the same expression).
+__device__ __forceinline__ void eps_regen4(const InstDesc& d, unsigned long long ctr, int k,
+                                           int b, int TM, float* x) {
+  const float4 z4 = philox_normals(d, ctr, k, b);
+  const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int c = 4 * b + e;
+    x[e] = 0.f;
+    if (c < TM) {
+      const int q = c % d.m;
+      const float nom = d.U[c];
+      x[e] = sampled_control(nom, d.sigma[q], zz[e], d.u_min[q], d.u_max[q]) - nom;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- TMA bulk copy
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);

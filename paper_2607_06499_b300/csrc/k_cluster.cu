@@ -1205,7 +1205,7 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
 // weights are left unnormalised (the update multiplies by 1/Z); the nonzero
 // ones are also listed by ascending k when there are at most kSparseMax.
 constexpr int kWin = 512;   // clusters per statistics window
-constexpr int kUpdProdMax = 2048;   // products staged per pass of the listed update
+constexpr int kUpdProdMax = 4096;   // products staged per pass of the listed update
 constexpr int kSlots = 2;   // per-warp label cache of the cluster statistics
 
 // One thread-block cluster of CL CTAs per instance.  Each CTA sums the
@@ -1495,14 +1495,19 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
                      : d.eps[arm ? (size_t)k * d.eps_ld_k + c : (size_t)c * d.eps_ld_c + k];
       };
       if (!arm) {
-        // lanes over k, four columns at a time (independent loads in flight)
+        // lanes over k, four columns at a time (independent loads in flight;
+        // drawn again: the four columns are one Philox block)
         for (int c0 = 0; c0 < TM; c0 += 4) {
           float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
           for (int k = kb + lane; k < ke; k += 32) {
             const float wk = d.w_k[k];
-            float x[4];
+            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            if (regen) {
+              if (wk != 0.f) eps_regen4(d, ctr, k, c0 >> 2, TM, x);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) x[q] = (wk != 0.f && c0 + q < TM) ? val(k, c0 + q) : 0.f;
+              for (int q = 0; q < 4; ++q) x[q] = (wk != 0.f && c0 + q < TM) ? val(k, c0 + q) : 0.f;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk * x[q]);
           }
@@ -1692,21 +1697,34 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
   const float iz = ctl->invZ;
   const unsigned long long ctr = *d.counter;
   // the products w_j eps'_j[c] of JB list entries at a time are formed by all
-  // threads at once (independent loads or Philox draws), then each column's
-  // thread adds them in list order (Kahan)
+  // threads at once (independent loads, or one Philox block of four columns
+  // per thread), then each column's thread adds them in list order (Kahan)
   __shared__ float prod[kUpdProdMax];
-  const int JB = max(1, min(kUpdProdMax / max(TM, 1), (int)blockDim.x / max(TM, 1)));
+  const bool regen = d.regen;
+  const int NB = (TM + 3) >> 2;   // Philox blocks of a rollout's columns
+  const int per = regen ? NB : TM;   // threads per list entry
+  const int JB = max(1, min(kUpdProdMax / max(TM, 1), (int)blockDim.x / max(per, 1)));
   float s = 0.f, e = 0.f;   // column threadIdx.x (one pass) 
   const bool one_pass = TM <= (int)blockDim.x && TM * JB <= kUpdProdMax;
   if (one_pass) {
     for (int j0 = 0; j0 < nnz; j0 += JB) {
       const int jn = min(JB, nnz - j0);
-      for (int t = threadIdx.x; t < jn * TM; t += blockDim.x) {
-        const int jj = t / TM, c = t - jj * TM, k = d.nzk[j0 + jj];
-        const float x = d.regen ? eps_regen(d, ctr, k, c)
-                        : arm   ? d.eps[(size_t)k * d.eps_ld_k + c]
-                                : d.eps[(size_t)c * d.eps_ld_c + k];
-        prod[t] = d.nze[j0 + jj] * x;
+      if (regen) {
+        for (int t = threadIdx.x; t < jn * NB; t += blockDim.x) {
+          const int jj = t / NB, b = t - jj * NB, k = d.nzk[j0 + jj];
+          const float wj = d.nze[j0 + jj];
+          float x[4];
+          eps_regen4(d, ctr, k, b, TM, x);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (4 * b + q < TM) prod[jj * TM + 4 * b + q] = wj * x[q];
+        }
+      } else {
+        for (int t = threadIdx.x; t < jn * TM; t += blockDim.x) {
+          const int jj = t / TM, c = t - jj * TM, k = d.nzk[j0 + jj];
+          const float x = arm ? d.eps[(size_t)k * d.eps_ld_k + c] : d.eps[(size_t)c * d.eps_ld_c + k];
+          prod[t] = d.nze[j0 + jj] * x;
+        }
       }
       __syncthreads();
       if ((int)threadIdx.x < TM)
