@@ -30,3 +30,51 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_stage_stamps_skips_repeats_and_counts_clustered(monkeypatch):
+    """The stamp reader takes a replan once (by its start stamp), its DBSCAN
+    phases only when the replan clustered (phase stamps after the prune's end),
+    and restarts the episodes on schedule."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+
+    def stamps(t0, clustered):
+        c = np.zeros(12, np.int64)
+        c[9] = t0                       # kernel start
+        c[10] = t0 + 100                # end of prune
+        if clustered:
+            c[0:9] = t0 + 100 + 10 * np.arange(1, 10)   # DBSCAN phases
+            c[11] = t0 + 100 + 95       # end of DBSCAN
+        else:
+            c[0:9] = t0 - 50            # left from an earlier replan
+            c[11] = t0 + 100
+        return c
+
+    class Fake:
+        def __init__(self, seq):
+            self.seq, self.i = seq, -1
+
+        def step(self):
+            self.i += 1
+
+        def peek(self, name):
+            assert name == "DBCYC"
+            return self.seq[self.i]
+
+    a = Fake([stamps(1000, True), stamps(2000, True), stamps(3000, True), stamps(4000, True)])
+    b = Fake([stamps(500, False), stamps(500, False), stamps(900, True), stamps(900, True)])
+    restarts = []
+
+    def replay():
+        a.step()
+        b.step()
+
+    out = bench.stage_stamps([a, b], replay, lambda: restarts.append(1), n_steps=4, episode=3)
+    assert restarts == [1]
+    assert out["replans"] == 4 + 2 and out["clustered"] == 4 + 1
+    assert out["prune"] == [100, 100] and out["dbscan"] == [95, 95]
+    assert out["dbscan_phases"]["cell unions"] == [10, 10]
