@@ -267,7 +267,9 @@ ce_status_t ce_mppi_server_submit(ce_mppi_server* s, int session, const float* x
 /* Queue n replans at once without tickets (results only counted in the
  * statistics): session ids sids[n]; the inputs of request i follow those of
  * request i-1 in x0s (n floats each), hists ([H][n_obs[i]][p] each) and radii
- * (n_obs[i] each).  For load generators.                                     */
+ * (n_obs[i] each).  For load generators.  Requests are taken in order: on an
+ * INVALID_ARG for request i (no such session, bad obstacle count, NULL
+ * obstacle arrays), requests 0 .. i-1 stay queued and the rest are not.      */
 ce_status_t ce_mppi_server_submit_many(ce_mppi_server* s, int n, const int* sids,
                                        const float* x0s, const float* hists,
                                        const float* radii, const int* n_obs);
