@@ -194,10 +194,21 @@ def cpu_baseline(scenes, u_init, max_threads: int, budget_s: float = 10.0) -> di
         rnd += 1
         if time.perf_counter() - t0 > budget_s:
             break
+    # the latency of one replan on one host thread (comparable with the GPU's
+    # plain form): the median of two
+    sc = scenes[0]
+    lat = []
+    for r in range(2):
+        P = oracle.make_params(sc["cfg"], counter=rnd + r)
+        _, dt = oracle.replan_many([P], [sc["x0"]], [u_init(sc)], [W.history(sc, 0)],
+                                   [sc["radius"]], n_threads=1)
+        lat.append(dt)
     return {"value": units / secs, "unit": UNIT, "cores": nthr,
             "kind": "oracle", "seconds": secs,
+            "replan_ms_one_thread": 1e3 * float(np.median(lat)),
             "sample": f"{done} full replans (first replan of the episodes, warm nominal, "
-                      f"successive counters), {nthr} host threads; FP64, O(|V|^2) DBSCAN"}
+                      f"successive counters), {nthr} host threads; FP64, O(|V|^2) DBSCAN; "
+                      f"plus two replans of episode 0 on one thread for the latency"}
 
 
 def run_reference(args) -> None:
