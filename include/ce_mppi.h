@@ -99,7 +99,11 @@ typedef struct {
   int noise_regen;       /* 0: the rollouts store eps' (K*T*m floats) for the      */
                          /*    update; 1: nothing is stored, the update draws the  */
                          /*    same Philox numbers again for the rollouts of       */
-                         /*    nonzero weight (less memory; peek of EPS refused)   */
+                         /*    nonzero weight (less memory; peek of EPS refused).  */
+                         /*    Cheaper when few weights are nonzero; an update over */
+                         /*    many rollouts (the no-collision fallback with close  */
+                         /*    costs) draws them all again, slower than reading    */
+                         /*    stored ones                                          */
 } ce_mppi_params;
 
 /* Per-replan diagnostics. */
