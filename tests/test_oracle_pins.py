@@ -446,6 +446,54 @@ def test_replan_without_collision_is_standard_mppi():
                                rtol=1e-10, atol=1e-14)
 
 
+def test_replan_all_colliding_is_standard_mppi_over_all_rollouts():
+    """Every rollout collides (the robot starts inside a disc, so its step-1
+    position, which equals x_0 for a double integrator at rest, is inside for
+    every k): V is empty, and the update is Eq. 6-7 over all K -- the reading
+    taken where Algorithm 1 leaves this case undefined.  Weighting over V
+    (empty) or over C_col minus some rollouts would fail here."""
+    sc = W.make("di_static", seed=0, K=300, T=12)
+    sc["radius"] = np.append(sc["radius"], 1.0)
+    start = np.array(sc["x0"][:2])
+    sc["obs"] = np.concatenate(
+        [sc["obs"], np.broadcast_to(start, (sc["obs"].shape[0], 1, 2))], axis=1)
+    P = oracle.make_params(sc["cfg"])
+    r = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
+    d = r["diag"]
+    assert d["mode"] == oracle.MODE_ALLCOL and d["n_valid"] == 0 and d["n_col"] == 300
+    assert d["n_clusters"] == 0 and d["sel_label"] == -1 and np.all(r["col"] == 1)
+    ws = special.softmax(-r["S"] / P.lam)
+    np.testing.assert_allclose(r["w"], ws, rtol=1e-12, atol=1e-300)
+    assert np.count_nonzero(r["w"]) == np.count_nonzero(ws) and r["w"][np.argmin(r["S"])] > 0
+    np.testing.assert_allclose(r["U_new"], sc["U0"] + np.einsum("k,kjd->jd", ws, r["eps"]),
+                               rtol=1e-12, atol=1e-14)
+    assert d["S_min"] == r["S"].min()
+
+
+def test_replan_all_noise_is_standard_mppi_over_the_valid_rollouts():
+    """DBSCAN finds no cluster (minPts above |V|, so no point is core): the
+    update is Eq. 6-7 over V alone -- colliding rollouts keep zero weight
+    (the reading taken where Algorithm 1 leaves this case undefined)."""
+    sc = W.make("di_blocked", seed=0, K=400)
+    P = oracle.make_params(sc["cfg"])
+    P.min_pts = 401
+    r = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
+    d = r["diag"]
+    assert d["n_col"] > 0 and d["n_valid"] > 0
+    assert d["mode"] == oracle.MODE_ALLNOISE and d["n_clusters"] == 0 and d["sel_label"] == -1
+    assert np.all(r["labels"] == -1)
+    V = np.flatnonzero(r["col"] == 0)
+    C_col = np.flatnonzero(r["col"] == 1)
+    ws = special.softmax(-r["S"][V] / P.lam)
+    np.testing.assert_allclose(r["w"][V], ws, rtol=1e-12, atol=1e-300)
+    assert np.all(r["w"][C_col] == 0)
+    np.testing.assert_allclose(r["U_new"],
+                               sc["U0"] + np.einsum("k,kjd->jd", ws, r["eps"][V]),
+                               rtol=1e-12, atol=1e-14)
+    # the least cost is taken over V, not over all K
+    assert d["S_min"] == r["S"][V].min()
+
+
 @pytest.mark.parametrize("name", ["di_blocked", "unicycle_paper", "arm_paper", "unicycle_blocked"])
 def test_replan_invariants(name):
     kw = dict(K=1024) if name == "unicycle_blocked" else {}
