@@ -104,11 +104,18 @@ typedef struct {
                          /*    many rollouts (the no-collision fallback with close  */
                          /*    costs) draws them all again, slower than reading    */
                          /*    stored ones                                          */
+  int uf_limit;          /* parent reads allowed per union-find operation of the   */
+                         /*    grid DBSCAN (0: the default, 2^20, never reached by */
+                         /*    valid data).  When one runs out, the replan reports */
+                         /*    CE_MPPI_ERR_TIMEOUT in diag.status and takes the    */
+                         /*    all-noise fallback; 1 makes every union give up (a  */
+                         /*    hook for testing that failure path), >= 0           */
 } ce_mppi_params;
 
 /* Per-replan diagnostics. */
 typedef struct {
-  int mode;        /* ce_mode_t                                                   */
+  int mode;        /* ce_mode_t; -1 when the replan was refused (status != 0 and  */
+                   /* nothing updated: a non-finite device input)                 */
   int n_col;       /* |C_col|                                                     */
   int n_valid;     /* |V|                                                         */
   int n_clusters;  /* M_t                                                         */
@@ -158,15 +165,33 @@ ce_status_t ce_mppi_get_counter(ce_mppi_handle* h, unsigned long long* counter);
  * obs_radius [n_obs] to the device, runs Algorithm 1, copies the updated
  * nominal (before the shift) to u_out [T][m] and the diagnostics to diag
  * (nullable), and returns when done.  Afterwards the handle's nominal is the
- * shifted sequence and its counter has advanced by one.
+ * shifted sequence and its counter has advanced by one.  The inputs are
+ * checked first as by ce_mppi_check_inputs (NaN or infinity: INVALID_ARG,
+ * nothing launched).
  * Errors: INVALID_ARG, CUDA, TIMEOUT (device-side wait limit reached).       */
 ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_hist,
                            const float* obs_radius, int n_obs, float* u_out,
                            ce_mppi_diag* diag);
 
+/* Check the host inputs of one replan for a planner created with params,
+ * without a GPU and without launching anything: params as ce_mppi_create
+ * validates them; x0 [n] non-NULL and finite; 0 <= n_obs <= n_obs_max;
+ * obs_hist [H][n_obs][p] and obs_radius [n_obs] non-NULL when n_obs > 0, every
+ * value finite and every radius >= 0.  ce_mppi_replan and the server's submit
+ * calls apply the same check before they copy anything.  Device-buffer replans
+ * (ce_mppi_replan_dev, batches) cannot be checked on the host: their obstacle
+ * track kernel reports a non-finite x0, observation or radius as INVALID_ARG
+ * in diag->status instead.  Errors: INVALID_ARG.                             */
+ce_status_t ce_mppi_check_inputs(const ce_mppi_params* params, const float* x0,
+                                 const float* obs_hist, const float* obs_radius, int n_obs);
+
 /* One replan from device buffers, queued on the handle's stream; returns
  * without waiting.  Device-side faults of the bounded waits are reported in
- * diag->status.  Errors: INVALID_ARG, CUDA.                                   */
+ * diag->status.  A NaN or infinity in x0, the observation window or the
+ * radii (or a negative radius) is found by the first kernel of the replan:
+ * diag->status = INVALID_ARG, diag->mode = -1, u_out receives the current
+ * nominal, and the nominal, the counter and x_next are left unchanged.
+ * Errors: INVALID_ARG, CUDA.                                                  */
 ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* req);
 
 /* Batches: n handles replanned together by one replan chain for all of them

@@ -41,7 +41,7 @@ class Params(C.Structure):
         ("n_obs_max", C.c_int), ("hist_len", C.c_int), ("robot_radius", C.c_float),
         ("norm_eps", C.c_float), ("v_static_thresh", C.c_float), ("seed", C.c_ulonglong),
         ("ref_mode", C.c_int), ("check_j0", C.c_int), ("mppi_only", C.c_int),
-        ("noise_regen", C.c_int),
+        ("noise_regen", C.c_int), ("uf_limit", C.c_int),
     ]
 
 
@@ -71,7 +71,8 @@ class Request(C.Structure):
 
 EXPORTS = (
     "ce_mppi_create", "ce_mppi_destroy", "ce_mppi_set_nominal", "ce_mppi_get_nominal",
-    "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_replan_dev",
+    "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_check_inputs",
+    "ce_mppi_replan_dev",
     "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_config",
     "ce_mppi_batch_set_post_ctas", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
@@ -101,6 +102,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_set_counter.argtypes = [vp, u64]
         L.ce_mppi_get_counter.argtypes = [vp, C.POINTER(u64)]
         L.ce_mppi_replan.argtypes = [vp, vp, vp, vp, i, vp, C.POINTER(Diag)]
+        L.ce_mppi_check_inputs.argtypes = [C.POINTER(Params), vp, vp, vp, i]
         L.ce_mppi_replan_dev.argtypes = [vp, C.POINTER(Request)]
         L.ce_mppi_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Request), i, vp, i, i,
                                            C.POINTER(vp)]
@@ -162,7 +164,19 @@ def make_params(cfg: dict, n_obs_max: int) -> Params:
     P.ref_mode, P.check_j0 = cfg.get("ref_mode", 0), cfg.get("check_j0", 0)
     P.mppi_only = cfg.get("mppi_only", 0)
     P.noise_regen = cfg.get("noise_regen", 0)
+    P.uf_limit = cfg.get("uf_limit", 0)
     return P
+
+
+def check_inputs(cfg: dict, x0, hist, radius, n_obs_max: int | None = None):
+    """Host-side check of one replan's inputs (no GPU needed); raises CeError."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    hist = np.ascontiguousarray(hist, dtype=np.float32)
+    radius = np.ascontiguousarray(radius, dtype=np.float32)
+    n_obs = int(radius.shape[0])
+    P = make_params(cfg, n_obs if n_obs_max is None else n_obs_max)
+    _check(lib().ce_mppi_check_inputs(C.byref(P), x0.ctypes.data, hist.ctypes.data,
+                                      radius.ctypes.data, n_obs))
 
 
 def _stream_ptr(stream) -> int:

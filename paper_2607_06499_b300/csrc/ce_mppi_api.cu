@@ -61,16 +61,22 @@ float eps_squared(float eps) {
   return e * e;  // FP32 product of the FP32 radius (the predicate's eps^2)
 }
 
-std::once_flag g_cfg_once;
+std::mutex g_cfg_mu;
+std::vector<int> g_cfg_devices;   // devices whose kernel attributes are set
 
 }  // namespace
 
 namespace cem {
 void set_last_error(const char* msg) { g_err = msg; }
 
-void configure_kernels() {
+void ensure_configured() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  if (std::find(g_cfg_devices.begin(), g_cfg_devices.end(), dev) != g_cfg_devices.end()) return;
   configure_rollout();
-  configure_cluster();
+  configure_cluster(g_cfg_devices.empty());
+  g_cfg_devices.push_back(dev);
 }
 }  // namespace cem
 
@@ -104,6 +110,7 @@ ce_status_t validate(const ce_mppi_params* P) {
     return fail(CE_MPPI_ERR_INVALID_ARG, "mppi_only must be 0 or 1");
   if (P->noise_regen < 0 || P->noise_regen > 1)
     return fail(CE_MPPI_ERR_INVALID_ARG, "noise_regen must be 0 or 1");
+  if (P->uf_limit < 0) return fail(CE_MPPI_ERR_INVALID_ARG, "uf_limit must be >= 0");
   int n, m, p;
   dims_of(P->dyn, &n, &m, &p);
   for (int i = 0; i < m; ++i) {
@@ -226,6 +233,7 @@ void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h)
   d.n_obs_max = P->n_obs_max; d.H = P->hist_len; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
   d.check_j0 = P->check_j0; d.G = G; d.R = R; d.regen = P->noise_regen;
   d.mppi_only = P->mppi_only;
+  d.uf_limit = P->uf_limit > 0 ? P->uf_limit : kUfLimit;
   d.eps_ld_c = is_arm(P->dyn) ? 1 : Kp;
   d.eps_ld_k = is_arm(P->dyn) ? h->TMp : 1;
   d.dt = P->dt; d.obs_dt = P->obs_dt; d.inv_lambda = 1.0f / P->lambda;
@@ -236,6 +244,28 @@ void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h)
   for (int i = 0; i < 8; ++i) d.w[i] = P->w[i];
   d.seed_lo = (unsigned)P->seed; d.seed_hi = (unsigned)(P->seed >> 32);
   d.TMp = h->TMp;
+}
+
+// Host inputs of one replan: x0 [n], obs_hist [H][n_obs][p], obs_radius
+// [n_obs], every value finite and every radius >= 0 (checked before anything
+// is copied or launched).
+ce_status_t check_inputs_dims(int n, int p, int H, int n_obs_max, const float* x0,
+                              const float* obs_hist, const float* obs_radius, int n_obs) {
+  if (!x0) return fail(CE_MPPI_ERR_INVALID_ARG, "x0 is NULL");
+  if (n_obs < 0 || n_obs > n_obs_max)
+    return fail(CE_MPPI_ERR_INVALID_ARG, "n_obs must be in [0, n_obs_max]");
+  if (n_obs > 0 && (!obs_hist || !obs_radius))
+    return fail(CE_MPPI_ERR_INVALID_ARG, "obs_hist / obs_radius is NULL");
+  for (int i = 0; i < n; ++i)
+    if (!finite(x0[i])) return fail(CE_MPPI_ERR_INVALID_ARG, "x0 holds a NaN or an infinity");
+  const size_t nh = (size_t)H * n_obs * p;
+  for (size_t i = 0; i < nh; ++i)
+    if (!finite(obs_hist[i]))
+      return fail(CE_MPPI_ERR_INVALID_ARG, "obs_hist holds a NaN or an infinity");
+  for (int i = 0; i < n_obs; ++i)
+    if (!finite(obs_radius[i]) || !(obs_radius[i] >= 0.0f))
+      return fail(CE_MPPI_ERR_INVALID_ARG, "obs_radius must be finite and >= 0");
+  return CE_MPPI_OK;
 }
 
 ce_status_t check_req(const ce_mppi_handle* h, const ce_mppi_request* q) {
@@ -250,6 +280,14 @@ ce_status_t check_req(const ce_mppi_handle* h, const ce_mppi_request* q) {
 
 }  // namespace
 
+namespace cem {
+ce_status_t check_host_inputs(const ce_mppi_handle* h, const float* x0, const float* obs_hist,
+                              const float* obs_radius, int n_obs) {
+  return check_inputs_dims(h->n, h->p, h->P.hist_len, h->P.n_obs_max, x0, obs_hist, obs_radius,
+                           n_obs);
+}
+}  // namespace cem
+
 extern "C" {
 
 const char* ce_mppi_last_error(void) { return g_err.c_str(); }
@@ -259,7 +297,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   *out = nullptr;
   ce_status_t st = validate(P);
   if (st != CE_MPPI_OK) return st;
-  std::call_once(g_cfg_once, cem::configure_kernels);
+  cem::ensure_configured();
   ce_mppi_handle* h = new (std::nothrow) ce_mppi_handle();
   if (!h) return fail(CE_MPPI_ERR_NO_MEMORY, "host allocation failed");
   h->P = *P;
@@ -433,13 +471,21 @@ ce_status_t ce_mppi_replan_dev(ce_mppi_handle* h, const ce_mppi_request* q) {
   return CE_MPPI_OK;
 }
 
+ce_status_t ce_mppi_check_inputs(const ce_mppi_params* P, const float* x0,
+                                 const float* obs_hist, const float* obs_radius, int n_obs) {
+  ce_status_t st = validate(P);
+  if (st != CE_MPPI_OK) return st;
+  int n, m, p;
+  dims_of(P->dyn, &n, &m, &p);
+  return check_inputs_dims(n, p, P->hist_len, P->n_obs_max, x0, obs_hist, obs_radius, n_obs);
+}
+
 ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_hist,
                            const float* obs_radius, int n_obs, float* u_out, ce_mppi_diag* diag) {
   if (!h || !x0 || !u_out) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
-  if (n_obs < 0 || n_obs > h->P.n_obs_max)
-    return fail(CE_MPPI_ERR_INVALID_ARG, "n_obs must be in [0, n_obs_max]");
-  if (n_obs > 0 && (!obs_hist || !obs_radius))
-    return fail(CE_MPPI_ERR_INVALID_ARG, "obs_hist / obs_radius is NULL");
+  ce_status_t st0 = check_inputs_dims(h->n, h->p, h->P.hist_len, h->P.n_obs_max, x0, obs_hist,
+                                      obs_radius, n_obs);
+  if (st0 != CE_MPPI_OK) return st0;
   const int n = h->n, p = h->p, H = h->P.hist_len, TM = h->P.T * h->m;
   unsigned char* hin = h->h_stage;
   unsigned char* hout = h->h_stage + h->in_bytes;
@@ -466,7 +512,9 @@ ce_status_t ce_mppi_replan(ce_mppi_handle* h, const float* x0, const float* obs_
   ce_mppi_diag dg;
   std::memcpy(&dg, hout + ((char*)h->d_diag - (char*)h->d_uout), sizeof(dg));
   if (diag) *diag = dg;
-  if (dg.status != 0) return fail((ce_status_t)dg.status, "device-side bounded wait gave up");
+  if (dg.status == CE_MPPI_ERR_TIMEOUT)
+    return fail(CE_MPPI_ERR_TIMEOUT, "device-side bounded wait gave up");
+  if (dg.status != 0) return fail((ce_status_t)dg.status, "input refused on the device");
   return CE_MPPI_OK;
 }
 
@@ -976,7 +1024,7 @@ ce_status_t ce_mppi_dbscan_dev(const float* z, int n, int ld, int p, float eps, 
   int G, R, nc;
   dbscan_grid(eps, p, &ci, &G, &R, &nc);
   if (nc > kMaxCells) return fail(CE_MPPI_ERR_INVALID_ARG, "eps too small for the DBSCAN grid");
-  std::call_once(g_cfg_once, cem::configure_kernels);
+  cem::ensure_configured();
   launch_dbscan_standalone(z, n, ld, p, eps_squared(eps), ci, G, R, min_pts, labels, n_clusters,
                            ws, static_cast<cudaStream_t>(stream));
   CE_CUDA(cudaGetLastError());

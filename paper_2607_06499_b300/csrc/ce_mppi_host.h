@@ -63,10 +63,13 @@ void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const 
                int n_upd, int smem_roll, int max_cells, cudaStream_t s,
                const int* pre_roll = nullptr, const int* pre_upd = nullptr);
 ce_status_t validate_params(const ce_mppi_params* P);
+// Host inputs of one replan of h (pointers, obstacle count, finite values,
+// radii >= 0); sets the thread's last error when they are refused.
+ce_status_t check_host_inputs(const ce_mppi_handle* h, const float* x0, const float* obs_hist,
+                              const float* obs_radius, int n_obs);
 // True when a planner created with P would have h's buffer layout.
 bool same_layout(const ce_mppi_handle* h, const ce_mppi_params* P);
 // Reuse h's buffers for parameters P of the same layout: new parameters,
 // nominal and replan counter back to zero (blocking on h's stream).
 ce_status_t handle_retarget(ce_mppi_handle* h, const ce_mppi_params* P);
-void configure_kernels();
 }  // namespace cem

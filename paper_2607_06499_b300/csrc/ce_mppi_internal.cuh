@@ -21,7 +21,8 @@ constexpr int kMaxOcc = 2048;           // DBSCAN occupied cells held in shared 
 constexpr int kMaxObs = 4096;           // obstacle bitmap in shared memory
 constexpr int kMaxT = 256;
 constexpr int kMaxSmemTracks = 200 * 1024;
-constexpr long long kSpinLimit = 1ll << 22;   // bounded waits (mbarrier, union-find)
+constexpr long long kSpinLimit = 1ll << 22;   // bounded waits (mbarrier)
+constexpr int kUfLimit = 1 << 20;       // parent reads per union-find operation (default)
 constexpr int kSparseMax = 256;         // nonzero update weights kept as a sorted list
 constexpr int kPruneRanges = 256;       // fixed rollout ranges of the pbar sums
 
@@ -33,6 +34,7 @@ struct Ctl {
   int nnz;                        // nonzero update weights listed (-1: more than kSparseMax)
   int updated;                    // the update was applied by the fused per-instance kernel
   int nnz_all;                    // nonzero weights of the replan (all CTAs of the instance)
+  int rejected;                   // the track kernel found a non-finite input: no update
   float pbar[3], v_obs[3], p0[3];
   unsigned int done;              // last-CTA ticket of the update stage
   int col_tests;                  // circle/sphere tests per rollout after reach culling
@@ -53,6 +55,7 @@ struct InstDesc {
   int dyn, K, Kp, T, m, n, p, n_obs_max, H, min_pts, ref_mode, check_j0;
   int regen;                      // eps' is not stored: the update draws it again
   int mppi_only;                  // standard MPPI: no pruning or clustering
+  int uf_limit;                   // parent reads per DBSCAN union-find operation
   int G, R, eps_ld_c, eps_ld_k;   // DBSCAN grid size/reach; eps strides (column, rollout)
   float dt, obs_dt, inv_lambda, eps2, cell_inv, robot_radius, norm_eps, v_static_thresh;
   float sigma[6], u_min[6], u_max[6], goal[16], w[8];
@@ -399,7 +402,10 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
 int rollout_threads(int dyn);
 void configure_rollout();
 void set_last_error(const char* msg);   // message returned by ce_mppi_last_error()
-void configure_cluster();
+void configure_cluster(bool fits);
+// Configure the kernels for the current device once (thread-safe; every entry
+// point that launches calls it first).
+void ensure_configured();
 size_t dbscan_ws_bytes(int n);
 
 }  // namespace cem

@@ -30,7 +30,6 @@ static __device__ __align__(256) unsigned char g_dbscan_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
-bool g_configured = false;
 
 ce_status_t noalloc_fail(ce_status_t s, const char* msg) {
   cem::set_last_error(msg);   // read back through ce_mppi_last_error()
@@ -63,15 +62,16 @@ ce_status_t ce_mppi_dbscan_noalloc_dev(const float* z, int n, int ld, int p, flo
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return noalloc_fail(CE_MPPI_ERR_CUDA, "cudaGetDevice failed");
+  if (cem::dbscan_ws_bytes(n) > kNoAllocBytes)   // (the carving must fit the array)
+    return noalloc_fail(CE_MPPI_ERR_INVALID_ARG, "scratch layout larger than the fixed array");
+  // the kernels' shared-memory limits on this device (the library's one
+  // configuration guard, shared with every other entry point)
+  cem::ensure_configured();
   void* scratch = nullptr;
   {
     // Set-up, once per device, with that device current: the device address
-    // of the scratch array, and the kernels' shared-memory limits.
+    // of the scratch array.
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_configured) {
-      cem::configure_cluster();
-      g_configured = true;
-    }
     if (!g_scratch_ptr[dev]) {
       void* ptr = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&ptr, g_dbscan_scratch);

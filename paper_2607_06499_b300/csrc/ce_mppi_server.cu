@@ -455,10 +455,8 @@ ce_status_t ce_mppi_server_submit(ce_mppi_server* s, int sid, const float* x0,
     if (s->worker_status) return srv_fail((ce_status_t)s->worker_status, "server worker failed");
     Session& ss = s->sessions[sid];
     const ce_mppi_handle* h = ss.h;
-    if (n_obs < 0 || n_obs > h->P.n_obs_max)
-      return srv_fail(CE_MPPI_ERR_INVALID_ARG, "n_obs must be in [0, n_obs_max]");
-    if (n_obs > 0 && (!obs_hist || !obs_radius))
-      return srv_fail(CE_MPPI_ERR_INVALID_ARG, "obs_hist / obs_radius is NULL");
+    if (cem::check_host_inputs(h, x0, obs_hist, obs_radius, n_obs) != CE_MPPI_OK)
+      return CE_MPPI_ERR_INVALID_ARG;   // (the message is set)
     const size_t nh = (size_t)h->P.hist_len * n_obs * h->p;
     ss.in.resize(h->n + nh + n_obs);
     std::memcpy(ss.in.data(), x0, sizeof(float) * h->n);
@@ -506,6 +504,9 @@ ce_status_t ce_mppi_server_submit_many(ce_mppi_server* s, int n, const int* sids
       if (no < 0 || no > h->P.n_obs_max || (no > 0 && (!hists || !radii)))
         return srv_fail(CE_MPPI_ERR_INVALID_ARG, "bad obstacle count or NULL obstacle arrays");
       const size_t nh = (size_t)h->P.hist_len * no * h->p;
+      if (cem::check_host_inputs(h, x0s + ox, no > 0 ? hists + oh : nullptr,
+                                 no > 0 ? radii + orad : nullptr, no) != CE_MPPI_OK)
+        return CE_MPPI_ERR_INVALID_ARG;   // (the message is set)
       ss.in.resize(h->n + nh + no);
       std::memcpy(ss.in.data(), x0s + ox, sizeof(float) * h->n);
       if (no > 0) {

@@ -467,8 +467,14 @@ __device__ __forceinline__ int cell_coord(float v, float cell_inv, int G) {
   return (int)fminf(fmaxf(f, 0.0f), (float)(G - 1));
 }
 
-__device__ __forceinline__ int cfind(int* par, int x) {
-  for (int it = 0; it < 1 << 20; ++it) {
+// Union-find over cell ids with a bounded budget of parent reads: each read
+// spends one unit of `budget`; once it is spent the search stops at the node
+// reached (always a valid cell id) with budget 0, and the caller reports
+// CE_MPPI_ERR_TIMEOUT.  (The default budget, 2^20 reads per operation, is
+// never reached by a valid parent forest; a tiny one is a test hook.)
+__device__ __forceinline__ int cfind(int* par, int x, int& budget) {
+  while (budget > 0) {
+    --budget;
     const int p = par[x];
     if (p == x) return x;
     const int gp = par[p];
@@ -478,17 +484,30 @@ __device__ __forceinline__ int cfind(int* par, int x) {
   return x;
 }
 
-__device__ __forceinline__ bool cunion(int* par, int a, int b) {
-  for (int it = 0; it < 1 << 20; ++it) {
-    a = cfind(par, a);
-    b = cfind(par, b);
+// Join the sets of a and b (the larger root points to the smaller); false
+// when the budget ran out first.
+__device__ __forceinline__ bool cunion(int* par, int a, int b, int budget) {
+  while (budget > 0) {
+    a = cfind(par, a, budget);
+    b = cfind(par, b, budget);
+    if (budget <= 0) return false;
     if (a == b) return true;
     if (a > b) { const int t = a; a = b; b = t; }
+    --budget;
     const int old = atomicCAS(&par[b], b, a);
     if (old == b) return true;
     b = old;
   }
   return false;
+}
+
+// True when a and b are known to share a root (false when the budget ran out:
+// the caller then searches and unions, which reports the timeout).
+__device__ __forceinline__ bool cjoined(int* par, int a, int b, int limit) {
+  int budget = limit;
+  const int ra = cfind(par, a, budget);
+  const int rb = cfind(par, b, budget);
+  return budget > 0 && ra == rb;
 }
 
 // Inverse of float_key.
@@ -632,7 +651,7 @@ template <int p>
 __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld, int n,
                                              float eps2, float cell_inv, int G, int R, int min_pts,
                                              DbWork w, int* labels, int* M_out, int* status,
-                                             int* smem, long long* cyc) {
+                                             int* smem, long long* cyc, int uf_limit) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
@@ -954,7 +973,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
           cm &= cm - 1;
           const int Bc = __shfl_sync(FULL, B, src);
           int joined = 0;
-          if (lane == 0) joined = cfind(opar0, A) == cfind(opar0, Bc);
+          if (lane == 0) joined = cjoined(opar0, A, Bc, uf_limit);
           if (__shfl_sync(FULL, joined, 0)) continue;   // warp-uniform decision
           // the smaller cell's core points within eps of the other cell's core
           // box are found 32 at a time (lane-parallel screening); each of them
@@ -978,7 +997,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
             // a long search stops once other warps have joined the two cells
             if (cb && px0 > ostart[X]) {
               int jn = 0;
-              if (lane == 0) jn = cfind(opar0, A) == cfind(opar0, Bc);
+              if (lane == 0) jn = cjoined(opar0, A, Bc, uf_limit);
               if (__shfl_sync(FULL, jn, 0)) break;
             }
             while (cb && !found) {
@@ -1000,7 +1019,8 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
               }
             }
           }
-          if (found && lane == 0 && !cunion(opar0, A, Bc)) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
+          if (found && lane == 0 && !cunion(opar0, A, Bc, uf_limit))
+            atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
           __syncwarp();
         }
       }
@@ -1012,7 +1032,11 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   //    then every CTA copies parents and minima
   if (rank == 0) {
     for (int o = tid; o < n_occ; o += blockDim.x)
-      if (opar[o] >= 0) opar[o] = cfind(opar, o);
+      if (opar[o] >= 0) {
+        int budget = uf_limit;
+        opar[o] = cfind(opar, o, budget);
+        if (budget <= 0) atomicCAS(status, 0, CE_MPPI_ERR_TIMEOUT);
+      }
     __syncthreads();
     for (int o = tid; o < n_occ; o += blockDim.x)
       if (opar[o] >= 0 && opar[o] != o) atomicMin(&omin[opar[o]], omin[o]);
@@ -1157,12 +1181,16 @@ __device__ __forceinline__ void dbscan_stage(const KArgs& a, int* smem_i) {
   __shared__ int M;
   if (d.p == 3)
     dbscan_block<3>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
-                    &ctl->status, smem_i, ctl->dbcyc);
+                    &ctl->status, smem_i, ctl->dbcyc, d.uf_limit);
   else
     dbscan_block<2>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
-                    &ctl->status, smem_i, ctl->dbcyc);
+                    &ctl->status, smem_i, ctl->dbcyc, d.uf_limit);
   __syncthreads();
   if (threadIdx.x == 0 && cluster.block_rank() == 0) {
+    // a union-find that gave up leaves labels that cannot be trusted: the
+    // replan takes the all-noise fallback (every status raise of the stage
+    // happened before its last cluster barrier)
+    if (__ldcg(&ctl->status) != 0) M = 0;
     ctl->M = M;
     if (M == 0) ctl->mode = CE_MODE_ALLNOISE;
   }
@@ -1187,10 +1215,10 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
   int* st0 = cluster.map_shared_rank(&status, 0);
   if (p == 3)
     dbscan_block<3>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i,
-                    nullptr);
+                    nullptr, kUfLimit);
   else
     dbscan_block<2>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i,
-                    nullptr);
+                    nullptr, kUfLimit);
   cluster.sync();   // every CTA's status updates have landed
   if (threadIdx.x == 0 && cluster.block_rank() == 0) *n_clusters = status ? -status : M;
 }
@@ -1611,9 +1639,40 @@ __global__ void __maxnreg__(64) k_select(KArgs a) {
 // stages follow each other at cluster barriers instead of kernel boundaries,
 // each instance at its own pace.  The selection's accumulators reuse the
 // DBSCAN tables' shared memory.
+// A replan whose inputs the track kernel refused (a NaN or infinity in a
+// device buffer): the outputs get the current nominal and the diagnostics the
+// status; the nominal, the counter and x_next are left as they are.
+__device__ void refuse_replan(const InstDesc& d, const Req& r) {
+  Ctl* ctl = d.ctl;
+  const int TM = d.T * d.m;
+  if (r.u_out)
+    for (int c = threadIdx.x; c < TM; c += blockDim.x) r.u_out[c] = d.U[c];
+  if (threadIdx.x == 0) {
+    if (r.diag) {
+      ce_mppi_diag g;
+      g.mode = -1; g.n_col = 0; g.n_valid = 0; g.n_clusters = 0; g.sel_label = -1;
+      g.o_star = -1; g.dynamic = 0; g.status = ctl->status; g.S_min = 0.f;
+      for (int i = 0; i < 3; ++i) { g.pbar[i] = 0.f; g.v_obs[i] = 0.f; }
+      g.counter = *d.counter;
+      g.col_tests = 0;
+      *r.diag = g;
+    }
+    ctl->updated = 1;
+  }
+}
+
 __global__ void __maxnreg__(64) k_post(KArgs a) {
   extern __shared__ __align__(16) int smem_post[];
   cg::cluster_group cluster = cg::this_cluster();
+  {
+    // (the flag is the track kernel's, the same for every CTA of the cluster)
+    const int inst = blockIdx.x / cluster.num_blocks();
+    const InstDesc& d = desc_of(a, inst);
+    if (d.ctl->rejected) {
+      if (cluster.block_rank() == 0) refuse_replan(d, req_of(a, inst));
+      return;
+    }
+  }
   // stage clock stamps of rank 0 (diagnostics): start, after prune, after DBSCAN
   long long* cyc = desc_of(a, blockIdx.x / cluster.num_blocks()).ctl->dbcyc;
   const bool st = threadIdx.x == 0 && cluster.block_rank() == 0;
@@ -1756,6 +1815,10 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
   if (d.ctl->updated) return;   // done by the fused per-instance kernel
+  if (d.ctl->rejected) {        // inputs refused by the track kernel: no update
+    if (tile.y == 0) refuse_replan(d, req_of(a, tile.x));
+    return;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int K = d.K, TM = d.T * d.m;
   const bool arm = is_arm(d.dyn);
@@ -1972,16 +2035,20 @@ bool launch_post(const KArgs& a, int max_cells, cudaStream_t s) {
   return true;
 }
 
-void configure_cluster() {
-  g_fit_prune = query_fit(k_prune, kBlock, 0);
-  g_fit_select = query_fit(k_select, kBlock, 0);
+// Kernel attributes of the current device (shared-memory limits); with
+// `fits`, also the cluster-size fits (queried once per process, on the first
+// device configured: the devices of one process are taken to be one model).
+void configure_cluster(bool fits) {
   cudaFuncSetAttribute(k_dbscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)dbscan_smem(kMaxCells));
   cudaFuncSetAttribute(k_dbscan_standalone, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)dbscan_smem(kMaxCells));
-  for (int c = 0; c < 3; ++c) g_fit_db[c] = query_fit(k_dbscan, kBlock, dbscan_smem(kFitCells[c]));
   cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)post_smem(kMaxCells));
+  if (!fits) return;
+  g_fit_prune = query_fit(k_prune, kBlock, 0);
+  g_fit_select = query_fit(k_select, kBlock, 0);
+  for (int c = 0; c < 3; ++c) g_fit_db[c] = query_fit(k_dbscan, kBlock, dbscan_smem(kFitCells[c]));
   for (int c = 0; c < 3; ++c) g_fit_post[c] = query_fit(k_post, kBlock, post_smem(kFitCells[c]));
 }
 

@@ -41,6 +41,23 @@ __global__ void k_tracks(KArgs a) {
     d.ctl->updated = 0;
     d.ctl->nnz_all = 0;
   }
+  {
+    // device-buffer inputs are not seen by the host: a NaN or infinity in x0,
+    // the observation window or the radii (or a negative radius) is reported
+    // as INVALID_ARG in the replan's status, and the replan is refused (the
+    // later stages leave the nominal and the counter as they are)
+    const int nh = H * n_obs * p, tot = d.n + nh + n_obs;
+    bool bad = false;
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+      const float v = i < d.n ? r.x0[i] : i < d.n + nh ? h[i - d.n] : r.obs_radius[i - d.n - nh];
+      bad |= !isfinite(v) || (i >= d.n + nh && !(v >= 0.0f));
+    }
+    const bool any_bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      d.ctl->rejected = any_bad ? 1 : 0;
+      if (any_bad) raise_status(d.ctl, CE_MPPI_ERR_INVALID_ARG);
+    }
+  }
   if (is_arm(d.dyn)) {
     const int total = (T + 1) * n_obs;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {

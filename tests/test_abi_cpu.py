@@ -126,3 +126,30 @@ def test_twelve_d_arm_dims_and_parameters_accepted_by_validation():
     h = C.c_void_p()
     st = pkg.lib().ce_mppi_create(C.byref(P), None, C.byref(h))
     assert st != 1, pkg.lib().ce_mppi_last_error().decode()
+
+
+def test_host_inputs_checked_without_a_gpu():
+    """ce_mppi_check_inputs (the check ce_mppi_replan and the server's submit
+    calls run before copying anything) refuses NaN and infinite inputs."""
+    sc = W.make("unicycle", seed=0, K=256)
+    cfg, hist, rad = sc["cfg"], W.history(sc, 0), sc["radius"]
+    pkg.check_inputs(cfg, sc["x0"], hist, rad)          # valid inputs pass
+    bad_cases = []
+    x = sc["x0"].copy(); x[2] = np.nan; bad_cases.append((x, hist, rad, "x0"))
+    x = sc["x0"].copy(); x[0] = np.inf; bad_cases.append((x, hist, rad, "x0"))
+    h = hist.copy(); h[4, 17, 1] = np.nan; bad_cases.append((sc["x0"], h, rad, "obs_hist"))
+    h = hist.copy(); h[0, 0, 0] = -np.inf; bad_cases.append((sc["x0"], h, rad, "obs_hist"))
+    r = rad.copy(); r[3] = np.nan; bad_cases.append((sc["x0"], hist, r, "obs_radius"))
+    r = rad.copy(); r[3] = -0.1; bad_cases.append((sc["x0"], hist, r, "obs_radius"))
+    for x, h, r, what in bad_cases:
+        with pytest.raises(pkg.CeError) as e:
+            pkg.check_inputs(cfg, x, h, r)
+        assert e.value.status == 1 and what in str(e.value)
+    with pytest.raises(pkg.CeError) as e:                 # more obstacles than the planner holds
+        pkg.check_inputs(cfg, sc["x0"], hist, rad, n_obs_max=10)
+    assert "n_obs" in str(e.value)
+    P = pkg.make_params(cfg, 50)
+    P.lam = float("nan")                                   # the parameters are checked too
+    st = pkg.lib().ce_mppi_check_inputs(C.byref(P), sc["x0"].astype(np.float32).ctypes.data,
+                                         None, None, 0)
+    assert st == 1 and "lambda" in pkg.lib().ce_mppi_last_error().decode()

@@ -427,6 +427,38 @@ def test_host_replan_rejects_too_many_obstacles():
     pl.close()
 
 
+def test_non_finite_inputs_rejected_or_reported():
+    """Host buffers with a NaN are refused before anything runs (the planner's
+    counter does not move); device buffers with a NaN or infinity are reported
+    by the track kernel as INVALID_ARG in diag.status; the planner stays usable."""
+    sc = W.make("unicycle", seed=0, K=1024)
+    pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+    hist = W.history(sc, 0)
+    x_bad = sc["x0"].copy()
+    x_bad[1] = np.nan
+    with pytest.raises(pkg.CeError) as e:
+        pl.replan(x_bad, hist, sc["radius"])
+    assert e.value.status == 1 and pl.get_counter() == 0
+    dev = "cuda"
+    for what in ("x0", "hist", "radius"):
+        x = torch.tensor(sc["x0"], dtype=torch.float32, device=dev)
+        h = torch.tensor(hist, dtype=torch.float32, device=dev)
+        r = torch.tensor(sc["radius"], dtype=torch.float32, device=dev)
+        {"x0": x, "hist": h, "radius": r}[what].view(-1)[1] = float("inf") if what == "hist" else float("nan")
+        diag = torch.zeros(128, dtype=torch.uint8, device=dev)
+        u_out = torch.full((sc["cfg"]["T"], 2), 7.0, device=dev)
+        pl.replan_dev(x, h, r, u_out=u_out, diag=diag)
+        torch.cuda.synchronize()
+        dg = np.frombuffer(diag.cpu().numpy().tobytes()[:32], np.int32)
+        assert dg[7] == 1 and dg[0] == -1, (what, dg)          # status, mode
+        # refused: the nominal comes back unchanged, the counter does not move
+        np.testing.assert_array_equal(u_out.cpu().numpy(), sc["U0"].astype(np.float32) * 0)
+        assert pl.get_counter() == 0
+    u, d = pl.replan(sc["x0"], hist, sc["radius"])   # valid inputs still work
+    assert d["status"] == 0 and np.all(np.isfinite(u)) and pl.get_counter() == 1
+    pl.close()
+
+
 @pytest.mark.parametrize("name,kw", [
     ("unicycle_blocked", dict(K=2000)),                 # few nonzero weights: listed
     ("unicycle_blocked", dict(K=2000, lam=1e4)),        # all weights nonzero: dense tiles
@@ -548,3 +580,39 @@ def test_task_level_scenarios_run():
             r = SC.run(kind, mppi, episodes=4, steps=60)
             assert r["episodes"] == 4
             assert 0 <= r["collided"] <= 4 and 0 <= r["reached"] <= 4
+
+
+def test_union_find_limit_reports_timeout_and_falls_back():
+    """The failure path of a bounded device wait, exercised without a fault:
+    with uf_limit = 1 every union of the grid DBSCAN (3-D features) gives up.
+    The host call returns CE_MPPI_ERR_TIMEOUT; a device replan reports it in
+    diag.status and applies the all-noise fallback (standard MPPI over V);
+    the same planner parameters with the default limit cluster normally."""
+    sc = W.make("arm_blocked", seed=0)
+    hist = W.history(sc, 0)
+    ok = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+    ok.set_nominal(sc["U0"])
+    _, d_ok = ok.replan(sc["x0"], hist, sc["radius"])
+    ok.close()
+    assert d_ok["status"] == 0 and d_ok["n_clusters"] >= 1
+    cfg = dict(sc["cfg"], uf_limit=1)
+    pl = pkg.Planner(cfg, n_obs_max=sc["radius"].shape[0])
+    pl.set_nominal(sc["U0"])
+    with pytest.raises(pkg.CeError) as e:
+        pl.replan(sc["x0"], hist, sc["radius"])
+    assert e.value.status == 4
+    dev = "cuda"
+    diag = torch.zeros(128, dtype=torch.uint8, device=dev)
+    u_out = torch.zeros((cfg["T"], 6), device=dev)
+    pl.replan_dev(torch.tensor(sc["x0"], dtype=torch.float32, device=dev),
+                  torch.tensor(hist, dtype=torch.float32, device=dev),
+                  torch.tensor(sc["radius"], dtype=torch.float32, device=dev),
+                  u_out=u_out, diag=diag)
+    torch.cuda.synchronize()
+    dg = np.frombuffer(diag.cpu().numpy().tobytes()[:32], np.int32)
+    assert dg[7] == 4 and dg[0] == 2 and dg[3] == 0, dg     # status, mode, n_clusters
+    assert np.all(np.isfinite(u_out.cpu().numpy()))
+    w = pl.peek("W")
+    idxc = pl.peek("IDXC")[: dg[1]]
+    assert np.all(w[idxc] == 0) and abs(w.sum() - 1) < 1e-5   # the fallback is over V
+    pl.close()

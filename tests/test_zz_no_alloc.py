@@ -30,7 +30,9 @@ def _points(seed, n, p):
 
 @pytest.mark.parametrize("p,eps,mp", [(2, 0.25, 20), (3, 0.2, 16)])
 def test_noalloc_matches_workspace_entry_point_twice(p, eps, mp):
-    for call, (seed, n) in enumerate([(11, 5000), (12, 16384)]):
+    # calls in a row, largest first: each later call finds the previous,
+    # larger call's data in the shared scratch and must not depend on it
+    for call, (seed, n) in enumerate([(11, 16384), (12, 5000), (13, 700)]):
         z = _points(seed + p, n, p)
         lab_ref, M_ref = pkg.dbscan_dev(z, eps, mp)
         lab, M = pkg.dbscan_noalloc_dev(z, eps, mp)
