@@ -330,7 +330,7 @@ def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
     a replan that clustered contributes its DBSCAN phases); the episodes are
     restarted every `episode` steps, as in the timed loop."""
     import torch
-    prune, dbs, phases = [], [], []
+    prune, dbs, phases, sel, dense, upd, whole = [], [], [], [], [], [], []
     last = [None] * len(planners)
     for s in range(n_steps):
         if s and s % episode == 0:
@@ -343,12 +343,20 @@ def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
                 continue   # this instance did not replan in the step
             last[i] = c.copy()
             prune.append(c[10] - c[9])
+            if c[14] > c[13] >= c[12] > c[11]:   # the selection and update stamps of this replan
+                sel.append(c[12] - c[11])
+                dense.append(c[13] - c[12])
+                upd.append(c[14] - c[13])
+                whole.append(c[14] - c[9])
             if c[0] > c[10] and c[11] > c[8]:   # clustered in this replan
                 phases.append(np.diff(c[0:9]))
                 dbs.append(c[11] - c[10])
-    out = {"replans": len(prune), "clustered": len(dbs),
-           "prune": [int(np.mean(prune)), int(np.max(prune))] if prune else None,
-           "dbscan": [int(np.mean(dbs)), int(np.max(dbs))] if dbs else None}
+    def mm(v):
+        return [int(np.mean(v)), int(np.max(v))] if v else None
+
+    out = {"replans": len(prune), "clustered": len(dbs), "prune": mm(prune), "dbscan": mm(dbs),
+           "select_weights": mm(sel), "dense_update_sums": mm(dense),
+           "update_shift": mm(upd), "kernel": mm(whole)}
     if phases:
         ph = np.array(phases)
         out["dbscan_phases"] = {n: [int(ph[:, k].mean()), int(ph[:, k].max())]

@@ -324,7 +324,13 @@ typedef enum {
   CE_BUF_LABEL = 8,   /* int   [K]      DBSCAN label of V, -1 noise                 */
   CE_BUF_W = 9,       /* float [K]      normalised update weights (Eq. 6 / Eq. 19)  */
   CE_BUF_HITJ = 10,   /* int   [K]      horizon step of the first hit, -1 if none   */
-  CE_BUF_DBCYC = 11   /* long long [12] SM clock stamps of the DBSCAN phases        */
+  CE_BUF_DBCYC = 11   /* long long [16] SM clock stamps (SM cycles) that thread 0 of  */
+                      /* the clustering kernel's first CTA leaves: [0..8] the DBSCAN */
+                      /* phases, [9] kernel start, [10] after pruning, [11] after   */
+                      /* DBSCAN, [12] after the statistics, selection and weights, */
+                      /* [13] after the partial sums of a dense update (rank 0     */
+                      /* alone from here), [14] after the update and its shift;    */
+                      /* [15] unused                                                */
 } ce_buf_t;
 ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* host_dst, size_t bytes);
 

@@ -237,6 +237,11 @@ class Planner:
         x0 = np.ascontiguousarray(x0, dtype=np.float32)
         hist = np.ascontiguousarray(hist, dtype=np.float32)
         radius = np.ascontiguousarray(radius, dtype=np.float32)
+        n_obs = int(radius.shape[0])
+        # the library reads exactly these many floats from each buffer
+        if x0.size != self.n or hist.size != self.cfg["hist_len"] * n_obs * self.p:
+            raise ValueError(f"x0 must hold {self.n} floats and hist "
+                             f"{self.cfg['hist_len']} x {n_obs} x {self.p}")
         u = np.zeros((self.T, self.m), np.float32)
         dg = Diag()
         _check(lib().ce_mppi_replan(self.h, x0.ctypes.data, hist.ctypes.data, radius.ctypes.data,
@@ -252,7 +257,7 @@ class Planner:
     def peek(self, name: str) -> np.ndarray:
         K, p, TM = self.K, self.p, self.T * self.m
         shapes = dict(S=(K,), HIT=(K,), PN=(p, K), EPS=(K, self.T, self.m), IDXV=(K,),
-                      IDXC=(K,), Z=(p, K), G=(p, K), LABEL=(K,), W=(K,), HITJ=(K,), DBCYC=(12,))
+                      IDXC=(K,), Z=(p, K), G=(p, K), LABEL=(K,), W=(K,), HITJ=(K,), DBCYC=(16,))
         ints = ("HIT", "IDXV", "IDXC", "LABEL", "HITJ")
         dt = np.int64 if name == "DBCYC" else (np.int32 if name in ints else np.float32)
         out = np.zeros(shapes[name], dt)

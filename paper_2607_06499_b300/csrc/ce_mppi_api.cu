@@ -970,8 +970,8 @@ ce_status_t ce_mppi_peek(ce_mppi_handle* h, int which, void* dst, size_t bytes) 
     return CE_MPPI_OK;
   }
   if (which == CE_BUF_DBCYC) {
-    if (want(sizeof(long long) * 12) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
-    CE_CUDA(cudaMemcpy(dst, d.ctl->dbcyc, sizeof(long long) * 12, cudaMemcpyDeviceToHost));
+    if (want(sizeof(long long) * 16) != CE_MPPI_OK) return CE_MPPI_ERR_INVALID_ARG;
+    CE_CUDA(cudaMemcpy(dst, d.ctl->dbcyc, sizeof(long long) * 16, cudaMemcpyDeviceToHost));
     return CE_MPPI_OK;
   }
   if (which == CE_BUF_EPS) {

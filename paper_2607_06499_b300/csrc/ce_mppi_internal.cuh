@@ -39,7 +39,7 @@ struct Ctl {
   unsigned int done;              // last-CTA ticket of the update stage
   int col_tests;                  // circle/sphere tests per rollout after reach culling
   unsigned long long counter_used;
-  long long dbcyc[12];            // DBSCAN phase clock stamps of the last replan
+  long long dbcyc[16];            // stage clock stamps of the last replan (see ce_mppi_peek)
 };
 
 // Static description of one planner instance: parameters and device buffers.

@@ -1506,6 +1506,7 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   __syncthreads();
   if (tid == 0 && lnz) atomicAdd(&ctl->nnz_all, lnz);
   cluster.sync();   // the list, the range partials and the nonzero count are complete
+  if (fused && tid == 0 && rank == 0) ctl->dbcyc[12] = clock64();   // (stage clock stamp)
   if (fused && a.post_dense && __ldcg(&ctl->nnz_all) > kSparseMax) {
     // dense update by every CTA: per fixed rollout range and column, the
     // weighted eps' sum (Kahan, lanes in k order, fixed trees), into rpart;
@@ -1580,6 +1581,7 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
     cluster.sync();   // every range's partials are written
   }
   if (rank != 0) return;
+  if (fused && tid == 0) ctl->dbcyc[13] = clock64();
   // rank 0: Z in range order, the list by ascending k, the control block
   if (wid == 0) {
     constexpr int per = kPruneRanges / 32;
@@ -1626,6 +1628,7 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
       finalize(d, req_of(a, inst));
       if (tid == 0) ctl->updated = 1;
     }
+    if (tid == 0) ctl->dbcyc[14] = clock64();
   }
 }
 

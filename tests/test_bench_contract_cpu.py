@@ -43,7 +43,7 @@ def test_stage_stamps_skips_repeats_and_counts_clustered(monkeypatch):
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
 
     def stamps(t0, clustered):
-        c = np.zeros(12, np.int64)
+        c = np.zeros(16, np.int64)
         c[9] = t0                       # kernel start
         c[10] = t0 + 100                # end of prune
         if clustered:
@@ -52,6 +52,9 @@ def test_stage_stamps_skips_repeats_and_counts_clustered(monkeypatch):
         else:
             c[0:9] = t0 - 50            # left from an earlier replan
             c[11] = t0 + 100
+        c[12] = c[11] + 40              # statistics, selection, weights
+        c[13] = c[12] + 7               # (dense update sums)
+        c[14] = c[13] + 30              # update and shift
         return c
 
     class Fake:
@@ -78,3 +81,5 @@ def test_stage_stamps_skips_repeats_and_counts_clustered(monkeypatch):
     assert out["replans"] == 4 + 2 and out["clustered"] == 4 + 1
     assert out["prune"] == [100, 100] and out["dbscan"] == [95, 95]
     assert out["dbscan_phases"]["cell unions"] == [10, 10]
+    assert out["select_weights"] == [40, 40] and out["update_shift"] == [30, 30]
+    assert out["kernel"][1] == 100 + 95 + 77

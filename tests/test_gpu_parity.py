@@ -21,16 +21,9 @@ from paper_2607_06499_b300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-BAND = 1e-5
-RTOL = 1e-4
+from parity_check import BAND, RTOL, check_outputs, parity_report_fixture  # noqa: E402
 
-
-def _rel(a, ref, floor):
-    a = np.asarray(a, np.float64)
-    ref = np.asarray(ref, np.float64)
-    if a.size == 0:
-        return 0.0
-    return float(np.max(np.abs(a - ref) / np.maximum(np.abs(ref), floor)))
+_parity_report = parity_report_fixture()
 
 
 def _run(sc, r=0, counter=0):
@@ -49,99 +42,9 @@ def _run(sc, r=0, counter=0):
 
 
 def _check_replan(sc, counter=0, report=None):
-    cfg = sc["cfg"]
-    n, m, p = pkg.DIMS[cfg["dyn"]]
-    K = cfg["K"]
     u, diag, out, hist = _run(sc, counter=counter)
-    assert diag["status"] == 0
-    P = oracle.make_params(cfg, counter=counter)
-    trk = oracle.tracks(P, hist)
-    ref = oracle.rollouts(P, sc["x0"], sc["U0"], trk, sc["radius"])
-    # ---- rollouts: flags outside the band, first hit, costs, positions, perturbations
-    col_g = out["HIT"] >= 0
-    col_o = ref["col"] == 1
-    clear = ref["min_abs_clear"] > BAND
-    assert not np.any((col_g != col_o) & clear), "collision flag differs outside the band"
-    assert np.array_equal(out["HIT"][clear], ref["hit"][clear])
-    assert np.array_equal(out["HITJ"][clear], ref["hit_j"][clear])
-    errS = _rel(out["S"][clear], ref["S"][clear], 1.0)
-    errP = _rel(out["PN"].T[clear], ref["pN"][clear], 1.0)
-    # eps' = u - U with u = U + eps' held in FP32: its rounding scales with
-    # |U| + |eps'| (the magnitude of the applied control); the normal behind it
-    # carries an absolute error up to 4.6e-6 (the Box-Muller angle's sine and
-    # cosine from the special-function unit, 2^-21.41 + pi 2^-24, times the
-    # radius <= 5.77, plus a few ulp of the radius), i.e. sigma * 4.6e-6, so
-    # the scale is floored at 0.05 sigma (4.6e-6 / 1e-4)
-    sig = np.array(cfg["sigma"])[None, None, :]
-    scaleE = np.maximum(np.abs(sc["U0"])[None] + np.abs(ref["eps"]), 0.05 * sig)
-    errE = float(np.max(np.abs(out["EPS"] - ref["eps"]) / scaleE))
-    assert errS < RTOL and errP < RTOL and errE < RTOL, (errS, errP, errE)
-    # ---- pruning (bit-exact on the GPU's flags)
-    idxV, idxC = oracle.prune(col_g.astype(np.int32))
-    nV, nC = diag["n_valid"], diag["n_col"]
-    assert (nV, nC) == (len(idxV), len(idxC))
-    assert np.array_equal(out["IDXV"][:nV], idxV) and np.array_equal(out["IDXC"][:nC], idxC)
-    S_g = out["S"].astype(np.float64)
-    eps_g = out["EPS"].astype(np.float64)
-    pN_g = out["PN"].T.astype(np.float64)
-    errs = dict(S=errS, pN=errP, eps=errE)
-    if cfg.get("mppi_only", 0):
-        assert diag["mode"] == 5          # standard MPPI over all K
-        members = np.arange(K, dtype=np.int32)
-    elif nC == 0 or nV == 0:
-        assert diag["mode"] == (0 if nC == 0 else 1)
-        members = np.arange(K, dtype=np.int32)
-    else:
-        # ---- reference point and features (GPU flags and positions handed in)
-        o_star, pbar = oracle.reference_point(P, sc["x0"], trk, sc["radius"], idxC,
-                                              out["HIT"], pN_g)
-        assert o_star == diag["o_star"]
-        errs["pbar"] = _rel(np.array(diag["pbar"][:p]), pbar, 1.0)
-        assert errs["pbar"] < RTOL
-        z_ref, g_ref = oracle.features(P, sc["x0"], pbar, idxV, pN_g)
-        dnorm = np.linalg.norm(pN_g[idxV] - pbar[None, :], axis=1)
-        tol_z = RTOL + 4e-6 / np.maximum(dnorm, 1e-9)
-        z_g = out["Z"][:, :nV].T.astype(np.float64)
-        g_g = out["G"][:, :nV].T.astype(np.float64)
-        assert np.all(np.abs(z_g - z_ref).max(axis=1) <= tol_z)
-        enorm = np.linalg.norm(pN_g[idxV] - oracle.task_pos(P, sc["x0"])[None, :], axis=1)
-        assert np.all(np.abs(g_g - g_ref).max(axis=1) <= RTOL + 4e-6 / np.maximum(enorm, 1e-9))
-        # ---- DBSCAN on the GPU's own features: bit-exact
-        lab_o, M_o = oracle.dbscan(out["Z"][:, :nV].T, cfg["dbscan_eps"], cfg["min_pts"])
-        assert M_o == diag["n_clusters"]
-        assert np.array_equal(lab_o, out["LABEL"][:nV])
-        if M_o == 0:
-            assert diag["mode"] == 2
-            members = idxV
-        else:
-            v_obs = oracle.obstacle_velocity(P, hist)[o_star]
-            sel = oracle.select(P, lab_o, idxV, S_g, g_g, M_o, v_obs)
-            assert diag["dynamic"] == sel["dynamic"]
-            assert diag["mode"] == (4 if sel["dynamic"] else 3)
-            crit = sel["Sbar"] if not sel["dynamic"] else sel["vhat"] @ (v_obs / (np.linalg.norm(v_obs) + 1e-6))
-            srt = np.sort(crit)
-            near_tie = len(srt) > 1 and (srt[1] - srt[0]) <= 1e-5 * max(1.0, abs(srt[0]))
-            if not near_tie:
-                assert diag["sel_label"] == sel["sel"]
-            members = idxV[lab_o == diag["sel_label"]]
-    # ---- update (GPU costs, perturbations and selection handed in)
-    U_ref, w_ref, smin = oracle.update(P, sc["U0"], S_g, eps_g, members)
-    # relative to the magnitude of the terms of U + sum_k w_k eps'_k (the
-    # condition of the weighted sum), floored at 1e-3 sigma
-    sig2 = np.array(cfg["sigma"])[None, :]
-    scaleU = np.maximum(np.abs(sc["U0"]) + np.einsum("k,kjd->jd", w_ref, np.abs(eps_g)), 1e-3 * sig2)
-    scaleU = np.maximum(scaleU, np.abs(U_ref))
-    errs["U"] = float(np.max(np.abs(u - U_ref) / scaleU))
-    errs["w"] = float(np.max(np.abs(out["W"] - w_ref)))
-    assert errs["U"] < RTOL, errs
-    assert errs["w"] < 1e-5 + 1e-4 * w_ref.max()
-    assert abs(out["W"].sum() - 1.0) < 1e-5
-    # ---- receding-horizon shift and counter
-    np.testing.assert_array_equal(out["nominal_after"], np.vstack([u[1:], u[-1:]]))
-    assert out["counter_after"] == counter + 1 and diag["counter"] == counter
-    if report is not None:
-        report.update(errs)
-    return diag, errs
+    return check_outputs(sc["cfg"], sc["x0"], sc["U0"], hist, sc["radius"], counter, u, diag,
+                         out, report=report)
 
 
 @pytest.mark.parametrize("name,kw", [
@@ -474,7 +377,7 @@ def test_noise_regen_same_bits(name, kw):
     kw = dict(kw)
     lam = kw.pop("lam", None)
     for regen in (0, 1):
-        sc = W.make(name, seed=0, noise_regen=regen, **kw)
+        sc = W.make(name, seed=0, noise_regen=regen, n_replans=3, **kw)
         cfg = sc["cfg"]
         if lam is not None:
             cfg["lambda"] = lam
