@@ -320,6 +320,9 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
 STAMP_PHASES = ("cells and per-CTA counts", "occupied cells, offsets, cursors",
                 "scatter into cell order, cell boxes", "core flags", "core boxes",
                 "cell unions", "components, ids, core labels", "border points")
+# the angle-bucket DBSCAN of 2-D features (stamp 15 = 1)
+STAMP_PHASES_ANG = ("angle buckets, counts, radius range", "totals, scan, scatter",
+                    "core flags", "runs, boundaries, components, ids", "labels")
 
 
 def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
@@ -331,6 +334,7 @@ def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
     restarted every `episode` steps, as in the timed loop."""
     import torch
     prune, dbs, phases, sel, dense, upd, whole = [], [], [], [], [], [], []
+    phases_ang, dbs_ang = [], []
     last = [None] * len(planners)
     for s in range(n_steps):
         if s and s % episode == 0:
@@ -349,7 +353,11 @@ def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
                 upd.append(c[14] - c[13])
                 whole.append(c[14] - c[9])
             if c[0] > c[10] and c[11] > c[8]:   # clustered in this replan
-                phases.append(np.diff(c[0:9]))
+                if c[15] == 1:
+                    phases_ang.append(np.diff(c[0:6]))
+                    dbs_ang.append(c[11] - c[10])
+                else:
+                    phases.append(np.diff(c[0:9]))
                 dbs.append(c[11] - c[10])
     def mm(v):
         return [int(np.mean(v)), int(np.max(v))] if v else None
@@ -361,6 +369,11 @@ def stage_stamps(planners, replay, restart, n_steps: int, episode: int) -> dict:
         ph = np.array(phases)
         out["dbscan_phases"] = {n: [int(ph[:, k].mean()), int(ph[:, k].max())]
                                 for k, n in enumerate(STAMP_PHASES)}
+    if phases_ang:
+        ph = np.array(phases_ang)
+        out["dbscan_angular"] = len(dbs_ang)
+        out["dbscan_angular_phases"] = {n: [int(ph[:, k].mean()), int(ph[:, k].max())]
+                                        for k, n in enumerate(STAMP_PHASES_ANG)}
     return out
 
 

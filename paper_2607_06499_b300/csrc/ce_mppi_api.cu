@@ -233,6 +233,7 @@ void fill_scalars(InstDesc& d, const ce_mppi_params* P, const ce_mppi_handle* h)
   d.n_obs_max = P->n_obs_max; d.H = P->hist_len; d.min_pts = P->min_pts; d.ref_mode = P->ref_mode;
   d.check_j0 = P->check_j0; d.G = G; d.R = R; d.regen = P->noise_regen;
   d.mppi_only = P->mppi_only;
+  d.gsz = is_arm(P->dyn) ? 1 : 32;
   d.uf_limit = P->uf_limit > 0 ? P->uf_limit : kUfLimit;
   d.eps_ld_c = is_arm(P->dyn) ? 1 : Kp;
   d.eps_ld_k = is_arm(P->dyn) ? h->TMp : 1;
@@ -326,9 +327,13 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   const size_t eps_elems = P->noise_regen ? 0
                           : is_arm(P->dyn) ? (size_t)Kp * h->TMp : (size_t)T * m * Kp;
   const size_t o_eps = take(4 * eps_elems);
-  size_t o_int[9];
-  for (int i = 0; i < 9; ++i) o_int[i] = take(4 * Kp);
+  size_t o_int[8];
+  for (int i = 0; i < 8; ++i) o_int[i] = take(4 * Kp);
+  const int gsz = is_arm(P->dyn) ? 1 : 32, ngroups = (K + gsz - 1) / gsz;
+  const size_t o_gcnt = take(sizeof(int2) * ngroups), o_gS = take(sizeof(float4) * ngroups);
+  const size_t o_osum = take(sizeof(long long) * 4 * (size_t)std::max(nobs, 1));
   const size_t o_bbox = take(sizeof(float) * 6 * h->ncells);
+  const size_t o_ang = take(sizeof(int) * 2 * kAngBuckets);
   const size_t o_upart = take(sizeof(float) * (size_t)((K + kUpdChunkArm - 1) / kUpdChunkArm) * h->TMp);
   // host-path staging: inputs then outputs
   const size_t in_x0 = 0, in_hist = align_up(4 * n, 16),
@@ -370,10 +375,13 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.g = reinterpret_cast<float*>(b + o_g);
   d.zs = reinterpret_cast<float*>(b + o_zs);
   d.eps = P->noise_regen ? nullptr : reinterpret_cast<float*>(b + o_eps);
-  int** ints[9] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent,
-                   &d.vpos};
-  for (int i = 0; i < 9; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
+  int** ints[8] = {&d.hit, &d.hitj, &d.idxV, &d.idxC, &d.label, &d.cell, &d.sorted, &d.parent};
+  for (int i = 0; i < 8; ++i) *ints[i] = reinterpret_cast<int*>(b + o_int[i]);
+  d.gcnt = reinterpret_cast<int2*>(b + o_gcnt);
+  d.gS = reinterpret_cast<float4*>(b + o_gS);
+  d.osum = reinterpret_cast<long long*>(b + o_osum);
   d.bbox = reinterpret_cast<float*>(b + o_bbox);
+  d.ang = reinterpret_cast<int*>(b + o_ang);
   d.upart = reinterpret_cast<float*>(b + o_upart);
   d.TMp = h->TMp;
   h->d_x0 = reinterpret_cast<float*>(b + o_in + in_x0);

@@ -25,6 +25,7 @@ constexpr long long kSpinLimit = 1ll << 22;   // bounded waits (mbarrier)
 constexpr int kUfLimit = 1 << 20;       // parent reads per union-find operation (default)
 constexpr int kSparseMax = 256;         // nonzero update weights kept as a sorted list
 constexpr int kPruneRanges = 256;       // fixed rollout ranges of the pbar sums
+constexpr int kAngBuckets = 4096;       // angle buckets of the 2-D DBSCAN
 
 // Per-instance control block written by the stages of one replan.
 struct Ctl {
@@ -71,8 +72,12 @@ struct InstDesc {
   float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
   int TMp;       // T*m rounded up to a multiple of 4
   int *hit, *hitj, *idxV, *idxC, *label, *cell, *sorted, *parent;
-  int* vpos;     // [Kp] position of rollout k in V, -1 when it collides
+  int gsz;       // rollouts per group record: 32 (2-D, one warp), 1 (arm)
+  int2* gcnt;    // [ceil(K / gsz)] per group: rollouts in V, in C_col
+  float4* gS;    // [ceil(K / gsz)] per group: max |S| over V, min S over V, min S
+  long long* osum;   // [n_obs_max][4] per obstacle hit first: count, fixed-point sum of p(x_T)
   float* bbox;   // [G^p][6] DBSCAN per-cell core bounding boxes
+  int* ang;      // [2][kAngBuckets] angular DBSCAN: bucket counts, least core index
   Ctl* ctl;
 };
 
@@ -299,6 +304,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 __device__ __forceinline__ void raise_status(Ctl* c, int code) { atomicCAS(&c->status, 0, code); }
+
+// Task positions as 32.32 fixed point: sums over any number of rollouts are
+// exact, so they do not depend on the order the atomics land in.
+__device__ __forceinline__ long long pos_fixed(float v) { return __float2ll_rn(v * 4294967296.0f); }
+constexpr float kPosFixedInv = 2.3283064365386963e-10f;   // 2^-32
 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {

@@ -17,10 +17,11 @@ namespace {
 // Largest point count the fixed scratch serves.
 constexpr int kNoAllocMaxPoints = 16384;
 // Bytes of scratch the standalone DBSCAN needs for kNoAllocMaxPoints points
-// (same carving as its workspace: cell, sorted, core, 3 coordinates, boxes).
+// (same carving as its workspace: cell, sorted, core, 3 coordinates, boxes,
+// two angle-bucket tables); each call checks the workspace size against it.
 constexpr size_t kNoAllocBytes =
     (size_t)kNoAllocMaxPoints * (3 * sizeof(int) + 3 * sizeof(float)) +
-    (size_t)cem::kMaxCells * 6 * sizeof(float);
+    (size_t)cem::kMaxCells * 6 * sizeof(float) + 2 * sizeof(int) * (size_t)cem::kAngBuckets;
 
 // The scratch: one copy per device that loads the library, kept until exit.
 // Its name is only a host-side stand-in in host code; kernels get the device

@@ -44,16 +44,6 @@ __device__ __forceinline__ int block_scan_flag(bool f, int* wsum, int* total) {
   return r;
 }
 
-// 4-byte asynchronous copy global -> shared (cp.async), and the wait for all
-// of this thread's copies.
-__device__ __forceinline__ void async_copy4(float* dst, const float* src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
-}
-__device__ __forceinline__ void async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, float* p0) {
   if (is_arm(d.dyn)) {
     float q[6], O[7][3], R[9];
@@ -72,141 +62,85 @@ __device__ __forceinline__ void task_pos0(const InstDesc& d, const float* x0, fl
 // hit obstacle o* and the reference point pbar (Eq. 11), the features z
 // (Eq. 12-13) and g (Eq. 15) of V, and the velocity estimate of o* (Eq. 17).
 // One thread-block cluster of CL CTAs per instance (CL = 1 .. 8, chosen at
-// launch); the K rollouts are split into CL * 32 contiguous warp ranges, each
-// read three times, coalesced: pass 1 counts V / C_col and marks the
-// obstacles hit first; the CTAs then exchange their counts and marks through
-// distributed shared memory (o* follows from the marks); pass 2 writes V,
-// C_col, each k's position in V and S in V order, and sums the terminal
-// positions for pbar; the CTAs exchange those partial sums (added in rank
-// order: deterministic); pass 3 writes the features.
+// launch), CTAs independent of each other: the rollout kernel has left, per
+// group of rollouts, the sizes of V and C_col and the extremes of S, and per
+// obstacle hit first, the count and the exact fixed-point sums of p(x_T).  So
+// every CTA finds the instance's totals, its warps' list offsets, o* and pbar
+// from those records, then reads its warps' contiguous rollout ranges once
+// (coalesced) and writes V, C_col, S in V order and the features.
 __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
+  (void)fused;
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int inst = blockIdx.x / CL;
   const InstDesc& d = desc_of(a, inst);
   const Req r = req_of(a, inst);
   Ctl* ctl = d.ctl;
-  __shared__ unsigned hitmask[kMaxObs / 32];
   __shared__ unsigned long long best;
   __shared__ float p0s[3];
-  __shared__ unsigned long long wpack[33];
-  __shared__ float red[3][33];
-  __shared__ float vpart[4][kPruneRanges];   // per range: count, sum x, y, z
-  __shared__ unsigned long long cbase;   // V / C_col counts of the lower ranks
-  __shared__ unsigned long long tall;    // V / C_col counts of the instance
+  __shared__ int wv[32], wc[32];            // counts of each warp's range
+  __shared__ float wred[32][3];             // per-warp extremes of S
+  __shared__ int wlow[32][4];               // per-warp totals: V, C_col, V and C_col below rank
+  __shared__ long long wsum4[32][4];        // per-warp sums for pbar over all of C_col
+  __shared__ float tv[8];
   const int K = d.K, Kp = d.Kp, p = d.p, n_obs = r.n_obs, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const int nmw = (n_obs + 31) / 32;
-  const int* __restrict__ hit = d.hit;
-  const float* __restrict__ pN = d.pN;
-  const float* __restrict__ Sg = d.S;
-  int* idxV = d.idxV;
-  int* idxC = d.idxC;
-  int* vpos = d.vpos;
-  float* Sv = d.Sv;
-  float* zf = d.z;
-  float* gf = d.g;
-  const int ref_mode = d.ref_mode;
-  for (int i = tid; i < nmw; i += blockDim.x) hitmask[i] = 0u;
+  const int gsz = d.gsz, ng = (K + gsz - 1) / gsz;
   if (tid == 0) {
     best = ~0ull;
     task_pos0(d, r.x0, p0s);
   }
-  __syncthreads();
-  // kPruneRanges contiguous ranges of Lv rollouts; a warp owns m consecutive
-  // ranges.  The pbar sums are reduced per range and the ranges added in
-  // order, so the result does not depend on CL.
-  const int Lv = (((K + kPruneRanges - 1) / kPruneRanges) + 31) & ~31;
-  const int m_r = kPruneRanges / (CL * nw);
-  const int L = m_r * Lv;
+  // warp ranges: contiguous, multiples of 32 rollouts (aligned to the groups)
+  const int L = (((K + CL * nw - 1) / (CL * nw)) + 31) & ~31;
   const int beg = min(K, (rank * nw + wid) * L), end = min(K, beg + L);
-  const unsigned lt = (1u << lane) - 1u;
-  // The warp's rollouts are taken kPG steps of 32 at a time, the inputs of a
-  // group (first hit, S, p(x_T)) loaded together.  A warp whose range is one
-  // group keeps them in registers for all three passes.
-  constexpr int kPG = 2;
-  const bool one_group = end - beg <= 32 * kPG;
-  int hc[kPG];
-  float sc[kPG], pc[kPG][3];
-  auto load_group = [&](int g0, bool want_s, bool want_p) {
-#pragma unroll
-    for (int u = 0; u < kPG; ++u) {
-      const int k = g0 + 32 * u + lane;
-      const bool in = k < end;
-      hc[u] = in ? __ldg(hit + k) : -1;
-      sc[u] = in && want_s ? __ldg(Sg + k) : INFINITY;
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        pc[u][c] = in && want_p && c < p ? __ldg(pN + (size_t)c * Kp + k) : 0.f;
-    }
-  };
-  // ---- pass 1
+  const int g_rank = min(ng, rank * nw * L / gsz);   // first group of this rank
+  // ---- totals, the lower ranks' counts, the extremes of S (from the group
+  //      records, every CTA alike); this warp's counts
   {
-    unsigned long long cnt = 0;
-    for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
-      load_group(g0, one_group, one_group);
-#pragma unroll
-      for (int u = 0; u < kPG; ++u) {
-        const int s0 = g0 + 32 * u;
-        if (s0 >= end) break;
-        const int k = s0 + lane;
-        const int h = hc[u];
-        // one shared-memory OR per distinct mask word in the warp
-        const unsigned grp = __match_any_sync(FULL, h >= 0 ? (h >> 5) : -1);
-        const unsigned bits = __reduce_or_sync(grp, h >= 0 ? 1u << (h & 31) : 0u);
-        if (h >= 0 && lane == __ffs(grp) - 1) atomicOr(&hitmask[h >> 5], bits);
-        cnt += __popc(__ballot_sync(FULL, k < end && h < 0)) |
-               ((unsigned long long)__popc(__ballot_sync(FULL, h >= 0)) << 32);
-      }
+    int tvv = 0, tcc = 0, lvv = 0, lcc = 0;
+    float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
+    for (int gi = tid; gi < ng; gi += blockDim.x) {
+      const int2 c = __ldcg(d.gcnt + gi);
+      const float4 e = __ldcg(d.gS + gi);
+      tvv += c.x;
+      tcc += c.y;
+      if (gi < g_rank) { lvv += c.x; lcc += c.y; }
+      vmax = fmaxf(vmax, e.x);
+      vmin = fminf(vmin, e.y);
+      amin = fminf(amin, e.z);
     }
-    if (lane == 0) wpack[wid] = cnt;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    const unsigned long long v = lane < nw ? wpack[lane] : 0ull;
-    unsigned long long x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += y;
-    }
-    wpack[lane] = x - v;
-    if (lane == 31) wpack[32] = x;
-  }
-  cluster.sync();   // counts and marks of every CTA of the instance are final
-  // totals, the lower ranks' counts, and the union of the marks (the ranks'
-  // wpack and hitmask are not written again)
-  if (wid == 0) {
-    unsigned long long t = 0ull, lo = 0ull;
-    if (lane < CL) {
-      t = cluster.map_shared_rank(wpack, lane)[32];
-      lo = lane < rank ? t : 0ull;
+    int mvv = 0, mcc = 0;
+    const int gb = beg / gsz, ge = (end + gsz - 1) / gsz;
+    for (int gi = gb + lane; gi < ge; gi += 32) {
+      const int2 c = __ldcg(d.gcnt + gi);
+      mvv += c.x;
+      mcc += c.y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      t += __shfl_xor_sync(FULL, t, o);
-      lo += __shfl_xor_sync(FULL, lo, o);
+      tvv += __shfl_xor_sync(FULL, tvv, o);
+      tcc += __shfl_xor_sync(FULL, tcc, o);
+      lvv += __shfl_xor_sync(FULL, lvv, o);
+      lcc += __shfl_xor_sync(FULL, lcc, o);
+      mvv += __shfl_xor_sync(FULL, mvv, o);
+      mcc += __shfl_xor_sync(FULL, mcc, o);
+      vmax = fmaxf(vmax, __shfl_xor_sync(FULL, vmax, o));
+      vmin = fminf(vmin, __shfl_xor_sync(FULL, vmin, o));
+      amin = fminf(amin, __shfl_xor_sync(FULL, amin, o));
     }
     if (lane == 0) {
-      tall = t;
-      cbase = lo;
+      wlow[wid][0] = tvv; wlow[wid][1] = tcc; wlow[wid][2] = lvv; wlow[wid][3] = lcc;
+      wv[wid] = mvv; wc[wid] = mcc;
+      wred[wid][0] = vmax; wred[wid][1] = vmin; wred[wid][2] = amin;
     }
   }
-  __shared__ unsigned allmask[kMaxObs / 32];
-  for (int i = tid; i < nmw; i += blockDim.x) {
-    unsigned m = 0u;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)   // (loads of all ranks in flight together)
-      if (q < CL) m |= cluster.map_shared_rank(hitmask, q)[i];
-    allmask[i] = m;
-  }
-  __syncthreads();
+  // ---- o*: least clearance |p(x_0) - o_t| - r_o among the obstacles some
+  //      rollout hit first (count > 0); ties to the lowest index
+  __syncthreads();   // (p0s)
   {
-    // o*: least clearance |p(x_0) - o_t| - r_o among obstacles hit first by
-    // some rollout; ties to the lowest index (packed key, atomicMin)
     const float* hn = hist_of(r, d) + (size_t)(d.H - 1) * n_obs * p;   // newest observation
     for (int o = tid; o < n_obs; o += blockDim.x) {
-      if (!((allmask[o >> 5] >> (o & 31)) & 1u)) continue;
+      if (__ldcg(d.osum + 4 * (size_t)o) == 0) continue;
       const float dx = p0s[0] - hn[o * p], dy = p0s[1] - hn[o * p + 1];
       const float dz = p == 3 ? p0s[2] - hn[o * p + 2] : 0.f;
       const float clear = sqrtf(dx * dx + dy * dy + dz * dz) - r.obs_radius[o];
@@ -214,206 +148,136 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
     }
   }
   __syncthreads();
-  const int nV = (int)(tall & 0xffffffffull), nC = (int)(tall >> 32);
+  if (wid == 0) {
+    int t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = lane < nw ? wlow[lane][q] : 0;
+    float e0 = lane < nw ? wred[lane][0] : 0.f, e1 = lane < nw ? wred[lane][1] : INFINITY,
+          e2 = lane < nw ? wred[lane][2] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] += __shfl_xor_sync(FULL, t[q], o);
+      e0 = fmaxf(e0, __shfl_xor_sync(FULL, e0, o));
+      e1 = fminf(e1, __shfl_xor_sync(FULL, e1, o));
+      e2 = fminf(e2, __shfl_xor_sync(FULL, e2, o));
+    }
+    // exclusive scan of the warps' counts, after the lower ranks'
+    const int v = lane < nw ? wv[lane] : 0, c = lane < nw ? wc[lane] : 0;
+    int sv = v, sc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yv = __shfl_up_sync(FULL, sv, o), yc = __shfl_up_sync(FULL, sc, o);
+      if (lane >= o) { sv += yv; sc += yc; }
+    }
+    if (lane < nw) { wv[lane] = t[2] + sv - v; wc[lane] = t[3] + sc - c; }
+    if (lane == 0) {
+      tv[0] = e0; tv[1] = e1; tv[2] = e2;
+      tv[3] = __int_as_float(t[0]);
+      tv[4] = __int_as_float(t[1]);
+    }
+  }
+  __syncthreads();
+  const int nV = __float_as_int(tv[3]), nC = __float_as_int(tv[4]);
   const int o_star = nC > 0 ? (int)(best & 0xffffffffull) : -1;
-  // newest and oldest observation of o* for its velocity (Eq. 17): copied
-  // into shared memory now (asynchronously, no registers held), used at the end
-  __shared__ float vo_obs[2][3];
-  // (only on the clustering path, which waits for them before its end)
-  if (tid == 0 && rank == 0 && o_star >= 0 && nV > 0 && !d.mppi_only) {
-    const float* h = hist_of(r, d);
-    for (int c = 0; c < p; ++c) {
-      async_copy4(&vo_obs[0][c], h + ((size_t)(d.H - 1) * n_obs + o_star) * p + c);
-      async_copy4(&vo_obs[1][c], h + (size_t)o_star * p + c);
-    }
-  }
-  // ---- pass 2: lists, S in V order, S extremes; pbar sums over the colliding
-  // rollouts whose first hit is o* (ref_mode 0) or over all of them (ref_mode 1)
-  float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
-  float cntp = 0.f, acc[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
-  {
-    int bv = (int)(wpack[wid] & 0xffffffffull) + (int)(cbase & 0xffffffffull);
-    int bc = (int)(wpack[wid] >> 32) + (int)(cbase >> 32);
-    const int v0 = (rank * nw + wid) * m_r;   // first range of this warp
-    auto flush = [&](int v) {
-      const float c4[4] = {warp_sum(cntp), warp_sum(acc[0]), warp_sum(acc[1]), warp_sum(acc[2])};
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) vpart[q][v] = c4[q];
-      cntp = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] = cmp[c] = 0.f;
-    };
-    // one loop over the warp's ranges (loads of consecutive steps overlap);
-    // each range's sums are flushed at its end
-    int jr = 0;
-    for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
-      if (!one_group) load_group(g0, true, true);
-#pragma unroll
-      for (int u = 0; u < kPG; ++u) {
-        const int s0 = g0 + 32 * u;
-        if (s0 >= end) break;
-        const int k = s0 + lane;
-        const int h = hc[u];
-        const float Sk = sc[u];
-        const bool isV = k < end && h < 0, isC = h >= 0;
-        const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
-        amin = fminf(amin, Sk);
-        if (isV) {
-          const int pos = bv + __popc(mv & lt);
-          idxV[pos] = k;
-          vpos[k] = pos;
-          Sv[pos] = Sk;
-          vmax = fmaxf(vmax, fabsf(Sk));
-          vmin = fminf(vmin, Sk);
-        }
-        if (isC) {
-          idxC[bc + __popc(mc & lt)] = k;
-          vpos[k] = -1;
-          if (ref_mode != 0 || h == o_star) {
-            cntp += 1.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              if (c < p) kahan_add(acc[c], cmp[c], pc[u][c]);
-          }
-        }
-        bv += __popc(mv);
-        bc += __popc(mc);
-        if (s0 + 32 - beg == (jr + 1) * Lv) flush(v0 + jr++);
-      }
-    }
-    for (; jr < m_r; ++jr) flush(v0 + jr);   // a range cut by K, and ranges past it
-  }
-  // block extremes of S (order-free), then the instance's values: extremes
-  // over the ranks, and the range partials of pbar added in range order
-  {
-    float v3[3] = {vmax, vmin, amin};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      v3[0] = fmaxf(v3[0], __shfl_xor_sync(FULL, v3[0], o));
-      v3[1] = fminf(v3[1], __shfl_xor_sync(FULL, v3[1], o));
-      v3[2] = fminf(v3[2], __shfl_xor_sync(FULL, v3[2], o));
-    }
-    if (lane == 0)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) red[q][wid] = v3[q];
-    __syncthreads();
-    if (wid == 0) {
-      float t[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) t[q] = red[q][lane];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        t[0] = fmaxf(t[0], __shfl_xor_sync(FULL, t[0], o));
-        t[1] = fminf(t[1], __shfl_xor_sync(FULL, t[1], o));
-        t[2] = fminf(t[2], __shfl_xor_sync(FULL, t[2], o));
-      }
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) red[q][32] = t[q];
-    }
-  }
-  cluster.sync();   // every rank's extremes and range partials are final
-  __shared__ float tv[7];
-  if (wid < 4) {
-    // warp q takes partial q (count, sum x, y, z): lane l adds ranges
-    // 8l .. 8l+7 (owned by rank 8l / (32 m_r)), then a fixed tree over the
-    // lanes
-    constexpr int per = kPruneRanges / 32;
-    const int own = 32 * m_r;   // ranges per rank
-    const float* vp = cluster.map_shared_rank(&vpart[wid][0], (per * lane) / own);
-    float c1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < per; ++j) c1 += vp[per * lane + j];
-    c1 = warp_sum(c1);
-    if (lane == 0) tv[3 + wid] = c1;
-  } else if (wid == 4) {
-    float e3[3] = {0.f, INFINITY, INFINITY};
-    if (lane < CL) {
-      const float* rr = cluster.map_shared_rank(&red[0][0], lane);
-      e3[0] = rr[0 * 33 + 32];
-      e3[1] = rr[1 * 33 + 32];
-      e3[2] = rr[2 * 33 + 32];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      e3[0] = fmaxf(e3[0], __shfl_xor_sync(FULL, e3[0], o));
-      e3[1] = fminf(e3[1], __shfl_xor_sync(FULL, e3[1], o));
-      e3[2] = fminf(e3[2], __shfl_xor_sync(FULL, e3[2], o));
-    }
-    if (lane == 0) { tv[0] = e3[0]; tv[1] = e3[1]; tv[2] = e3[2]; }
-  }
-  // no distributed shared memory access after this point; inside the fused
-  // kernel the caller's cluster barrier after this stage keeps every CTA
-  // (and its shared memory) alive until all reads are done
-  if (fused) __syncthreads();
-  else cluster.sync();
   if (tid == 0 && rank == 0) {
     ctl->S_absmax_V = tv[0];
     ctl->S_min_V = tv[1];
     ctl->S_min_all = tv[2];
   }
-  if (nC == 0 || nV == 0 || d.mppi_only) {
-    if (tid == 0 && rank == 0) {
-      ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = -1;
-      ctl->dynamic = 0;
-      ctl->mode = d.mppi_only ? CE_MODE_MPPI : nC == 0 ? CE_MODE_NOCOL : CE_MODE_ALLCOL;
-      for (int i = 0; i < 3; ++i) { ctl->pbar[i] = 0.f; ctl->v_obs[i] = 0.f; ctl->p0[i] = p0s[i]; }
-    }
-    return;
+  // the fallbacks (no clustering): the lists are still written, not the features
+  const bool fallback = nC == 0 || nV == 0 || d.mppi_only;
+  if (fallback && tid == 0 && rank == 0) {
+    ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = -1;
+    ctl->dynamic = 0;
+    ctl->mode = d.mppi_only ? CE_MODE_MPPI : nC == 0 ? CE_MODE_NOCOL : CE_MODE_ALLCOL;
+    for (int i = 0; i < 3; ++i) { ctl->pbar[i] = 0.f; ctl->v_obs[i] = 0.f; ctl->p0[i] = p0s[i]; }
   }
-  const float ncnt = tv[3];
+  // ---- pbar (Eq. 11): the mean p(x_T) of the colliding rollouts whose first
+  //      hit is o* (ref_mode 0) or of all of them (ref_mode 1), from the exact
+  //      fixed-point sums
   float pbar[3] = {0.f, 0.f, 0.f};
+  if (!fallback && d.ref_mode == 0) {
+    const long long* os = d.osum + 4 * (size_t)o_star;
+    const float cnt = (float)__ldcg(os);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) pbar[c] = c < p ? tv[4 + c] / ncnt : 0.f;
-  // ---- pass 3: features of V (positions as in pass 2)
+    for (int c = 0; c < 3; ++c)
+      if (c < p) pbar[c] = __ll2float_rn(__ldcg(os + 1 + c)) * kPosFixedInv / cnt;
+  } else if (!fallback) {
+    long long s4[4] = {0, 0, 0, 0};
+    for (int o = tid; o < n_obs; o += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s4[q] += __ldcg(d.osum + 4 * (size_t)o + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s4[q] += __shfl_xor_sync(FULL, s4[q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wsum4[wid][q] = s4[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s4[q] = 0;
+      for (int w2 = 0; w2 < nw; ++w2) s4[q] += wsum4[w2][q];   // (exact: any order)
+    }
+    const float cnt = (float)s4[0];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < p) pbar[c] = __ll2float_rn(s4[1 + c]) * kPosFixedInv / cnt;
+  }
+  // ---- the pass over the warp's rollouts: lists, S in V order, features
   const float ne = d.norm_eps;
-  {
-    int bv = (int)(wpack[wid] & 0xffffffffull) + (int)(cbase & 0xffffffffull);
-    for (int g0 = beg; g0 < end; g0 += 32 * kPG) {
-      if (!one_group) load_group(g0, false, true);
+  const unsigned lt = (1u << lane) - 1u;
+  int bv = wv[wid], bc = wc[wid];
+  for (int s0 = beg; s0 < end; s0 += 32) {
+    const int k = s0 + lane;
+    const bool in = k < end;
+    const int h = in ? __ldg(d.hit + k) : -1;
+    const bool isV = in && h < 0, isC = h >= 0;
+    const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
+    if (isV) {
+      const int i = bv + __popc(mv & lt);
+      d.idxV[i] = k;
+      d.Sv[i] = __ldg(d.S + k);
+    }
+    if (isV && !fallback) {
+      const int i = bv + __popc(mv & lt);
+      float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
 #pragma unroll
-      for (int u = 0; u < kPG; ++u) {
-        const int s0 = g0 + 32 * u;
-        if (s0 >= end) break;
-        const int k = s0 + lane;
-        const bool isV = k < end && hc[u] < 0;
-        const unsigned mv = __ballot_sync(FULL, isV);
-        if (isV) {
-          const int i = bv + __popc(mv & lt);
-          float dv[3] = {0.f, 0.f, 0.f}, ev[3] = {0.f, 0.f, 0.f}, nd = 0.f, nn = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        if (c >= p) continue;
+        const float pk = __ldg(d.pN + (size_t)c * Kp + k);
+        dv[c] = pk - pbar[c];
+        ev[c] = pk - p0s[c];
+        nd += dv[c] * dv[c];
+        nn += ev[c] * ev[c];
+      }
+      const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (c >= p) continue;
-            const float pk = pc[u][c];
-            dv[c] = pk - pbar[c];
-            ev[c] = pk - p0s[c];
-            nd += dv[c] * dv[c];
-            nn += ev[c] * ev[c];
-          }
-          const float izd = 1.0f / (sqrtf(nd) + ne), izn = 1.0f / (sqrtf(nn) + ne);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (c >= p) continue;
-            zf[(size_t)c * Kp + i] = dv[c] * izd;
-            gf[(size_t)c * Kp + i] = ev[c] * izn;
-          }
-        }
-        bv += __popc(mv);
+      for (int c = 0; c < 3; ++c) {
+        if (c >= p) continue;
+        d.z[(size_t)c * Kp + i] = dv[c] * izd;
+        d.g[(size_t)c * Kp + i] = ev[c] * izn;
       }
     }
+    if (isC) d.idxC[bc + __popc(mc & lt)] = k;
+    bv += __popc(mv);
+    bc += __popc(mc);
   }
-  if (tid == 0 && rank == 0) {
+  if (tid == 0 && rank == 0 && !fallback) {
     const int H = d.H;
     const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
-    async_wait_all();   // this thread's copies of o*'s observations
+    const float* h = hist_of(r, d);
     ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = o_star;
     ctl->dynamic = 0; ctl->mode = CE_MODE_STATIC;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       ctl->pbar[c] = c < p ? pbar[c] : 0.f;
       ctl->p0[c] = p0s[c];
-      ctl->v_obs[c] = c < p ? (vo_obs[0][c] - vo_obs[1][c]) * inv : 0.f;
+      ctl->v_obs[c] = c < p ? (h[((size_t)(H - 1) * n_obs + o_star) * p + c] -
+                               h[(size_t)o_star * p + c]) * inv
+                            : 0.f;
     }
   }
 }
@@ -434,6 +298,8 @@ struct DbWork {
   int ld_s;
   int* core;     // [n] core flag
   float* bbox;   // [ncells][6] core bounding box (min xyz, max xyz)
+  int* ahist;    // [kAngBuckets] angle-bucket counts (zero at entry), angular method
+  int* amin;     // [kAngBuckets] least core index per bucket (INT_MAX at entry)
 };
 
 // The 125 neighbour-cell offsets of a 3-D point (reach R = 2 cells), nearest
@@ -710,10 +576,13 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   // 2. counts of the whole set per cell; occupied cells in cell order: id,
   //    offsets, reset of the per-cell summaries; map becomes cell -> occupied
   //    id.  Identical in every CTA.
-  int anybad = 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (q < CL) anybad |= *cluster.map_shared_rank(&bad, q);
+  // (the ranks' flags read once, by warp 0, and shared through this CTA)
+  __shared__ int anybad_s;
+  if (tid < 32) {
+    const int f = lane < CL ? *cluster.map_shared_rank(&bad, lane) : 0;
+    const unsigned any = __reduce_or_sync(FULL, (unsigned)f);
+    if (lane == 0) anybad_s = (int)any;
+  }
   for (int c = tid; c < nc; c += blockDim.x) {
     int t = 0;
 #pragma unroll
@@ -782,6 +651,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   }
   __syncthreads();
   const int n_occ = n_occ_s;
+  const int anybad = anybad_s;   // (set before the barriers above)
   if (anybad || n_occ > S) {
     for (int i = i0 + tid; i < i1; i += blockDim.x) labels[i] = -1;
     if (tid == 0 && rank == 0) { *M_out = 0; atomicCAS(status, 0, CE_MPPI_ERR_INVALID_ARG); }
@@ -1155,6 +1025,532 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   stamp(8);
 }
 
+// ========================================================================= angular DBSCAN
+// For p = 2 the features z = d / (|d| + eps_n) of Eq. 13 lie on or just inside
+// the unit circle, so DBSCAN can work on their angles.  A point's angle (FP32
+// atan2) puts it in one of kAngBuckets equal buckets around the circle.  With
+// r_lo <= |z| <= r_hi over the set, two points at true angle difference phi
+// have squared distance (r_a - r_b)^2 + 4 r_a r_b sin^2(phi/2), so
+//   phi <= Phi_lo = 2 asin(sqrt(eps^2 - (r_hi - r_lo)^2) / (2 r_hi))  => neighbours,
+//   phi >  Phi_hi = 2 asin(eps / (2 r_lo))                            => not.
+// With margins for the FP32 predicate's rounding (|s - d^2| <= 4 2^-24 d^2,
+// taken as 1e-6 relative), for atan2f and the bucket mapping (1.5e-5 rad per
+// point), two points whose buckets are D apart (circularly) are neighbours
+// for sure when D <= D_lo and cannot be when D > D_hi; only the few buckets
+// in between (the band, D_hi - D_lo ~ 3) need the exact FP32 predicate.  So:
+//   * core counting is a difference of the bucket prefix sums over the
+//     window |D| <= D_lo, plus exact tests in the band when that count is
+//     below minPts;
+//   * core buckets within D_lo of each other are connected (all their core
+//     points are pairwise neighbours): runs of core buckets whose gaps are
+//     <= D_lo are connected sets; with D_hi <= 2 D_lo + 1 an edge can only
+//     join two runs that are adjacent around the circle, across a gap of at
+//     most D_hi, and only between their end buckets -- the exact predicate
+//     decides those few pairs;
+//   * a border point's lowest-index core neighbour is the least index over
+//     the core points of the window (per-bucket minima) and of the band (exact
+//     tests).
+// The partition is the one the definition gives (every decision is either
+// proven by the bounds or taken by the exact predicate).  Used when the set
+// allows it (|z| >= 0.5 everywhere, D_lo >= 4, D_hi <= 2 D_lo + 1, windows
+// shorter than the circle); otherwise the grid DBSCAN runs.
+constexpr int kAngSmemInts = 5 * kAngBuckets + 2;
+constexpr double kAngSlack = 1.5e-5;   // rad per point: atan2f error + bucket mapping
+
+__device__ __forceinline__ int ang_wrap(int b) { return b & (kAngBuckets - 1); }
+
+__device__ __forceinline__ int ang_bucket(float x, float y) {
+  const float th = atan2f(y, x);   // [-pi, pi]
+  const float f = (th + 3.14159265358979f) * ((float)kAngBuckets / 6.28318530717959f);
+  return min(max((int)floorf(f), 0), kAngBuckets - 1);
+}
+
+// Block-wide scan of a[0 .. kAngBuckets) in place (blockDim.x * 4 ==
+// kAngBuckets): exclusive sum (MAX = false) or exclusive max with identity
+// -1 (MAX = true).  Returns the total (sum or max).
+template <bool MAX>
+__device__ __forceinline__ int ang_scan(int* a, int* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int b0 = 4 * tid;
+  const int v0 = a[b0], v1 = a[b0 + 1], v2 = a[b0 + 2], v3 = a[b0 + 3];
+  auto op = [](int x, int y) { return MAX ? max(x, y) : x + y; };
+  const int id = MAX ? -1 : 0;
+  const int t = op(op(v0, v1), op(v2, v3));
+  int x = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x = op(x, y);
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int w = wsum[lane];
+    int s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s = op(s, y);
+    }
+    const int sp = __shfl_up_sync(FULL, s, 1);
+    wsum[lane] = lane ? sp : id;   // exclusive over warps
+    if (lane == 31) wsum[32] = s;
+  }
+  __syncthreads();
+  const int xp = __shfl_up_sync(FULL, x, 1);
+  int e = lane ? op(wsum[wid], xp) : wsum[wid];   // exclusive before this thread
+  a[b0] = e;
+  e = op(e, v0);
+  a[b0 + 1] = e;
+  e = op(e, v1);
+  a[b0 + 2] = e;
+  a[b0 + 3] = op(e, v2);
+  const int total = wsum[32];
+  __syncthreads();
+  return total;
+}
+
+// Positions (in bucket order) of the circular bucket range [b0, b1]
+// (b1 - b0 < kAngBuckets): one or two contiguous ranges of st[] (the bucket
+// starts, st[kAngBuckets] = n).
+__device__ __forceinline__ void ang_range(const int* st, int b0, int b1, int* p0, int* p1,
+                                          int* q0, int* q1) {
+  *q0 = *q1 = 0;
+  if (b1 < 0) {
+    b0 += kAngBuckets;
+    b1 += kAngBuckets;
+  } else if (b0 >= kAngBuckets) {
+    b0 -= kAngBuckets;
+    b1 -= kAngBuckets;
+  }
+  if (b0 < 0) {
+    *p0 = st[b0 + kAngBuckets]; *p1 = st[kAngBuckets];
+    *q0 = st[0]; *q1 = st[b1 + 1];
+  } else if (b1 >= kAngBuckets) {
+    *p0 = st[b0]; *p1 = st[kAngBuckets];
+    *q0 = st[0]; *q1 = st[b1 + 1 - kAngBuckets];
+  } else {
+    *p0 = st[b0]; *p1 = st[b1 + 1];
+  }
+}
+
+__device__ __forceinline__ int ang_count(const int* st, int b0, int b1) {
+  int p0, p1, q0, q1;
+  ang_range(st, b0, b1, &p0, &p1, &q0, &q1);
+  return (p1 - p0) + (q1 - q0);
+}
+
+// Up to four position ranges walked as one index space, so that a warp loads
+// the points of every range in the same steps (one memory round trip covers
+// the whole band of a sparse point).
+struct AngRanges {
+  int a[4], e[4];
+  int tot;
+  __device__ __forceinline__ void set(const int* st, int b0, int b1, int c0, int c1) {
+    ang_range(st, b0, b1, &a[0], &e[0], &a[1], &e[1]);
+    ang_range(st, c0, c1, &a[2], &e[2], &a[3], &e[3]);
+    tot = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tot += e[k] - a[k];
+  }
+  __device__ __forceinline__ int pos(int t) const {   // t < tot
+    int base = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int len = e[k] - a[k];
+      if (t < base + len) return a[k] + t - base;
+      base += len;
+    }
+    return -1;
+  }
+};
+
+// Thresholds from the radius range and eps^2; false when the angular method
+// does not apply to this set.  FP32 (FP64 is slow on this GPU): every input
+// and result is widened by 1e-5 relative toward the safe side, far above the
+// few-ulp errors of sqrtf / asinf, so D_lo stays a proven-neighbour distance
+// and D_hi a proven-apart one.
+__device__ __forceinline__ bool ang_thresholds(float rmin2, float rmax2, float eps2, int* Dlo,
+                                               int* Dhi) {
+  const float r_lo = sqrtf(rmin2) * (1.0f - 1e-5f);
+  const float r_hi = sqrtf(rmax2) * (1.0f + 1e-5f);
+  if (!(r_lo >= 0.5f) || !(r_hi <= 2.0f)) return false;
+  const float e_lo2 = eps2 * (1.0f - 1e-5f), e_hi2 = eps2 * (1.0f + 1e-5f);
+  const float dr = (r_hi - r_lo) * (1.0f + 1e-5f);
+  const float s_lo = sqrtf(fmaxf(0.0f, e_lo2 - dr * dr)) / (2.0f * r_hi) * (1.0f - 1e-5f);
+  const float s_hi = sqrtf(e_hi2) / (2.0f * r_lo) * (1.0f + 1e-5f);
+  if (!(s_hi < 1.0f)) return false;
+  const float phi_lo = 2.0f * asinf(fminf(1.0f, s_lo)) * (1.0f - 1e-5f);
+  const float phi_hi = 2.0f * asinf(s_hi) * (1.0f + 1e-5f);
+  const float beta = 6.2831853f / (float)kAngBuckets;
+  *Dlo = (int)floorf((phi_lo - 2.0f * (float)kAngSlack) / beta) - 1;
+  *Dhi = (int)floorf((phi_hi + 2.0f * (float)kAngSlack) / beta) + 1;
+  return *Dlo >= 4 && *Dhi <= 2 * *Dlo + 1 && 2 * *Dhi + 2 < kAngBuckets;
+}
+
+// The angular DBSCAN of n points z ([2][ld], slice [i0, i1) of this CTA) by
+// one thread-block cluster.  Pass 1 (buckets, counts, radius range) has run:
+// w.cell holds each point's bucket, w.core its offset inside the bucket,
+// w.ahist the counts, and the cluster barrier after it has been taken.  Dlo /
+// Dhi from ang_thresholds.  Shared memory (ints): hcnt, st (+1), cur, gmin,
+// aux of kAngBuckets.
+__device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int ld, int n,
+                                               float eps2, int min_pts, int Dlo, int Dhi,
+                                               DbWork w, int* labels, int* M_out, int* smem,
+                                               long long* cyc, int i0, int i1) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+  constexpr int NB = kAngBuckets;
+  int* hcnt = smem;             // [NB] boundary list, then component minima
+  int* st = hcnt + NB;          // [NB + 1] bucket starts in bucket order
+  int* cur = st + NB + 1;       // [NB] run flags, then the component of each bucket
+  int* gmin = cur + NB;         // [NB] least core index per bucket, whole set
+  int* aux = gmin + NB;         // [NB] scans, then the canonical id of each component
+  int* lst = reinterpret_cast<int*>(w.zs + 2 * (size_t)w.ld_s);   // (z's unused third row)
+  __shared__ int wsum[33];
+  __shared__ int n_list, n_cs_s;
+  auto stamp = [&](int k) {
+    if (cyc && tid == 0 && rank == 0) cyc[k] = clock64();
+  };
+  // ---- 2. bucket starts (every CTA alike, from the instance's count table),
+  //    scatter of the slice into bucket order at the offsets pass 1 handed out
+  for (int b = tid; b < NB; b += blockDim.x) st[b] = __ldcg(&w.ahist[b]);
+  __syncthreads();
+  ang_scan<false>(st, wsum);
+  if (tid == 0) st[NB] = n;
+  __syncthreads();
+  for (int i = i0 + tid; i < i1; i += blockDim.x) {
+    const int pos = st[w.cell[i]] + w.core[i];
+    w.sorted[pos] = i;
+    w.zs[pos] = z[i];
+    w.zs[(size_t)w.ld_s + pos] = z[(size_t)ld + i];
+  }
+  cluster.sync();   // (2) bucket order complete in global memory
+  stamp(2);
+  // ---- 3. core flags: window count, exact tests in the band when short
+  if (tid == 0) n_list = 0;
+  __syncthreads();
+  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+    const int i = b0 + tid;
+    bool need = false;
+    if (i < i1) {
+      const int b = w.cell[i];
+      const int c = ang_count(st, b - Dlo, b + Dlo);
+      w.core[i] = c >= min_pts ? 1 : 0;
+      need = c < min_pts;
+    }
+    const unsigned bl = __ballot_sync(FULL, need);
+    int base = 0;
+    if (bl && lane == __ffs(bl) - 1) base = atomicAdd(&n_list, __popc(bl));
+    base = __shfl_sync(FULL, base, bl ? __ffs(bl) - 1 : 0);   // (from the lane that added)
+    if (need) lst[i0 + base + __popc(bl & ((1u << lane) - 1u))] = i;
+  }
+  __syncthreads();
+  const int nl = n_list;
+  for (int li = wid; li < nl; li += nwarp) {
+    const int i = lst[i0 + li];
+    const int b = w.cell[i];
+    const float za[2] = {z[i], z[(size_t)ld + i]};
+    int count = ang_count(st, b - Dlo, b + Dlo);
+    // the two band ranges, (b + Dlo, b + Dhi] and [b - Dhi, b - Dlo)
+    AngRanges br;
+    br.set(st, b + Dlo + 1, b + Dhi, b - Dhi, b - Dlo - 1);
+    for (int t0 = 0; t0 < br.tot && count < min_pts; t0 += 32) {
+      const int t = t0 + lane;
+      bool hit = false;
+      if (t < br.tot) {
+        const int q = br.pos(t);
+        const float zb[2] = {w.zs[q], w.zs[(size_t)w.ld_s + q]};
+        hit = nb_pred_t<2>(za, zb, eps2);
+      }
+      count += __popc(__ballot_sync(FULL, hit));
+    }
+    if (lane == 0) w.core[i] = count >= min_pts ? 1 : 0;
+  }
+  __syncthreads();
+  // least core index per bucket (one atomic per warp and bucket, on the
+  // instance's table in global memory)
+  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+    const int i = b0 + tid;
+    const int b = (i < i1 && w.core[i]) ? w.cell[i] : -1;
+    const unsigned peers = __match_any_sync(FULL, b);
+    if (b >= 0) {
+      const int mn = __reduce_min_sync(peers, i);
+      if (lane == __ffs(peers) - 1) atomicMin(&w.amin[b], mn);
+    }
+  }
+  cluster.sync();   // (3) core flags and bucket minima of every CTA
+  stamp(3);
+  // ---- 4. components over the core buckets (every CTA alike)
+  for (int b = tid; b < NB; b += blockDim.x) {
+    const int m = __ldcg(&w.amin[b]);
+    gmin[b] = m;
+    aux[b] = m != 0x7fffffff ? b : -1;   // (for the previous-core-bucket scan)
+  }
+  __syncthreads();
+  const int last_core = ang_scan<true>(aux, wsum);   // aux[b] = largest core bucket < b
+  // run starts (flag 1) and the boundaries an edge may cross (flag 2, listed
+  // in hcnt, free since barrier 2, and checked below)
+  if (tid == 0) n_list = 0;
+  __syncthreads();
+  for (int b = tid; b < NB; b += blockDim.x) {
+    int f = 0;
+    if (gmin[b] != 0x7fffffff) {
+      const int prev = aux[b] >= 0 ? aux[b] : last_core - NB;   // (wraps to the last)
+      const int gap = b - prev;
+      if (gap > Dlo) {
+        f = 1;
+        if (gap <= Dhi) {
+          f = 2;   // to be checked
+          hcnt[atomicAdd(&n_list, 1)] = b;
+        }
+      }
+    }
+    cur[b] = f;
+  }
+  __syncthreads();
+  // a boundary is closed when some core point of the buckets before it and
+  // some core point after it, at most Dhi buckets apart, are neighbours: the
+  // core points of buckets [b - Dhi, prev] (X) against those of [b, prev + Dhi]
+  // (Y), 32 x 32 pairs per step (X in the lanes, Y broadcast by shuffles).
+  // Pairs more than Dhi buckets apart are proven non-neighbours, so testing
+  // them too changes nothing.
+  {
+    const int nbd = n_list;
+    for (int bi = wid; bi < nbd; bi += nwarp) {
+      const int b = hcnt[bi];
+      const int prev = aux[b] >= 0 ? aux[b] : last_core - NB;
+      AngRanges X, Y;
+      X.set(st, b - Dhi, prev, 0, -1);
+      Y.set(st, b, prev + Dhi, 0, -1);
+      bool found = false;
+      for (int x0 = 0; x0 < X.tot && !found; x0 += 32) {
+        float xa[2] = {0.f, 0.f};
+        bool xv = false;
+        if (x0 + lane < X.tot) {
+          const int q = X.pos(x0 + lane);
+          xv = w.core[w.sorted[q]] != 0;
+          xa[0] = w.zs[q];
+          xa[1] = w.zs[(size_t)w.ld_s + q];
+        }
+        for (int y0 = 0; y0 < Y.tot && !found; y0 += 32) {
+          float ya[2] = {0.f, 0.f};
+          bool yv = false;
+          if (y0 + lane < Y.tot) {
+            const int q = Y.pos(y0 + lane);
+            yv = w.core[w.sorted[q]] != 0;
+            ya[0] = w.zs[q];
+            ya[1] = w.zs[(size_t)w.ld_s + q];
+          }
+          bool hit = false;
+          for (int j = 0; j < 32; ++j) {
+            const float yb[2] = {__shfl_sync(FULL, ya[0], j), __shfl_sync(FULL, ya[1], j)};
+            const bool vj = __shfl_sync(FULL, yv, j);
+            hit |= xv && vj && nb_pred_t<2>(xa, yb, eps2);
+          }
+          found = __any_sync(FULL, hit);
+        }
+      }
+      if (lane == 0 && found) cur[ang_wrap(b)] = 3;   // closed
+    }
+  }
+  __syncthreads();
+  // component starts: open run starts (flag 1, or 2 left unclosed)
+  for (int b = tid; b < NB; b += blockDim.x) aux[b] = (cur[b] == 1 || cur[b] == 2) ? 1 : 0;
+  __syncthreads();
+  ang_scan<false>(aux, wsum);   // aux[b] = component starts before b
+  if (tid == 0) n_cs_s = 0;
+  __syncthreads();
+  for (int b = tid; b < NB; b += blockDim.x) {
+    const bool cs = cur[b] == 1 || cur[b] == 2;
+    if (cs) atomicAdd(&n_cs_s, 1);
+  }
+  __syncthreads();
+  const int n_cs = n_cs_s;
+  // component of each core bucket: starts up to and including b, minus one;
+  // core buckets before the first start belong to the last component (wrap)
+  for (int b = tid; b < NB; b += blockDim.x) {
+    int c = -1;
+    if (gmin[b] != 0x7fffffff) {
+      const bool cs = cur[b] == 1 || cur[b] == 2;
+      const int upto = aux[b] + (cs ? 1 : 0);
+      c = n_cs == 0 ? 0 : (upto >= 1 ? upto - 1 : n_cs - 1);
+    }
+    cur[b] = c;   // (run flags no longer needed)
+  }
+  __syncthreads();
+  // least core index of each component (hcnt is free now), canonical ids
+  const int n_comp = last_core >= 0 ? max(n_cs, 1) : 0;
+  for (int c = tid; c < n_comp; c += blockDim.x) hcnt[c] = 0x7fffffff;
+  __syncthreads();
+  for (int b = tid; b < NB; b += blockDim.x)
+    if (cur[b] >= 0) atomicMin(&hcnt[cur[b]], gmin[b]);
+  __syncthreads();
+  for (int c = tid; c < n_comp; c += blockDim.x) {
+    const int key = hcnt[c];
+    int id = 0;
+    for (int u = 0; u < n_comp; ++u) id += hcnt[u] < key;
+    aux[c] = id;   // canonical id of component c
+  }
+  __syncthreads();
+  stamp(4);
+  // ---- 5. labels of the slice: core points from their bucket's component;
+  //    the others from their lowest-index core neighbour (window minima, then
+  //    exact tests in the band), else noise
+  if (tid == 0) n_list = 0;
+  __syncthreads();
+  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+    const int i = b0 + tid;
+    bool border = false;
+    if (i < i1) {
+      if (w.core[i]) labels[i] = aux[cur[w.cell[i]]];
+      else border = true;
+    }
+    const unsigned bl = __ballot_sync(FULL, border);
+    int base = 0;
+    if (bl && lane == __ffs(bl) - 1) base = atomicAdd(&n_list, __popc(bl));
+    base = __shfl_sync(FULL, base, bl ? __ffs(bl) - 1 : 0);   // (from the lane that added)
+    if (border) lst[i0 + base + __popc(bl & ((1u << lane) - 1u))] = i;
+  }
+  __syncthreads();
+  const int nb_pts = n_list;
+  for (int li = wid; li < nb_pts; li += nwarp) {
+    const int i = lst[i0 + li];
+    const int b = w.cell[i];
+    const float za[2] = {z[i], z[(size_t)ld + i]};
+    int best = 0x7fffffff;
+    for (int d0 = -Dlo; d0 <= Dlo; d0 += 32) {
+      const int dd = d0 + lane;
+      if (dd <= Dlo) best = min(best, gmin[ang_wrap(b + dd)]);
+    }
+    best = __reduce_min_sync(FULL, best);
+    AngRanges br;
+    br.set(st, b + Dlo + 1, b + Dhi, b - Dhi, b - Dlo - 1);
+    for (int t0 = 0; t0 < br.tot; t0 += 32) {
+      const int t = t0 + lane;
+      int cand = 0x7fffffff;
+      if (t < br.tot) {
+        const int q = br.pos(t);
+        const int sid = w.sorted[q];
+        const float zb[2] = {w.zs[q], w.zs[(size_t)w.ld_s + q]};
+        if (sid < best && w.core[sid] && nb_pred_t<2>(za, zb, eps2)) cand = sid;
+      }
+      best = min(best, __reduce_min_sync(FULL, cand));
+    }
+    if (lane == 0) labels[i] = best == 0x7fffffff ? -1 : aux[cur[w.cell[best]]];
+  }
+  if (tid == 0 && rank == 0) *M_out = n_comp;
+  stamp(5);
+}
+
+
+// DBSCAN of 2-D points: pass 1 (angle buckets, per-CTA counts, radius range,
+// the coordinate check), then the angular method when the set allows it, else
+// the grid method.  Same interface as dbscan_block<2>.
+__device__ __forceinline__ void dbscan2(const float* __restrict__ z, int ld, int n, float eps2,
+                                        float cell_inv, int G, int R, int min_pts, DbWork w,
+                                        int* labels, int* M_out, int* status, int* smem,
+                                        long long* cyc, int uf_limit) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ unsigned s_rmin, s_rmax;   // squared radii as float bits (>= 0: ordered as ints)
+  __shared__ int s_bad;
+  if (cyc && tid == 0 && rank == 0) cyc[0] = clock64();
+  const int chunk = (((n + CL - 1) / CL) + 31) & ~31;
+  const int i0 = min(n, rank * chunk), i1 = min(n, i0 + chunk);
+  if (tid == 0) {
+    s_rmin = 0x7f800000u;   // +inf
+    s_rmax = 0u;
+    s_bad = 0;
+  }
+  __syncthreads();
+  // ---- 1. bucket of each point of the slice, counts, radius range.  The
+  //    count atomics (one per warp and bucket, on the instance's table in
+  //    global memory) also give each point its offset inside its bucket,
+  //    kept in w.core until the core flags replace it.
+  {
+    float rmn = INFINITY, rmx = 0.f;
+    bool bad = false;
+    for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+      const int i = b0 + tid;
+      int b = -1;
+      if (i < i1) {
+        const float x = z[i], y = z[(size_t)ld + i];
+        bad |= !(x >= -1.0f && x <= 1.0f && y >= -1.0f && y <= 1.0f);
+        b = ang_bucket(x, y);
+        w.cell[i] = b;
+        const float r2 = x * x + y * y;
+        rmn = fminf(rmn, r2);
+        rmx = fmaxf(rmx, r2);
+      }
+      const unsigned peers = __match_any_sync(FULL, b);
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (b >= 0 && lane == leader) base = atomicAdd(&w.ahist[b], __popc(peers));
+      base = __shfl_sync(FULL, base, leader);
+      if (b >= 0) w.core[i] = base + __popc(peers & ((1u << lane) - 1u));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rmn = fminf(rmn, __shfl_xor_sync(FULL, rmn, o));
+      rmx = fmaxf(rmx, __shfl_xor_sync(FULL, rmx, o));
+    }
+    if (lane == 0) {
+      atomicMin(&s_rmin, __float_as_uint(rmn));
+      atomicMax(&s_rmax, __float_as_uint(rmx));
+    }
+    if (bad) s_bad = 1;
+  }
+  cluster.sync();   // (1) every CTA's counts and radius range (the table is complete)
+  if (cyc && tid == 0 && rank == 0) cyc[1] = clock64();
+  // the ranks' scalars are read once (lanes of warp 0) and the thresholds
+  // (FP64 arithmetic, slow on this GPU) computed by one thread for the CTA
+  __shared__ int s_dec[4];   // any bad coordinate, angular method, Dlo, Dhi
+  if (tid < 32) {
+    unsigned rmin_u = 0x7f800000u, rmax_u = 0u;
+    int bad = 0;
+    if (lane < CL) {
+      rmin_u = *cluster.map_shared_rank(&s_rmin, lane);
+      rmax_u = *cluster.map_shared_rank(&s_rmax, lane);
+      bad = *cluster.map_shared_rank(&s_bad, lane);
+    }
+    rmin_u = __reduce_min_sync(FULL, rmin_u);
+    rmax_u = __reduce_max_sync(FULL, rmax_u);
+    bad = __reduce_or_sync(FULL, (unsigned)bad);
+    if (lane == 0) {
+      int Dlo = 0, Dhi = 0;
+      const bool ok = !bad && n > 0 &&
+                      ang_thresholds(__uint_as_float(rmin_u), __uint_as_float(rmax_u), eps2,
+                                     &Dlo, &Dhi);
+      s_dec[0] = bad;
+      s_dec[1] = ok;
+      s_dec[2] = Dlo;
+      s_dec[3] = Dhi;
+    }
+  }
+  __syncthreads();
+  const int anybad = s_dec[0];
+  if (anybad) {   // coordinates outside [-1, 1]: refused, as the grid method does
+    for (int i = i0 + tid; i < i1; i += blockDim.x) labels[i] = -1;
+    if (tid == 0 && rank == 0) { *M_out = 0; atomicCAS(status, 0, CE_MPPI_ERR_INVALID_ARG); }
+    cluster.sync();   // no CTA leaves while another reads its scalars
+    return;
+  }
+  const bool ang = s_dec[1] != 0;
+  const int Dlo = s_dec[2], Dhi = s_dec[3];
+  if (cyc && tid == 0 && rank == 0) cyc[15] = ang ? 1 : 2;
+  if (ang) {
+    dbscan_angular(z, ld, n, eps2, min_pts, Dlo, Dhi, w, labels, M_out, smem, cyc, i0, i1);
+    if (cyc && tid == 0 && rank == 0) cyc[6] = cyc[7] = cyc[8] = cyc[5];
+  } else {
+    cluster.sync();   // the scalars are no longer read: the grid method reuses the memory
+    dbscan_block<2>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, M_out, status, smem,
+                    cyc, uf_limit);
+  }
+}
+
 __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
   DbWork w;
   w.cell = d.cell;
@@ -1164,7 +1560,21 @@ __device__ __forceinline__ DbWork db_work_of(const InstDesc& d) {
   w.core = d.parent;
   w.bbox = d.bbox;
   w.labels_tmp = d.label;
+  w.ahist = d.ang;
+  w.amin = d.ang + kAngBuckets;
   return w;
+}
+
+// The angular method's two bucket tables start at zero counts and INT_MAX
+// minima; this CTA's share of them is reset here (the caller's cluster barrier
+// orders it before the method's atomics).
+__device__ __forceinline__ void ang_reset(const DbWork& w) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  for (int b = rank * blockDim.x + threadIdx.x; b < kAngBuckets; b += CL * blockDim.x) {
+    w.ahist[b] = 0;
+    w.amin[b] = 0x7fffffff;
+  }
 }
 
 // One cluster per instance; rank 0 publishes the cluster count and the mode.
@@ -1183,8 +1593,8 @@ __device__ __forceinline__ void dbscan_stage(const KArgs& a, int* smem_i) {
     dbscan_block<3>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
                     &ctl->status, smem_i, ctl->dbcyc, d.uf_limit);
   else
-    dbscan_block<2>(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
-                    &ctl->status, smem_i, ctl->dbcyc, d.uf_limit);
+    dbscan2(d.z, d.Kp, nV, d.eps2, d.cell_inv, d.G, d.R, d.min_pts, w, d.label, &M,
+            &ctl->status, smem_i, ctl->dbcyc, d.uf_limit);
   __syncthreads();
   if (threadIdx.x == 0 && cluster.block_rank() == 0) {
     // a union-find that gave up leaves labels that cannot be trusted: the
@@ -1198,6 +1608,9 @@ __device__ __forceinline__ void dbscan_stage(const KArgs& a, int* smem_i) {
 
 __global__ void __maxnreg__(64) k_dbscan(KArgs a) {
   extern __shared__ int smem_i[];
+  cg::cluster_group cluster = cg::this_cluster();
+  ang_reset(db_work_of(desc_of(a, blockIdx.x / cluster.num_blocks())));
+  cluster.sync();   // (the tables are reset before any CTA counts)
   dbscan_stage(a, smem_i);
 }
 
@@ -1211,14 +1624,15 @@ __global__ void __maxnreg__(64) k_dbscan_standalone(const float* z, int n, int l
   __shared__ int status;
   w.labels_tmp = labels;
   if (threadIdx.x == 0) status = 0;
-  cluster.sync();   // rank 0's status is cleared before any CTA may raise it
+  ang_reset(w);
+  cluster.sync();   // rank 0's status is cleared and the bucket tables reset before use
   int* st0 = cluster.map_shared_rank(&status, 0);
   if (p == 3)
     dbscan_block<3>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i,
                     nullptr, kUfLimit);
   else
-    dbscan_block<2>(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i,
-                    nullptr, kUfLimit);
+    dbscan2(z, ld, n, eps2, cell_inv, G, R, min_pts, w, labels, &M, st0, smem_i, nullptr,
+            kUfLimit);
   cluster.sync();   // every CTA's status updates have landed
   if (threadIdx.x == 0 && cluster.block_rank() == 0) *n_clusters = status ? -status : M;
 }
@@ -1676,6 +2090,9 @@ __global__ void __maxnreg__(64) k_post(KArgs a) {
       return;
     }
   }
+  // the angular DBSCAN's bucket tables (ordered before its atomics by the
+  // prune stage's cluster barriers)
+  ang_reset(db_work_of(desc_of(a, blockIdx.x / cluster.num_blocks())));
   // stage clock stamps of rank 0 (diagnostics): start, after prune, after DBSCAN
   long long* cyc = desc_of(a, blockIdx.x / cluster.num_blocks()).ctl->dbcyc;
   const bool st = threadIdx.x == 0 && cluster.block_rank() == 0;
@@ -2022,7 +2439,10 @@ void launch_prune(const KArgs& a, cudaStream_t s) {
   launch_clustered(k_prune, cl, a.n_inst, kBlock, 0, s, a);
 }
 
-static size_t dbscan_smem(int nc) { return dbscan_smem_bytes(nc); }
+// (2-D sets may take the angular method, whose tables are kAngSmemInts ints)
+static size_t dbscan_smem(int nc) {
+  return std::max(dbscan_smem_bytes(nc), sizeof(int) * (size_t)kAngSmemInts);
+}
 
 static ClusterFit g_fit_post[3];
 static size_t post_smem(int nc) { return std::max(dbscan_smem(nc), sizeof(SelSmem)); }
@@ -2083,7 +2503,9 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
   w.core = reinterpret_cast<int*>(b); b += sizeof(int) * ldn;
   w.zs = reinterpret_cast<float*>(b); b += sizeof(float) * 3 * ldn;
   w.ld_s = ldn;
-  w.bbox = reinterpret_cast<float*>(b);
+  w.bbox = reinterpret_cast<float*>(b); b += sizeof(float) * 6 * kMaxCells;
+  w.ahist = reinterpret_cast<int*>(b); b += sizeof(int) * kAngBuckets;
+  w.amin = reinterpret_cast<int*>(b);
   const int fc = fit_class(nc);
   const size_t smem = dbscan_smem(kFitCells[fc]);
   const int cl = cluster_ctas(g_fit_db[fc], 1);
@@ -2093,7 +2515,8 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
 
 size_t dbscan_ws_bytes(int n) {
   const size_t ldn = (size_t)((n + 31) & ~31);
-  return ldn * (3 * sizeof(int) + 3 * sizeof(float)) + (size_t)kMaxCells * 6 * sizeof(float);
+  return ldn * (3 * sizeof(int) + 3 * sizeof(float)) + (size_t)kMaxCells * 6 * sizeof(float) +
+         2 * sizeof(int) * (size_t)kAngBuckets;
 }
 
 }  // namespace cem

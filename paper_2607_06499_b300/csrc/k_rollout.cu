@@ -58,6 +58,8 @@ __global__ void k_tracks(KArgs a) {
       if (any_bad) raise_status(d.ctl, CE_MPPI_ERR_INVALID_ARG);
     }
   }
+  // per-obstacle sums of the pruning stage, filled by the rollout kernel
+  for (int e = threadIdx.x; e < 4 * n_obs; e += blockDim.x) d.osum[e] = 0;
   if (is_arm(d.dyn)) {
     const int total = (T + 1) * n_obs;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -339,24 +341,59 @@ __global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
     }
     ja = jb;
   }
-  if (!ok) {
-    if (threadIdx.x == 0) raise_status(d.ctl, CE_MPPI_ERR_TIMEOUT);
-    return;
+  if (!ok && threadIdx.x == 0) raise_status(d.ctl, CE_MPPI_ERR_TIMEOUT);
+  if (act) {
+    if (DYN == 0) {
+      const float ex = s0 - g0, ey = s1 - g1;
+      kahan_add(S, Sc, w2 * (ex * ex + ey * ey));
+    } else {
+      const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
+      kahan_add(S, Sc, w3 * ex * ex + w4 * ey * ey + w5 * et * et);
+    }
+    if (first >= 0) kahan_add(S, Sc, d.w[7]);   // collision penalty (0 for CE-MPPI)
+    d.S[k] = S;
+    d.hit[k] = first;
+    d.hitj[k] = first_j;
+    d.pN[k] = s0;
+    d.pN[Kp + k] = s1;
   }
-  if (!act) return;
-  if (DYN == 0) {
-    const float ex = s0 - g0, ey = s1 - g1;
-    kahan_add(S, Sc, w2 * (ex * ex + ey * ey));
-  } else {
-    const float ex = s0 - g0, ey = s1 - g1, et = s2 - g2;
-    kahan_add(S, Sc, w3 * ex * ex + w4 * ey * ey + w5 * et * et);
+  // the pruning stage's inputs in aggregate (Eq. 9-11): for this warp's 32
+  // rollouts the sizes of V and C_col and the extremes of S; for each
+  // obstacle hit first, the count and the fixed-point sum of p(x_T)
+  const int lane = threadIdx.x & 31;
+  const bool isV = act && first < 0, isC = act && first >= 0;
+  const unsigned mv = __ballot_sync(0xffffffffu, isV), mc = __ballot_sync(0xffffffffu, isC);
+  float vmax = isV ? fabsf(S) : 0.f, vmin = isV ? S : INFINITY, amin = act ? S : INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, o));
   }
-  if (first >= 0) kahan_add(S, Sc, d.w[7]);   // collision penalty (0 for CE-MPPI)
-  d.S[k] = S;
-  d.hit[k] = first;
-  d.hitj[k] = first_j;
-  d.pN[k] = s0;
-  d.pN[Kp + k] = s1;
+  const int g = k >> 5;   // (lane 0's k is a multiple of 32)
+  if (lane == 0 && 32 * g < d.K) {
+    d.gcnt[g] = make_int2(__popc(mv), __popc(mc));
+    d.gS[g] = make_float4(vmax, vmin, amin, 0.f);
+  }
+  for (unsigned pend = mc; pend;) {   // one round per distinct obstacle
+    const int leader = __ffs(pend) - 1;
+    const int o = __shfl_sync(0xffffffffu, first, leader);
+    const bool mine = isC && first == o;
+    const unsigned grp = __ballot_sync(0xffffffffu, mine);
+    long long sx = mine ? pos_fixed(s0) : 0ll, sy = mine ? pos_fixed(s1) : 0ll;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, off);
+      sy += __shfl_xor_sync(0xffffffffu, sy, off);
+    }
+    if (lane == leader) {
+      long long* os = d.osum + 4 * (size_t)o;
+      atomicAdd(reinterpret_cast<unsigned long long*>(os), (unsigned long long)__popc(grp));
+      atomicAdd(reinterpret_cast<unsigned long long*>(os + 1), (unsigned long long)sx);
+      atomicAdd(reinterpret_cast<unsigned long long*>(os + 2), (unsigned long long)sy);
+    }
+    pend &= ~grp;
+  }
 }
 
 // ------------------------------------------------------------------ 6-DoF arm
@@ -540,6 +577,17 @@ __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
     d.pN[k] = pN[0];
     d.pN[d.Kp + k] = pN[1];
     d.pN[2 * d.Kp + k] = pN[2];
+    // the pruning stage's inputs in aggregate (Eq. 9-11): this rollout's
+    // group record, and its obstacle's count and fixed-point sums of p(x_T)
+    const bool col = first >= 0;
+    d.gcnt[k] = make_int2(col ? 0 : 1, col ? 1 : 0);
+    d.gS[k] = make_float4(col ? 0.f : fabsf(S), col ? INFINITY : S, S, 0.f);
+    if (col) {
+      unsigned long long* os = reinterpret_cast<unsigned long long*>(d.osum + 4 * (size_t)first);
+      atomicAdd(os, 1ull);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) atomicAdd(os + 1 + c, (unsigned long long)pos_fixed(pN[c]));
+    }
   }
 }
 

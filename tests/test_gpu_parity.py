@@ -198,6 +198,77 @@ def test_dbscan_standalone_bit_exact(p, n, eps, mp):
     assert np.array_equal(lab.cpu().numpy(), lab_o)
 
 
+def _circle_features(rng, n, k, spread, jitter, seam):
+    """2-D features like Eq. 13's: unit directions in k arcs, radii just below 1."""
+    c = rng.uniform(-math.pi, math.pi, size=k)
+    if seam:
+        c[0] = math.pi - 0.02          # an arc across the +-pi seam of atan2
+    ang = c[rng.integers(0, k, n)] + rng.normal(scale=spread, size=n)
+    rad = 1.0 - rng.uniform(0.0, jitter, size=n)
+    return np.stack([np.cos(ang) * rad, np.sin(ang) * rad], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,k,spread,eps,mp,seam", [
+    (16384, 4, 0.12, 0.25, 20, True), (16384, 8, 0.05, 0.25, 20, False),
+    (5000, 3, 0.2, 0.3, 10, True), (777, 5, 0.1, 0.1, 5, True), (3000, 6, 0.08, 0.05, 3, False),
+    (2049, 2, 0.3, 0.25, 40, False), (64, 1, 0.5, 0.25, 2, True)])
+def test_dbscan_angular_bit_exact(n, k, spread, eps, mp, seam):
+    """Features on (or just inside) the unit circle take the angle-bucket
+    DBSCAN: labels and cluster count bit-exact against the O(n^2) oracle,
+    including arcs across the atan2 seam and clusters split by gaps near eps."""
+    rng = np.random.default_rng(n + k)
+    z = _circle_features(rng, n, k, spread, 1e-3, seam)
+    zt = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
+    lab, M = pkg.dbscan_dev(zt, eps, mp)
+    torch.cuda.synchronize()
+    lab_o, M_o = oracle.dbscan(z, eps, mp)
+    assert int(M.item()) == M_o
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+
+
+def test_dbscan_angular_band_decisions():
+    """Two arcs whose gap is within 3 % of eps and radii spread by up to 1e-3:
+    the pairs across the gap fall in the band between the proven-neighbour and
+    proven-apart bucket distances and are decided by the exact predicate."""
+    rng = np.random.default_rng(5)
+    for t in range(40):
+        eps = float(rng.choice([0.1, 0.25, 0.3]))
+        gap = eps * rng.uniform(0.97, 1.03)
+        n = int(rng.integers(50, 2000))
+        ang = np.concatenate([rng.uniform(-0.3, 0.0, n // 2) + 1.0,
+                              rng.uniform(0.0, 0.3, n - n // 2) + 1.0 + gap])
+        rad = 1.0 - rng.uniform(0.0, 1e-3, n)
+        z = np.stack([np.cos(ang) * rad, np.sin(ang) * rad], 1).astype(np.float32)
+        mp = int(rng.integers(1, 10))
+        zt = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
+        lab, M = pkg.dbscan_dev(zt, eps, mp)
+        torch.cuda.synchronize()
+        lab_o, M_o = oracle.dbscan(z, eps, mp)
+        assert int(M.item()) == M_o, t
+        assert np.array_equal(lab.cpu().numpy(), lab_o), t
+
+
+def test_dbscan_in_pipeline_takes_the_angular_method():
+    """The benchmark's features (unicycle, Eq. 13) run the angular DBSCAN
+    (stage stamp 15 = 1); features with small norms fall back to the grid."""
+    sc = W.make("unicycle_blocked", seed=0)
+    pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+    pl.set_nominal(sc["U0"])
+    _, d = pl.replan(sc["x0"], W.history(sc, 0), sc["radius"])
+    c = pl.peek("DBCYC")
+    pl.close()
+    assert d["n_clusters"] >= 1 and c[15] == 1 and np.all(np.diff(c[0:6]) >= 0)
+    # small-norm points: the grid path, still bit-exact
+    rng = np.random.default_rng(3)
+    z = _circle_features(rng, 3000, 4, 0.1, 1e-3, False)
+    z[:50] *= 0.3
+    zt = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
+    lab, M = pkg.dbscan_dev(zt, 0.25, 10)
+    torch.cuda.synchronize()
+    lab_o, M_o = oracle.dbscan(z, 0.25, 10)
+    assert int(M.item()) == M_o and np.array_equal(lab.cpu().numpy(), lab_o)
+
+
 def test_dbscan_edge_cases():
     def run(z, eps, mp):
         zt = torch.from_numpy(np.ascontiguousarray(np.asarray(z, np.float32).T.reshape(2, -1))).cuda()
