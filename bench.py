@@ -65,8 +65,6 @@ STAGES = ("tracks", "rollout", "prune", "dbscan", "select", "update")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one rollout
 # launch over the workload's instances, from one ncu capture of the current
 # kernel on this workload; issue-slot use of the same capture.
-ROLLOUT_NCU = {"unicycle": {"traffic": 0.694e6, "issue_active": 0.746}}
-EPISODE = 200   # closed-loop replans per episode
 
 
 def peaks():
@@ -90,8 +88,11 @@ def alu_peak_tflops(sm_count: int, mhz: float) -> float:
 
 
 class ClockSampler:
-    """SM clock and throttle reasons sampled every 10 ms through NVML during the
-    timed region (nvidia-smi every 50 ms where NVML is unavailable)."""
+    """SM clock, utilisation and throttle reasons sampled through NVML every
+    10 ms (nvidia-smi every 50 ms where NVML is unavailable), from start() to
+    stop() -- the whole benchmark run, so that a short timed region still has
+    samples around it.  The clock reported is the median over the samples that
+    saw the GPU busy."""
 
     REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
                ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
@@ -100,10 +101,11 @@ class ClockSampler:
 
     def __init__(self, index: int, bus_id: str = ""):
         import threading
-        self.sm, self.reasons, self.max = [], set(), None
+        self.sm, self.util, self.reasons, self.max = [], [], set(), None
         self.stop_ev = threading.Event()
         self.p = None
         self.thread = None
+        self.nvml_error = None
         try:
             import pynvml as nv
             nv.nvmlInit()
@@ -120,6 +122,7 @@ class ClockSampler:
                 while not self.stop_ev.is_set():
                     try:
                         self.sm.append(float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)))
+                        self.util.append(float(nv.nvmlDeviceGetUtilizationRates(h).gpu))
                         r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
                         for nm, mk in masks:
                             if r & mk:
@@ -130,13 +133,13 @@ class ClockSampler:
 
             self.thread = threading.Thread(target=loop, daemon=True)
             self.thread.start()
-            self.source = "nvml, 10 ms"
+            self.source = "nvml, 10 ms, whole run"
             return
-        except Exception:
-            pass
-        self.source = "nvidia-smi, 50 ms"
+        except Exception as e:   # (no NVML in this container: nvidia-smi instead)
+            self.nvml_error = repr(e)[:120]
+        self.source = "nvidia-smi, 50 ms, whole run"
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+        q = ("clocks.sm,clocks.max.sm,utilization.gpu,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         try:
@@ -146,32 +149,41 @@ class ClockSampler:
         except OSError:
             self.p = None
 
+    def _summary(self, sm, util, mx):
+        busy = [c for c, u in zip(sm, util) if u > 0]
+        use = busy if busy else sm
+        out = {"sm_mhz": float(np.median(use)) if use else None, "sm_max_mhz": mx,
+               "reasons": sorted(self.reasons), "samples": len(sm),
+               "samples_busy": len(busy), "source": self.source}
+        if self.nvml_error:
+            out["nvml"] = self.nvml_error
+        return out
+
     def stop(self) -> dict:
         if self.thread is not None:
             self.stop_ev.set()
             self.thread.join()
-            return {"sm_mhz": float(np.median(self.sm)) if self.sm else None,
-                    "sm_max_mhz": self.max, "reasons": sorted(self.reasons),
-                    "samples": len(self.sm), "source": self.source}
+            return self._summary(self.sm, self.util, self.max)
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"]}
         self.p.terminate()
         self.p.wait()
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
-        sm, mx, reasons = [], None, set()
+        sm, util, mx = [], [], None
         names = [nm for nm, _ in self.REASONS]
         for r in rows:
             try:
-                sm.append(float(r[0]))
-                mx = float(r[1])
+                c, m, u = float(r[0]), float(r[1]), float(r[2])
+                sm.append(c)
+                util.append(u)
+                mx = m
                 for nm, v in zip(names, r[3:7]):
                     if v.strip().lower() == "active":
-                        reasons.add(nm)
+                        self.reasons.add(nm)
             except (ValueError, IndexError):
                 continue
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
+        return self._summary(sm, util, mx)
 
 
 def cpu_baseline(scenes, u_init, max_threads: int, budget_s: float = 10.0) -> dict:
@@ -211,48 +223,94 @@ def cpu_baseline(scenes, u_init, max_threads: int, budget_s: float = 10.0) -> di
                       f"plus two replans of episode 0 on one thread for the latency"}
 
 
+def bench_config(wl_name: str, world: int, noise_regen: int) -> dict:
+    """The workload description both arms print (identical for the same run)."""
+    return dict(WORKLOADS[wl_name]["config"],
+                parallelism=f"replicas x{world}, instances sharded by rank",
+                noise_regen=noise_regen, closed_loop=True,
+                episode_replans=WORKLOADS[wl_name]["episode"])
+
+
 def run_reference(args) -> None:
-    """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 oracle, as it stands, timed on the host cores on
+    the same closed-loop episodes as the GPU arm (rank 0 only): each step is
+    one replan of every episode -- the oracle's own replans, state and shifted
+    nominal carried from step to step -- run as one host thread per episode
+    (up to the core count).  A step is seconds long, so the run is bounded:
+    after the warm-up, steps are timed until --steps are done or about two
+    minutes of oracle time have passed (the sample is stated)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
-    nthr = max(1, min(os.cpu_count() or 1, 8))
-    scenes = [W.make("unicycle", seed=s) for s in range(nthr)]
-    Ps = [oracle.make_params(s["cfg"]) for s in scenes]
-    inputs = ([s["x0"] for s in scenes], [s["U0"] for s in scenes],
-              [W.history(s, 0) for s in scenes], [s["radius"] for s in scenes])
+    wl_name = args.workload if args.workload in WORKLOADS else "unicycle"
+    wl = WORKLOADS[wl_name]
+    regen = args.noise_regen if args.noise_regen >= 0 else (0 if wl_name in ("arm", "arm12") else 1)
+    n_inst = wl["n"] if wl_name != "batch" else 16
+    nthr = max(1, min(os.cpu_count() or 1, n_inst))
+    episode = wl["episode"]
+    scenes = [W.make(wl["scene"], seed=s, n_replans=episode + 8, noise_regen=regen)
+              for s in shard_seeds(0, n_inst)]
+    m = W.DIMS[scenes[0]["cfg"]["dyn"]][1]
+
+    def u0(sc):
+        T_ = sc["cfg"]["T"]
+        return np.zeros((T_, m)) if wl["u_init"] is None else np.tile(wl["u_init"], (T_, 1))
+
+    xs = [np.asarray(sc["x0"], float) for sc in scenes]
+    Us = [u0(sc) for sc in scenes]
+    units = sum(sc["cfg"]["K"] * sc["cfg"]["T"] for sc in scenes)
+
+    def step(r):
+        Ps = [oracle.make_params(sc["cfg"], counter=r) for sc in scenes]
+        U_new, dt = oracle.replan_many(Ps, xs, Us, [W.history(sc, r) for sc in scenes],
+                                       [sc["radius"] for sc in scenes], n_threads=nthr)
+        for i, (P, sc) in enumerate(zip(Ps, scenes)):   # (closed loop, untimed)
+            xs[i] = oracle.step(P, xs[i], U_new[i][0])
+            Us[i] = oracle.shift(P, U_new[i])
+        return dt
+
+    r = 0
     for _ in range(args.warmup):
-        oracle.replan_many(Ps, *inputs, n_threads=nthr)
-    t = []
-    for _ in range(args.steps):
-        _, dt = oracle.replan_many(Ps, *inputs, n_threads=nthr)
-        t.append(dt)
+        step(r % episode)
+        r += 1
+    t, budget = [], 120.0
+    while len(t) < args.steps and (not t or sum(t) < budget):
+        t.append(step(r % episode))
+        r += 1
+    done = len(t)
     tot = float(np.sum(t))
-    cfg = scenes[0]["cfg"]
-    value = len(scenes) * cfg["K"] * cfg["T"] * args.steps / tot
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": WORKLOAD,
+    value = units * done / tot
+    sample = (f"{done} of {args.steps} steps (each: one closed-loop replan of each of the "
+              f"{n_inst} episodes, replans {args.warmup}..{args.warmup + done - 1}), "
+              f"{nthr} host threads, FP64, O(|V|^2) DBSCAN" +
+              ("" if done == args.steps else f"; stopped after {budget:.0f} s of oracle time"))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / done, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": bench_config(wl_name, args.gpus, regen),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle",
-                             "sample": f"each step: {nthr} full replans (episodes 0..{nthr - 1}), "
-                                       f"one per host thread"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: float = 200.0,
-              max_batch: int = 1024, n_streams: int = 3) -> dict:
+              max_batch: int = 1024, n_streams: int = 3, warmup_s: float = 20.0) -> dict:
     """The served request loop: controller sessions arrive as a Poisson process
     (rate_hz), 70 % unicycle (K in {1024, 4096, 16384}, T=50, 50 discs) and 30 %
     arm (K in {2048, 4096}, T=32, 20 spheres); each asks for a replan every 20 ms
     for a lifetime U[2, 20] s.  Sessions are admitted by the server's
     device-memory budget.  Requests are submitted in real time (1 ms ticks);
     a session's request that is still queued when its next one arrives is
-    replaced by the newer one.  Returns served throughput and latency."""
-    arrivals = W.session_arrivals(rate_hz, seconds, seed=seed)
+    replaced by the newer one.  The first warmup_s seconds (the concurrency
+    ramping up: lifetimes reach 20 s) are not measured; the statistics are
+    reset then and cover the next `seconds`.  Returns served throughput,
+    latency and the concurrency seen."""
+    total = warmup_s + seconds
+    arrivals = W.session_arrivals(rate_hz, total, seed=seed)
     n_rep = int(20.0 / 0.02) + 8
     tmpl = {"unicycle": [W.make("unicycle", seed=100 + i, n_replans=n_rep) for i in range(8)],
             "arm": [W.make("arm", seed=200 + i, n_replans=n_rep) for i in range(8)]}
@@ -266,12 +324,22 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
     rejected = opened = 0
     submitted = {"unicycle": 0, "arm": 0}
     steps_sub = 0.0
+    conc = []
     nxt = 0
+    measuring = warmup_s <= 0
     t0 = time.perf_counter()
+    t_meas = t0
     while True:
         t = time.perf_counter() - t0
-        if t >= seconds:
+        if t >= total:
             break
+        if not measuring and t >= warmup_s:
+            srv.stats(reset=True)
+            submitted = {"unicycle": 0, "arm": 0}
+            steps_sub = 0.0
+            rejected = opened = 0
+            measuring = True
+            t_meas = time.perf_counter()
         while nxt < len(arrivals) and arrivals[nxt]["t"] <= t:
             a = arrivals[nxt]
             nxt += 1
@@ -287,6 +355,8 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
         for sid in [s_ for s_, v in active.items() if v[3] <= t]:
             srv.close_session(sid)
             del active[sid]
+        if measuring:
+            conc.append(len(active))
         for kind in ("unicycle", "arm"):
             due = [s_ for s_, v in active.items() if v[0] == kind and v[4] <= t]
             if not due:
@@ -302,13 +372,15 @@ def run_serve(pkg, seconds: float, budget_gb: float, seed: int = 0, rate_hz: flo
                 steps_sub += active[s_][5] * active[s_][6]
         time.sleep(max(0.0, 0.001 - ((time.perf_counter() - t0) - t)))
     st = srv.stats()
-    elapsed = time.perf_counter() - t0
+    elapsed = time.perf_counter() - t_meas
     for sid in list(active):
         srv.close_session(sid)
     srv.close()
     n_sub = sum(submitted.values())
     frac_served = st["replans"] / max(1, n_sub)
-    return {"seconds": elapsed, "sessions_opened": opened, "sessions_rejected": rejected,
+    return {"seconds": elapsed, "warmup_s": warmup_s, "sessions_opened": opened,
+            "sessions_rejected": rejected, "sessions_concurrent_mean": float(np.mean(conc)) if conc else 0.0,
+            "sessions_concurrent_peak": int(max(conc)) if conc else 0,
             "requests_submitted": n_sub, "replans_served": st["replans"],
             "superseded": st["superseded"], "replans_per_s": st["replans"] / elapsed,
             "rollout_steps_per_s": steps_sub * frac_served / elapsed,
@@ -422,78 +494,32 @@ def aggregate(tot_ms: float, units_per_rank: float, steps: int, world: int, dist
     return world * units_per_rank * steps / (tot_ms / 1e3), tot_ms
 
 
-def main() -> None:
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000,
-                    help="timed steps (the 200-replan episodes restart every 200 steps)")
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--plain-steps", type=int, default=10)
-    ap.add_argument("--profile-steps", type=int, default=40)
-    ap.add_argument("--branches", type=int, default=0,
-                    help="concurrent branches of the batch (0: autotuned)")
-    ap.add_argument("--workload", default="unicycle", choices=sorted(WORKLOADS) + ["serve"])
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="length of the served run (0: skip)")
-    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
-    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
-                    help="1: two halves of the episodes software-pipelined in one graph")
-    ap.add_argument("--pipe-post-ctas", type=int, default=0, choices=[0, 1, 2, 4, 8],
-                    help="clustering-kernel CTAs per instance in the pipelined halves "
-                         "(0: from the occupancy, as if each half ran alone)")
-    ap.add_argument("--stamps", type=int, default=0,
-                    help="pipelined steps over which to read the clustering kernel's stage "
-                         "clock stamps (0: off)")
-    ap.add_argument("--noise-regen", type=int, default=-1, choices=[-1, 0, 1],
-                    help="1: perturbations not stored, drawn again by the update; "
-                         "-1: 1 for 2-D robots (few nonzero weights), 0 for the arms")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        run_reference(args)
-        return
+# Algorithmic bytes per rollout of the clustering stages (the fused kernel,
+# prune through the update): ~40 B read and written by pruning, DBSCAN and the
+# selection (hit, S, p(x_T); the V / C_col lists, S in V order, z, g, cells,
+# cell order, labels, weights), plus the update's least traffic when eps' is
+# drawn again, (5 + 2p) 4 B per rollout (its records) -- 76 B for p = 2.
+POST_BYTES_PER_ROLLOUT = {2: 40 + 36, 3: 40 + 44}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch over
+# the benchmark's 8 pipelined instances, from one ncu capture of the current
+# kernels on this workload (None: not captured for the current build).
+POST_NCU_TRAFFIC = None
+ROLLOUT_NCU_TRAFFIC = None   # (16 instances: the stage-by-stage profile launch)
 
-    import torch
-    import paper_2607_06499_b300 as pkg
 
-    if args.workload == "serve":
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        served = run_serve(pkg, max(args.serve_seconds, 1.0), args.serve_budget_gb)
-        plain = plain_mix_latency(pkg)
-        line = {"metric": "CE-MPPI served replans (rollout-steps/s)",
-                "value": served["rollout_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-                "steps": served["replans_served"], "warmup": 0, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "served request loop, Poisson sessions at 200/s, "
-                                       "70 % unicycle / 30 % arm, replan every 20 ms"},
-                "served": served, "plain": plain}
-        print(json.dumps(line), flush=True)
-        return
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    props = torch.cuda.get_device_properties(dev)
-
-    wl = WORKLOADS[args.workload]
-    if args.noise_regen < 0:
-        args.noise_regen = 0 if args.workload in ("arm", "arm12") else 1
-    EPISODE = wl["episode"]
-    N_INST = wl["n"]
-    seeds = shard_seeds(rank, N_INST)
-    scenes = [W.make(wl["scene"], seed=s, n_replans=EPISODE + 8, noise_regen=args.noise_regen)
-              for s in seeds]
+def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: int, dist,
+                 steps: int, warmup: int, flush, profile: bool):
+    """Build the workload's device-resident closed-loop episodes, time `steps`
+    pipelined steps (one replan of every episode each), and measure the
+    stage times.  Returns the measurements and the objects to close."""
+    wl = WORKLOADS[wl_name]
+    regen = args.noise_regen if args.noise_regen >= 0 else (0 if wl_name in ("arm", "arm12") else 1)
+    episode = args.episode_len if (args.episode_len > 0 and wl_name == args.workload) else wl["episode"]
+    n_inst = wl["n"]
+    seeds = shard_seeds(rank, n_inst)
+    scenes = [W.make(wl["scene"], seed=s, n_replans=episode + 8, noise_regen=regen) for s in seeds]
     cfg0 = scenes[0]["cfg"]
-    m = pkg.DIMS[cfg0["dyn"]][1]
-    p_dim = pkg.DIMS[cfg0["dyn"]][2]
+    n_, m, p_dim = pkg.DIMS[cfg0["dyn"]]
 
     def u_init(sc):
         T_ = sc["cfg"]["T"]
@@ -524,18 +550,14 @@ def main() -> None:
 
     reset_episodes()
     batch = pkg.Batch(planners, reqs, stream=stream, use_graph=True, n_branches=args.branches)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # Software pipeline of two halves A, B of the episodes (independent
     # instances): one graph replay = [B clustering + update (replan s-1) |
     # A tracks + rollouts (s)], then [A clustering + update (s) | B tracks +
     # rollouts (s)] -- one replan of every episode per replay, each half's
     # latency-bound stages over the other half's rollouts.
     pipe = None
-    if args.pipeline and N_INST >= 2:
-        half = N_INST // 2
-        # (not autotuned: the tuner times whole replans, and the halves run
-        # beside each other's rollouts, where the occupancy-chosen cluster
-        # size measures better)
+    if args.pipeline and n_inst >= 2:
+        half = n_inst // 2
         bA = pkg.Batch(planners[:half], reqs[:half], stream=stream, use_graph=False)
         bB = pkg.Batch(planners[half:], reqs[half:], stream=stream, use_graph=False)
         bA.set_post_ctas(args.pipe_post_ctas)
@@ -544,22 +566,21 @@ def main() -> None:
         graph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
         with torch.cuda.graph(graph):
-            main = torch.cuda.current_stream()
-            side.wait_stream(main)
-            bB.run_part(1, main)
+            main_s = torch.cuda.current_stream()
+            side.wait_stream(main_s)
+            bB.run_part(1, main_s)
             bA.run_part(0, side)
-            main.wait_stream(side)
-            side.wait_stream(main)
-            bA.run_part(1, main)
+            main_s.wait_stream(side)
+            side.wait_stream(main_s)
+            bA.run_part(1, main_s)
             bB.run_part(0, side)
-            main.wait_stream(side)
+            main_s.wait_stream(side)
         torch.cuda.synchronize()
         pipe = (bA, bB, graph)
 
     def prologue():
-        """(pipelined) B's first tracks + rollouts, untimed"""
         if pipe:
-            pipe[1].run_part(0, stream)
+            pipe[1].run_part(0, stream)   # B's first tracks + rollouts, untimed
 
     def step():
         if pipe:
@@ -569,74 +590,168 @@ def main() -> None:
 
     reset_episodes()
     prologue()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     reset_episodes()
     prologue()
-    assert args.steps >= 1
     if dist:
         dist.barrier()
-    bus = ""
-    try:
-        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
-    except AttributeError:
-        pass
-    clocks = ClockSampler(local, bus)
     step_ms = []
     done = 0
-    while done < args.steps:
-        n = min(EPISODE, args.steps - done)
+    while done < steps:
+        n = min(episode, steps - done)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(n)]
+        torch.cuda.synchronize()
         for i in range(n):
             flush.fill_(float(i))
             ev[i][0].record(stream)
             step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-        step_ms += [a.elapsed_time(b) for a, b in ev]
+        step_ms += [x.elapsed_time(y) for x, y in ev]
         done += n
-        if done < args.steps:
+        if done < steps:
             reset_episodes()
             prologue()
-    clk = clocks.stop()
     step_ms = np.array(step_ms)
-    value, tot_ms = aggregate(float(step_ms.sum()), units_per_step, args.steps, world, dist)
+    value, tot_ms = aggregate(float(step_ms.sum()), units_per_step, steps, world, dist)
     if dist:
         dist.barrier()
     modes = {}
     for r in reqs:
         d = np.frombuffer(r["diag"].cpu().numpy().tobytes()[:32], dtype=np.int32)
-        modes[pkg.MODES[int(d[0])]] = modes.get(pkg.MODES[int(d[0])], 0) + 1
+        modes[pkg.MODES.get(int(d[0]), int(d[0]))] = modes.get(pkg.MODES.get(int(d[0]), int(d[0])), 0) + 1
         assert d[7] == 0, f"device status {d[7]}"
-
+    out = {"value": value, "tot_ms": tot_ms, "step_ms": step_ms,
+           "replans_per_s": world * n_inst * steps / (tot_ms / 1e3),
+           "units_per_step": units_per_step, "modes_last_step": modes, "regen": regen,
+           "batch_config": pipe[0].config() if pipe else batch.config(),
+           "n_inst": n_inst, "episode": episode, "pipelined": bool(pipe)}
+    objs = [batch] + (list(pipe[:2]) if pipe else [])
+    if not profile:
+        return out, objs, planners, scenes, u_init, reset_episodes, step, prologue
     # per-stage device times: stage-by-stage replans over the start of the
     # episodes, L2 flushed before each; obstacle tests per rollout from diag
     reset_episodes()
-    prof = {s: [] for s in STAGES}
+    prof = {s_: [] for s_ in STAGES}
     tests = []
     for i in range(args.profile_steps):
         flush.fill_(float(i))
-        for s, ms in batch.profile().items():
-            prof[s].append(ms)
+        for s_, ms in batch.profile().items():
+            prof[s_].append(ms)
         for r in reqs:
             tests.append(int(np.frombuffer(r["diag"].cpu().numpy().tobytes()[72:76], np.int32)[0]))
-    stage_ms = {s: float(np.mean(v)) for s, v in prof.items()}
-    roll_ms = stage_ms["rollout"]
-    # the fused clustering kernel as the chain runs it: whole-batch half
-    # replans, events around part 1 (prune + DBSCAN + selection + update)
+    out["stage_ms"] = {s_: float(np.mean(v)) for s_, v in prof.items()}
+    out["tests"] = np.array(tests, dtype=np.float64).reshape(args.profile_steps, len(reqs)).mean(0)
+    # the fused clustering kernel as the pipeline launches it: one half's
+    # instances, events around part 1 (prune + DBSCAN + selection + update)
     reset_episodes()
+    bsrc = pipe[0] if pipe else batch
     post = []
     for i in range(args.profile_steps):
         flush.fill_(float(i))
-        batch.run_part(0, stream)
+        bsrc.run_part(0, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        batch.run_part(1, stream)
+        bsrc.run_part(1, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         post.append(e0.elapsed_time(e1))
-    post_ms = float(np.mean(post))
+    out["post_ms"] = float(np.mean(post))
+    out["post_rollouts"] = sum(sc["cfg"]["K"] for sc in scenes[: (len(scenes) // 2 if pipe else len(scenes))])
+    out["p_dim"] = p_dim
+    out["Ks"] = np.array([sc["cfg"]["K"] for sc in scenes], dtype=np.float64)
+    out["Ts"] = np.array([sc["cfg"]["T"] for sc in scenes], dtype=np.float64)
+    return out, objs, planners, scenes, u_init, reset_episodes, step, prologue
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000,
+                    help="timed steps (the 200-replan episodes restart every 200 steps)")
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the arm and uneven-batch workloads measured beside the main one")
+    ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--profile-steps", type=int, default=40)
+    ap.add_argument("--extra-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--branches", type=int, default=0,
+                    help="concurrent branches of the batch (0: autotuned)")
+    ap.add_argument("--workload", default="unicycle", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="measured length of the served run, after its warm-up (0: skip)")
+    ap.add_argument("--serve-warmup", type=float, default=20.0,
+                    help="unmeasured start of the served run (the concurrency ramps up)")
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
+    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
+                    help="1: two halves of the episodes software-pipelined in one graph")
+    ap.add_argument("--pipe-post-ctas", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="clustering-kernel CTAs per instance in the pipelined halves "
+                         "(0: from the occupancy, as if each half ran alone)")
+    ap.add_argument("--stamps", type=int, default=0,
+                    help="pipelined steps over which to read the clustering kernel's stage "
+                         "clock stamps (0: off)")
+    ap.add_argument("--episode-len", type=int, default=0,
+                    help="closed-loop replans before the episodes restart (0: the workload's, "
+                         "200 for the unicycle); longer episodes reach other states")
+    ap.add_argument("--noise-regen", type=int, default=-1, choices=[-1, 0, 1],
+                    help="1: perturbations not stored, drawn again by the update; "
+                         "-1: 1 for 2-D robots (few nonzero weights), 0 for the arms")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2607_06499_b300 as pkg
+
+    if args.workload == "serve":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        served = run_serve(pkg, max(args.serve_seconds, 1.0), args.serve_budget_gb,
+                           warmup_s=args.serve_warmup)
+        plain = plain_mix_latency(pkg)
+        line = {"metric": "CE-MPPI served replans (rollout-steps/s)",
+                "value": served["rollout_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+                "steps": served["replans_served"], "warmup": 0, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "served request loop, Poisson sessions at 200/s, "
+                                       "70 % unicycle / 30 % arm, replan every 20 ms"},
+                "served": served, "plain": plain}
+        print(json.dumps(line), flush=True)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    bus = ""
+    try:
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        pass
+    clocks = ClockSampler(local, bus)   # (the whole run)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    assert args.steps >= 1
+
+    res, objs, planners, scenes, u_init, reset_episodes, step, prologue = run_workload(
+        pkg, torch, args, args.workload, dev, stream, rank, world, dist, args.steps, args.warmup,
+        flush, profile=True)
+    value, tot_ms, step_ms = res["value"], res["tot_ms"], res["step_ms"]
+    n_inst, episode, regen = res["n_inst"], res["episode"], res["regen"]
+    cfg0 = scenes[0]["cfg"]
+    n_dim, m, p_dim = pkg.DIMS[cfg0["dyn"]]
     stamps = None
     if args.stamps > 0:
         def restart():
@@ -644,81 +759,86 @@ def main() -> None:
             prologue()
 
         restart()
-        stamps = stage_stamps(planners, step, restart, args.stamps, EPISODE)
-    # algorithmic bytes of the clustering stages per rollout (read + written,
-    # each array once): prune reads hit, S, p(x_T), writes V/C_col lists, V
-    # positions, S in V order, z, g; DBSCAN reads z, writes cells, cell order,
-    # coordinates in cell order, labels; selection reads labels, S, g, writes w
-    pd = p_dim
-    post_bytes = float(sum(sc["cfg"]["K"] for sc in scenes)) * (4 * (1 + 1 + pd) + 4 * 4 + 8 * pd + 4 * pd
-                                    + 4 * (3 + pd) + 4 * (2 + pd + 1))
-    # per instance: obstacle tests per rollout (after culling) from diag
-    tests = np.array(tests, dtype=np.float64).reshape(args.profile_steps, N_INST).mean(0)
-    Ks = np.array([sc["cfg"]["K"] for sc in scenes], dtype=np.float64)
-    Ts = np.array([sc["cfg"]["T"] for sc in scenes], dtype=np.float64)
+        stamps = stage_stamps(planners, step, restart, args.stamps, episode)
+
+    # ---- rooflines.  The fused clustering kernel (k_post) against HBM with
+    # the algorithmic bytes above, and the rollout kernel against the FP32 ALU
+    # peak; the kernel with the larger share of the step's device time heads
+    # the line.
+    pk, pk_kind = peaks()
+    stage_ms = res["stage_ms"]
+    post_ms = res["post_ms"]
+    post_bytes = POST_BYTES_PER_ROLLOUT[p_dim] * res["post_rollouts"]
+    post_gbs = post_bytes / (post_ms * 1e-3) / 1e9
+    hbm = pk.get("hbm_gbs", 6400.0)
+    tests = res["tests"]
+    Ks, Ts = res["Ks"], res["Ts"]
     if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12):
         # per step: FK (6 DH transforms ~ 6*40) + 24 sphere centres (3*3*24)
         # + pose cost (~60); per sphere test 8 (3 sub, mul, 2 fma x2, compare)
         flops_roll = Ks * (Ts * (240 + 216 + 60) + 24 * 8 * tests)
     else:
+        # 6 per circle test kept by the culling (2 sub, mul, fma counted 2,
+        # compare) plus 60 per step for the clip, the cost and the model step
         flops_roll = Ks * (6.0 * tests + 60.0 * Ts)
-    tests_per_rollout = float(np.mean(tests))
-    flops_per_rollout = float(flops_roll.sum() / Ks.sum())
+    roll_ms = stage_ms["rollout"]
     achieved = float(flops_roll.sum()) / (roll_ms * 1e-3) / 1e12
-    pk, pk_kind = peaks()
     peak = alu_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2032.0))
+    launches_post = 2 if res["pipelined"] else 1
+    post_share = launches_post * post_ms
+    roll_share = roll_ms
+    roof_post = {"kernel": "k_post (prune + DBSCAN + selection + update)", "bound": "hbm",
+                 "achieved": post_gbs, "peak": hbm, "unit": "GB/s", "frac": post_gbs / hbm,
+                 "traffic": POST_NCU_TRAFFIC, "peak_kind": f"copy bandwidth ({pk_kind})",
+                 "ms_per_launch": post_ms, "algorithmic_bytes_per_launch": post_bytes,
+                 "bytes_per_rollout": POST_BYTES_PER_ROLLOUT[p_dim],
+                 "note": "latency-bound: chains of dependent L2 accesses between cluster "
+                         "barriers, far below the bandwidth bound"}
+    roof_roll = {"kernel": "k_rollout_arm" if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12)
+                 else "k_rollout2d<unicycle>", "bound": "alu", "achieved": achieved,
+                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": ROLLOUT_NCU_TRAFFIC,
+                 "peak_kind": f"FP32 lanes x 2 x max SM clock ({pk_kind} clock)",
+                 "ms_per_launch": roll_ms,
+                 "flops_per_rollout": float(flops_roll.sum() / Ks.sum()),
+                 "obstacle_tests_per_rollout": float(np.mean(tests))}
+    dominant_post = post_share >= roll_share
 
-    # end to end through the public API with host buffers: per step, the
-    # observation windows go host -> device, the new nominals come back.
-    # All instances' observation windows live in one device buffer and all
-    # new nominals in another (the requests hold views), so a step moves its
-    # inputs in one host -> device copy from pinned memory (the windows of
-    # every episode packed per step) and its results in one copy back.
-    H = cfg0["hist_len"]
-    e2e_pl, e2e_req = [], []
-    hsz = [H * sc["radius"].shape[0] * p_dim for sc in scenes]
-    usz = [sc["cfg"]["T"] * m for sc in scenes]
-    hoff, uoff = np.concatenate([[0], np.cumsum(hsz)]), np.concatenate([[0], np.cumsum(usz)])
-    hist_all = torch.zeros(int(hoff[-1]), dtype=torch.float32, device=dev)
-    u_all = torch.zeros(int(uoff[-1]), dtype=torch.float32, device=dev)
-    for i, sc in enumerate(scenes):
-        pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+    # ---- end to end through the public API with host buffers: the batch
+    # entry point that takes packed host arrays (ce_mppi_batch_run_host) --
+    # per step the states and observation windows go in, the new nominals,
+    # next states and diagnostics come back, one copy each way inside the
+    # call; the loop is closed on the host (x0 <- x_next).
+    e2e_pl = [pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0]) for sc in scenes]
+    for pl, sc in zip(e2e_pl, scenes):
         pl.set_nominal(u_init(sc))
-        n_o = sc["radius"].shape[0]
-        e2e_req.append(dict(
-            x0=torch.tensor(sc["x0"], dtype=torch.float32, device=dev),
-            hist=hist_all[hoff[i]:hoff[i + 1]].view(H, n_o, p_dim),
-            radius=torch.tensor(sc["radius"], dtype=torch.float32, device=dev),
-            u_out=u_all[uoff[i]:uoff[i + 1]].view(sc["cfg"]["T"], m)))
-        e2e_req[-1]["x_next"] = e2e_req[-1]["x0"]
-        e2e_pl.append(pl)
-    e2e_batch = pkg.Batch(e2e_pl, e2e_req, stream=stream, use_graph=True,
-                          n_branches=args.branches)
-    n_e2e = min(args.steps, EPISODE)
-    n_w = n_e2e + 3
-    host_obs = torch.zeros((n_w, int(hoff[-1])), dtype=torch.float32).pin_memory()
-    for r in range(n_w):
-        host_obs[r] = torch.from_numpy(np.concatenate(
-            [np.asarray(sc["obs"][r:r + H], np.float32).ravel() for sc in scenes]))
-    host_u = torch.zeros(int(uoff[-1]), dtype=torch.float32).pin_memory()
-    h2d = int(hoff[-1]) * 4
-    d2h = int(uoff[-1]) * 4
+    n_obs_l = [sc["radius"].shape[0] for sc in scenes]
+    hb = pkg.HostBatch(e2e_pl, n_obs_l, stream=stream, use_graph=True, n_branches=args.branches)
+    H = cfg0["hist_len"]
+    n_e2e = max(1, min(args.e2e_steps, episode))
+    windows = [np.concatenate([np.asarray(sc["obs"][r:r + H], np.float32).ravel()
+                               for sc in scenes]) for r in range(n_e2e + 3)]
+    radii = np.concatenate([sc["radius"] for sc in scenes]).astype(np.float32)
+    x_host = np.concatenate([sc["x0"] for sc in scenes]).astype(np.float32)
+    u_host = np.empty(hb.u_size, np.float32)
+    xn_host = np.empty(hb.x_size, np.float32)
 
-    def e2e_step(r):
-        hist_all.copy_(host_obs[r], non_blocking=True)
-        e2e_batch.run()
-        host_u.copy_(u_all, non_blocking=True)
-        stream.synchronize()
+    def al16(v):
+        return (v + 15) // 16 * 16
 
-    for r in range(min(args.warmup, 3)):
-        e2e_step(r)
+    h2d = sum(al16(4 * (n_dim + H * no * p_dim + no)) for no in n_obs_l)
+    d2h = sum(al16(4 * (sc["cfg"]["T"] * m + n_dim)) + al16(80) for sc in scenes)
+    for r in range(3):
+        hb.run(x_host, windows[r], radii, u_host, xn_host)
+        x_host, xn_host = xn_host, x_host
     t0 = time.perf_counter()
     for r in range(n_e2e):
-        e2e_step(r)
+        hb.run(x_host, windows[r + 3], radii, u_host, xn_host)
+        x_host, xn_host = xn_host, x_host
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * units_per_step * n_e2e / e2e_s
+    e2e_value = world * res["units_per_step"] * n_e2e / e2e_s
 
-    # plain form: one instance per launch chain, blocking host-buffer call
+    # ---- plain form: one instance per launch chain, blocking host-buffer call
     plain_pl = [pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0]) for sc in scenes]
     for pl, sc in zip(plain_pl, scenes):
         pl.set_nominal(u_init(sc))
@@ -730,69 +850,80 @@ def main() -> None:
             plain_pl[i].replan(sc["x0"], W.history(sc, r), sc["radius"])
             lat.append(time.perf_counter() - t1)
     t_plain = time.perf_counter() - t_plain
-    lat = np.array(lat[N_INST:]) * 1e3  # first round is warm-up
+    lat = np.array(lat[n_inst:]) * 1e3  # first round is warm-up
     plain = {"replans_per_s": 1e3 / float(lat.mean()), "p50_ms": float(np.percentile(lat, 50)),
              "p99_ms": float(np.percentile(lat, 99)),
-             "rollout_steps_per_s": units_per_step * args.plain_steps / t_plain}
+             "rollout_steps_per_s": res["units_per_step"] * args.plain_steps / t_plain}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(wl["config"], parallelism=f"replicas x{world}, instances sharded by rank",
-                       pipeline=args.pipeline, pipe_post_ctas=args.pipe_post_ctas,
-                       noise_regen=args.noise_regen,
-                       batch_config=(pipe[0].config() if pipe else batch.config())),
-        "replans_per_s": world * N_INST * args.steps / (tot_ms / 1e3),
+        "config": bench_config(args.workload, world, regen),
+        "run": {"pipeline": args.pipeline, "pipe_post_ctas": args.pipe_post_ctas,
+                "batch_config": res["batch_config"],
+                "l2": "flushed between timed steps (256 MB write)"},
+        "replans_per_s": res["replans_per_s"],
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)),
-                       "note": f"batched step: all {N_INST} replans complete"},
+                       "note": f"batched step: all {n_inst} replans complete"},
         "plain": plain,
         "stage_ms": stage_ms,
-        "modes_last_step": modes,
-        "roofline": {"kernel": "k_rollout_arm" if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12) else "k_rollout2d<unicycle>",
-                     "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": ROLLOUT_NCU.get(args.workload, {}).get("traffic"),
-                     "issue_active_ncu": ROLLOUT_NCU.get(args.workload, {}).get("issue_active"),
-                     "peak_kind": f"FP32 lanes x 2 x max SM clock ({pk_kind} clock)",
-                     "flops_per_rollout": flops_per_rollout,
-                     "obstacle_tests_per_rollout": tests_per_rollout},
-        "roofline_post": {"kernel": "k_post (prune + DBSCAN + selection + update)",
-                          "bound": "hbm", "achieved": post_bytes / (post_ms * 1e-3) / 1e9,
-                          "peak": pk.get("hbm_gbs", 6400.0), "unit": "GB/s",
-                          "frac": post_bytes / (post_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6400.0),
-                          "ms_per_launch": post_ms, "algorithmic_bytes": post_bytes,
-                          "note": "latency-bound (dependent L2 accesses between cluster "
-                                  "barriers), far below the bandwidth bound"},
+        "modes_last_step": res["modes_last_step"],
+        "roofline": roof_post if dominant_post else roof_roll,
+        ("roofline_rollout" if dominant_post else "roofline_post"):
+            roof_roll if dominant_post else roof_post,
+        "device_time_share_ms_per_step": {"k_post": post_share, "k_rollout": roll_share},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "api": "ce_mppi_batch_run_host (packed host buffers, one copy each way, "
+                       "graph replay, host-side closed loop)", "steps": n_e2e},
         # kernels per replan chain: tracks, rollouts, the fused clustering +
         # update kernel (+ the tiled update for the arms); per step two half
         # chains (pipelined) or one chain per branch (the L2 flush is torch's)
         "gpu_launches": (4 if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12) else 3)
-                        * (2 if pipe else batch.config()["n_branches"]) * args.steps,
-        "clocks": clk,
+                        * (2 if res["pipelined"] else res["batch_config"]["n_branches"])
+                        * args.steps,
     }
     if stamps is not None:
         line["post_stamps_cycles"] = stamps
+    for obj in objs + [hb] + planners + e2e_pl + plain_pl:
+        obj.close()
+    # ---- the arm (config 3) and the uneven batch (config 4), measured
+    # briefly beside the main workload (device-resident, graph, pipelined)
+    if rank == 0 and not args.no_extra and args.workload == "unicycle":
+        extra = {}
+        for name in ("arm", "batch"):
+            r2, objs2, pls2, _, _, _, _, _ = run_workload(
+                pkg, torch, args, name, dev, stream, 0, 1, None, args.extra_steps, 3, flush,
+                profile=False)
+            extra[name] = {"config": bench_config(name, 1, r2["regen"]), "value": r2["value"],
+                           "unit": UNIT, "replans_per_s": r2["replans_per_s"],
+                           "ms_per_step": r2["tot_ms"] / args.extra_steps,
+                           "steps": args.extra_steps,
+                           "latency_ms": {"p50": float(np.percentile(r2["step_ms"], 50)),
+                                          "p99": float(np.percentile(r2["step_ms"], 99))},
+                           "modes_last_step": r2["modes_last_step"]}
+            for obj in objs2 + pls2:
+                obj.close()
+        line["extra_workloads"] = extra
     if rank == 0 and args.serve_seconds > 0 and args.workload == "unicycle":
-        line["served"] = run_serve(pkg, args.serve_seconds, args.serve_budget_gb)
+        line["served"] = run_serve(pkg, args.serve_seconds, args.serve_budget_gb,
+                                   warmup_s=args.serve_warmup)
         line["served"]["plain_mix"] = plain_mix_latency(pkg)
         # the plain form under the same offered load: the same server with one
         # instance per launch chain and one stream (a session's queued request
         # is still replaced by its newer one, which bounds the queue)
         line["served"]["plain_same_load"] = run_serve(pkg, min(args.serve_seconds, 5.0),
                                                       args.serve_budget_gb, max_batch=1,
-                                                      n_streams=1)
+                                                      n_streams=1, warmup_s=0.0)
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
         line["cpu_baseline"] = cpu_baseline(scenes, u_init, max_threads=16)
+    line["clocks"] = clocks.stop()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for obj in [batch, e2e_batch] + (list(pipe[:2]) if pipe else []) + planners + e2e_pl + plain_pl:
-        obj.close()
     if dist:
         dist.destroy_process_group()
 

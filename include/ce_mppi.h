@@ -230,6 +230,26 @@ ce_status_t ce_mppi_batch_config(const ce_mppi_batch* b, int* n_branches, int* p
 ce_status_t ce_mppi_batch_set_post_ctas(ce_mppi_batch* b, int post_ctas);
 /* Queue one replan of every instance of the batch; returns without waiting.  */
 ce_status_t ce_mppi_batch_run(ce_mppi_batch* b);
+/* A batch fed from host buffers (the counterpart of ce_mppi_replan for many
+ * planners): as ce_mppi_batch_create, but the requests are the batch's own --
+ * one device staging block (inputs, then outputs) mirrored in pinned host
+ * memory, owned and freed by the batch.  n_obs[i] fixes instance i's obstacle
+ * count (0 .. its n_obs_max).  Errors: INVALID_ARG, NO_MEMORY, CUDA.          */
+ce_status_t ce_mppi_batch_create_host(ce_mppi_handle* const* hs, const int* n_obs, int n,
+                                      void* stream, int use_graph, int n_branches,
+                                      ce_mppi_batch** out);
+/* One replan of every instance of a host-buffer batch, blocking: the inputs
+ * of instance i follow those of instance i-1 in x0s ([n] each), hists
+ * ([H][n_obs[i]][p] each) and radii ([n_obs[i]] each); they are checked as by
+ * ce_mppi_check_inputs, packed and copied in one transfer; the batch runs as
+ * ce_mppi_batch_run; the updated nominals (u_outs, [T][m] each), the next
+ * states (x_nexts, [n] each, nullable) and the diagnostics (diags, nullable)
+ * come back in one transfer.  Afterwards every handle's nominal is shifted and
+ * its counter advanced.  Errors: INVALID_ARG (not a host-buffer batch, a
+ * refused input: nothing launched), CUDA, TIMEOUT.                            */
+ce_status_t ce_mppi_batch_run_host(ce_mppi_batch* b, const float* x0s, const float* hists,
+                                   const float* radii, float* u_outs, float* x_nexts,
+                                   ce_mppi_diag* diags);
 /* Queue one half of a replan of every instance, without a graph, on stream (a
  * cudaStream_t; NULL: the batch's stream): part 0 = obstacle tracks and the
  * rollouts (Algorithm 1 [Rollouts]); part 1 = pruning, reference point,

@@ -74,6 +74,7 @@ EXPORTS = (
     "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_check_inputs",
     "ce_mppi_replan_dev",
     "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_config",
+    "ce_mppi_batch_create_host", "ce_mppi_batch_run_host",
     "ce_mppi_batch_set_post_ctas", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
     "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
@@ -107,6 +108,8 @@ def lib() -> C.CDLL:
         L.ce_mppi_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Request), i, vp, i, i,
                                            C.POINTER(vp)]
         L.ce_mppi_batch_run.argtypes = [vp]
+        L.ce_mppi_batch_create_host.argtypes = [C.POINTER(vp), vp, i, vp, i, i, C.POINTER(vp)]
+        L.ce_mppi_batch_run_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.ce_mppi_batch_run_part.argtypes = [vp, i, vp]
         L.ce_mppi_batch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
         L.ce_mppi_batch_set_post_ctas.argtypes = [vp, i]
@@ -314,6 +317,52 @@ class Batch:
         ms = (C.c_float * 6)()
         _check(lib().ce_mppi_batch_profile(self.b, ms))
         return dict(zip(self.STAGES, list(ms)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().ce_mppi_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostBatch:
+    """Planners replanned together from host buffers (one packed copy each way
+    per replan, inside the library): run(x0s, hists, radii) with packed numpy
+    float32 arrays returns (u_outs, x_nexts) packed the same way."""
+
+    def __init__(self, planners, n_obs, stream=None, use_graph=True, n_branches=1):
+        n = len(planners)
+        self.planners = planners
+        self.stream = _stream_ptr(stream)
+        hs = (C.c_void_p * n)(*[pl.h.value for pl in planners])
+        self.n_obs = np.ascontiguousarray(n_obs, dtype=np.int32)
+        b = C.c_void_p()
+        _check(lib().ce_mppi_batch_create_host(hs, self.n_obs.ctypes.data, n,
+                                               C.c_void_p(self.stream), int(use_graph),
+                                               int(n_branches), C.byref(b)))
+        self.b = b
+        self.u_size = sum(pl.T * pl.m for pl in planners)
+        self.x_size = sum(pl.n for pl in planners)
+        self.diags = (Diag * n)()
+
+    def run(self, x0s, hists, radii, u_out=None, x_next=None):
+        x0s = np.ascontiguousarray(x0s, dtype=np.float32)
+        hists = np.ascontiguousarray(hists, dtype=np.float32)
+        radii = np.ascontiguousarray(radii, dtype=np.float32)
+        u = np.empty(self.u_size, np.float32) if u_out is None else u_out
+        x = np.empty(self.x_size, np.float32) if x_next is None else x_next
+        _check(lib().ce_mppi_batch_run_host(self.b, x0s.ctypes.data, hists.ctypes.data,
+                                            radii.ctypes.data, u.ctypes.data, x.ctypes.data,
+                                            C.cast(self.diags, C.c_void_p)))
+        return u, x
+
+    def diag(self, i: int) -> dict:
+        return self.diags[i].as_dict()
 
     def close(self):
         if getattr(self, "b", None):

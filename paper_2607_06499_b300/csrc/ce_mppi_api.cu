@@ -151,12 +151,11 @@ void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const 
   a.tprefix = pre_roll;
   a.n_tiles = n_roll;
   launch_rollout(dyn, a, smem_roll, s);
-  // The fused kernel applies the update; a dense one (many nonzero weights,
-  // usual for the arms' small costs) only for 2-D robots -- for the arms the
-  // tiled update kernel follows, which then skips sparse replans already done.
-  a.post_dense = !is_arm(dyn);
+  // The fused kernel applies the update when few weights are nonzero; a dense
+  // one (many nonzero weights: the arms' small costs, a no-collision replan
+  // with close costs) is left to the tiled update kernel that follows over the
+  // whole GPU, which skips the replans already done.
   const bool fused = launch_post(a, max_cells, s);
-  if (fused && a.post_dense) return;
   if (!fused) {
     launch_prune(a, s);
     launch_dbscan(a, max_cells, s);
@@ -203,7 +202,7 @@ void tiles_of(const ce_mppi_handle* h, int inst, std::vector<int2>& roll, std::v
   // update tiles: (column block, rollout chunk) enumerated as kc * ncb + cb
   const int TM = h->P.T * h->m;
   const bool arm = is_arm(h->P.dyn);
-  const int cper = arm ? 32 : kUpdateWarps, kch = arm ? kUpdChunkArm : kUpdChunk2D;
+  const int cper = 32, kch = arm ? kUpdChunkArm : kUpdChunk2D;   // (as k_update)
   const int ncb = (TM + cper - 1) / cper, nkc = (h->P.K + kch - 1) / kch;
   for (int t = 0; t < ncb * nkc; ++t) upd.push_back(make_int2(inst, t));
 }
@@ -320,8 +319,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   const size_t o_trk = take(track_bytes(T, nobs) + 16);
   const size_t o_S = take(4 * Kp), o_w = take(4 * Kp), o_Sv = take(4 * Kp),
                o_cmin = take(4 * Kp), o_nzk = take(4 * kSparseMax), o_nze = take(4 * kSparseMax),
-               o_zpart = take(4 * kPruneRanges),
-               o_rpart = take(4 * (size_t)kPruneRanges * h->TMp);
+               o_zpart = take(4 * kPruneRanges);
   const size_t o_pN = take(4 * 3 * Kp), o_z = take(4 * 3 * Kp), o_g = take(4 * 3 * Kp),
                o_zs = take(4 * 3 * Kp);
   const size_t eps_elems = P->noise_regen ? 0
@@ -369,7 +367,6 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   d.nzk = reinterpret_cast<int*>(b + o_nzk);
   d.nze = reinterpret_cast<float*>(b + o_nze);
   d.zpart = reinterpret_cast<float*>(b + o_zpart);
-  d.rpart = reinterpret_cast<float*>(b + o_rpart);
   d.pN = reinterpret_cast<float*>(b + o_pN);
   d.z = reinterpret_cast<float*>(b + o_z);
   d.g = reinterpret_cast<float*>(b + o_g);
@@ -542,6 +539,8 @@ void free_batch(ce_mppi_batch* b) {
   cudaFree(b->dreq);
   cudaFree(b->dtiles_roll);
   cudaFree(b->dtiles_upd);
+  if (b->d_stage) cudaFree(b->d_stage);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
   delete b;
 }
 
@@ -879,18 +878,15 @@ ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
     a.n_tiles = b->n_roll;
     launch_rollout(b->dyn, a, b->smem_roll, s);
   } else {
-    a.post_dense = !is_arm(b->dyn);   // (as in a whole replan's chain)
-    const bool fused = launch_post(a, b->max_cells, s);
+    const bool fused = launch_post(a, b->max_cells, s);   // (as in a whole replan's chain)
     if (!fused) {
       launch_prune(a, s);
       launch_dbscan(a, b->max_cells, s);
       launch_select(a, s);
     }
-    if (!fused || !a.post_dense) {
-      a.tiles = b->dtiles_upd;
-      a.n_tiles = b->n_upd;
-      launch_update(a, s);
-    }
+    a.tiles = b->dtiles_upd;
+    a.n_tiles = b->n_upd;
+    launch_update(a, s);
   }
   CE_CUDA(cudaGetLastError());
   return CE_MPPI_OK;
@@ -938,6 +934,127 @@ ce_status_t ce_mppi_batch_destroy(ce_mppi_batch* b) {
   for (auto& br : b->branches)
     if (br.stream) cudaStreamSynchronize(br.stream);
   free_batch(b);
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_batch_create_host(ce_mppi_handle* const* hs, const int* n_obs, int n,
+                                      void* stream, int use_graph, int n_branches,
+                                      ce_mppi_batch** out) {
+  if (!out) return fail(CE_MPPI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!hs || !n_obs || n < 1) return fail(CE_MPPI_ERR_INVALID_ARG, "empty batch");
+  // staging layout per instance: inputs x0 [n], obs_hist [H][n_obs][p],
+  // obs_radius [n_obs]; outputs u_out [T][m], x_next [n], diag (16-byte aligned)
+  std::vector<size_t> in_off(n), out_off(n);
+  size_t in_b = 0, out_b = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL handle in batch");
+    const ce_mppi_handle* h = hs[i];
+    if (n_obs[i] < 0 || n_obs[i] > h->P.n_obs_max)
+      return fail(CE_MPPI_ERR_INVALID_ARG, "n_obs must be in [0, n_obs_max]");
+    in_off[i] = in_b;
+    in_b += align_up(4 * ((size_t)h->n + (size_t)h->P.hist_len * n_obs[i] * h->p + n_obs[i]), 16);
+    out_off[i] = out_b;
+    out_b += align_up(4 * ((size_t)h->P.T * h->m + h->n), 16) + align_up(sizeof(ce_mppi_diag), 16);
+  }
+  unsigned char* d_stage = nullptr;
+  unsigned char* h_stage = nullptr;
+  cudaError_t e = cudaMalloc(&d_stage, in_b + out_b);
+  if (e != cudaSuccess) return fail(CE_MPPI_ERR_NO_MEMORY, "device allocation failed");
+  e = cudaHostAlloc((void**)&h_stage, in_b + out_b, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaFree(d_stage);
+    return fail(CE_MPPI_ERR_NO_MEMORY, "pinned host allocation failed");
+  }
+  std::memset(h_stage, 0, in_b + out_b);
+  std::vector<ce_mppi_request> reqs(n);
+  for (int i = 0; i < n; ++i) {
+    const ce_mppi_handle* h = hs[i];
+    float* in = reinterpret_cast<float*>(d_stage + in_off[i]);
+    float* o = reinterpret_cast<float*>(d_stage + in_b + out_off[i]);
+    std::memset(&reqs[i], 0, sizeof(ce_mppi_request));
+    reqs[i].x0 = in;
+    reqs[i].obs_hist = in + h->n;
+    reqs[i].obs_radius = in + h->n + (size_t)h->P.hist_len * n_obs[i] * h->p;
+    reqs[i].n_obs = n_obs[i];
+    reqs[i].u_out = o;
+    reqs[i].x_next = o + (size_t)h->P.T * h->m;
+    reqs[i].diag = reinterpret_cast<ce_mppi_diag*>(
+        d_stage + in_b + out_off[i] + align_up(4 * ((size_t)h->P.T * h->m + h->n), 16));
+  }
+  // (the staging holds valid zeros: the tuner's trial replans read them)
+  if ((e = cudaMemset(d_stage, 0, in_b + out_b)) != cudaSuccess) {
+    cudaFree(d_stage);
+    cudaFreeHost(h_stage);
+    return cuda_fail(e, "staging set-up");
+  }
+  ce_status_t st = ce_mppi_batch_create(hs, reqs.data(), n, stream, use_graph, n_branches, out);
+  if (st != CE_MPPI_OK) {
+    cudaFree(d_stage);
+    cudaFreeHost(h_stage);
+    return st;
+  }
+  ce_mppi_batch* b = *out;
+  b->d_stage = d_stage;
+  b->h_stage = h_stage;
+  b->in_bytes = in_b;
+  b->out_bytes = out_b;
+  b->n_obs.assign(n_obs, n_obs + n);
+  b->in_off = in_off;
+  b->out_off = out_off;
+  return CE_MPPI_OK;
+}
+
+ce_status_t ce_mppi_batch_run_host(ce_mppi_batch* b, const float* x0s, const float* hists,
+                                   const float* radii, float* u_outs, float* x_nexts,
+                                   ce_mppi_diag* diags) {
+  if (!b || !b->h_stage) return fail(CE_MPPI_ERR_INVALID_ARG, "not a host-buffer batch");
+  const int n = (int)b->hs.size();
+  if (!x0s || !u_outs) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL argument");
+  // inputs: checked (as ce_mppi_check_inputs), then packed into the pinned block
+  size_t ox = 0, oh = 0, orr = 0;
+  for (int i = 0; i < n; ++i) {
+    const ce_mppi_handle* h = b->hs[i];
+    const int no = b->n_obs[i];
+    const size_t nh = (size_t)h->P.hist_len * no * h->p;
+    ce_status_t st = check_host_inputs(h, x0s + ox, no > 0 ? hists + oh : nullptr,
+                                       no > 0 ? radii + orr : nullptr, no);
+    if (st != CE_MPPI_OK) return st;
+    float* in = reinterpret_cast<float*>(b->h_stage + b->in_off[i]);
+    std::memcpy(in, x0s + ox, 4 * (size_t)h->n);
+    if (no > 0) {
+      std::memcpy(in + h->n, hists + oh, 4 * nh);
+      std::memcpy(in + h->n + nh, radii + orr, 4 * (size_t)no);
+    }
+    ox += h->n;
+    oh += nh;
+    orr += no;
+  }
+  // one copy in, the batch's launches (or graph), one copy out
+  CE_CUDA(cudaMemcpyAsync(b->d_stage, b->h_stage, b->in_bytes, cudaMemcpyHostToDevice, b->stream));
+  ce_status_t st = ce_mppi_batch_run(b);
+  if (st != CE_MPPI_OK) return st;
+  CE_CUDA(cudaMemcpyAsync(b->h_stage + b->in_bytes, b->d_stage + b->in_bytes, b->out_bytes,
+                          cudaMemcpyDeviceToHost, b->stream));
+  CE_CUDA(cudaStreamSynchronize(b->stream));
+  size_t ou = 0, on = 0;
+  int bad = 0;
+  for (int i = 0; i < n; ++i) {
+    const ce_mppi_handle* h = b->hs[i];
+    const size_t TM = (size_t)h->P.T * h->m;
+    const float* o = reinterpret_cast<const float*>(b->h_stage + b->in_bytes + b->out_off[i]);
+    std::memcpy(u_outs + ou, o, 4 * TM);
+    if (x_nexts) std::memcpy(x_nexts + on, o + TM, 4 * (size_t)h->n);
+    ce_mppi_diag dg;
+    std::memcpy(&dg, b->h_stage + b->in_bytes + b->out_off[i] + align_up(4 * (TM + h->n), 16),
+                sizeof(dg));
+    if (diags) diags[i] = dg;
+    if (dg.status != 0 && !bad) bad = dg.status;
+    ou += TM;
+    on += h->n;
+  }
+  if (bad == CE_MPPI_ERR_TIMEOUT) return fail(CE_MPPI_ERR_TIMEOUT, "device-side bounded wait gave up");
+  if (bad) return fail((ce_status_t)bad, "input refused on the device");
   return CE_MPPI_OK;
 }
 

@@ -52,6 +52,13 @@ struct ce_mppi_batch {
   std::vector<Branch> branches;
   cudaEvent_t fork = nullptr;
   int post_ctas = 0;   // CTAs per instance of the fused kernel (0: occupancy fit)
+  // host-buffer batches (ce_mppi_batch_create_host): the requests point into
+  // one device staging block, inputs then outputs, mirrored in pinned memory
+  unsigned char* h_stage = nullptr;
+  unsigned char* d_stage = nullptr;
+  size_t in_bytes = 0, out_bytes = 0;
+  std::vector<int> n_obs;                  // per instance
+  std::vector<size_t> in_off, out_off;     // per instance, in the staging block
 };
 
 

@@ -13,8 +13,8 @@ constexpr int kMaxM = 6;
 constexpr int kRolloutThreads = 128;    // 2-D rollouts: one rollout per thread
 constexpr int kArmWarps = 8;            // arm rollouts: one warp per rollout
 constexpr int kBlock = 1024;            // per-instance CTAs (prune, DBSCAN, select)
-constexpr int kUpdateWarps = 8;         // update CTA: one warp per column
-constexpr int kUpdChunk2D = 4096;       // rollouts per update tile (2-D layout)
+constexpr int kUpdateWarps = 8;         // update CTA: 8 warps, 32 columns per tile
+constexpr int kUpdChunk2D = 1024;       // rollouts per update tile (2-D layout)
 constexpr int kUpdChunkArm = 512;       // rollouts per update tile (arm layout)
 constexpr int kMaxCells = 8192;         // DBSCAN grid cells (cell -> occupied map in smem)
 constexpr int kMaxOcc = 2048;           // DBSCAN occupied cells held in shared memory
@@ -67,7 +67,6 @@ struct InstDesc {
   float4* tracks;
   float *S, *w_k, *pN, *eps, *z, *g, *zs, *Sv, *cmin, *nze;
   float* zpart;  // [kPruneRanges] range partials of the softmin normaliser
-  float* rpart;  // [kPruneRanges][TMp] range partials of the dense update (fused kernel)
   int* nzk;
   float* upart;  // [ceil(K/512)][TMp] partial sums of the update tiles
   int TMp;       // T*m rounded up to a multiple of 4
@@ -110,7 +109,6 @@ struct KArgs {
   int n_inst;
   int n_tiles;
   int n_conc;   // instances whose per-instance stages run at the same time (sizes clusters)
-  int post_dense;   // the fused kernel also applies a dense update (else k_update follows)
   int post_ctas;    // CTAs per instance of the fused kernel (0: from the occupancy fit)
 };
 

@@ -211,7 +211,7 @@ struct ce_mppi_server {
       slots[i] = f.members[i];
       const int per = is_arm(dyn) ? kArmWarps : kRolloutThreads;
       const int TM = h->P.T * h->m;
-      const int cper = is_arm(dyn) ? 32 : kUpdateWarps;
+      const int cper = 32;   // (columns per update tile, as k_update)
       const int kch = is_arm(dyn) ? kUpdChunkArm : kUpdChunk2D;
       pre_roll[i + 1] = pre_roll[i] + (h->P.K + per - 1) / per;
       pre_upd[i + 1] = pre_upd[i] + ((TM + cper - 1) / cper) * ((h->P.K + kch - 1) / kch);

@@ -1921,79 +1921,6 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   if (tid == 0 && lnz) atomicAdd(&ctl->nnz_all, lnz);
   cluster.sync();   // the list, the range partials and the nonzero count are complete
   if (fused && tid == 0 && rank == 0) ctl->dbcyc[12] = clock64();   // (stage clock stamp)
-  if (fused && a.post_dense && __ldcg(&ctl->nnz_all) > kSparseMax) {
-    // dense update by every CTA: per fixed rollout range and column, the
-    // weighted eps' sum (Kahan, lanes in k order, fixed trees), into rpart;
-    // rank 0 adds the ranges in order below
-    const int TM = d.T * d.m, TMp = d.TMp;
-    const bool arm = is_arm(d.dyn), regen = d.regen;
-    const unsigned long long ctr = *d.counter;
-    const int Lk = (((K + kPruneRanges - 1) / kPruneRanges) + 31) & ~31;
-    const int m_k = kPruneRanges / (CL * nw);
-    for (int j = 0; j < m_k; ++j) {
-      const int v = (rank * nw + wid) * m_k + j;
-      const int kb = min(K, v * Lk), ke = min(K, kb + Lk);
-      auto val = [&](int k, int c) {
-        return regen ? eps_regen(d, ctr, k, c)
-                     : d.eps[arm ? (size_t)k * d.eps_ld_k + c : (size_t)c * d.eps_ld_c + k];
-      };
-      if (!arm) {
-        // lanes over k, four columns at a time (independent loads in flight;
-        // drawn again: the four columns are one Philox block)
-        for (int c0 = 0; c0 < TM; c0 += 4) {
-          float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int k = kb + lane; k < ke; k += 32) {
-            const float wk = d.w_k[k];
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (regen) {
-              if (wk != 0.f) eps_regen4(d, ctr, k, c0 >> 2, TM, x);
-            } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) x[q] = (wk != 0.f && c0 + q < TM) ? val(k, c0 + q) : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk * x[q]);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float t = warp_sum(s[q]);
-            if (lane == 0 && c0 + q < TM) d.rpart[(size_t)v * TMp + c0 + q] = t;
-          }
-        }
-      } else {
-        // lanes over columns, up to six 32-column chunks per pass (one row of
-        // eps' per k), k in steps of two: 12 independent loads in flight
-        constexpr int kCh = 6;
-        for (int cp = 0; cp < TM; cp += 32 * kCh) {
-          float s[kCh], e[kCh];
-#pragma unroll
-          for (int q = 0; q < kCh; ++q) s[q] = e[q] = 0.f;
-          for (int k = kb; k < ke; k += 2) {
-            float wk[2], x[2][kCh];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              wk[u] = k + u < ke ? d.w_k[k + u] : 0.f;
-#pragma unroll
-              for (int q = 0; q < kCh; ++q) {
-                const int c = cp + q * 32 + lane;
-                x[u][q] = (wk[u] != 0.f && c < TM) ? val(k + u, c) : 0.f;
-              }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-              for (int q = 0; q < kCh; ++q) kahan_add(s[q], e[q], wk[u] * x[u][q]);
-          }
-#pragma unroll
-          for (int q = 0; q < kCh; ++q) {
-            const int c = cp + q * 32 + lane;
-            if (c < TM) d.rpart[(size_t)v * TMp + c] = s[q];
-          }
-        }
-      }
-    }
-    cluster.sync();   // every range's partials are written
-  }
   if (rank != 0) return;
   if (fused && tid == 0) ctl->dbcyc[13] = clock64();
   // rank 0: Z in range order, the list by ascending k, the control block
@@ -2028,20 +1955,8 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   }
   if (fused) {
     __syncthreads();
-    if (nl <= kSparseMax) {
-      update_sparse_finalize(a, d, inst);
-    } else if (a.post_dense) {
-      const int TM = d.T * d.m, TMp = d.TMp;
-      const float iz = 1.0f / red[32];
-      for (int c = tid; c < TM; c += blockDim.x) {
-        float t = 0.f;
-        for (int v = 0; v < kPruneRanges; ++v) t += __ldcg(d.rpart + (size_t)v * TMp + c);
-        d.Unew[c] = d.U[c] + t * iz;
-      }
-      __syncthreads();
-      finalize(d, req_of(a, inst));
-      if (tid == 0) ctl->updated = 1;
-    }
+    // (a dense update is left to the tiled update kernel over the whole GPU)
+    if (nl <= kSparseMax) update_sparse_finalize(a, d, inst);
     if (tid == 0) ctl->dbcyc[14] = clock64();
   }
 }
@@ -2243,7 +2158,7 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   const int K = d.K, TM = d.T * d.m;
   const bool arm = is_arm(d.dyn);
   const int kch = arm ? kUpdChunkArm : kUpdChunk2D;
-  const int cper = arm ? 32 : kUpdateWarps;
+  const int cper = 32;   // columns per tile (2-D: four per warp; arm: one per lane)
   const int ncb = (TM + cper - 1) / cper;
   const int cb = tile.y % ncb, kc = tile.y / ncb;
   const int c0 = cb * cper, k0 = kc * kch, k1 = min(K, k0 + kch);
@@ -2256,18 +2171,29 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
     // few nonzero weights, listed by ascending k: the tiles of the first
     // rollout chunk sum over the list, the others contribute zeros
     if (!arm) {
-      const int c = c0 + wid;
-      if (c < TM) {
-        float s = 0.f, e = 0.f;
-        if (kc == 0) {
-          const float* col = d.regen ? nullptr : eps + (size_t)c * d.eps_ld_c;
+      // warp wid: the four columns of one Philox block, lanes over the list
+      const int cw = c0 + 4 * wid;
+      if (cw < TM) {
+        float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+        if (kc == 0)
           for (int j = lane; j < nnz; j += 32) {
             const int k = d.nzk[j];
-            kahan_add(s, e, d.nze[j] * (col ? col[k] : eps_regen(d, ctr, k, c)));
+            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            if (regen) {
+              eps_regen4(d, ctr, k, cw >> 2, TM, x);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (cw + q < TM) x[q] = eps[(size_t)(cw + q) * d.eps_ld_c + k];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], d.nze[j] * x[q]);
           }
-          s = warp_sum(s);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float t = warp_sum(s[q]);
+          if (lane == 0 && cw + q < TM) d.upart[(size_t)kc * d.TMp + cw + q] = t;
         }
-        if (lane == 0) d.upart[(size_t)kc * d.TMp + c] = s;
       }
     } else {
       const int c = c0 + lane;
@@ -2287,45 +2213,34 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
       }
     }
   } else if (!arm) {
-    const int c = c0 + wid;
-    if (c < TM) {
-      const float* col = eps + (size_t)c * d.eps_ld_c;
+    // dense: warp wid takes the four columns of one Philox block, lanes the
+    // tile's rollouts (k in steps of 32, Kahan per column); eps' is read (or
+    // drawn again, one Philox block for the four columns) only where the
+    // weight is nonzero -- with the least cost subtracted, exp underflows to
+    // exactly 0 for most rollouts at small lambda, and adding 0 keeps the
+    // sums' bits as if they were read.  The same order either way.
+    const int cw = c0 + 4 * wid;
+    if (cw < TM) {
       float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
-      int k = k0 + lane;
-      // eps' is read only where the weight is nonzero: with the minimum
-      // subtracted, exp underflows to exactly 0 for most rollouts at small
-      // lambda, and their sectors are never fetched (adding 0 keeps the sums'
-      // bits as if they were).
-      // eps' stored, or drawn again (same order of the sums either way)
-      if (!regen) {
-        for (; k + 96 < k1; k += 128) {
-          float wk[4];
+      for (int k = k0 + lane; k < k1; k += 32) {
+        const float wk = w[k];
+        if (wk == 0.f) continue;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (regen) {
+          eps_regen4(d, ctr, k, cw >> 2, TM, x);
+        } else {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) wk[u] = w[k + 32 * u];
+          for (int q = 0; q < 4; ++q)
+            if (cw + q < TM) x[q] = eps[(size_t)(cw + q) * d.eps_ld_c + k];
+        }
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            kahan_add(s[u], e[u], wk[u] != 0.f ? wk[u] * col[k + 32 * u] : 0.f);
-        }
-        for (; k < k1; k += 32) {
-          const float wk = w[k];
-          kahan_add(s[0], e[0], wk != 0.f ? wk * col[k] : 0.f);
-        }
-      } else {
-        for (; k + 96 < k1; k += 128) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float wk = w[k + 32 * u];
-            kahan_add(s[u], e[u], wk != 0.f ? wk * eps_regen(d, ctr, k + 32 * u, c) : 0.f);
-          }
-        }
-        for (; k < k1; k += 32) {
-          const float wk = w[k];
-          kahan_add(s[0], e[0], wk != 0.f ? wk * eps_regen(d, ctr, k, c) : 0.f);
-        }
+        for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk * x[q]);
       }
-      float t = (s[0] + s[1]) + (s[2] + s[3]);
-      t = warp_sum(t);
-      if (lane == 0) d.upart[(size_t)kc * d.TMp + c] = t;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float t = warp_sum(s[q]);
+        if (lane == 0 && cw + q < TM) d.upart[(size_t)kc * d.TMp + cw + q] = t;
+      }
     }
   } else {
     const int c = c0 + lane;

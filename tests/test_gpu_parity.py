@@ -590,3 +590,43 @@ def test_union_find_limit_reports_timeout_and_falls_back():
     idxc = pl.peek("IDXC")[: dg[1]]
     assert np.all(w[idxc] == 0) and abs(w.sum() - 1) < 1e-5   # the fallback is over V
     pl.close()
+
+
+def test_host_buffer_batch_equals_single_host_replans():
+    """ce_mppi_batch_run_host (packed host inputs and outputs, one copy each
+    way) gives every instance the bits of its own ce_mppi_replan, over two
+    successive replans; a NaN input is refused before anything runs."""
+    scs = [W.make("batch_instance", seed=s, n_replans=3) for s in (3, 4, 5, 6)]
+    singles = []
+    for sc in scs:
+        pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+        pl.set_nominal(sc["U0"])
+        us = []
+        for r in range(2):
+            u, d = pl.replan(sc["x0"], W.history(sc, r), sc["radius"])
+            us.append(u)
+        singles.append(us)
+        pl.close()
+    pls = [pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0]) for sc in scs]
+    for pl, sc in zip(pls, scs):
+        pl.set_nominal(sc["U0"])
+    hb = pkg.HostBatch(pls, [sc["radius"].shape[0] for sc in scs], use_graph=True)
+    for r in range(2):
+        x0s = np.concatenate([sc["x0"] for sc in scs]).astype(np.float32)
+        hists = np.concatenate([W.history(sc, r).ravel() for sc in scs]).astype(np.float32)
+        radii = np.concatenate([sc["radius"] for sc in scs]).astype(np.float32)
+        u, x = hb.run(x0s, hists, radii)
+        off = 0
+        for i, sc in enumerate(scs):
+            TM = sc["cfg"]["T"] * 2
+            np.testing.assert_array_equal(u[off:off + TM].reshape(-1, 2), singles[i][r])
+            assert hb.diag(i)["status"] == 0 and hb.diag(i)["counter"] == r
+            off += TM
+    bad = x0s.copy()
+    bad[4] = np.nan
+    with pytest.raises(pkg.CeError):
+        hb.run(bad, hists, radii)
+    assert pls[0].get_counter() == 2
+    hb.close()
+    for pl in pls:
+        pl.close()
