@@ -332,7 +332,8 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   const size_t o_osum = take(sizeof(long long) * 4 * (size_t)std::max(nobs, 1));
   const size_t o_bbox = take(sizeof(float) * 6 * h->ncells);
   const size_t o_ang = take(sizeof(int) * 2 * kAngBuckets);
-  const size_t o_upart = take(sizeof(float) * (size_t)((K + kUpdChunkArm - 1) / kUpdChunkArm) * h->TMp);
+  const int kch_min = std::min(kUpdChunkArm, kUpdChunk2D);   // most rollout chunks of an update
+  const size_t o_upart = take(sizeof(float) * (size_t)((K + kch_min - 1) / kch_min) * h->TMp);
   // host-path staging: inputs then outputs
   const size_t in_x0 = 0, in_hist = align_up(4 * n, 16),
                in_rad = align_up(in_hist + 4 * (size_t)H * nobs * p, 16),

@@ -11,11 +11,14 @@ namespace cem {
 
 constexpr int kMaxM = 6;
 constexpr int kRolloutThreads = 128;    // 2-D rollouts: one rollout per thread
+constexpr int kRolloutMinCtas = 6;      // 2-D rollouts: CTAs per SM the registers allow (80 a thread)
 constexpr int kArmWarps = 8;            // arm rollouts: one warp per rollout
 constexpr int kBlock = 1024;            // per-instance CTAs (prune, DBSCAN, select)
 constexpr int kUpdateWarps = 8;         // update CTA: 8 warps, 32 columns per tile
 constexpr int kUpdChunk2D = 1024;       // rollouts per update tile (2-D layout)
-constexpr int kUpdChunkArm = 512;       // rollouts per update tile (arm layout)
+constexpr int kUpdChunkArm = 1024;      // rollouts per update tile (arm layout)
+constexpr int kUpdUnroll = 4;           // stored eps': rollouts in flight per lane (2-D)
+constexpr int kUpdArmUnroll = 32;       // stored eps': rows in flight per warp (arm)
 constexpr int kMaxCells = 8192;         // DBSCAN grid cells (cell -> occupied map in smem)
 constexpr int kMaxOcc = 2048;           // DBSCAN occupied cells held in shared memory
 constexpr int kMaxObs = 4096;           // obstacle bitmap in shared memory

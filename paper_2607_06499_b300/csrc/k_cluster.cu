@@ -2075,11 +2075,13 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
   }
 }
 
-// 2-D layout eps[T*m][Kp]: tile = (8 columns, 4096 rollouts), one warp per
-// column with lanes over k (coalesced), four independent Kahan accumulators.
-// Arm layout eps[Kp][T*m]: tile = (32 columns, 512 rollouts), lanes over the
-// columns, warps over k.  Each tile writes its partial sums; the last tile of
-// the instance adds them in chunk order (deterministic) and finalizes.
+// The tiled update over the whole GPU (k_update).  2-D layout eps[T*m][Kp]:
+// tile = (32 columns, kUpdChunk2D rollouts), a warp per four columns (one
+// Philox block when eps' is drawn again) with lanes over k (coalesced).  Arm
+// layout eps[Kp][T*m]: tile = (32 columns, kUpdChunkArm rollouts), lanes over
+// the columns, each warp a contiguous block of rows.  Each tile writes its
+// partial sums; the last tile of the instance adds them in chunk order
+// (deterministic) and finalizes.
 // The fused per-instance kernel's update when at most kSparseMax weights are
 // nonzero (rank 0 of the cluster, all columns): U_new[c] = U[c] + (1/Z) sum_j
 // w_j eps'[c][k_j] over the list in ascending k (Kahan), then finalize.
@@ -2146,6 +2148,8 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
 
 __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   __shared__ float part[kUpdateWarps][32];
+  __shared__ float wtile[kUpdChunkArm];   // arm, eps' stored: the warps' lists of
+  __shared__ int rtile[kUpdChunkArm];     // nonzero weights and their rows
   __shared__ int last;
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
@@ -2222,19 +2226,38 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
     const int cw = c0 + 4 * wid;
     if (cw < TM) {
       float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int k = k0 + lane; k < k1; k += 32) {
-        const float wk = w[k];
-        if (wk == 0.f) continue;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        if (regen) {
+      if (regen) {
+        for (int k = k0 + lane; k < k1; k += 32) {
+          const float wk = w[k];
+          if (wk == 0.f) continue;
+          float x[4];
           eps_regen4(d, ctr, k, cw >> 2, TM, x);
-        } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (cw + q < TM) x[q] = eps[(size_t)(cw + q) * d.eps_ld_c + k];
+          for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk * x[q]);
         }
+      } else {
+        // kUpdUnroll rollouts per lane in flight: their weights, then the
+        // eps' of the nonzero ones, all loaded before the first add (the
+        // adds keep the order of the plain loop)
+        for (int kb = k0 + lane; kb < k1; kb += 32 * kUpdUnroll) {
+          float wk[kUpdUnroll], x[kUpdUnroll][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk * x[q]);
+          for (int u = 0; u < kUpdUnroll; ++u) {
+            const int k = kb + 32 * u;
+            wk[u] = k < k1 ? w[k] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < kUpdUnroll; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              x[u][q] = (wk[u] != 0.f && cw + q < TM)
+                            ? eps[(size_t)(cw + q) * d.eps_ld_c + kb + 32 * u] : 0.f;
+#pragma unroll
+          for (int u = 0; u < kUpdUnroll; ++u)
+            if (wk[u] != 0.f)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) kahan_add(s[q], e[q], wk[u] * x[u][q]);
+        }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -2245,16 +2268,61 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   } else {
     const int c = c0 + lane;
     float s = 0.f, e = 0.f;
-    if (c < TM && !regen)
-      for (int k = k0 + wid; k < k1; k += kUpdateWarps) {
-        const float wk = w[k];   // warp-uniform: rows of zero weight are skipped
-        if (wk != 0.f) kahan_add(s, e, wk * eps[(size_t)k * d.eps_ld_k + c]);
+    // warp wid takes the rows [k0 + wid R, k0 + (wid + 1) R) in order, lanes
+    // the columns; rows of zero weight are neither read (or drawn) nor added
+    constexpr int R = kUpdChunkArm / kUpdateWarps;
+    const int r0 = wid * R, r1 = min(r0 + R, k1 - k0);
+    if (!regen) {
+      // the warp's rows of nonzero weight listed in ascending order (weight,
+      // row) in its own segment of shared memory, padded with zero weights
+      // to a multiple of kUpdArmUnroll; then kUpdArmUnroll rows at a time,
+      // every load in bounds and issued before the first add (a padded entry
+      // reads a listed row and is not added: the adds are those of the plain
+      // loop over the nonzero rows)
+      float* wl = wtile + r0;
+      int* rl = rtile + r0;
+      int n = 0;
+      float wv[R / 32];   // the warp's weights, all loads in flight at once
+#pragma unroll
+      for (int j = 0; j < R / 32; ++j) {
+        const int r = r0 + 32 * j + lane;
+        wv[j] = r < r1 ? w[k0 + r] : 0.f;
       }
-    else if (c < TM)
-      for (int k = k0 + wid; k < k1; k += kUpdateWarps) {
-        const float wk = w[k];
-        if (wk != 0.f) kahan_add(s, e, wk * eps_regen(d, ctr, k, c));
+#pragma unroll
+      for (int j = 0; j < R / 32; ++j) {
+        const unsigned nz = __ballot_sync(FULL, wv[j] != 0.f);
+        if (wv[j] != 0.f) {
+          const int pos = n + __popc(nz & ((1u << lane) - 1u));
+          wl[pos] = wv[j];
+          rl[pos] = r0 + 32 * j + lane;
+        }
+        n += __popc(nz);
       }
+      __syncwarp();
+      const int npad = (n + kUpdArmUnroll - 1) / kUpdArmUnroll * kUpdArmUnroll;
+      for (int i = n + lane; i < npad; i += 32) {
+        wl[i] = 0.f;
+        rl[i] = rl[0];
+      }
+      __syncwarp();
+      const int cc = min(c, TM - 1);
+      for (int i = 0; i < npad; i += kUpdArmUnroll) {
+        float x[kUpdArmUnroll];
+#pragma unroll
+        for (int u = 0; u < kUpdArmUnroll; ++u)
+          x[u] = eps[(size_t)(k0 + rl[i + u]) * d.eps_ld_k + cc];
+#pragma unroll
+        for (int u = 0; u < kUpdArmUnroll; ++u) {
+          const float wk = wl[i + u];
+          if (wk != 0.f) kahan_add(s, e, wk * x[u]);
+        }
+      }
+    } else if (c < TM) {
+      for (int r = r0; r < r1; ++r) {
+        const float wk = w[k0 + r];   // warp-uniform
+        if (wk != 0.f) kahan_add(s, e, wk * eps_regen(d, ctr, k0 + r, c));
+      }
+    }
     part[wid][lane] = s;
     __syncthreads();
     if (wid == 0 && c < TM) {

@@ -197,7 +197,7 @@ __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float
 // arrives by one bulk copy; a larger one is staged in runs of whole rows,
 // each run by one bulk copy, the CTA advancing the horizon run by run.
 template <int DYN>
-__global__ void __launch_bounds__(kRolloutThreads, 8) k_rollout2d(KArgs a) {
+__global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   __shared__ int whole;

@@ -549,11 +549,23 @@ def test_task_level_scenarios_run():
     """Short closed-loop runs of both methods on both scenes (a smoke test of
     the task-level runner: counts are in range, the robots move)."""
     from paper_2607_06499_b300 import scenarios as SC
-    for kind in ("static", "crossing"):
+    for kind in ("static", "blocking", "crossing"):
         for mppi in (False, True):
             r = SC.run(kind, mppi, episodes=4, steps=60)
             assert r["episodes"] == 4
             assert 0 <= r["collided"] <= 4 and 0 <= r["reached"] <= 4
+
+
+def test_blocking_scene_averaging_failure():
+    """The averaging-induced failure (Sec. I, Fig. 1; Sec. III-B) on the GPU
+    path: driving straight at a disc on the line to the goal, CE-MPPI's new
+    nominal passes on one side while standard MPPI's average of both sides
+    runs into the disc (same seeds: the same perturbations for both)."""
+    from paper_2607_06499_b300 import scenarios as SC
+    r = SC.approach_study(seeds=24, lams=(5.0,), Ks=(300,))["K=300/lam=5.0"]
+    assert r["ce_two_or_more_clusters"] >= 20
+    assert r["ce-mppi"]["nominal_meets_disc"] == 0
+    assert r["mppi"]["nominal_meets_disc"] >= 8
 
 
 def test_union_find_limit_reports_timeout_and_falls_back():

@@ -602,3 +602,32 @@ def test_scenario_scenes_and_evaluation():
     detour[:, 0, 1] = 1.5 * np.sin(np.pi * xs / 4.0)
     r = SC.evaluate([s], detour)
     assert r["collided"] == 0 and r["reached"] == 1 and r["time_to_goal_median_s"] > 0
+
+
+def test_averaging_failure_on_the_symmetric_blocking_scene():
+    """Sec. I (Fig. 1) and Sec. III-B, Scenario 1: with the robot driving
+    straight at a disc on its line to the goal, the free rollouts pass on both
+    sides.  Standard MPPI (softmin over all K with the collision penalty,
+    Eq. 6-7) averages the two sides into a nominal that still runs into the
+    disc; CE-MPPI clusters the free rollouts (two clusters) and updates within
+    one, so its nominal passes on one side.  Same seeds, so both methods see
+    the same perturbations."""
+    from paper_2607_06499_b300 import scenarios as SC
+    sc = SC.scene("blocking", 0, 8)
+    c, rad = sc["obs"][0, 0], sc["radius"]
+    x0 = np.array([1.1, 0.0, 0.0])
+    meets = {False: 0, True: 0}
+    two = 0
+    for seed in range(24):
+        for mppi in (False, True):
+            cfg = SC.planner_cfg(sc["goal"], mppi, seed, lam=5.0)
+            P = oracle.make_params(cfg)
+            U = np.tile([0.8, 0.0], (cfg["T"], 1))
+            r = oracle.replan(P, x0, U, sc["obs"][:sc["H"]], rad)
+            path = SC.nominal_path(x0, r["U_new"], sc["dt"])
+            meets[mppi] += int((np.linalg.norm(path[:, :2] - c[None], axis=1) - (rad[0] + 0.1)).min() < 0)
+            if not mppi:
+                two += int(r["diag"]["n_clusters"] >= 2)
+    assert two >= 20                       # the free rollouts split into two sides
+    assert meets[False] == 0               # CE-MPPI's nominal commits to one side
+    assert meets[True] >= 8                # MPPI's average runs into the disc
