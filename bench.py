@@ -500,11 +500,33 @@ def aggregate(tot_ms: float, units_per_rank: float, steps: int, world: int, dist
 # cell order, labels, weights), plus the update's least traffic when eps' is
 # drawn again, (5 + 2p) 4 B per rollout (its records) -- 76 B for p = 2.
 POST_BYTES_PER_ROLLOUT = {2: 40 + 36, 3: 40 + 44}
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch over
-# the benchmark's 8 pipelined instances, from one ncu capture of the current
-# kernels on this workload (None: not captured for the current build).
-POST_NCU_TRAFFIC = None
-ROLLOUT_NCU_TRAFFIC = None   # (16 instances: the stage-by-stage profile launch)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
+# ncu capture of the current build of the kernel, on the launch the line's
+# timing covers: k_post over one pipelined half (8 instances), the rollout
+# kernel over all 16 instances (the stage-by-stage profile launch).  None: not
+# captured for the current build.
+NCU_TRAFFIC = {("unicycle", "k_post"): 1737472, ("unicycle", "rollout"): 93952,
+               ("arm", "k_post"): None, ("arm", "rollout"): 7056128,
+               ("arm", "k_update"): 50712320}
+
+
+def update_roofline(res: dict, m: int, hbm: float, pk_kind: str, wl_name: str):
+    """The tiled update kernel against HBM where eps' is stored: |C*| T m 4 B
+    read for the rows of nonzero weight + T m 8 B per instance, over the
+    kernel's event time in the stage-by-stage replans (None with noise
+    regeneration: the update then draws eps' again and reads no rows)."""
+    if res["regen"]:
+        return None
+    TMs = res["Ts"] * m
+    upd_bytes = float(np.sum(np.array(res["update_nnz"]) * TMs * 4 + TMs * 8))
+    upd_ms = res["stage_ms"]["update"]
+    upd_gbs = upd_bytes / (upd_ms * 1e-3) / 1e9
+    return {"kernel": "k_update (tiled, eps' stored)", "bound": "hbm", "achieved": upd_gbs,
+            "peak": hbm, "unit": "GB/s", "frac": upd_gbs / hbm,
+            "traffic": NCU_TRAFFIC.get((wl_name, "k_update")),
+            "peak_kind": f"copy bandwidth ({pk_kind})", "ms_per_launch": upd_ms,
+            "algorithmic_bytes_per_launch": upd_bytes,
+            "nonzero_weights_mean": float(np.mean(res["update_nnz"]))}
 
 
 def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: int, dist,
@@ -644,6 +666,9 @@ def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: 
             tests.append(int(np.frombuffer(r["diag"].cpu().numpy().tobytes()[72:76], np.int32)[0]))
     out["stage_ms"] = {s_: float(np.mean(v)) for s_, v in prof.items()}
     out["tests"] = np.array(tests, dtype=np.float64).reshape(args.profile_steps, len(reqs)).mean(0)
+    # nonzero weights of each instance's last profiled replan: the rows of
+    # eps' the update reads (the update kernel's algorithmic bytes)
+    out["update_nnz"] = [int(np.count_nonzero(pl.peek("W"))) for pl in planners]
     # the fused clustering kernel as the pipeline launches it: one half's
     # instances, events around part 1 (prune + DBSCAN + selection + update)
     reset_episodes()
@@ -789,20 +814,24 @@ def main() -> None:
     roll_share = roll_ms
     roof_post = {"kernel": "k_post (prune + DBSCAN + selection + update)", "bound": "hbm",
                  "achieved": post_gbs, "peak": hbm, "unit": "GB/s", "frac": post_gbs / hbm,
-                 "traffic": POST_NCU_TRAFFIC, "peak_kind": f"copy bandwidth ({pk_kind})",
+                 "traffic": NCU_TRAFFIC.get((args.workload, "k_post")),
+                 "peak_kind": f"copy bandwidth ({pk_kind})",
                  "ms_per_launch": post_ms, "algorithmic_bytes_per_launch": post_bytes,
                  "bytes_per_rollout": POST_BYTES_PER_ROLLOUT[p_dim],
                  "note": "latency-bound: chains of dependent L2 accesses between cluster "
-                         "barriers, far below the bandwidth bound"}
+                         "barriers, far below the bandwidth bound; its DRAM traffic is below "
+                         "the algorithmic bytes (the rollout epilogue's group records replace "
+                         "per-rollout reads, and the working set stays in L2)"}
     roof_roll = {"kernel": "k_rollout_arm" if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12)
                  else "k_rollout2d<unicycle>", "bound": "alu", "achieved": achieved,
                  "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": ROLLOUT_NCU_TRAFFIC,
+                 "traffic": NCU_TRAFFIC.get((args.workload, "rollout")),
                  "peak_kind": f"FP32 lanes x 2 x max SM clock ({pk_kind} clock)",
                  "ms_per_launch": roll_ms,
                  "flops_per_rollout": float(flops_roll.sum() / Ks.sum()),
                  "obstacle_tests_per_rollout": float(np.mean(tests))}
     dominant_post = post_share >= roll_share
+    roof_upd = update_roofline(res, m, hbm, pk_kind, args.workload)
 
     # ---- end to end through the public API with host buffers: the batch
     # entry point that takes packed host arrays (ce_mppi_batch_run_host) --
@@ -874,15 +903,15 @@ def main() -> None:
         ("roofline_rollout" if dominant_post else "roofline_post"):
             roof_roll if dominant_post else roof_post,
         "device_time_share_ms_per_step": {"k_post": post_share, "k_rollout": roll_share},
+        **({"roofline_update": roof_upd} if roof_upd else {}),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "api": "ce_mppi_batch_run_host (packed host buffers, one copy each way, "
                        "graph replay, host-side closed loop)", "steps": n_e2e},
-        # kernels per replan chain: tracks, rollouts, the fused clustering +
-        # update kernel (+ the tiled update for the arms); per step two half
-        # chains (pipelined) or one chain per branch (the L2 flush is torch's)
-        "gpu_launches": (4 if cfg0["dyn"] in (pkg.DYN_ARM, pkg.DYN_ARM12) else 3)
-                        * (2 if res["pipelined"] else res["batch_config"]["n_branches"])
+        # kernels per replan chain: tracks, rollouts, the fused clustering
+        # kernel and the tiled update; per step two half chains (pipelined) or
+        # one chain per branch (the L2 flush is torch's)
+        "gpu_launches": 4 * (2 if res["pipelined"] else res["batch_config"]["n_branches"])
                         * args.steps,
     }
     if stamps is not None:
@@ -896,7 +925,7 @@ def main() -> None:
         for name in ("arm", "batch"):
             r2, objs2, pls2, _, _, _, _, _ = run_workload(
                 pkg, torch, args, name, dev, stream, 0, 1, None, args.extra_steps, 3, flush,
-                profile=False)
+                profile=(name == "arm"))
             extra[name] = {"config": bench_config(name, 1, r2["regen"]), "value": r2["value"],
                            "unit": UNIT, "replans_per_s": r2["replans_per_s"],
                            "ms_per_step": r2["tot_ms"] / args.extra_steps,
@@ -904,6 +933,10 @@ def main() -> None:
                            "latency_ms": {"p50": float(np.percentile(r2["step_ms"], 50)),
                                           "p99": float(np.percentile(r2["step_ms"], 99))},
                            "modes_last_step": r2["modes_last_step"]}
+            if name == "arm":
+                ru = update_roofline(r2, pkg.DIMS[pkg.DYN_ARM][1], hbm, pk_kind, "arm")
+                if ru:
+                    extra[name]["roofline_update"] = ru
             for obj in objs2 + pls2:
                 obj.close()
         line["extra_workloads"] = extra

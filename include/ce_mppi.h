@@ -115,7 +115,9 @@ typedef struct {
 /* Per-replan diagnostics. */
 typedef struct {
   int mode;        /* ce_mode_t; -1 when the replan was refused (status != 0 and  */
-                   /* nothing updated: a non-finite device input)                 */
+                   /* nothing updated, nominal and counter kept: a non-finite     */
+                   /* device input, INVALID_ARG; or a rollout CTA whose bounded   */
+                   /* wait for its copy of the obstacle tracks ran out, TIMEOUT)  */
   int n_col;       /* |C_col|                                                     */
   int n_valid;     /* |V|                                                         */
   int n_clusters;  /* M_t                                                         */

@@ -38,7 +38,7 @@ struct Ctl {
   int nnz;                        // nonzero update weights listed (-1: more than kSparseMax)
   int updated;                    // the update was applied by the fused per-instance kernel
   int nnz_all;                    // nonzero weights of the replan (all CTAs of the instance)
-  int rejected;                   // the track kernel found a non-finite input: no update
+  int rejected;                   // no update: 1 a non-finite input (track kernel), 2 a rollout CTA's copy timed out
   float pbar[3], v_obs[3], p0[3];
   unsigned int done;              // last-CTA ticket of the update stage
   int col_tests;                  // circle/sphere tests per rollout after reach culling

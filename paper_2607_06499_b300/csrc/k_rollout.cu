@@ -162,8 +162,16 @@ __global__ void k_tracks(KArgs a) {
   if (threadIdx.x == 0) d.ctl->col_tests = roff[T + 1] - roff[1];
 }
 
+// A rollout CTA whose copy of the track table did not land in time: the
+// replan reports TIMEOUT and is refused by the later stages (nominal and
+// counter kept), so no rollout record of this launch is ever used.
+__device__ __forceinline__ void give_up_replan(Ctl* c) {
+  raise_status(c, CE_MPPI_ERR_TIMEOUT);
+  atomicExch(&c->rejected, 2);
+}
+
 // Stage the instance's tracks and row counts (TMA bulk copy) and the nominal
-// into shared memory.  Returns false (and records a timeout) if the copy did
+// into shared memory.  Returns false (the replan given up) if the copy did
 // not land in time.
 __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float4* trk,
                                              float* Us, uint64_t* bar) {
@@ -175,13 +183,13 @@ __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float
     bulk_g2s(trk, d.tracks, bytes, bar);
   }
   for (int i = threadIdx.x; i < d.T * d.m; i += blockDim.x) Us[i] = d.U[i];
-  bool ok = true;
-  if (bytes > 0 && !mbar_wait(bar, 0)) {
-    raise_status(d.ctl, CE_MPPI_ERR_TIMEOUT);
-    mbar_wait(bar, 0);  // give the copy in flight one more bounded chance
-    ok = false;
+  // the CTA decides together: on a timeout the copy may still be landing, so
+  // every thread waits once more (bounded) before the CTA leaves
+  const bool ok = __syncthreads_and(bytes == 0 || mbar_wait(bar, 0));
+  if (!ok) {
+    if (threadIdx.x == 0) give_up_replan(d.ctl);
+    mbar_wait(bar, 0);
   }
-  __syncthreads();
   return ok;
 }
 
@@ -228,7 +236,10 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   }
   for (int i = threadIdx.x; i < T * d.m; i += blockDim.x) Us[i] = d.U[i];
   __syncthreads();
-  bool ok = mbar_wait(&bar, phase);
+  // CTA-uniform: a copy that did not land ends the CTA's work (no further
+  // copies on this barrier; one more bounded wait for it before the exit)
+  bool ok = __syncthreads_and(mbar_wait(&bar, phase));
+  uint32_t pend = phase;
   phase ^= 1u;
   const bool all = whole != 0;
   const int k = tile.y * kRolloutThreads + threadIdx.x;
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   int j = 0;
   // runs of rows [ja, jb): step j tests row j + 1; row 0 only with check_j0
-  for (int ja = 0; ja <= T;) {
+  for (int ja = 0; ok && ja <= T;) {
     int jb = T + 1;
     if (!all) {
       jb = ja + 1;
@@ -262,8 +273,10 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
         mbar_expect_tx(&bar, bytes);
         if (bytes > 0) bulk_g2s((void*)buf, gent + off[ja], bytes, &bar);
       }
-      ok = mbar_wait(&bar, phase) && ok;
+      ok = __syncthreads_and(mbar_wait(&bar, phase));
+      pend = phase;
       phase ^= 1u;
+      if (!ok) break;
     }
     const int base = all ? 0 : off[ja];
     if (ja == 0 && d.check_j0 && act) {
@@ -341,8 +354,11 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
     }
     ja = jb;
   }
-  if (!ok && threadIdx.x == 0) raise_status(d.ctl, CE_MPPI_ERR_TIMEOUT);
-  if (act) {
+  if (!ok) {
+    if (threadIdx.x == 0) give_up_replan(d.ctl);
+    mbar_wait(&bar, pend);
+  }
+  if (act && ok) {
     if (DYN == 0) {
       const float ex = s0 - g0, ey = s1 - g1;
       kahan_add(S, Sc, w2 * (ex * ex + ey * ey));
