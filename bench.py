@@ -590,12 +590,21 @@ def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: 
         with torch.cuda.graph(graph):
             main_s = torch.cuda.current_stream()
             side.wait_stream(main_s)
-            bB.run_part(1, main_s)
-            bA.run_part(0, side)
-            main_s.wait_stream(side)
-            side.wait_stream(main_s)
-            bA.run_part(1, main_s)
-            bB.run_part(0, side)
+            if args.pipeline == 2:
+                # the two halves as two chains joined only at the end: B's
+                # clustering (s-1) then B's rollouts (s) on one stream, A's
+                # rollouts (s) then A's clustering (s) on the other
+                bB.run_part(1, main_s)
+                bB.run_part(0, main_s)
+                bA.run_part(0, side)
+                bA.run_part(1, side)
+            else:
+                bB.run_part(1, main_s)
+                bA.run_part(0, side)
+                main_s.wait_stream(side)
+                side.wait_stream(main_s)
+                bA.run_part(1, main_s)
+                bB.run_part(0, side)
             main_s.wait_stream(side)
         torch.cuda.synchronize()
         pipe = (bA, bB, graph)
@@ -713,8 +722,10 @@ def main() -> None:
     ap.add_argument("--serve-warmup", type=float, default=20.0,
                     help="unmeasured start of the served run (the concurrency ramps up)")
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)
-    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
-                    help="1: two halves of the episodes software-pipelined in one graph")
+    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1, 2],
+                    help="1: two halves of the episodes software-pipelined in one graph, "
+                         "joined after each phase; 2: the same halves as two chains "
+                         "joined once per step")
     ap.add_argument("--pipe-post-ctas", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="clustering-kernel CTAs per instance in the pipelined halves "
                          "(0: from the occupancy, as if each half ran alone)")

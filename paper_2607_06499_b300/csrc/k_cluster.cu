@@ -99,7 +99,25 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
   {
     int tvv = 0, tcc = 0, lvv = 0, lcc = 0;
     float vmax = 0.f, vmin = INFINITY, amin = INFINITY;
-    for (int gi = tid; gi < ng; gi += blockDim.x) {
+    int mvv = 0, mcc = 0;
+    const int gb = beg / gsz, ge = (end + gsz - 1) / gsz;
+    {
+      // (the first records of both loops below are loaded together)
+      const int gi = tid, gj = gb + lane;
+      int2 c0 = make_int2(0, 0), c1 = make_int2(0, 0);
+      float4 e0 = make_float4(0.f, INFINITY, INFINITY, 0.f);
+      if (gi < ng) { c0 = __ldcg(d.gcnt + gi); e0 = __ldcg(d.gS + gi); }
+      if (gj < ge) c1 = __ldcg(d.gcnt + gj);
+      tvv += c0.x;
+      tcc += c0.y;
+      if (gi < g_rank) { lvv += c0.x; lcc += c0.y; }
+      vmax = fmaxf(vmax, e0.x);
+      vmin = fminf(vmin, e0.y);
+      amin = fminf(amin, e0.z);
+      mvv += c1.x;
+      mcc += c1.y;
+    }
+    for (int gi = tid + blockDim.x; gi < ng; gi += blockDim.x) {
       const int2 c = __ldcg(d.gcnt + gi);
       const float4 e = __ldcg(d.gS + gi);
       tvv += c.x;
@@ -109,9 +127,7 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
       vmin = fminf(vmin, e.y);
       amin = fminf(amin, e.z);
     }
-    int mvv = 0, mcc = 0;
-    const int gb = beg / gsz, ge = (end + gsz - 1) / gsz;
-    for (int gi = gb + lane; gi < ge; gi += 32) {
+    for (int gi = gb + 32 + lane; gi < ge; gi += 32) {
       const int2 c = __ldcg(d.gcnt + gi);
       mvv += c.x;
       mcc += c.y;
@@ -140,10 +156,14 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
   {
     const float* hn = hist_of(r, d) + (size_t)(d.H - 1) * n_obs * p;   // newest observation
     for (int o = tid; o < n_obs; o += blockDim.x) {
-      if (__ldcg(d.osum + 4 * (size_t)o) == 0) continue;
-      const float dx = p0s[0] - hn[o * p], dy = p0s[1] - hn[o * p + 1];
-      const float dz = p == 3 ? p0s[2] - hn[o * p + 2] : 0.f;
-      const float clear = sqrtf(dx * dx + dy * dy + dz * dz) - r.obs_radius[o];
+      // (count, centre and radius loaded together)
+      const long long cnt = __ldcg(d.osum + 4 * (size_t)o);
+      const float ox = hn[o * p], oy = hn[o * p + 1], oz = p == 3 ? hn[o * p + 2] : 0.f;
+      const float orad = r.obs_radius[o];
+      if (cnt == 0) continue;
+      const float dx = p0s[0] - ox, dy = p0s[1] - oy;
+      const float dz = p == 3 ? p0s[2] - oz : 0.f;
+      const float clear = sqrtf(dx * dx + dy * dy + dz * dz) - orad;
       atomicMin(&best, ((unsigned long long)float_key(clear) << 32) | (unsigned)o);
     }
   }
@@ -230,16 +250,33 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
   const float ne = d.norm_eps;
   const unsigned lt = (1u << lane) - 1u;
   int bv = wv[wid], bc = wc[wid];
+  // the first hit, cost and p(x_T) of the next 32 rollouts are loaded before
+  // this step's work
+  int nh = -1;
+  float nSk = 0.f, npk[3] = {0.f, 0.f, 0.f};
+  auto pfetch = [&](int k) {
+    nh = -1;
+    if (k < end) {
+      nh = __ldg(d.hit + k);
+      nSk = __ldg(d.S + k);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < p) npk[c] = __ldg(d.pN + (size_t)c * Kp + k);
+    }
+  };
+  pfetch(beg + lane);
   for (int s0 = beg; s0 < end; s0 += 32) {
     const int k = s0 + lane;
+    const int h = nh;
+    const float Sk = nSk, pk3[3] = {npk[0], npk[1], npk[2]};
+    pfetch(s0 + 32 + lane);
     const bool in = k < end;
-    const int h = in ? __ldg(d.hit + k) : -1;
     const bool isV = in && h < 0, isC = h >= 0;
     const unsigned mv = __ballot_sync(FULL, isV), mc = __ballot_sync(FULL, isC);
     if (isV) {
       const int i = bv + __popc(mv & lt);
       d.idxV[i] = k;
-      d.Sv[i] = __ldg(d.S + k);
+      d.Sv[i] = Sk;
     }
     if (isV && !fallback) {
       const int i = bv + __popc(mv & lt);
@@ -247,7 +284,7 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (c >= p) continue;
-        const float pk = __ldg(d.pN + (size_t)c * Kp + k);
+        const float pk = pk3[c];
         dv[c] = pk - pbar[c];
         ev[c] = pk - p0s[c];
         nd += dv[c] * dv[c];
@@ -269,15 +306,21 @@ __device__ __forceinline__ void prune_stage(const KArgs& a, bool fused) {
     const int H = d.H;
     const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
     const float* h = hist_of(r, d);
+    // the observations first, then the stores (see the selection's prefetch)
+    float hn[3] = {0.f, 0.f, 0.f}, ho[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < p) {
+        hn[c] = h[((size_t)(H - 1) * n_obs + o_star) * p + c];
+        ho[c] = h[(size_t)o_star * p + c];
+      }
     ctl->nV = nV; ctl->nC = nC; ctl->M = 0; ctl->sel = -1; ctl->o_star = o_star;
     ctl->dynamic = 0; ctl->mode = CE_MODE_STATIC;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       ctl->pbar[c] = c < p ? pbar[c] : 0.f;
       ctl->p0[c] = p0s[c];
-      ctl->v_obs[c] = c < p ? (h[((size_t)(H - 1) * n_obs + o_star) * p + c] -
-                               h[(size_t)o_star * p + c]) * inv
-                            : 0.f;
+      ctl->v_obs[c] = c < p ? (hn[c] - ho[c]) * inv : 0.f;
     }
   }
 }
@@ -568,8 +611,7 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
       }
       w.cell[i] = ci;
     }
-    const unsigned peers = __match_any_sync(FULL, ci);
-    if (ci >= 0 && lane == __ffs(peers) - 1) atomicAdd(&lcnt[ci], __popc(peers));
+    if (ci >= 0) atomicAdd(&lcnt[ci], 1);
   }
   cluster.sync();   // (1) every CTA's counts
   stamp(1);
@@ -669,17 +711,13 @@ __device__ __forceinline__ void dbscan_block(const float* __restrict__ z, int ld
   }
   __syncthreads();
   stamp(2);
-  // 3. scatter the slice into cell order (one cursor atomic per cell per warp)
+  // 3. scatter the slice into cell order (a shared-memory cursor atomic per
+  //    point: the order inside a cell does not enter the result)
   for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
     const int i = b0 + tid;
     const int o = i < i1 ? map[w.cell[i]] : -1;
-    const unsigned peers = __match_any_sync(FULL, o);
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (o >= 0 && lane == leader) base = atomicAdd(&ofill[o], __popc(peers));
-    base = __shfl_sync(FULL, base, leader);
     if (o >= 0) {
-      const int pos = base + __popc(peers & ((1u << lane) - 1u));
+      const int pos = atomicAdd(&ofill[o], 1);
       w.sorted[pos] = i;
 #pragma unroll
       for (int q = 0; q < p; ++q) w.zs[(size_t)q * w.ld_s + pos] = z[(size_t)q * ld + i];
@@ -1202,12 +1240,15 @@ __device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int 
   const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
   constexpr int NB = kAngBuckets;
-  int* hcnt = smem;             // [NB] boundary list, then component minima
+  int* hcnt = smem;             // [NB] the CTA's base in each bucket, boundary list, component minima
   int* st = hcnt + NB;          // [NB + 1] bucket starts in bucket order
   int* cur = st + NB + 1;       // [NB] run flags, then the component of each bucket
   int* gmin = cur + NB;         // [NB] least core index per bucket, whole set
   int* aux = gmin + NB;         // [NB] scans, then the canonical id of each component
   int* lst = reinterpret_cast<int*>(w.zs + 2 * (size_t)w.ld_s);   // (z's unused third row)
+  // the coordinates in bucket order as (x, y) pairs: one scattered store per
+  // point in the scatter, one load per point in the exact tests
+  float2* zs2 = reinterpret_cast<float2*>(w.zs);
   __shared__ int wsum[33];
   __shared__ int n_list, n_cs_s;
   auto stamp = [&](int k) {
@@ -1215,43 +1256,83 @@ __device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int 
   };
   // ---- 2. bucket starts (every CTA alike, from the instance's count table),
   //    scatter of the slice into bucket order at the offsets pass 1 handed out
-  for (int b = tid; b < NB; b += blockDim.x) st[b] = __ldcg(&w.ahist[b]);
+  {
+    int v[NB / kBlock];   // (blockDim.x * 4 == NB, as the scans assume)
+#pragma unroll
+    for (int q = 0; q < NB / kBlock; ++q) v[q] = __ldcg(&w.ahist[tid + q * kBlock]);
+#pragma unroll
+    for (int q = 0; q < NB / kBlock; ++q) st[tid + q * kBlock] = v[q];
+  }
   __syncthreads();
   ang_scan<false>(st, wsum);
   if (tid == 0) st[NB] = n;
   __syncthreads();
-  for (int i = i0 + tid; i < i1; i += blockDim.x) {
-    const int pos = st[w.cell[i]] + w.core[i];
-    w.sorted[pos] = i;
-    w.zs[pos] = z[i];
-    w.zs[(size_t)w.ld_s + pos] = z[(size_t)ld + i];
+  for (int b0 = i0; b0 < i1; b0 += 2 * (int)blockDim.x) {
+    int cb[2] = {0, 0}, co[2] = {0, 0};
+    float zx[2] = {0.f, 0.f}, zy[2] = {0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      if (i < i1) { cb[u] = w.cell[i]; co[u] = w.core[i]; zx[u] = z[i]; zy[u] = z[(size_t)ld + i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      if (i < i1) {
+        const int pos = st[cb[u]] + hcnt[cb[u]] + co[u];
+        w.sorted[pos] = i;
+        zs2[pos] = make_float2(zx[u], zy[u]);
+      }
+    }
   }
   cluster.sync();   // (2) bucket order complete in global memory
   stamp(2);
   // ---- 3. core flags: window count, exact tests in the band when short
   if (tid == 0) n_list = 0;
+  for (int b = tid; b < NB; b += blockDim.x) gmin[b] = 0x7fffffff;   // (the CTA's minima)
   __syncthreads();
-  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
-    const int i = b0 + tid;
-    bool need = false;
-    if (i < i1) {
-      const int b = w.cell[i];
-      const int c = ang_count(st, b - Dlo, b + Dlo);
-      w.core[i] = c >= min_pts ? 1 : 0;
-      need = c < min_pts;
+  for (int b0 = i0; b0 < i1; b0 += 2 * (int)blockDim.x) {
+    int cb[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      if (i < i1) cb[u] = w.cell[i];
     }
-    const unsigned bl = __ballot_sync(FULL, need);
-    int base = 0;
-    if (bl && lane == __ffs(bl) - 1) base = atomicAdd(&n_list, __popc(bl));
-    base = __shfl_sync(FULL, base, bl ? __ffs(bl) - 1 : 0);   // (from the lane that added)
-    if (need) lst[i0 + base + __popc(bl & ((1u << lane) - 1u))] = i;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      bool need = false;
+      if (i < i1) {
+        // core for sure with minPts points within D_lo; not core for sure
+        // with fewer than minPts within D_hi; the exact tests decide between
+        const int b = cb[u];
+        const int c = ang_count(st, b - Dlo, b + Dlo);
+        w.core[i] = c >= min_pts ? 1 : 0;
+        need = c < min_pts && ang_count(st, b - Dhi, b + Dhi) >= min_pts;
+      }
+      const unsigned bl = __ballot_sync(FULL, need);
+      int base = 0;
+      if (bl && lane == __ffs(bl) - 1) base = atomicAdd(&n_list, __popc(bl));
+      base = __shfl_sync(FULL, base, bl ? __ffs(bl) - 1 : 0);   // (from the lane that added)
+      if (need) lst[i0 + base + __popc(bl & ((1u << lane) - 1u))] = i;
+    }
   }
   __syncthreads();
   const int nl = n_list;
-  for (int li = wid; li < nl; li += nwarp) {
-    const int i = lst[i0 + li];
-    const int b = w.cell[i];
-    const float za[2] = {z[i], z[(size_t)ld + i]};
+  // a warp's entries are li = wid + j nwarp; lane j loads entry j's index,
+  // bucket and coordinates for 32 entries at a time, then the warp takes
+  // the entries in turn (their band tests)
+  for (int lb = wid; lb < nl; lb += 32 * nwarp) {
+    const int lj = lb + lane * nwarp;
+    int ei = 0, eb = 0;
+    float ex = 0.f, ey = 0.f;
+    if (lj < nl) ei = lst[i0 + lj];
+    if (lj < nl) { eb = w.cell[ei]; ex = z[ei]; ey = z[(size_t)ld + ei]; }
+    const int ne = min(32, (nl - lb + nwarp - 1) / nwarp);
+  for (int jj = 0; jj < ne; ++jj) {
+    const int i = __shfl_sync(FULL, ei, jj);
+    const int b = __shfl_sync(FULL, eb, jj);
+    const float za[2] = {__shfl_sync(FULL, ex, jj), __shfl_sync(FULL, ey, jj)};
     int count = ang_count(st, b - Dlo, b + Dlo);
     // the two band ranges, (b + Dlo, b + Dhi] and [b - Dhi, b - Dlo)
     AngRanges br;
@@ -1261,32 +1342,47 @@ __device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int 
       bool hit = false;
       if (t < br.tot) {
         const int q = br.pos(t);
-        const float zb[2] = {w.zs[q], w.zs[(size_t)w.ld_s + q]};
+        const float2 zq = zs2[q];
+        const float zb[2] = {zq.x, zq.y};
         hit = nb_pred_t<2>(za, zb, eps2);
       }
       count += __popc(__ballot_sync(FULL, hit));
     }
     if (lane == 0) w.core[i] = count >= min_pts ? 1 : 0;
   }
+  }
   __syncthreads();
-  // least core index per bucket (one atomic per warp and bucket, on the
-  // instance's table in global memory)
-  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
-    const int i = b0 + tid;
-    const int b = (i < i1 && w.core[i]) ? w.cell[i] : -1;
-    const unsigned peers = __match_any_sync(FULL, b);
-    if (b >= 0) {
-      const int mn = __reduce_min_sync(peers, i);
-      if (lane == __ffs(peers) - 1) atomicMin(&w.amin[b], mn);
+  // least core index per bucket: the slice's in shared memory, then one
+  // global atomic per occupied bucket
+  for (int b0 = i0; b0 < i1; b0 += 2 * (int)blockDim.x) {
+    int cf[2] = {0, 0}, cb[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      if (i < i1) { cf[u] = w.core[i]; cb[u] = w.cell[i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      if (i < i1 && cf[u]) atomicMin(&gmin[cb[u]], i);
     }
   }
+  __syncthreads();
+  for (int b = tid; b < NB; b += blockDim.x)
+    if (gmin[b] != 0x7fffffff) atomicMin(&w.amin[b], gmin[b]);
   cluster.sync();   // (3) core flags and bucket minima of every CTA
   stamp(3);
   // ---- 4. components over the core buckets (every CTA alike)
-  for (int b = tid; b < NB; b += blockDim.x) {
-    const int m = __ldcg(&w.amin[b]);
-    gmin[b] = m;
-    aux[b] = m != 0x7fffffff ? b : -1;   // (for the previous-core-bucket scan)
+  {
+    int v[NB / kBlock];
+#pragma unroll
+    for (int q = 0; q < NB / kBlock; ++q) v[q] = __ldcg(&w.amin[tid + q * kBlock]);
+#pragma unroll
+    for (int q = 0; q < NB / kBlock; ++q) {
+      const int b = tid + q * kBlock;
+      gmin[b] = v[q];
+      aux[b] = v[q] != 0x7fffffff ? b : -1;   // (for the previous-core-bucket scan)
+    }
   }
   __syncthreads();
   const int last_core = ang_scan<true>(aux, wsum);   // aux[b] = largest core bucket < b
@@ -1331,8 +1427,9 @@ __device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int 
         if (x0 + lane < X.tot) {
           const int q = X.pos(x0 + lane);
           xv = w.core[w.sorted[q]] != 0;
-          xa[0] = w.zs[q];
-          xa[1] = w.zs[(size_t)w.ld_s + q];
+          const float2 zq = zs2[q];
+          xa[0] = zq.x;
+          xa[1] = zq.y;
         }
         for (int y0 = 0; y0 < Y.tot && !found; y0 += 32) {
           float ya[2] = {0.f, 0.f};
@@ -1340,8 +1437,9 @@ __device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int 
           if (y0 + lane < Y.tot) {
             const int q = Y.pos(y0 + lane);
             yv = w.core[w.sorted[q]] != 0;
-            ya[0] = w.zs[q];
-            ya[1] = w.zs[(size_t)w.ld_s + q];
+            const float2 zq = zs2[q];
+            ya[0] = zq.x;
+            ya[1] = zq.y;
           }
           bool hit = false;
           for (int j = 0; j < 32; ++j) {
@@ -1400,45 +1498,79 @@ __device__ __forceinline__ void dbscan_angular(const float* __restrict__ z, int 
   //    exact tests in the band), else noise
   if (tid == 0) n_list = 0;
   __syncthreads();
-  for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
-    const int i = b0 + tid;
-    bool border = false;
-    if (i < i1) {
-      if (w.core[i]) labels[i] = aux[cur[w.cell[i]]];
-      else border = true;
+  for (int b0 = i0; b0 < i1; b0 += 2 * (int)blockDim.x) {
+    int cf[2] = {0, 0}, cb[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      if (i < i1) { cf[u] = w.core[i]; cb[u] = w.cell[i]; }
     }
-    const unsigned bl = __ballot_sync(FULL, border);
-    int base = 0;
-    if (bl && lane == __ffs(bl) - 1) base = atomicAdd(&n_list, __popc(bl));
-    base = __shfl_sync(FULL, base, bl ? __ffs(bl) - 1 : 0);   // (from the lane that added)
-    if (border) lst[i0 + base + __popc(bl & ((1u << lane) - 1u))] = i;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + u * blockDim.x + tid;
+      bool border = false;
+      if (i < i1) {
+        if (cf[u]) labels[i] = aux[cur[cb[u]]];
+        else border = true;
+      }
+      const unsigned bl = __ballot_sync(FULL, border);
+      int base = 0;
+      if (bl && lane == __ffs(bl) - 1) base = atomicAdd(&n_list, __popc(bl));
+      base = __shfl_sync(FULL, base, bl ? __ffs(bl) - 1 : 0);   // (from the lane that added)
+      if (border) lst[i0 + base + __popc(bl & ((1u << lane) - 1u))] = i;
+    }
   }
   __syncthreads();
   const int nb_pts = n_list;
-  for (int li = wid; li < nb_pts; li += nwarp) {
-    const int i = lst[i0 + li];
-    const int b = w.cell[i];
-    const float za[2] = {z[i], z[(size_t)ld + i]};
+  for (int lb = wid; lb < nb_pts; lb += 32 * nwarp) {   // (32 entries' loads at a time)
+    const int lj = lb + lane * nwarp;
+    int ei = 0, eb = 0;
+    float ex = 0.f, ey = 0.f;
+    if (lj < nb_pts) ei = lst[i0 + lj];
+    if (lj < nb_pts) { eb = w.cell[ei]; ex = z[ei]; ey = z[(size_t)ld + ei]; }
+    const int ne = min(32, (nb_pts - lb + nwarp - 1) / nwarp);
+  for (int jj = 0; jj < ne; ++jj) {
+    const int i = __shfl_sync(FULL, ei, jj);
+    const int b = __shfl_sync(FULL, eb, jj);
+    const float za[2] = {__shfl_sync(FULL, ex, jj), __shfl_sync(FULL, ey, jj)};
     int best = 0x7fffffff;
     for (int d0 = -Dlo; d0 <= Dlo; d0 += 32) {
       const int dd = d0 + lane;
       if (dd <= Dlo) best = min(best, gmin[ang_wrap(b + dd)]);
     }
     best = __reduce_min_sync(FULL, best);
+    // a core point of a band bucket has an index >= that bucket's least core
+    // index: when none is below best, the band cannot lower it
+    int bmin = 0x7fffffff;
+    {
+      const int nbb = Dhi - Dlo;   // band buckets on each side
+      if (lane < 2 * nbb) {
+        const int dd = lane < nbb ? Dlo + 1 + lane : -(Dlo + 1 + (lane - nbb));
+        bmin = gmin[ang_wrap(b + dd)];
+      }
+      for (int l2 = lane + 32; l2 < 2 * nbb; l2 += 32) {
+        const int dd = l2 < nbb ? Dlo + 1 + l2 : -(Dlo + 1 + (l2 - nbb));
+        bmin = min(bmin, gmin[ang_wrap(b + dd)]);
+      }
+      bmin = __reduce_min_sync(FULL, bmin);
+    }
     AngRanges br;
     br.set(st, b + Dlo + 1, b + Dhi, b - Dhi, b - Dlo - 1);
+    if (bmin >= best) br.tot = 0;
     for (int t0 = 0; t0 < br.tot; t0 += 32) {
       const int t = t0 + lane;
       int cand = 0x7fffffff;
       if (t < br.tot) {
         const int q = br.pos(t);
         const int sid = w.sorted[q];
-        const float zb[2] = {w.zs[q], w.zs[(size_t)w.ld_s + q]};
+        const float2 zq = zs2[q];
+        const float zb[2] = {zq.x, zq.y};
         if (sid < best && w.core[sid] && nb_pred_t<2>(za, zb, eps2)) cand = sid;
       }
       best = min(best, __reduce_min_sync(FULL, cand));
     }
     if (lane == 0) labels[i] = best == 0x7fffffff ? -1 : aux[cur[w.cell[best]]];
+  }
   }
   if (tid == 0 && rank == 0) *M_out = n_comp;
   stamp(5);
@@ -1467,30 +1599,43 @@ __device__ __forceinline__ void dbscan2(const float* __restrict__ z, int ld, int
   }
   __syncthreads();
   // ---- 1. bucket of each point of the slice, counts, radius range.  The
-  //    count atomics (one per warp and bucket, on the instance's table in
-  //    global memory) also give each point its offset inside its bucket,
-  //    kept in w.core until the core flags replace it.
+  //    counts are taken per CTA in shared memory (a point's offset inside
+  //    its bucket among the slice's points, kept in w.core until the core
+  //    flags replace it); then one global atomic per occupied bucket adds the
+  //    CTA's count to the instance's table and returns the CTA's base in the
+  //    bucket, kept in the first kAngBuckets ints of shared memory (the
+  //    angular method's scatter adds it; its boundary list reuses the space
+  //    later).
+  int* lbase = smem;
+  for (int b = tid; b < kAngBuckets; b += blockDim.x) lbase[b] = 0;
+  __syncthreads();
   {
     float rmn = INFINITY, rmx = 0.f;
     bool bad = false;
-    for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
-      const int i = b0 + tid;
-      int b = -1;
-      if (i < i1) {
-        const float x = z[i], y = z[(size_t)ld + i];
-        bad |= !(x >= -1.0f && x <= 1.0f && y >= -1.0f && y <= 1.0f);
-        b = ang_bucket(x, y);
-        w.cell[i] = b;
-        const float r2 = x * x + y * y;
-        rmn = fminf(rmn, r2);
-        rmx = fmaxf(rmx, r2);
+    // two points per thread and step: their loads, then their count atomics,
+    // in flight together
+    const int B = blockDim.x;
+    for (int b0 = i0; b0 < i1; b0 += 2 * B) {
+      float xs[2] = {0.f, 0.f}, ys[2] = {0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = b0 + u * B + tid;
+        if (i < i1) { xs[u] = z[i]; ys[u] = z[(size_t)ld + i]; }
       }
-      const unsigned peers = __match_any_sync(FULL, b);
-      const int leader = __ffs(peers) - 1;
-      int base = 0;
-      if (b >= 0 && lane == leader) base = atomicAdd(&w.ahist[b], __popc(peers));
-      base = __shfl_sync(FULL, base, leader);
-      if (b >= 0) w.core[i] = base + __popc(peers & ((1u << lane) - 1u));
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = b0 + u * B + tid;
+        if (i < i1) {
+          const float x = xs[u], y = ys[u];
+          bad |= !(x >= -1.0f && x <= 1.0f && y >= -1.0f && y <= 1.0f);
+          const int b = ang_bucket(x, y);
+          w.cell[i] = b;
+          w.core[i] = atomicAdd(&lbase[b], 1);
+          const float r2 = x * x + y * y;
+          rmn = fminf(rmn, r2);
+          rmx = fmaxf(rmx, r2);
+        }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1502,6 +1647,17 @@ __device__ __forceinline__ void dbscan2(const float* __restrict__ z, int ld, int
       atomicMax(&s_rmax, __float_as_uint(rmx));
     }
     if (bad) s_bad = 1;
+  }
+  __syncthreads();
+  {
+    int c[kAngBuckets / kBlock], bs[kAngBuckets / kBlock];
+#pragma unroll
+    for (int q = 0; q < kAngBuckets / kBlock; ++q) {
+      c[q] = lbase[tid + q * kBlock];
+      bs[q] = c[q] > 0 ? atomicAdd(&w.ahist[tid + q * kBlock], c[q]) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kAngBuckets / kBlock; ++q) lbase[tid + q * kBlock] = bs[q];
   }
   cluster.sync();   // (1) every CTA's counts and radius range (the table is complete)
   if (cyc && tid == 0 && rank == 0) cyc[1] = clock64();
@@ -1662,11 +1818,23 @@ struct SelSmem {
   unsigned int accM[kWin];
   int lk[kSparseMax];
   float le[kSparseMax];
+  // the fused kernel's rank 0: the sorted list, the nominal before and after
+  // the listed update, and what the finalize needs, read at the start of the
+  // selection so that the update and the finalize make no global round trip
+  int sk[kSparseMax];
+  float se[kSparseMax];
+  float Us[kMaxT * kMaxM], Un[kMaxT * kMaxM];
+  float x0s[12];
+  ce_mppi_diag dg;
+  unsigned long long ctr;
+  float invZ;
+  int nnz;
 };
 
 // fused: called after the DBSCAN stage in the same kernel; with few nonzero
 // weights rank 0 then also applies the update and finalizes the replan.
-__device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const InstDesc& d, int inst);
+__device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const InstDesc& d, int inst,
+                                                       SelSmem& sm);
 __device__ void finalize(const InstDesc& d, const Req& r);
 
 __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool fused) {
@@ -1690,6 +1858,35 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   const int nV = ctl->nV, M = ctl->M;
   int sel = -1, dynamic = 0;
   if (tid == 0) { lcount = 0; lnz = 0; }
+  if (fused && rank == 0) {
+    // (loads that complete while the selection runs)
+    const Req rq = req_of(a, inst);
+    for (int c = tid; c < d.T * d.m; c += blockDim.x) sm.Us[c] = d.U[c];
+    if (tid < d.n) sm.x0s[tid] = rq.x0[tid];
+    if (tid == 0) {
+      // every load first, then the stores (a store between them would hold
+      // the next load back until its own value arrived)
+      const int nC = ctl->nC, os = ctl->o_star, stt = ctl->status, ct = ctl->col_tests;
+      float pb[3], vo[3];
+      for (int i = 0; i < 3; ++i) { pb[i] = ctl->pbar[i]; vo[i] = ctl->v_obs[i]; }
+      const unsigned long long cr = *d.counter;
+      ce_mppi_diag& g = sm.dg;
+      g.n_col = nC; g.n_valid = nV; g.n_clusters = M; g.o_star = os; g.status = stt;
+      for (int i = 0; i < 3; ++i) { g.pbar[i] = pb[i]; g.v_obs[i] = vo[i]; }
+      g.col_tests = ct;
+      sm.ctr = cr;
+    }
+  }
+  // the weights of the rollouts outside the update set are zero; with a
+  // selection the window barriers below order these stores before the
+  // members' weights (and the list count's reset before other CTAs' adds),
+  // otherwise the barrier after this block does
+  const bool over_all0 = mode0 == CE_MODE_NOCOL || mode0 == CE_MODE_ALLCOL || mode0 == CE_MODE_MPPI;
+  if (!over_all0) {
+    const int chunk = (((K + CL - 1) / CL) + 31) & ~31;
+    const int kb = min(K, rank * chunk), ke = min(K, kb + chunk);
+    for (int k = kb + tid; k < ke; k += blockDim.x) d.w_k[k] = 0.f;
+  }
   if (mode0 == CE_MODE_STATIC) {
     // fixed-point scales: S in [-Smax, Smax], g in [-1, 1], at most nV terms
     const float sm = ctl->S_absmax_V;
@@ -1728,6 +1925,7 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
         aG[sl][0] = aG[sl][1] = aG[sl][2] = 0;
       }
       auto flush = [&](int sl) {
+        if (cl[sl] < 0) return;   // (an empty slot: warp-uniform)
         long long s = aS[sl], g0 = aG[sl][0], g1 = aG[sl][1], g2 = aG[sl][2];
         int nn = aN[sl];
 #pragma unroll
@@ -1739,7 +1937,7 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
           nn += __shfl_xor_sync(FULL, nn, o);
         }
         const uint32_t mk = __reduce_min_sync(FULL, aM[sl]);
-        if (lane == 0 && cl[sl] >= 0) {
+        if (lane == 0) {
           const int c = cl[sl] - w0;
           atomicAdd(&accS[c], (unsigned long long)s);
           atomicAdd(&accG[0][c], (unsigned long long)g0);
@@ -1773,23 +1971,18 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
         long long vS = 0, vG[3] = {0, 0, 0};
         uint32_t vM = 0xffffffffu;
         if (L >= w0 && L < w0 + kWin) {
-          vS = __float2ll_rn(ldexpf(Si, eS));
+          vS = f2ll_scaled(Si, eS);
           vM = float_key(Si);
 #pragma unroll
           for (int q = 0; q < 3; ++q)
-            if (q < p) vG[q] = __float2ll_rn(ldexpf(Gi[q], eG));
+            if (q < p) vG[q] = f2ll_scaled(Gi[q], eG);
         } else {
           L = -1;
         }
-        // accumulate the lanes whose label is cached; while some are not, flush
-        // the slots and load up to kSlots of the missing labels (each round
-        // retires at least one label, so at most 32 rounds)
-        auto cached = [&](int x) {
-          bool hit = false;
-#pragma unroll
-          for (int sl = 0; sl < kSlots; ++sl) hit |= (cl[sl] == x);
-          return hit;
-        };
+        // accumulate the lanes whose label is cached; while some are not,
+        // cache the first missing label in an empty slot (or in a slot
+        // flushed for it, in turn); each round retires at least one lane's
+        // label, so 33 rounds suffice
         bool done = L < 0;
         for (int round = 0; round <= 32; ++round) {
 #pragma unroll
@@ -1799,14 +1992,22 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
               aG[sl][0] += vG[0]; aG[sl][1] += vG[1]; aG[sl][2] += vG[2];
               done = true;
             }
-          if (!__any_sync(FULL, !done)) break;
+          const unsigned pend = __ballot_sync(FULL, !done);
+          if (!pend) break;
+          int vic = -1;
 #pragma unroll
-          for (int sl = 0; sl < kSlots; ++sl) flush(sl);
+          for (int sl = kSlots - 1; sl >= 0; --sl)
+            if (cl[sl] < 0) vic = sl;
+          if (vic < 0) {
+            vic = round % kSlots;
 #pragma unroll
-          for (int sl = 0; sl < kSlots; ++sl) {
-            const unsigned pend = __ballot_sync(FULL, !done && !cached(L));
-            if (pend) cl[sl] = __shfl_sync(FULL, L, __ffs(pend) - 1);
+            for (int sl = 0; sl < kSlots; ++sl)
+              if (sl == vic) flush(sl);
           }
+          const int Lm = __shfl_sync(FULL, L, __ffs(pend) - 1);
+#pragma unroll
+          for (int sl = 0; sl < kSlots; ++sl)
+            if (sl == vic) cl[sl] = Lm;
         }
       }
 #pragma unroll
@@ -1859,28 +2060,41 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   const int Lz = (((dom + kPruneRanges - 1) / kPruneRanges) + 31) & ~31;
   const int m_z = kPruneRanges / (CL * nw);
   const int v0 = (rank * nw + wid) * m_z;
-  if (!over_all) {
-    const int chunk = (((K + CL - 1) / CL) + 31) & ~31;
-    const int kb = min(K, rank * chunk), ke = min(K, kb + chunk);
-    for (int k = kb + tid; k < ke; k += blockDim.x) d.w_k[k] = 0.f;
-  }
-  cluster.sync();   // the zeros land before the members' weights
+  if (mode0 != CE_MODE_STATIC) cluster.sync();   // the zeros and the count's reset land first
   {
     const int zb = min(dom, v0 * Lz), ze = min(dom, zb + m_z * Lz);
     int jr = 0;
     float z = 0.f, zc = 0.f;
-#pragma unroll 4
+    // the loads of the next 32 positions are issued before this step's work
+    // (label, rollout index and cost together, members or not)
+    int nLab = -1, nIdx = 0;
+    float nS = 0.f;
+    auto wfetch = [&](int i) {
+      if (i < ze) {
+        if (over_all) {
+          nS = __ldg(d.S + i);
+        } else {
+          nLab = __ldg(d.label + i);
+          nIdx = __ldg(d.idxV + i);
+          nS = __ldg(d.Sv + i);
+        }
+      }
+    };
+    wfetch(zb + lane);
     for (int s0 = zb; s0 < ze; s0 += 32) {
       const int i = s0 + lane;
+      const int lab = nLab, kv = nIdx;
+      const float Sf = nS;
+      wfetch(s0 + 32 + lane);
       bool mem = false;
       int k = 0;
       float Sk = 0.f;
       if (i < ze) {
         if (over_all) {
-          mem = true; k = i; Sk = __ldg(d.S + i);
+          mem = true; k = i; Sk = Sf;
         } else {
-          mem = over_V || __ldg(d.label + i) == sel;
-          if (mem) { k = __ldg(d.idxV + i); Sk = __ldg(d.Sv + i); }
+          mem = over_V || lab == sel;
+          if (mem) { k = kv; Sk = Sf; }
         }
       }
       float e = 0.f;
@@ -1942,7 +2156,11 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
       ee = le[tid];
       for (int j = 0; j < nl; ++j) rk += lk[j] < kk;
     }
-    if (tid < nl) { d.nzk[rk] = kk; d.nze[rk] = ee; }
+    if (tid < nl) {
+      d.nzk[rk] = kk;
+      d.nze[rk] = ee;
+      if (fused) { sm.sk[rk] = kk; sm.se[rk] = ee; }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -1952,11 +2170,16 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
     ctl->S_min = smin;
     ctl->invZ = 1.0f / red[32];
     ctl->nnz = nl <= kSparseMax ? nl : -1;
+    if (fused) {
+      sm.invZ = 1.0f / red[32];
+      sm.nnz = nl <= kSparseMax ? nl : -1;
+      sm.dg.mode = mode; sm.dg.sel_label = sel; sm.dg.dynamic = dynamic; sm.dg.S_min = smin;
+    }
   }
   if (fused) {
     __syncthreads();
     // (a dense update is left to the tiled update kernel over the whole GPU)
-    if (nl <= kSparseMax) update_sparse_finalize(a, d, inst);
+    if (nl <= kSparseMax) update_sparse_finalize(a, d, inst, sm);
     if (tid == 0) ctl->dbcyc[14] = clock64();
   }
 }
@@ -1982,6 +2205,7 @@ __device__ void refuse_replan(const InstDesc& d, const Req& r) {
   if (threadIdx.x == 0) {
     if (r.diag) {
       ce_mppi_diag g;
+      memset(&g, 0, sizeof(g));
       g.mode = -1; g.n_col = 0; g.n_valid = 0; g.n_clusters = 0; g.sel_label = -1;
       g.o_star = -1; g.dynamic = 0; g.status = ctl->status; g.S_min = 0.f;
       for (int i = 0; i < 3; ++i) { g.pbar[i] = 0.f; g.v_obs[i] = 0.f; }
@@ -2026,6 +2250,23 @@ __device__ void finalize(const InstDesc& d, const Req& r);
 // Eq. 20 / Eq. 7: U_new[c] = U[c] + sum_k w_k eps'[c][k] (Kahan, fixed order),
 // then, in the last CTA of the instance, the outputs, the receding-horizon
 // shift of the nominal, x_next = f(x0, u_0), the diagnostics and the counter.
+// x <- f(x, u): one model step of the controller's own dynamics (the state
+// x_next handed back with the replan).
+__device__ __forceinline__ void step_model(const InstDesc& d, float* x, const float* u) {
+  const float dt = d.dt;
+  if (d.dyn == CE_DYN_DOUBLE_INT_2D) {
+    x[0] += x[2] * dt; x[1] += x[3] * dt; x[2] += u[0] * dt; x[3] += u[1] * dt;
+  } else if (d.dyn == CE_DYN_UNICYCLE) {
+    float sn, cs;
+    sincosf(x[2], &sn, &cs);
+    x[0] += u[0] * cs * dt; x[1] += u[0] * sn * dt; x[2] += u[1] * dt;
+  } else if (d.dyn == CE_DYN_ARM6_KIN) {
+    for (int i = 0; i < 6; ++i) x[i] += u[i] * dt;
+  } else {
+    for (int i = 0; i < 6; ++i) { x[i] += x[6 + i] * dt; x[6 + i] += u[i] * dt; }
+  }
+}
+
 __device__ void finalize(const InstDesc& d, const Req& r) {
   Ctl* ctl = d.ctl;
   const int T = d.T, m = d.m, TM = T * m;
@@ -2044,23 +2285,13 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
       float x[12], u[6];
       for (int i = 0; i < d.n; ++i) x[i] = r.x0[i];
       for (int i = 0; i < m; ++i) u[i] = __ldcg(d.Unew + i);
-      const float dt = d.dt;
-      if (d.dyn == CE_DYN_DOUBLE_INT_2D) {
-        x[0] += x[2] * dt; x[1] += x[3] * dt; x[2] += u[0] * dt; x[3] += u[1] * dt;
-      } else if (d.dyn == CE_DYN_UNICYCLE) {
-        float sn, cs;
-        sincosf(x[2], &sn, &cs);
-        x[0] += u[0] * cs * dt; x[1] += u[0] * sn * dt; x[2] += u[1] * dt;
-      } else if (d.dyn == CE_DYN_ARM6_KIN) {
-        for (int i = 0; i < 6; ++i) x[i] += u[i] * dt;
-      } else {
-        for (int i = 0; i < 6; ++i) { x[i] += x[6 + i] * dt; x[6 + i] += u[i] * dt; }
-      }
+      step_model(d, x, u);
       for (int i = 0; i < d.n; ++i) r.x_next[i] = x[i];
     }
     const unsigned long long c = *d.counter;
     if (r.diag) {
       ce_mppi_diag g;
+      memset(&g, 0, sizeof(g));
       g.mode = ctl->mode; g.n_col = ctl->nC; g.n_valid = ctl->nV; g.n_clusters = ctl->M;
       g.sel_label = ctl->sel; g.o_star = ctl->o_star; g.dynamic = ctl->dynamic;
       g.status = ctl->status; g.S_min = ctl->S_min;
@@ -2084,14 +2315,19 @@ __device__ void finalize(const InstDesc& d, const Req& r) {
 // (deterministic) and finalizes.
 // The fused per-instance kernel's update when at most kSparseMax weights are
 // nonzero (rank 0 of the cluster, all columns): U_new[c] = U[c] + (1/Z) sum_j
-// w_j eps'[c][k_j] over the list in ascending k (Kahan), then finalize.
+// w_j eps'[c][k_j] over the list in ascending k (Kahan), then the finalize --
+// the list, 1/Z, the nominal and the finalize's inputs from shared memory
+// (read at the start of the selection), U_new kept there too.
+__device__ void finalize_fused(const InstDesc& d, const Req& r, const SelSmem& sm);
 __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const InstDesc& d,
-                                                       int inst) {
+                                                       int inst, SelSmem& sm) {
   Ctl* ctl = d.ctl;
-  const int TM = d.T * d.m, nnz = ctl->nnz;
+  const int TM = d.T * d.m, nnz = sm.nnz;
   const bool arm = is_arm(d.dyn);
-  const float iz = ctl->invZ;
-  const unsigned long long ctr = *d.counter;
+  const float iz = sm.invZ;
+  const unsigned long long ctr = sm.ctr;
+  const int* nzk = sm.sk;
+  const float* nze = sm.se;
   // the products w_j eps'_j[c] of JB list entries at a time are formed by all
   // threads at once (independent loads, or one Philox block of four columns
   // per thread), then each column's thread adds them in list order (Kahan)
@@ -2100,15 +2336,15 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
   const int NB = (TM + 3) >> 2;   // Philox blocks of a rollout's columns
   const int per = regen ? NB : TM;   // threads per list entry
   const int JB = max(1, min(kUpdProdMax / max(TM, 1), (int)blockDim.x / max(per, 1)));
-  float s = 0.f, e = 0.f;   // column threadIdx.x (one pass) 
+  float s = 0.f, e = 0.f;   // column threadIdx.x (one pass)
   const bool one_pass = TM <= (int)blockDim.x && TM * JB <= kUpdProdMax;
   if (one_pass) {
     for (int j0 = 0; j0 < nnz; j0 += JB) {
       const int jn = min(JB, nnz - j0);
       if (regen) {
         for (int t = threadIdx.x; t < jn * NB; t += blockDim.x) {
-          const int jj = t / NB, b = t - jj * NB, k = d.nzk[j0 + jj];
-          const float wj = d.nze[j0 + jj];
+          const int jj = t / NB, b = t - jj * NB, k = nzk[j0 + jj];
+          const float wj = nze[j0 + jj];
           float x[4];
           eps_regen4(d, ctr, k, b, TM, x);
 #pragma unroll
@@ -2117,9 +2353,9 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
         }
       } else {
         for (int t = threadIdx.x; t < jn * TM; t += blockDim.x) {
-          const int jj = t / TM, c = t - jj * TM, k = d.nzk[j0 + jj];
+          const int jj = t / TM, c = t - jj * TM, k = nzk[j0 + jj];
           const float x = arm ? d.eps[(size_t)k * d.eps_ld_k + c] : d.eps[(size_t)c * d.eps_ld_c + k];
-          prod[t] = d.nze[j0 + jj] * x;
+          prod[t] = nze[j0 + jj] * x;
         }
       }
       __syncthreads();
@@ -2127,23 +2363,69 @@ __device__ __forceinline__ void update_sparse_finalize(const KArgs& a, const Ins
         for (int jj = 0; jj < jn; ++jj) kahan_add(s, e, prod[jj * TM + threadIdx.x]);
       __syncthreads();
     }
-    if ((int)threadIdx.x < TM) d.Unew[threadIdx.x] = d.U[threadIdx.x] + s * iz;
+    if ((int)threadIdx.x < TM) {
+      const float v = sm.Us[threadIdx.x] + s * iz;
+      sm.Un[threadIdx.x] = v;
+      d.Unew[threadIdx.x] = v;
+    }
   } else {
     for (int c = threadIdx.x; c < TM; c += blockDim.x) {
       float sc = 0.f, ec = 0.f;
       for (int j = 0; j < nnz; ++j) {
-        const int k = d.nzk[j];
+        const int k = nzk[j];
         const float x = d.regen ? eps_regen(d, ctr, k, c)
                         : arm   ? d.eps[(size_t)k * d.eps_ld_k + c]
                                 : d.eps[(size_t)c * d.eps_ld_c + k];
-        kahan_add(sc, ec, d.nze[j] * x);
+        kahan_add(sc, ec, nze[j] * x);
       }
-      d.Unew[c] = d.U[c] + sc * iz;
+      const float v = sm.Us[c] + sc * iz;
+      sm.Un[c] = v;
+      d.Unew[c] = v;
     }
   }
   __syncthreads();
-  finalize(d, req_of(a, inst));
+  finalize_fused(d, req_of(a, inst), sm);
   if (threadIdx.x == 0) ctl->updated = 1;
+}
+
+// The finalize of the fused kernel's rank 0 from shared memory: the outputs,
+// the receding-horizon shift, x_next = f(x0, u_0), the diagnostics (fields
+// read at the start of the selection; mode, c*, S_min from the selection) and
+// the counter.  The same values as finalize.
+__device__ void finalize_fused(const InstDesc& d, const Req& r, const SelSmem& sm) {
+  Ctl* ctl = d.ctl;
+  const int T = d.T, m = d.m, TM = T * m;
+  for (int c = threadIdx.x; c < TM; c += blockDim.x) {
+    if (r.u_out) r.u_out[c] = sm.Un[c];
+    const int j = c / m, dd = c - j * m;
+    const int src = j + 1 < T ? j + 1 : T - 1;
+    d.U[c] = sm.Un[src * m + dd];
+  }
+  if (threadIdx.x == 0) {
+    if (r.x_next) {
+      float x[12], u[6];
+      for (int i = 0; i < d.n; ++i) x[i] = sm.x0s[i];
+      for (int i = 0; i < m; ++i) u[i] = sm.Un[i];
+      step_model(d, x, u);
+      for (int i = 0; i < d.n; ++i) r.x_next[i] = x[i];
+    }
+    const unsigned long long c = sm.ctr;
+    if (r.diag) {
+      const ce_mppi_diag& f = sm.dg;
+      ce_mppi_diag g;
+      memset(&g, 0, sizeof(g));   // (padding bytes too: the outputs are compared bitwise)
+      g.mode = f.mode; g.n_col = f.n_col; g.n_valid = f.n_valid; g.n_clusters = f.n_clusters;
+      g.sel_label = f.sel_label; g.o_star = f.o_star; g.dynamic = f.dynamic;
+      g.status = f.status; g.S_min = f.S_min;
+      for (int i = 0; i < 3; ++i) { g.pbar[i] = f.pbar[i]; g.v_obs[i] = f.v_obs[i]; }
+      g.counter = c;
+      g.col_tests = f.col_tests;
+      *r.diag = g;
+    }
+    ctl->counter_used = c;
+    *d.counter = c + 1;
+    ctl->done = 0u;
+  }
 }
 
 __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
