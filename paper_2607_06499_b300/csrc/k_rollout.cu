@@ -236,9 +236,11 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   }
   for (int i = threadIdx.x; i < T * d.m; i += blockDim.x) Us[i] = d.U[i];
   __syncthreads();
-  // CTA-uniform: a copy that did not land ends the CTA's work (no further
-  // copies on this barrier; one more bounded wait for it before the exit)
-  bool ok = __syncthreads_and(mbar_wait(&bar, phase));
+  // A copy that did not land in time gives the replan up (TIMEOUT; the later
+  // kernels refuse it): the thread's rollout is left out, no further copy is
+  // issued on this barrier, and the thread waits once more (bounded) for the
+  // copy that may still be landing before the CTA leaves.
+  bool ok = mbar_wait(&bar, phase);
   uint32_t pend = phase;
   phase ^= 1u;
   const bool all = whole != 0;
@@ -262,21 +264,23 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   int j = 0;
   // runs of rows [ja, jb): step j tests row j + 1; row 0 only with check_j0
-  for (int ja = 0; ok && ja <= T;) {
+  for (int ja = 0; ja <= T;) {
     int jb = T + 1;
     if (!all) {
+      // (large tables) the CTA agrees that every copy so far has landed
+      // before the next one is issued; the previous run's entries are no
+      // longer read
+      if (!__syncthreads_and(ok)) break;
       jb = ja + 1;
       while (jb <= T && off[jb + 1] - off[ja] <= cap_e) ++jb;
-      __syncthreads();   // the previous run's entries are no longer read
       if (threadIdx.x == 0) {
         const uint32_t bytes = (uint32_t)(off[jb] - off[ja]) * 16u;
         mbar_expect_tx(&bar, bytes);
         if (bytes > 0) bulk_g2s((void*)buf, gent + off[ja], bytes, &bar);
       }
-      ok = __syncthreads_and(mbar_wait(&bar, phase));
+      ok = mbar_wait(&bar, phase);
       pend = phase;
       phase ^= 1u;
-      if (!ok) break;
     }
     const int base = all ? 0 : off[ja];
     if (ja == 0 && d.check_j0 && act) {
@@ -355,10 +359,10 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
     ja = jb;
   }
   if (!ok) {
-    if (threadIdx.x == 0) give_up_replan(d.ctl);
+    give_up_replan(d.ctl);
     mbar_wait(&bar, pend);
   }
-  if (act && ok) {
+  if (act) {
     if (DYN == 0) {
       const float ex = s0 - g0, ey = s1 - g1;
       kahan_add(S, Sc, w2 * (ex * ex + ey * ey));
