@@ -308,29 +308,7 @@ __device__ __forceinline__ void raise_status(Ctl* c, int code) { atomicCAS(&c->s
 
 // Task positions as 32.32 fixed point: sums over any number of rollouts are
 // exact, so they do not depend on the order the atomics land in.
-// x 2^e rounded to the nearest integer (ties to even) as int64, by integer
-// operations only: the value of __float2ll_rn(ldexpf(x, e)) whenever
-// |x 2^e| < 2^62 (the 64-bit float-to-integer conversion runs at a low rate
-// on this GPU).
-__device__ __forceinline__ long long f2ll_scaled(float x, int e) {
-  const unsigned u = __float_as_uint(x);
-  const int ex = (int)((u >> 23) & 0xffu);
-  const long long m = (long long)((u & 0x7fffffu) | (ex ? 0x800000u : 0u));
-  const int sh = (ex ? ex : 1) - 150 + e;   // x 2^e = m 2^sh
-  long long v;
-  if (sh >= 0) {
-    v = m << sh;
-  } else if (sh <= -26) {
-    v = 0;   // m 2^sh < 1/4
-  } else {
-    const int t = -sh;
-    const long long q = m >> t, r = m & ((1ll << t) - 1), half = 1ll << (t - 1);
-    v = q + ((r > half || (r == half && (q & 1))) ? 1 : 0);
-  }
-  return (u >> 31) ? -v : v;
-}
-
-__device__ __forceinline__ long long pos_fixed(float v) { return f2ll_scaled(v, 32); }
+__device__ __forceinline__ long long pos_fixed(float v) { return __float2ll_rn(v * 4294967296.0f); }
 constexpr float kPosFixedInv = 2.3283064365386963e-10f;   // 2^-32
 
 // ---------------------------------------------------------------- reductions

@@ -1971,11 +1971,11 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
         long long vS = 0, vG[3] = {0, 0, 0};
         uint32_t vM = 0xffffffffu;
         if (L >= w0 && L < w0 + kWin) {
-          vS = f2ll_scaled(Si, eS);
+          vS = __float2ll_rn(ldexpf(Si, eS));
           vM = float_key(Si);
 #pragma unroll
           for (int q = 0; q < 3; ++q)
-            if (q < p) vG[q] = f2ll_scaled(Gi[q], eG);
+            if (q < p) vG[q] = __float2ll_rn(ldexpf(Gi[q], eG));
         } else {
           L = -1;
         }
