@@ -306,6 +306,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ void raise_status(Ctl* c, int code) { atomicCAS(&c->status, 0, code); }
 
+// Programmatic dependent launch of the rollout kernel after the track kernel
+// in the same stream: the track kernel lets the dependent grid be scheduled
+// once its work is written out; the rollout kernel waits, before it reads
+// anything the track kernel writes, until that grid has completed and its
+// writes are visible (at once when its launch has no such dependency).
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Task positions as 32.32 fixed point: sums over any number of rollouts are
 // exact, so they do not depend on the order the atomics land in.
 __device__ __forceinline__ long long pos_fixed(float v) { return __float2ll_rn(v * 4294967296.0f); }

@@ -74,6 +74,7 @@ __global__ void k_tracks(KArgs a) {
     }
     for (int j = threadIdx.x; j <= T; j += blockDim.x) counts[j] = n_obs;
     if (threadIdx.x == 0) d.ctl->col_tests = T * n_obs;
+    pdl_trigger();
     return;
   }
   const float x0 = r.x0[0], y0 = r.x0[1];
@@ -160,6 +161,7 @@ __global__ void k_tracks(KArgs a) {
   for (int j = threadIdx.x; j <= T + 1; j += blockDim.x) off[j] = roff[j];
   // obstacle tests of a rollout at steps 1..T (row 0 only with check_j0)
   if (threadIdx.x == 0) d.ctl->col_tests = roff[T + 1] - roff[1];
+  pdl_trigger();
 }
 
 // A rollout CTA whose copy of the track table did not land in time: the
@@ -177,12 +179,13 @@ __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float
                                              float* Us, uint64_t* bar) {
   const uint32_t bytes = n_obs > 0 ? (uint32_t)track_bytes(d.T, n_obs) : 0u;
   if (threadIdx.x == 0 && bytes > 0) mbar_init(bar, 1);
+  for (int i = threadIdx.x; i < d.T * d.m; i += blockDim.x) Us[i] = d.U[i];
+  pdl_wait();   // (the nominal is the previous replan's; the table is the track kernel's)
   __syncthreads();
   if (threadIdx.x == 0 && bytes > 0) {
     mbar_expect_tx(bar, bytes);
     bulk_g2s(trk, d.tracks, bytes, bar);
   }
-  for (int i = threadIdx.x; i < d.T * d.m; i += blockDim.x) Us[i] = d.U[i];
   // the CTA decides together: on a timeout the copy may still be landing, so
   // every thread waits once more (bounded) before the CTA leaves
   const bool ok = __syncthreads_and(bytes == 0 || mbar_wait(bar, 0));
@@ -224,6 +227,8 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(cap_b));
   const int cap_e = (int)((cap_b - us_bytes - hdr) / 16u);
   uint32_t phase = 0;
+  for (int i = threadIdx.x; i < T * d.m; i += blockDim.x) Us[i] = d.U[i];
+  pdl_wait();   // (the nominal is the previous replan's; the table is the track kernel's)
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     const int tot = reinterpret_cast<const int*>(d.tracks)[T + 1];
@@ -234,7 +239,6 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
     bulk_g2s(smem_raw + us_bytes, d.tracks, bytes, &bar);
     whole = all;
   }
-  for (int i = threadIdx.x; i < T * d.m; i += blockDim.x) Us[i] = d.U[i];
   __syncthreads();
   // A copy that did not land in time gives the replan up (TIMEOUT; the later
   // kernels refuse it): the thread's rollout is left out, no further copy is
@@ -653,15 +657,33 @@ void configure_rollout() {
                        kMaxSmemTracks + 8192);
 }
 
+// The rollout kernels are launched as programmatic dependents of the track
+// kernel that precedes them in the stream (see pdl_wait).
+template <typename K>
+static void launch_dependent(K kern, int grid, int block, int smem, cudaStream_t s,
+                             const KArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s) {
   if (dyn == CE_DYN_DOUBLE_INT_2D)
-    k_rollout2d<0><<<a.n_tiles, kRolloutThreads, smem_bytes, s>>>(a);
+    launch_dependent(k_rollout2d<0>, a.n_tiles, kRolloutThreads, smem_bytes, s, a);
   else if (dyn == CE_DYN_UNICYCLE)
-    k_rollout2d<1><<<a.n_tiles, kRolloutThreads, smem_bytes, s>>>(a);
+    launch_dependent(k_rollout2d<1>, a.n_tiles, kRolloutThreads, smem_bytes, s, a);
   else if (dyn == CE_DYN_ARM6_KIN)
-    k_rollout_arm<false><<<a.n_tiles, kArmWarps * 32, smem_bytes, s>>>(a);
+    launch_dependent(k_rollout_arm<false>, a.n_tiles, kArmWarps * 32, smem_bytes, s, a);
   else
-    k_rollout_arm<true><<<a.n_tiles, kArmWarps * 32, smem_bytes, s>>>(a);
+    launch_dependent(k_rollout_arm<true>, a.n_tiles, kArmWarps * 32, smem_bytes, s, a);
 }
 
 void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
