@@ -41,18 +41,40 @@ __global__ void k_tracks(KArgs a) {
     d.ctl->updated = 0;
     d.ctl->nnz_all = 0;
   }
+  // 2-D robots: newest position, velocity and collision radius of the first
+  // obstacles, staged in shared memory (their loads in flight together with
+  // the input check's first ones)
+  constexpr int kObsSmem = 1024;
+  __shared__ float4 opv[kObsSmem];
+  __shared__ float orr[kObsSmem];
+  auto obstacle = [&](int o, float4* pv, float* R) {
+    const float* newest = h + ((size_t)(H - 1) * n_obs + o) * 2;
+    const float* oldest = h + (size_t)o * 2;
+    *pv = make_float4(newest[0], newest[1], (newest[0] - oldest[0]) * inv,
+                      (newest[1] - oldest[1]) * inv);
+    *R = r.obs_radius[o] + d.robot_radius;
+  };
+  const bool arm = is_arm(d.dyn);
   {
     // device-buffer inputs are not seen by the host: a NaN or infinity in x0,
     // the observation window or the radii (or a negative radius) is reported
     // as INVALID_ARG in the replan's status, and the replan is refused (the
     // later stages leave the nominal and the counter as they are)
     const int nh = H * n_obs * p, tot = d.n + nh + n_obs;
-    bool bad = false;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const float v = i < d.n ? r.x0[i] : i < d.n + nh ? h[i - d.n] : r.obs_radius[i - d.n - nh];
+    auto input = [&](int i) {
+      return i < d.n ? r.x0[i] : i < d.n + nh ? h[i - d.n] : r.obs_radius[i - d.n - nh];
+    };
+    const int i0 = threadIdx.x;
+    const float v0 = i0 < tot ? input(i0) : 0.f;
+    if (!arm)
+      for (int o = threadIdx.x; o < min(n_obs, kObsSmem); o += blockDim.x)
+        obstacle(o, &opv[o], &orr[o]);
+    bool bad = i0 < tot && (!isfinite(v0) || (i0 >= d.n + nh && !(v0 >= 0.0f)));
+    for (int i = i0 + blockDim.x; i < tot; i += blockDim.x) {
+      const float v = input(i);
       bad |= !isfinite(v) || (i >= d.n + nh && !(v >= 0.0f));
     }
-    const bool any_bad = __syncthreads_or(bad);
+    const bool any_bad = __syncthreads_or(bad);   // (also orders the staged obstacles)
     if (threadIdx.x == 0) {
       d.ctl->rejected = any_bad ? 1 : 0;
       if (any_bad) raise_status(d.ctl, CE_MPPI_ERR_INVALID_ARG);
@@ -60,7 +82,7 @@ __global__ void k_tracks(KArgs a) {
   }
   // per-obstacle sums of the pruning stage, filled by the rollout kernel
   for (int e = threadIdx.x; e < 4 * n_obs; e += blockDim.x) d.osum[e] = 0;
-  if (is_arm(d.dyn)) {
+  if (arm) {
     const int total = (T + 1) * n_obs;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int j = e / n_obs, o = e - j * n_obs;
@@ -84,19 +106,6 @@ __global__ void k_tracks(KArgs a) {
   const float m1 = fmaxf(fabsf(d.u_min[1]), fabsf(d.u_max[1]));
   const float amax = sqrtf(m0 * m0 + m1 * m1);
   __shared__ int roff[kMaxT + 2];
-  // newest position, velocity and collision radius of the first obstacles
-  constexpr int kObsSmem = 1024;
-  __shared__ float4 opv[kObsSmem];
-  __shared__ float orr[kObsSmem];
-  auto obstacle = [&](int o, float4* pv, float* R) {
-    const float* newest = h + ((size_t)(H - 1) * n_obs + o) * 2;
-    const float* oldest = h + (size_t)o * 2;
-    *pv = make_float4(newest[0], newest[1], (newest[0] - oldest[0]) * inv,
-                      (newest[1] - oldest[1]) * inv);
-    *R = r.obs_radius[o] + d.robot_radius;
-  };
-  for (int o = threadIdx.x; o < min(n_obs, kObsSmem); o += blockDim.x) obstacle(o, &opv[o], &orr[o]);
-  __syncthreads();
   int* off = reinterpret_cast<int*>(d.tracks);
   float4* ent = reinterpret_cast<float4*>(reinterpret_cast<char*>(d.tracks) + track_hdr_bytes(T));
   // pass 0 counts the kept entries of each row, pass 1 writes them
