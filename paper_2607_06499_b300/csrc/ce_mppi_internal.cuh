@@ -308,9 +308,9 @@ __device__ __forceinline__ void raise_status(Ctl* c, int code) { atomicCAS(&c->s
 
 // Programmatic dependent launch of the rollout kernel after the track kernel
 // in the same stream: the track kernel lets the dependent grid be scheduled
-// once its work is written out; the rollout kernel waits, before it reads
-// anything the track kernel writes, until that grid has completed and its
-// writes are visible (at once when its launch has no such dependency).
+// early; the rollout kernel waits, before it reads anything the track kernel
+// writes, until that grid has completed and its writes are visible (at once
+// when its launch has no such dependency).
 __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
