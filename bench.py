@@ -586,6 +586,14 @@ def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: 
         bB.set_post_ctas(args.pipe_post_ctas)
         side = torch.cuda.Stream()
         graph = torch.cuda.CUDAGraph()
+        # each half's rollouts wait for the other half's clustering kernel to
+        # have begun on all its CTAs (launch-completion events), so that the
+        # clustering CTAs, a whole SM each, are never left behind the rollouts
+        started = [None, None]
+        if getattr(args, "post_first", 1):
+            started = [torch.cuda.Event(enable_timing=False) for _ in range(2)]
+            for e in started:
+                e.record(stream)   # (creates the event)
         torch.cuda.synchronize()
         with torch.cuda.graph(graph):
             main_s = torch.cuda.current_stream()
@@ -599,11 +607,15 @@ def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: 
                 bA.run_part(0, side)
                 bA.run_part(1, side)
             else:
-                bB.run_part(1, main_s)
+                bB.run_part(1, main_s, started=started[1])
+                if started[1] is not None:
+                    side.wait_event(started[1])
                 bA.run_part(0, side)
                 main_s.wait_stream(side)
                 side.wait_stream(main_s)
-                bA.run_part(1, main_s)
+                bA.run_part(1, main_s, started=started[0])
+                if started[0] is not None:
+                    side.wait_event(started[0])
                 bB.run_part(0, side)
             main_s.wait_stream(side)
         torch.cuda.synchronize()
@@ -726,6 +738,9 @@ def main() -> None:
                     help="1: two halves of the episodes software-pipelined in one graph, "
                          "joined after each phase; 2: the same halves as two chains "
                          "joined once per step")
+    ap.add_argument("--post-first", type=int, default=1, choices=[0, 1],
+                    help="1: each half's tracks + rollouts wait on the other half's "
+                         "clustering kernel having begun on all its CTAs")
     ap.add_argument("--pipe-post-ctas", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="clustering-kernel CTAs per instance in the pipelined halves "
                          "(0: from the occupancy, as if each half ran alone)")
@@ -900,7 +915,8 @@ def main() -> None:
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": bench_config(args.workload, world, regen),
-        "run": {"pipeline": args.pipeline, "pipe_post_ctas": args.pipe_post_ctas,
+        "run": {"pipeline": args.pipeline, "post_first": args.post_first,
+                "pipe_post_ctas": args.pipe_post_ctas,
                 "batch_config": res["batch_config"],
                 "l2": "flushed between timed steps (256 MB write)"},
         "replans_per_s": res["replans_per_s"],

@@ -263,6 +263,18 @@ ce_status_t ce_mppi_batch_run_host(ce_mppi_batch* b, const float* x0s, const flo
  * example on two streams inside the caller's own CUDA graph.  The results are
  * bitwise those of ce_mppi_batch_run.  Errors: INVALID_ARG, CUDA.            */
 ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream);
+/* ce_mppi_batch_run_part with, for part 1, an event `started` (a cudaEvent_t
+ * created with cudaEventDisableTiming, or NULL) that the clustering kernel's
+ * launch records as its launch-completion event: it fires once every CTA of
+ * that kernel has begun execution (best effort: the runtime may fire it only
+ * when the kernel completes).  A stream that waits on it before launching the
+ * other half's rollouts lets the clustering kernel's CTAs, each of which
+ * needs a whole SM, take their SMs first; without it, whichever grid the
+ * device dispatches first may fill every SM and the two run one after the
+ * other.  Recorded in stream capture it becomes a launch-completion edge of
+ * the caller's graph.  `started` must be NULL for part 0.  The results do not
+ * depend on it.  Errors: INVALID_ARG, CUDA.                                  */
+ce_status_t ce_mppi_batch_run_part_ev(ce_mppi_batch* b, int part, void* stream, void* started);
 /* Run one replan of the batch stage by stage (no graph) with CUDA events
  * between the stage launches, wait for it, and write the device time of each
  * stage in milliseconds to stage_ms[6]: tracks, rollouts, prune + reference

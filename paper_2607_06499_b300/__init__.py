@@ -73,7 +73,7 @@ EXPORTS = (
     "ce_mppi_create", "ce_mppi_destroy", "ce_mppi_set_nominal", "ce_mppi_get_nominal",
     "ce_mppi_set_counter", "ce_mppi_get_counter", "ce_mppi_replan", "ce_mppi_check_inputs",
     "ce_mppi_replan_dev",
-    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_config",
+    "ce_mppi_batch_create", "ce_mppi_batch_run", "ce_mppi_batch_run_part", "ce_mppi_batch_run_part_ev", "ce_mppi_batch_config",
     "ce_mppi_batch_create_host", "ce_mppi_batch_run_host",
     "ce_mppi_batch_set_post_ctas", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_batch_create_host.argtypes = [C.POINTER(vp), vp, i, vp, i, i, C.POINTER(vp)]
         L.ce_mppi_batch_run_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.ce_mppi_batch_run_part.argtypes = [vp, i, vp]
+        L.ce_mppi_batch_run_part_ev.argtypes = [vp, i, vp, vp]
         L.ce_mppi_batch_config.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
         L.ce_mppi_batch_set_post_ctas.argtypes = [vp, i]
         L.ce_mppi_batch_profile.argtypes = [vp, C.POINTER(C.c_float)]
@@ -305,10 +306,18 @@ class Batch:
         graph (0: from the device occupancy, as if the batch ran alone)."""
         _check(lib().ce_mppi_batch_set_post_ctas(self.b, int(n)))
 
-    def run_part(self, part: int, stream=None):
-        """Half a replan (0: tracks + rollouts, 1: clustering + update) on stream."""
+    def run_part(self, part: int, stream=None, started=None):
+        """Half a replan (0: tracks + rollouts, 1: clustering + update) on stream.
+        started (part 1): a torch.cuda.Event(enable_timing=False) that fires once
+        every CTA of the clustering kernel has begun execution (the event must
+        exist: recorded once before)."""
         s = 0 if stream is None else _stream_ptr(stream)
-        _check(lib().ce_mppi_batch_run_part(self.b, int(part), C.c_void_p(s)))
+        ev = 0
+        if started is not None:
+            ev = started.cuda_event
+            if not ev:
+                raise ValueError("started: the event has not been created (record it once)")
+        _check(lib().ce_mppi_batch_run_part_ev(self.b, int(part), C.c_void_p(s), C.c_void_p(ev)))
 
     STAGES = ("tracks", "rollout", "prune", "dbscan", "select", "update")
 

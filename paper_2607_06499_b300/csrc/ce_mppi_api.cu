@@ -863,8 +863,14 @@ ce_status_t ce_mppi_batch_run(ce_mppi_batch* b) {
 }
 
 ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
+  return ce_mppi_batch_run_part_ev(b, part, stream, nullptr);
+}
+
+ce_status_t ce_mppi_batch_run_part_ev(ce_mppi_batch* b, int part, void* stream, void* started) {
   if (!b) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL batch");
   if (part != 0 && part != 1) return fail(CE_MPPI_ERR_INVALID_ARG, "part must be 0 or 1");
+  if (part == 0 && started) return fail(CE_MPPI_ERR_INVALID_ARG, "started event is for part 1");
+  cudaEvent_t ev = static_cast<cudaEvent_t>(started);
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->stream;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -879,9 +885,9 @@ ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
     a.n_tiles = b->n_roll;
     launch_rollout(b->dyn, a, b->smem_roll, s);
   } else {
-    const bool fused = launch_post(a, b->max_cells, s);   // (as in a whole replan's chain)
+    const bool fused = launch_post(a, b->max_cells, s, ev);   // (as in a whole replan's chain)
     if (!fused) {
-      launch_prune(a, s);
+      launch_prune(a, s, ev);
       launch_dbscan(a, b->max_cells, s);
       launch_select(a, s);
     }

@@ -406,12 +406,13 @@ __device__ __forceinline__ float rot_angle(const float R[9], const float* Rg) {
 // Host-side launchers of each stage (defined in the .cu files).
 void launch_tracks(const KArgs& a, cudaStream_t s);
 void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s);
-void launch_prune(const KArgs& a, cudaStream_t s);
+// (started: an optional launch-completion event of the launch)
+void launch_prune(const KArgs& a, cudaStream_t s, cudaEvent_t started = nullptr);
 void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s);
 void launch_select(const KArgs& a, cudaStream_t s);
 // prune + DBSCAN + selection (+ the update with few nonzero weights) as one
 // clustered launch; false when the shared memory does not allow it
-bool launch_post(const KArgs& a, int max_cells, cudaStream_t s);
+bool launch_post(const KArgs& a, int max_cells, cudaStream_t s, cudaEvent_t started = nullptr);
 void launch_update(const KArgs& a, cudaStream_t s);
 void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
                    unsigned int* out, cudaStream_t s);

@@ -2683,25 +2683,35 @@ static int fit_class(int nc) { return nc <= kFitCells[0] ? 0 : nc <= kFitCells[1
 
 template <typename... Args>
 static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int threads, size_t smem,
-                             cudaStream_t s, Args... args) {
+                             cudaStream_t s, cudaEvent_t started, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_inst * cl));
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)cl;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute at[2];
+  unsigned n = 0;
+  if (cl > 1) {   // (one CTA per instance: no cluster)
+    at[n].id = cudaLaunchAttributeClusterDimension;
+    at[n].val.clusterDim.x = (unsigned)cl;
+    at[n].val.clusterDim.y = 1;
+    at[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  if (started) {   // fires once every CTA has begun execution
+    at[n].id = cudaLaunchAttributeLaunchCompletionEvent;
+    at[n].val.launchCompletionEvent.event = started;
+    at[n].val.launchCompletionEvent.flags = 0;
+    ++n;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = cl > 1 ? 1 : 0;   // one CTA per instance: a plain launch
+  cfg.numAttrs = n;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-void launch_prune(const KArgs& a, cudaStream_t s) {
+void launch_prune(const KArgs& a, cudaStream_t s, cudaEvent_t started) {
   const int cl = cluster_ctas(g_fit_prune, a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_prune, cl, a.n_inst, kBlock, 0, s, a);
+  launch_clustered(k_prune, cl, a.n_inst, kBlock, 0, s, started, a);
 }
 
 // (2-D sets may take the angular method, whose tables are kAngSmemInts ints)
@@ -2712,14 +2722,14 @@ static size_t dbscan_smem(int nc) {
 static ClusterFit g_fit_post[3];
 static size_t post_smem(int nc) { return std::max(dbscan_smem(nc), sizeof(SelSmem)); }
 
-bool launch_post(const KArgs& a, int max_cells, cudaStream_t s) {
+bool launch_post(const KArgs& a, int max_cells, cudaStream_t s, cudaEvent_t started) {
   if (max_cells > kMaxCells) return false;
   const int fc = fit_class(max_cells);
   const size_t smem = post_smem(kFitCells[fc]);   // the class's size (a fit was queried for it)
   const ClusterFit& f = g_fit_post[fc];
   if (f.max_active[0] == 0) return false;   // (the launch would not fit)
   const int cl = a.post_ctas > 0 ? a.post_ctas : cluster_ctas(f, a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, a);
+  launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, started, a);
   return true;
 }
 
@@ -2744,12 +2754,12 @@ void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s) {
   const int fc = fit_class(max_cells);
   const size_t smem = dbscan_smem(kFitCells[fc]);
   const int cl = cluster_ctas(g_fit_db[fc], a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, a);
+  launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, nullptr, a);
 }
 
 void launch_select(const KArgs& a, cudaStream_t s) {
   const int cl = cluster_ctas(g_fit_select, a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_select, cl, a.n_inst, kBlock, 0, s, a);
+  launch_clustered(k_select, cl, a.n_inst, kBlock, 0, s, nullptr, a);
 }
 
 void launch_update(const KArgs& a, cudaStream_t s) {
@@ -2774,7 +2784,7 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
   const int fc = fit_class(nc);
   const size_t smem = dbscan_smem(kFitCells[fc]);
   const int cl = cluster_ctas(g_fit_db[fc], 1);
-  launch_clustered(k_dbscan_standalone, cl, 1, kBlock, smem, s, z, n, ld, p, eps2, cell_inv, G, R,
+  launch_clustered(k_dbscan_standalone, cl, 1, kBlock, smem, s, nullptr, z, n, ld, p, eps2, cell_inv, G, R,
                    min_pts, labels, n_clusters, w);
 }
 

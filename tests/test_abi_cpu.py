@@ -115,6 +115,8 @@ def test_batch_run_part_rejects_bad_arguments():
     assert "NULL" in L.ce_mppi_last_error().decode()
     assert L.ce_mppi_batch_set_post_ctas(None, 4) == 1
     assert "NULL" in L.ce_mppi_last_error().decode()
+    assert L.ce_mppi_batch_run_part_ev(None, 1, None, None) == 1
+    assert "NULL" in L.ce_mppi_last_error().decode()
 
 
 def test_twelve_d_arm_dims_and_parameters_accepted_by_validation():

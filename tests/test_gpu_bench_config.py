@@ -66,15 +66,22 @@ def test_benchmark_configuration_against_the_oracle():
     bB = pkg.Batch(planners[HALF:], reqs[HALF:], use_graph=False)
     side = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
+    # (as in the benchmark: each half's rollouts wait for the other half's
+    # clustering kernel to have begun on all its CTAs)
+    started = [torch.cuda.Event(enable_timing=False) for _ in range(2)]
+    for e in started:
+        e.record()
     torch.cuda.synchronize()
     with torch.cuda.graph(graph):
         main = torch.cuda.current_stream()
         side.wait_stream(main)
-        bB.run_part(1, main)
+        bB.run_part(1, main, started=started[1])
+        side.wait_event(started[1])
         bA.run_part(0, side)
         main.wait_stream(side)
         side.wait_stream(main)
-        bA.run_part(1, main)
+        bA.run_part(1, main, started=started[0])
+        side.wait_event(started[0])
         bB.run_part(0, side)
         main.wait_stream(side)
     torch.cuda.synchronize()
