@@ -34,16 +34,28 @@ __global__ void k_tracks(KArgs a) {
   const InstDesc& d = desc_of(a, inst);
   const Req r = req_of(a, inst);
   const float* h = hist_of(r, d);
-  const int n_obs = r.n_obs, p = d.p, H = d.H, T = d.T;
+  // every parameter read into registers ahead of the kernel's first store
+  // (a later read would wait behind the stores it might alias)
+  const int n_obs = r.n_obs, p = d.p, H = d.H, T = d.T, dyn = d.dyn, dn = d.n;
   const float inv = H >= 2 ? 1.0f / ((float)(H - 1) * d.obs_dt) : 0.0f;
+  const float dt = d.dt, robot = d.robot_radius;
+  const float umin0 = d.u_min[0], umin1 = d.u_min[1], umax0 = d.u_max[0], umax1 = d.u_max[1];
+  Ctl* const ctl = d.ctl;
+  long long* const osum = d.osum;
+  float4* const tracks = d.tracks;
+  const bool arm = is_arm(dyn);
+  const bool di = dyn == CE_DYN_DOUBLE_INT_2D;
+  const float x0 = r.x0[0], y0 = r.x0[1];
+  const float vx0 = di ? r.x0[2] : 0.f;
+  const float vy0 = di ? r.x0[3] : 0.f;
   const int ts = track_stride(n_obs);
-  int* counts = track_counts(d.tracks, T, n_obs);
+  int* counts = track_counts(tracks, T, n_obs);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {   // a new replan: clear the control block's flags
-    d.ctl->status = 0;
-    d.ctl->done = 0u;
-    d.ctl->updated = 0;
-    d.ctl->nnz_all = 0;
+    ctl->status = 0;
+    ctl->done = 0u;
+    ctl->updated = 0;
+    ctl->nnz_all = 0;
   }
   // 2-D robots: newest position, velocity and collision radius of the first
   // obstacles, staged in shared memory (their loads in flight together with
@@ -56,70 +68,66 @@ __global__ void k_tracks(KArgs a) {
     const float* oldest = h + (size_t)o * 2;
     *pv = make_float4(newest[0], newest[1], (newest[0] - oldest[0]) * inv,
                       (newest[1] - oldest[1]) * inv);
-    *R = r.obs_radius[o] + d.robot_radius;
+    *R = r.obs_radius[o] + robot;
   };
-  const bool arm = is_arm(d.dyn);
   {
     // device-buffer inputs are not seen by the host: a NaN or infinity in x0,
     // the observation window or the radii (or a negative radius) is reported
     // as INVALID_ARG in the replan's status, and the replan is refused (the
     // later stages leave the nominal and the counter as they are)
-    const int nh = H * n_obs * p, tot = d.n + nh + n_obs;
+    const int nh = H * n_obs * p, tot = dn + nh + n_obs;
     auto input = [&](int i) {
-      return i < d.n ? r.x0[i] : i < d.n + nh ? h[i - d.n] : r.obs_radius[i - d.n - nh];
+      return i < dn ? r.x0[i] : i < dn + nh ? h[i - dn] : r.obs_radius[i - dn - nh];
     };
     const int i0 = threadIdx.x;
     const float v0 = i0 < tot ? input(i0) : 0.f;
     if (!arm)
       for (int o = threadIdx.x; o < min(n_obs, kObsSmem); o += blockDim.x)
         obstacle(o, &opv[o], &orr[o]);
-    bool bad = i0 < tot && (!isfinite(v0) || (i0 >= d.n + nh && !(v0 >= 0.0f)));
+    bool bad = i0 < tot && (!isfinite(v0) || (i0 >= dn + nh && !(v0 >= 0.0f)));
     for (int i = i0 + blockDim.x; i < tot; i += blockDim.x) {
       const float v = input(i);
-      bad |= !isfinite(v) || (i >= d.n + nh && !(v >= 0.0f));
+      bad |= !isfinite(v) || (i >= dn + nh && !(v >= 0.0f));
     }
     const bool any_bad = __syncthreads_or(bad);   // (also orders the staged obstacles)
     if (threadIdx.x == 0) {
-      d.ctl->rejected = any_bad ? 1 : 0;
-      if (any_bad) raise_status(d.ctl, CE_MPPI_ERR_INVALID_ARG);
+      ctl->rejected = any_bad ? 1 : 0;
+      if (any_bad) raise_status(ctl, CE_MPPI_ERR_INVALID_ARG);
     }
   }
   // per-obstacle sums of the pruning stage, filled by the rollout kernel
-  for (int e = threadIdx.x; e < 4 * n_obs; e += blockDim.x) d.osum[e] = 0;
+  for (int e = threadIdx.x; e < 4 * n_obs; e += blockDim.x) osum[e] = 0;
   if (arm) {
     const int total = (T + 1) * n_obs;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int j = e / n_obs, o = e - j * n_obs;
       const float* newest = h + ((size_t)(H - 1) * n_obs + o) * p;
       const float* oldest = h + (size_t)o * p;
-      const float tj = (float)j * d.dt;
+      const float tj = (float)j * dt;
       float c[3];
       for (int i = 0; i < 3; ++i) c[i] = newest[i] + ((newest[i] - oldest[i]) * inv) * tj;
-      const float R = r.obs_radius[o] + d.robot_radius;
-      d.tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R);
+      const float R = r.obs_radius[o] + robot;
+      tracks[(size_t)j * ts + o] = make_float4(c[0], c[1], c[2], R);
     }
     for (int j = threadIdx.x; j <= T; j += blockDim.x) counts[j] = n_obs;
-    if (threadIdx.x == 0) d.ctl->col_tests = T * n_obs;
+    if (threadIdx.x == 0) ctl->col_tests = T * n_obs;
     return;
   }
-  const float x0 = r.x0[0], y0 = r.x0[1];
-  const float vx0 = d.dyn == CE_DYN_DOUBLE_INT_2D ? r.x0[2] : 0.f;
-  const float vy0 = d.dyn == CE_DYN_DOUBLE_INT_2D ? r.x0[3] : 0.f;
-  const float m0 = fmaxf(fabsf(d.u_min[0]), fabsf(d.u_max[0]));
-  const float m1 = fmaxf(fabsf(d.u_min[1]), fabsf(d.u_max[1]));
+  const float m0 = fmaxf(fabsf(umin0), fabsf(umax0));
+  const float m1 = fmaxf(fabsf(umin1), fabsf(umax1));
   const float amax = sqrtf(m0 * m0 + m1 * m1);
   __shared__ int roff[kMaxT + 2];
-  int* off = reinterpret_cast<int*>(d.tracks);
-  float4* ent = reinterpret_cast<float4*>(reinterpret_cast<char*>(d.tracks) + track_hdr_bytes(T));
+  int* off = reinterpret_cast<int*>(tracks);
+  float4* ent = reinterpret_cast<float4*>(reinterpret_cast<char*>(tracks) + track_hdr_bytes(T));
   // pass 0 counts the kept entries of each row, pass 1 writes them
   for (int pass = 0; pass < 2; ++pass) {
     for (int j = wid; j <= T; j += nw) {
-      const float tj = (float)j * d.dt;
+      const float tj = (float)j * dt;
       float cx = x0, cy = y0, rj;
-      if (d.dyn == CE_DYN_DOUBLE_INT_2D) {
+      if (di) {
         cx = x0 + tj * vx0;
         cy = y0 + tj * vy0;
-        rj = d.dt * d.dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
+        rj = dt * dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
       } else {
         rj = tj * m0;
       }
@@ -172,7 +180,7 @@ __global__ void k_tracks(KArgs a) {
   }
   for (int j = threadIdx.x; j <= T + 1; j += blockDim.x) off[j] = roff[j];
   // obstacle tests of a rollout at steps 1..T (row 0 only with check_j0)
-  if (threadIdx.x == 0) d.ctl->col_tests = roff[T + 1] - roff[1];
+  if (threadIdx.x == 0) ctl->col_tests = roff[T + 1] - roff[1];
 }
 
 // A rollout CTA whose copy of the track table did not land in time: the
