@@ -354,7 +354,12 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
       e_hi = off[jj + 2] - base;
       if (first < 0) {
         int h = n_obs;
-        for (int e = e_hi - 1; e >= e_lo; --e) {   // descending: the lowest index wins
+        // descending: the lowest index wins.  Unrolled by four (measured
+        // against one and two: 0.1565 and 0.1513 against 0.1480 ms per
+        // pipelined step over whole episodes, whose later rows hold more
+        // entries; a clamped four-wide body without a remainder loop: 0.172)
+#pragma unroll 4
+        for (int e = e_hi - 1; e >= e_lo; --e) {
           const float4 t = buf[e];
           const float dx = s0 - t.x, dy = s1 - t.y;
           h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
