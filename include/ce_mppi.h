@@ -378,12 +378,18 @@ ce_status_t ce_mppi_philox_dev(unsigned long long seed, unsigned long long count
 /* The first n standard normals of rollouts k < K: out[k][n]: normal i is
  * element i % 4 of block i / 4; Box-Muller on the uniforms ((w >> 9) + 1/2)
  * 2^-23 of the word pairs (w0,w1) and (w2,w3): r = sqrt(-2 ln u1),
- * (r cos 2 pi u2, r sin 2 pi u2).  FP32: the logarithm at full accuracy, the
+ * (r cos 2 pi u2, r sin 2 pi u2).  FP32: -2 ln u1 as ce_mppi_neg2ln_dev, the
  * sine and cosine from the special-function unit, so each normal is within
  * ~5e-6 of exact (absolute; the largest radius is 5.77).  These are the
  * normals the rollouts draw.                                                 */
 ce_status_t ce_mppi_normals_dev(unsigned long long seed, unsigned long long counter, int K,
                                 int n, float* out, void* stream);
+/* -2 ln u, the squared Box-Muller radius, for every uniform the rollouts can
+ * draw: out[m] for u = (m + 1/2) 2^-23, m = 0 .. 2^23 - 1 (out: 2^23 floats,
+ * device).  FP32: a Taylor series in u - 1 for u > 7/8, the special-function
+ * unit's base-2 logarithm elsewhere; relative error under 2^-20 (checked
+ * against the exact values).  Errors: INVALID_ARG (NULL out), CUDA.          */
+ce_status_t ce_mppi_neg2ln_dev(float* out, void* stream);
 /* DBSCAN (Sec. II-B2) of n points z stored as [p][ld] (SoA, p = 2 or 3):
  * neighbours when the FP32 sum of squared coordinate differences (coordinate
  * order, no fused multiply-add) is <= fl32(eps^2); core when at least min_pts

@@ -77,7 +77,7 @@ EXPORTS = (
     "ce_mppi_batch_create_host", "ce_mppi_batch_run_host",
     "ce_mppi_batch_set_post_ctas", "ce_mppi_batch_profile",
     "ce_mppi_batch_destroy", "ce_mppi_peek",
-    "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_dbscan_workspace_bytes",
+    "ce_mppi_philox_dev", "ce_mppi_normals_dev", "ce_mppi_neg2ln_dev", "ce_mppi_dbscan_workspace_bytes",
     "ce_mppi_dbscan_dev", "ce_mppi_dbscan_noalloc_dev", "ce_mppi_arm_fk", "ce_mppi_last_error",
     "ce_mppi_server_create", "ce_mppi_server_destroy", "ce_mppi_server_open",
     "ce_mppi_server_close", "ce_mppi_server_submit", "ce_mppi_server_submit_many",
@@ -119,6 +119,7 @@ def lib() -> C.CDLL:
         L.ce_mppi_peek.argtypes = [vp, i, vp, C.c_size_t]
         L.ce_mppi_philox_dev.argtypes = [u64, u64, i, i, vp, vp]
         L.ce_mppi_normals_dev.argtypes = [u64, u64, i, i, vp, vp]
+        L.ce_mppi_neg2ln_dev.argtypes = [vp, vp]
         L.ce_mppi_dbscan_workspace_bytes.argtypes = [i]
         L.ce_mppi_dbscan_workspace_bytes.restype = C.c_size_t
         L.ce_mppi_dbscan_dev.argtypes = [vp, i, i, i, f, i, vp, vp, vp, C.c_size_t, vp]
@@ -393,6 +394,11 @@ def philox_dev(seed: int, counter: int, K: int, nblk: int, out, stream=None):
 def normals_dev(seed: int, counter: int, K: int, n: int, out, stream=None):
     _check(lib().ce_mppi_normals_dev(seed, counter, K, n, out.data_ptr(),
                                      C.c_void_p(_stream_ptr(stream))))
+
+
+def neg2ln_dev(out, stream=None):
+    """-2 ln u for every uniform u = (m + 1/2) 2^-23 (out: 2^23 float32, device)."""
+    _check(lib().ce_mppi_neg2ln_dev(out.data_ptr(), C.c_void_p(_stream_ptr(stream))))
 
 
 def dbscan_dev(z, eps: float, min_pts: int, stream=None):

@@ -1141,6 +1141,13 @@ ce_status_t ce_mppi_normals_dev(unsigned long long seed, unsigned long long coun
   return CE_MPPI_OK;
 }
 
+ce_status_t ce_mppi_neg2ln_dev(float* out, void* stream) {
+  if (!out) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL output");
+  launch_neg2ln(out, static_cast<cudaStream_t>(stream));
+  CE_CUDA(cudaGetLastError());
+  return CE_MPPI_OK;
+}
+
 size_t ce_mppi_dbscan_workspace_bytes(int n) { return n < 0 ? 0 : dbscan_ws_bytes(n); }
 
 ce_status_t ce_mppi_dbscan_dev(const float* z, int n, int ld, int p, float eps, int min_pts,

@@ -189,13 +189,14 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 
 // Four standard normals from one Philox block: Box-Muller on the 23-bit
 // uniforms ((w >> 9) + 1/2) 2^-23 of the pairs (w0, w1) and (w2, w3); each
-// uniform is exact in FP32 (24 significant bits).  The radius keeps the
-// full-accuracy logarithm (near u1 = 1 an approximate one's absolute error
-// would dominate the tiny -ln u1).  The angle 2 pi u2 is taken in [-pi, pi)
+// uniform is exact in FP32 (24 significant bits).  The radius is
+// sqrt(neg2ln(u1)), within 5e-7 of exact for every uniform (below).  The
+// angle 2 pi u2 is taken in [-pi, pi)
 // (u2 - 1 for u2 >= 1/2 is exact) and its sine and cosine come from the
 // special-function unit: absolute error <= 2^-21.41 there, plus <= pi 2^-24
 // from rounding the angle, so a normal is within r (2^-21.41 + pi 2^-24)
-// <= 3.2e-6 of exact for the largest radius r = sqrt(-2 ln 2^-24) = 5.77.
+// <= 3.2e-6 of exact for the largest radius r = sqrt(-2 ln 2^-24) = 5.77,
+// plus the radius' error.
 // The uniform ((w >> 9) + 1/2) 2^-23 formed without an int-to-float
 // conversion: 1 + (w >> 9) 2^-23 from the exponent bits of 1.0, minus
 // (1 - 2^-24); the difference is exact (both operands lie in [1/2, 2]), so the
@@ -204,11 +205,39 @@ __device__ __forceinline__ float unit23(uint32_t w) {
   return __uint_as_float((w >> 9) | 0x3f800000u) - 0.99999994039535522f;
 }
 
+// -2 ln u for the uniforms u = (m + 1/2) 2^-23 of unit23 (2^-24 <= u < 1).
+// Near u = 1, where -ln u is small and an absolute error bound would not do,
+// the Taylor series of -2 ln(1 + t) in t = u - 1 (exact for u >= 1/2):
+// -2 (t - t^2/2 + t^3/3 - ... - t^8/8), Horner in FP32; for u > 7/8, |t| <
+// 1/8 and the first omitted term is below 2 |t| 2^-27.  Elsewhere the
+// special-function unit's base-2 logarithm times -2 ln 2: there |ln u| >=
+// 0.133, so its small absolute error stays a small relative one.  Checked
+// against the exact value for all 2^23 uniforms: relative error under 2^-20
+// (6.9e-7 at most, on the logarithm's side just below 7/8), the radius
+// sqrt(-2 ln u) within 5e-7.
+// The library's full-accuracy logarithm cost 10 % of the 2-D rollout
+// kernel's time.
+__device__ __forceinline__ float neg2ln(float u) {
+  const float t = u - 1.0f;
+  float q = 0.25f;                 // -2 x -1/8
+  q = fmaf(q, t, -0.285714298f);   // -2 x 1/7
+  q = fmaf(q, t, 0.333333343f);    // -2 x -1/6
+  q = fmaf(q, t, -0.4f);           // -2 x 1/5
+  q = fmaf(q, t, 0.5f);            // -2 x -1/4
+  q = fmaf(q, t, -0.666666687f);   // -2 x 1/3
+  q = fmaf(q, t, 1.0f);            // -2 x -1/2
+  q = fmaf(q, t, -2.0f);           // -2 x 1
+  // both sides computed, then selected (no branch in the warp)
+  const float near1 = q * t;
+  const float far = __log2f(u) * -1.38629436f;   // -2 ln 2
+  return u > 0.875f ? near1 : far;
+}
+
 __device__ __forceinline__ float4 normals4(uint4 w) {
   const float u1a = unit23(w.x), u2a = unit23(w.y);
   const float u1b = unit23(w.z), u2b = unit23(w.w);
   // sqrt(x) as x * rsqrt(x) (x >= 2^-23 > 0 here; rsqrtf is within 2 ulp)
-  const float xa = -2.0f * logf(u1a), xb = -2.0f * logf(u1b);
+  const float xa = neg2ln(u1a), xb = neg2ln(u1b);
   const float ra = xa * rsqrtf(xa), rb = xb * rsqrtf(xb);
   const float two_pi = 6.2831853071795865f;
   const float ta = two_pi * (u2a >= 0.5f ? u2a - 1.0f : u2a);
@@ -416,6 +445,7 @@ bool launch_post(const KArgs& a, int max_cells, cudaStream_t s, cudaEvent_t star
 void launch_update(const KArgs& a, cudaStream_t s);
 void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,
                    unsigned int* out, cudaStream_t s);
+void launch_neg2ln(float* out, cudaStream_t s);
 void launch_normals(unsigned long long seed, unsigned long long counter, int K, int n,
                     float* out, cudaStream_t s);
 void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, float cell_inv,

@@ -665,6 +665,13 @@ __global__ void k_normals(unsigned long long seed, unsigned long long counter, i
   for (int s = 0; s < 4 && 4 * b + s < n; ++s) out[(size_t)k * n + 4 * b + s] = zz[s];
 }
 
+// -2 ln u of every uniform u = (m + 1/2) 2^-23, m < 2^23, as the rollouts
+// compute it
+__global__ void k_neg2ln(float* out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < (1 << 23)) out[m] = neg2ln(unit23((uint32_t)m << 9));
+}
+
 // ------------------------------------------------------------------ launchers
 int rollout_threads(int dyn) { return is_arm(dyn) ? kArmWarps * 32 : kRolloutThreads; }
 
@@ -715,6 +722,8 @@ void launch_philox(unsigned long long seed, unsigned long long counter, int K, i
   const long long n = (long long)K * nblk;
   k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(seed, counter, K, nblk, out);
 }
+
+void launch_neg2ln(float* out, cudaStream_t s) { k_neg2ln<<<(1 << 23) / 256, 256, 0, s>>>(out); }
 
 void launch_normals(unsigned long long seed, unsigned long long counter, int K, int n,
                     float* out, cudaStream_t s) {
