@@ -610,6 +610,10 @@ def test_union_find_limit_reports_timeout_and_falls_back():
     with pytest.raises(pkg.CeError) as e:
         pl.replan(sc["x0"], hist, sc["radius"])
     assert e.value.status == 4
+    # the same replan through the device entry (the host replan's fallback
+    # advanced the nominal and the counter)
+    pl.set_nominal(sc["U0"])
+    pl.set_counter(0)
     dev = "cuda"
     diag = torch.zeros(128, dtype=torch.uint8, device=dev)
     u_out = torch.zeros((cfg["T"], 6), device=dev)

@@ -64,6 +64,33 @@ def test_normals_depend_on_rollout_counter_and_seed():
     assert np.array_equal(oracle.normals(1, 0, 5, 7), base[:7])
 
 
+def test_normals_lie_on_the_23_bit_uniform_grid():
+    """Each pair (z0, z1) is (r cos 2 pi u2, r sin 2 pi u2), r^2 = -2 ln u1,
+    with u1, u2 on the grid (f + 1/2) 2^-23 of 23-bit fields: exp(-r^2/2) 2^23
+    - 1/2 and the angle's fraction of a turn times 2^23 - 1/2 are integers.
+    Normals 4b .. 4b+3 come from Philox block b (words pinned by the published
+    test vectors): pair p's u1 and u2 are the top 23 bits of words 2p and
+    2p + 1."""
+    z = np.concatenate([oracle.normals(11, 5, k, 60) for k in range(200)]).reshape(-1, 2)
+    r2 = (z ** 2).sum(1)
+    f1 = np.exp(-r2 / 2) * 2.0 ** 23 - 0.5
+    ang = np.mod(np.arctan2(z[:, 1], z[:, 0]) / (2 * np.pi), 1.0)
+    f2 = ang * 2.0 ** 23 - 0.5
+    assert np.abs(f1 - np.round(f1)).max() < 1e-2
+    # (the angle's fraction of a turn is u2 or u2 - 1, both on the grid mod 1)
+    d2 = np.abs(f2 - np.round(f2))
+    assert np.minimum(d2, 1 - d2).max() < 1e-2
+    seed, counter, k, b = 0x299F31D0A4093822, (7 << 32) + 12345, 3, 2
+    zk = oracle.normals(seed, counter, k, 4 * (b + 1))[4 * b:]
+    w = oracle.philox4x32_10([k, b, counter & 0xFFFFFFFF, counter >> 32],
+                             [seed & 0xFFFFFFFF, seed >> 32])
+    for p in range(2):
+        r2p = zk[2 * p] ** 2 + zk[2 * p + 1] ** 2
+        assert abs(np.exp(-r2p / 2) * 2.0 ** 23 - 0.5 - (int(w[2 * p]) >> 9)) < 1e-2
+        a = np.mod(np.arctan2(zk[2 * p + 1], zk[2 * p]) / (2 * np.pi), 1.0) * 2.0 ** 23 - 0.5
+        assert abs(a - (int(w[2 * p + 1]) >> 9)) < 1e-2
+
+
 # --------------------------------------------------------------------------- Eq. 17
 def test_obstacle_velocity_telescopes():
     sc = _cfg("unicycle", K=64)
@@ -496,12 +523,17 @@ def test_replan_all_noise_is_standard_mppi_over_the_valid_rollouts():
 
 @pytest.mark.parametrize("name", ["di_blocked", "unicycle_paper", "arm_paper", "unicycle_blocked"])
 def test_replan_invariants(name):
+    # the first seed whose first replan clusters (with the paper's K = 50 for
+    # the arm, a collision is a matter of the draw)
     kw = dict(K=1024) if name == "unicycle_blocked" else {}
-    sc = W.make(name, seed=0, **kw)
-    cfg = sc["cfg"]
-    P = oracle.make_params(cfg)
-    r = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
-    d = r["diag"]
+    for seed in range(10):
+        sc = W.make(name, seed=seed, **kw)
+        cfg = sc["cfg"]
+        P = oracle.make_params(cfg)
+        r = oracle.replan(P, sc["x0"], sc["U0"], W.history(sc, 0), sc["radius"])
+        d = r["diag"]
+        if d["n_col"] > 0 and d["n_valid"] > 0 and d["n_clusters"] >= 1:
+            break
     assert d["n_col"] > 0 and d["n_valid"] > 0 and d["n_clusters"] >= 1
     w = r["w"]
     assert abs(w.sum() - 1) < 1e-12
