@@ -393,7 +393,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   h->n_upd = (int)upd.size();
   h->smem_roll = is_arm(P->dyn)
                      ? (int)(track_bytes(T, nobs) + (size_t)T * m * 4)
-                     : (int)((((size_t)T * m * 4 + 15) & ~(size_t)15) + kTrackSmem2D);
+                     : (int)((((size_t)T * m * 4 + 15) & ~(size_t)15) + track_smem_2d(T, nobs));
   auto cleanup = [&]() {
     cudaFree(h->dmem);
     cudaFree(h->ddesc);

@@ -144,9 +144,15 @@ __host__ __device__ __forceinline__ int track_stride(int n_obs) { return n_obs |
 __host__ __device__ __forceinline__ size_t track_hdr_bytes(int T) {
   return ((size_t)(T + 2) * 4 + 15) & ~(size_t)15;
 }
-// Shared memory the 2-D rollout kernel stages a packed table into; a larger
-// table is read from global memory (L1) instead.
+// Shared memory the 2-D rollout kernel stages a packed table into (the row
+// offsets, then an entry buffer): at least kTrackSmem2D, and at least one row
+// of n_obs_max entries, so that every run of rows holds one row or more; a
+// larger table is staged in runs of whole rows.
 constexpr int kTrackSmem2D = 8 * 1024;
+__host__ __device__ __forceinline__ size_t track_smem_2d(int T, int n_obs_max) {
+  const size_t row = track_hdr_bytes(T) + (size_t)(n_obs_max > 1 ? n_obs_max : 1) * 16;
+  return row > (size_t)kTrackSmem2D ? row : (size_t)kTrackSmem2D;
+}
 // Bytes of the track table: (T+1) rows of track_stride float4, then the
 // (T+1) row counts (int), padded to 16 bytes.
 __host__ __device__ __forceinline__ size_t track_bytes(int T, int n_obs) {

@@ -296,6 +296,17 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
       if (!__syncthreads_and(ok)) break;
       jb = ja + 1;
       while (jb <= T && off[jb + 1] - off[ja] <= cap_e) ++jb;
+      if (off[jb] - off[ja] > cap_e) {
+        // a row longer than the buffer (the launch's shared memory is sized
+        // for the largest row, so this does not happen): the replan is
+        // refused instead of copying past the buffer
+        if (threadIdx.x == 0) {
+          raise_status(d.ctl, CE_MPPI_ERR_INVALID_ARG);
+          atomicExch(&d.ctl->rejected, 2);
+        }
+        ok = false;
+        break;
+      }
       if (threadIdx.x == 0) {
         const uint32_t bytes = (uint32_t)(off[jb] - off[ja]) * 16u;
         mbar_expect_tx(&bar, bytes);

@@ -119,6 +119,28 @@ def test_stage_parity_track_table_in_runs(check_j0):
     print("PARITY track runs", diag["col_tests"], errs)
 
 
+@pytest.mark.parametrize("check_j0", [0, 1])
+def test_stage_parity_track_rows_longer_than_the_default_buffer(check_j0):
+    """1200 discs of radius 0.3 m centred within 0.25 m of the start (T = 8):
+    every row of the packed track table holds 1200 or more entries (19 KB),
+    more than the rollout kernel's default 8 KB entry buffer; the launch's
+    shared memory is sized for the largest row and the table arrives one row
+    per run."""
+    sc = W.make("di_static", seed=0, check_j0=check_j0, T=8, K=1024)
+    rng = np.random.default_rng(7)
+    n_extra = 1200
+    ang = rng.uniform(0.0, 2.0 * np.pi, n_extra)
+    rad = rng.uniform(0.0, 0.25, n_extra)
+    c = np.asarray(sc["x0"][:2]) + np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1)
+    extra = np.broadcast_to(c, (sc["obs"].shape[0], n_extra, 2))
+    sc["obs"] = np.concatenate([sc["obs"], extra], axis=1)
+    sc["radius"] = np.concatenate([sc["radius"], np.full(n_extra, 0.3)])
+    diag, errs = _check_replan(sc)
+    assert diag["status"] == 0
+    assert diag["col_tests"] >= 8 * n_extra and diag["n_col"] > 0
+    print("PARITY long rows", diag["col_tests"], errs)
+
+
 def test_stage_parity_full_size_unicycle():
     """The benchmark's workload: unicycle, K=16384, T=50, 50 (+1) moving discs."""
     sc = W.make("unicycle_blocked", seed=0)
