@@ -316,7 +316,7 @@ ce_status_t ce_mppi_create(const ce_mppi_params* P, void* stream, ce_mppi_handle
   const size_t o_ctr = take(8), o_ctl = take(sizeof(Ctl));
   const size_t o_U = take(sizeof(float) * T * m), o_Unew = take(sizeof(float) * T * m);
   // + 16: the packed 2-D table's header may round up 16 bytes past the rows'
-  const size_t o_trk = take(track_bytes(T, nobs) + 16);
+  const size_t o_trk = take(std::max(track_bytes(T, nobs), track_pair_bytes(T, nobs)) + 16);
   const size_t o_S = take(4 * Kp), o_w = take(4 * Kp), o_Sv = take(4 * Kp),
                o_cmin = take(4 * Kp), o_nzk = take(4 * kSparseMax), o_nze = take(4 * kSparseMax),
                o_zpart = take(4 * kPruneRanges);

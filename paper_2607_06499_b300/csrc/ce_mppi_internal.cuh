@@ -138,11 +138,16 @@ __host__ __device__ __forceinline__ bool is_arm(int dyn) {
 }
 
 __host__ __device__ __forceinline__ int track_stride(int n_obs) { return n_obs | 1; }
-// 2-D robots use a packed table instead: row offsets off[0..T+1] (int,
-// padded to 16 bytes), then the kept entries of rows 0..T back to back
-// (row j = entries [off[j], off[j+1])).
+// 2-D robots use a packed table instead: row offsets off[0..Q+1] (int, Q =
+// (T + 1) / 2; T + 2 of them reserved, padded to 16 bytes), then the kept
+// entries of rows 0..Q back to back (row r = entries [off[r], off[r+1]), an
+// entry two float4): row 0 the current state's, row q + 1 the pair of steps
+// 2q, 2q + 1.
 __host__ __device__ __forceinline__ size_t track_hdr_bytes(int T) {
   return ((size_t)(T + 2) * 4 + 15) & ~(size_t)15;
+}
+__host__ __device__ __forceinline__ size_t track_pair_bytes(int T, int n_obs) {
+  return track_hdr_bytes(T) + (size_t)(1 + (T + 1) / 2) * (size_t)(n_obs > 1 ? n_obs : 1) * 32;
 }
 // Shared memory the 2-D rollout kernel stages a packed table into (the row
 // offsets, then an entry buffer): at least kTrackSmem2D, and at least one row
@@ -150,7 +155,7 @@ __host__ __device__ __forceinline__ size_t track_hdr_bytes(int T) {
 // larger table is staged in runs of whole rows.
 constexpr int kTrackSmem2D = 8 * 1024;
 __host__ __device__ __forceinline__ size_t track_smem_2d(int T, int n_obs_max) {
-  const size_t row = track_hdr_bytes(T) + (size_t)(n_obs_max > 1 ? n_obs_max : 1) * 16;
+  const size_t row = track_hdr_bytes(T) + (size_t)(n_obs_max > 1 ? n_obs_max : 1) * 32;
   return row > (size_t)kTrackSmem2D ? row : (size_t)kTrackSmem2D;
 }
 // Bytes of the track table: (T+1) rows of track_stride float4, then the

@@ -20,9 +20,13 @@ namespace cem {
 // (unicycle: c_j = p_0, r_j = j dt max|v|; double integrator: c_j = p_0 + j dt
 // v_0, r_j = dt^2 j (j-1)/2 |a|max), so an obstacle farther than
 // r_j + r_o + r_robot (+1 mm slack) from c_j cannot be hit at step j and is
-// left out.  This changes no collision result.  Entries are (x, y, (r_o +
-// r_robot)^2, obstacle index as int bits), packed row after row behind the
-// row offsets (a count pass, a scan of the row counts, a write pass).
+// left out.  This changes no collision result.  The rows are pairs of steps
+// (below): a pair's row lists the obstacles reachable at either step, with
+// both centres and a widened radius for one test at the pair's end, so a
+// rollout makes one test per entry per two steps and the exact tests only
+// where that one passes (consecutive rows share ~97 % of their obstacles, so
+// a pair's row is barely longer than one step's).  Rows are packed behind
+// the row offsets (a count pass, a scan of the row counts, a write pass).
 // Arm: every row holds every obstacle as (x, y, z, r_o + r_robot), rows of
 // track_stride entries, then the row counts.
 __global__ void k_tracks(KArgs a) {
@@ -119,23 +123,47 @@ __global__ void k_tracks(KArgs a) {
   __shared__ int roff[kMaxT + 2];
   int* off = reinterpret_cast<int*>(tracks);
   float4* ent = reinterpret_cast<float4*>(reinterpret_cast<char*>(tracks) + track_hdr_bytes(T));
-  // pass 0 counts the kept entries of each row, pass 1 writes them
+  // the reach disc of time step j (centre, radius)
+  auto disc = [&](int j, float* cx, float* cy, float* rj) {
+    const float tj = (float)j * dt;
+    *cx = x0;
+    *cy = y0;
+    if (di) {
+      *cx = x0 + tj * vx0;
+      *cy = y0 + tj * vy0;
+      *rj = dt * dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
+    } else {
+      *rj = tj * m0;
+    }
+  };
+  const float v0n = sqrtf(vx0 * vx0 + vy0 * vy0);
+  const int Q = (T + 1) / 2;   // pairs of steps
+  // Row 0: time 0 (the current state, check_j0).  Row q + 1: the pair of
+  // steps 2q, 2q + 1, whose end positions are those of times j1 = 2q + 1 and
+  // j2 = 2q + 2 (j2 <= T, else one step): the obstacles reachable at either.
+  // An entry is two float4: (o(j2), R'^2, index) and (o(j1), R^2, 0), where
+  // R' = R + the position's largest move over step j1 + |o(j2) - o(j1)| +
+  // slack: a rollout within R of o(j1) at time j1 is within R' of o(j2) at
+  // time j2, so one test at the pair's end (against R') finds every pair
+  // that may hold a collision, and only those are tested exactly.
+  // Pass 0 counts the kept entries of each row, pass 1 writes them.
   for (int pass = 0; pass < 2; ++pass) {
-    for (int j = wid; j <= T; j += nw) {
-      const float tj = (float)j * dt;
-      float cx = x0, cy = y0, rj;
-      if (di) {
-        cx = x0 + tj * vx0;
-        cy = y0 + tj * vy0;
-        rj = dt * dt * (0.5f * (float)j * (float)(j - 1 > 0 ? j - 1 : 0)) * amax;
-      } else {
-        rj = tj * m0;
-      }
-      int cnt = pass ? roff[j] : 0;
+    for (int rw = wid; rw <= Q; rw += nw) {
+      const int j1 = rw == 0 ? 0 : 2 * rw - 1;
+      const bool two = rw > 0 && j1 + 1 <= T;
+      const int j2 = two ? j1 + 1 : j1;
+      float c1x, c1y, r1, c2x, c2y, r2;
+      disc(j1, &c1x, &c1y, &r1);
+      disc(j2, &c2x, &c2y, &r2);
+      const float t1 = (float)j1 * dt, t2 = (float)j2 * dt;
+      // the largest move of the position over step j1 (unicycle: max |v| dt;
+      // double integrator: (|v0| + j1 dt |a|max) dt)
+      const float smax = di ? (v0n + (float)j1 * dt * amax) * dt : m0 * dt;
+      int cnt = pass ? roff[rw] : 0;
       for (int o0 = 0; o0 < n_obs; o0 += 32) {
         const int o = o0 + lane;
         bool keep = false;
-        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
         if (o < n_obs) {
           float4 pv;
           float R;
@@ -145,42 +173,53 @@ __global__ void k_tracks(KArgs a) {
           } else {
             obstacle(o, &pv, &R);
           }
-          const float ox = pv.x + pv.z * tj;
-          const float oy = pv.y + pv.w * tj;
-          const float reach = rj + R + 1e-3f * (1.0f + rj);
-          const float ddx = ox - cx, ddy = oy - cy;
-          keep = ddx * ddx + ddy * ddy <= reach * reach;
-          e = make_float4(ox, oy, R * R, __int_as_float(o));
+          const float o1x = pv.x + pv.z * t1, o1y = pv.y + pv.w * t1;
+          const float o2x = pv.x + pv.z * t2, o2y = pv.y + pv.w * t2;
+          const float reach1 = r1 + R + 1e-3f * (1.0f + r1);
+          const float reach2 = r2 + R + 1e-3f * (1.0f + r2);
+          const float d1x = o1x - c1x, d1y = o1y - c1y, d2x = o2x - c2x, d2y = o2y - c2y;
+          keep = d1x * d1x + d1y * d1y <= reach1 * reach1 ||
+                 d2x * d2x + d2y * d2y <= reach2 * reach2;
+          const float mx = o2x - o1x, my = o2y - o1y;
+          const float Rc = R + smax + sqrtf(mx * mx + my * my) + 1e-3f * (1.0f + r2);
+          ea = make_float4(o2x, o2y, Rc * Rc, __int_as_float(o));
+          eb = make_float4(o1x, o1y, R * R, 0.f);
+          if (rw == 0) ea.z = R * R;   // (row 0: an exact test only)
         }
         const unsigned b = __ballot_sync(0xffffffffu, keep);
-        if (pass && keep) ent[cnt + __popc(b & ((1u << lane) - 1u))] = e;
+        if (pass && keep) {
+          const int e = cnt + __popc(b & ((1u << lane) - 1u));
+          ent[2 * e] = ea;
+          ent[2 * e + 1] = eb;
+        }
         cnt += __popc(b);
       }
-      if (!pass && lane == 0) roff[j] = cnt;
+      if (!pass && lane == 0) roff[rw] = cnt;
     }
     __syncthreads();
     if (!pass && wid == 0) {
-      // exclusive scan of the T + 1 row counts, 32 at a time with a carry
+      // exclusive scan of the Q + 1 row counts, 32 at a time with a carry
       int carry = 0;
-      for (int j0 = 0; j0 <= T; j0 += 32) {
+      for (int j0 = 0; j0 <= Q; j0 += 32) {
         const int j = j0 + lane;
-        const int v = j <= T ? roff[j] : 0;
+        const int v = j <= Q ? roff[j] : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int y = __shfl_up_sync(0xffffffffu, x, o);
           if (lane >= o) x += y;
         }
-        if (j <= T) roff[j] = carry + x - v;
+        if (j <= Q) roff[j] = carry + x - v;
         carry += __shfl_sync(0xffffffffu, x, 31);
       }
-      if (lane == 0) roff[T + 1] = carry;
+      if (lane == 0) roff[Q + 1] = carry;
     }
     __syncthreads();
   }
-  for (int j = threadIdx.x; j <= T + 1; j += blockDim.x) off[j] = roff[j];
-  // obstacle tests of a rollout at steps 1..T (row 0 only with check_j0)
-  if (threadIdx.x == 0) ctl->col_tests = roff[T + 1] - roff[1];
+  for (int j = threadIdx.x; j <= Q + 1; j += blockDim.x) off[j] = roff[j];
+  // obstacle tests of a rollout at the pairs' ends (row 0 only with check_j0;
+  // the exact tests of a pair that may hold a collision come on top)
+  if (threadIdx.x == 0) ctl->col_tests = roff[Q + 1] - roff[1];
 }
 
 // A rollout CTA whose copy of the track table did not land in time: the
@@ -244,16 +283,17 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
       reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(d.tracks) + hdr);
   uint32_t cap_b;
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(cap_b));
-  const int cap_e = (int)((cap_b - us_bytes - hdr) / 16u);
+  const int cap_e = (int)((cap_b - us_bytes - hdr) / 32u);   // entries of two float4
+  const int Q = (T + 1) / 2;   // rows 1..Q: pairs of steps
   uint32_t phase = 0;
   for (int i = threadIdx.x; i < T * d.m; i += blockDim.x) Us[i] = d.U[i];
   pdl_wait();   // (the nominal is the previous replan's; the table is the track kernel's)
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
-    const int tot = reinterpret_cast<const int*>(d.tracks)[T + 1];
+    const int tot = reinterpret_cast<const int*>(d.tracks)[Q + 1];
     const bool all = tot <= cap_e;
     // everything at once, or the row offsets alone (the runs follow)
-    const uint32_t bytes = hdr + (all ? (uint32_t)tot * 16u : 0u);
+    const uint32_t bytes = hdr + (all ? (uint32_t)tot * 32u : 0u);
     mbar_expect_tx(&bar, bytes);
     bulk_g2s(smem_raw + us_bytes, d.tracks, bytes, &bar);
     whole = all;
@@ -286,17 +326,58 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   int first = -1, first_j = -1;
   float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   int j = 0;
-  // runs of rows [ja, jb): step j tests row j + 1; row 0 only with check_j0
-  for (int ja = 0; ja <= T;) {
-    int jb = T + 1;
+  // the collision tests of pair q (steps 2q and, with two, 2q + 1): the
+  // position after step 2q was (p1x, p1y), after step 2q + 1 it is (s0, s1).
+  // One test per entry at the pair's end against the widened radius; only
+  // where one passes, the exact tests of the two steps in turn (descending:
+  // the lowest index wins).
+  auto pair_test = [&](int q, float p1x, float p1y, bool two, int base) {
+    if (first >= 0) return;
+    const int e_lo = off[q + 1] - base, e_hi = off[q + 2] - base;
+    bool may = !two;
+    if (two) {
+#pragma unroll 4
+      for (int e = e_lo; e < e_hi; ++e) {
+        const float4 t = buf[2 * e];
+        const float dx = s0 - t.x, dy = s1 - t.y;
+        may |= dx * dx + dy * dy < t.z;
+      }
+    }
+    if (may) {
+      int h = n_obs;
+      for (int e = e_hi - 1; e >= e_lo; --e) {
+        const float4 t = buf[2 * e + 1];
+        const float dx = p1x - t.x, dy = p1y - t.y;
+        h = (dx * dx + dy * dy < t.z) ? __float_as_int(buf[2 * e].w) : h;
+      }
+      if (h < n_obs) {
+        first = h;
+        first_j = 2 * q + 1;
+      } else if (two) {
+        for (int e = e_hi - 1; e >= e_lo; --e) {
+          const float4 t = buf[2 * e];
+          const float dx = s0 - t.x, dy = s1 - t.y;
+          h = (dx * dx + dy * dy < buf[2 * e + 1].z) ? __float_as_int(t.w) : h;
+        }
+        if (h < n_obs) {
+          first = h;
+          first_j = 2 * q + 2;
+        }
+      }
+    }
+  };
+  // runs of rows [ra, rb): row 0 (the current state, only with check_j0),
+  // row q + 1 the pair of steps 2q, 2q + 1
+  for (int ra = 0; ra <= Q;) {
+    int rb = Q + 1;
     if (!all) {
       // (large tables) the CTA agrees that every copy so far has landed
       // before the next one is issued; the previous run's entries are no
       // longer read
       if (!__syncthreads_and(ok)) break;
-      jb = ja + 1;
-      while (jb <= T && off[jb + 1] - off[ja] <= cap_e) ++jb;
-      if (off[jb] - off[ja] > cap_e) {
+      rb = ra + 1;
+      while (rb <= Q && off[rb + 1] - off[ra] <= cap_e) ++rb;
+      if (off[rb] - off[ra] > cap_e) {
         // a row longer than the buffer (the launch's shared memory is sized
         // for the largest row, so this does not happen): the replan is
         // refused instead of copying past the buffer
@@ -308,30 +389,29 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
         break;
       }
       if (threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)(off[jb] - off[ja]) * 16u;
+        const uint32_t bytes = (uint32_t)(off[rb] - off[ra]) * 32u;
         mbar_expect_tx(&bar, bytes);
-        if (bytes > 0) bulk_g2s((void*)buf, gent + off[ja], bytes, &bar);
+        if (bytes > 0) bulk_g2s((void*)buf, gent + 2 * (size_t)off[ra], bytes, &bar);
       }
       ok = mbar_wait(&bar, phase);
       pend = phase;
       phase ^= 1u;
     }
-    const int base = all ? 0 : off[ja];
-    if (ja == 0 && d.check_j0 && act) {
+    const int base = all ? 0 : off[ra];
+    if (ra == 0 && d.check_j0 && act) {
       int h = n_obs;
       for (int e = off[1] - 1 - base; e >= off[0] - base; --e) {
-        const float4 t = buf[e];
+        const float4 t = buf[2 * e];
         const float dx = s0 - t.x, dy = s1 - t.y;
         h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
       }
       if (h < n_obs) { first = h; first_j = 0; }
     }
-    int e_hi = off[j + 1] - base;   // end of row j + 1's entries is off[j + 2]
-    const int jend = act ? min(jb - 1, T) : j;
+    const int jend = act ? min(2 * (rb - 1), T) : j;
     const bool store = !d.regen;
     float* ep = store ? eps + (size_t)(2 * j) * Kp + k : nullptr;   // eps' of step j (advances 2 Kp a step)
-    // one horizon step with normals (z0, z1)
-    auto step = [&](int jj, float z0, float z1) {
+    // one horizon step's control, cost and motion with normals (z0, z1)
+    auto advance = [&](int jj, float z0, float z1) {
       const float n0 = Us[2 * jj], n1 = Us[2 * jj + 1];
       const float u0 = sampled_control(n0, sg0, z0, lo0, hi0);
       const float u1 = sampled_control(n1, sg1, z1, lo1, hi1);
@@ -361,41 +441,23 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
         s1 += vdt * sn;
         s2 += u1 * dt;
       }
-      const int e_lo = e_hi;
-      e_hi = off[jj + 2] - base;
-      if (first < 0) {
-        int h = n_obs;
-        // descending: the lowest index wins.  Unrolled by four (measured
-        // against one and two: 0.1565 and 0.1513 against 0.1480 ms per
-        // pipelined step over whole episodes, whose later rows hold more
-        // entries; a clamped four-wide body without a remainder loop: 0.172)
-#pragma unroll 4
-        for (int e = e_hi - 1; e >= e_lo; --e) {
-          const float4 t = buf[e];
-          const float dx = s0 - t.x, dy = s1 - t.y;
-          h = (dx * dx + dy * dy < t.z) ? __float_as_int(t.w) : h;
-        }
-        if (h < n_obs) { first = h; first_j = jj + 1; }
-      }
     };
     // normals 2j, 2j+1 of step j are elements (2j) % 4, (2j) % 4 + 1 of
-    // Philox block j / 2: two steps per block
-    if (j < jend && (j & 1)) {   // a run that starts on an odd step
-      z4 = philox_normals(d, ctr, k, j >> 1);
-      step(j, z4.z, z4.w);
-      ++j;
-    }
+    // Philox block j / 2: a pair of steps per block (runs start on even steps)
     for (; j + 1 < jend; j += 2) {
       z4 = philox_normals(d, ctr, k, j >> 1);
-      step(j, z4.x, z4.y);
-      step(j + 1, z4.z, z4.w);
+      advance(j, z4.x, z4.y);
+      const float p1x = s0, p1y = s1;
+      advance(j + 1, z4.z, z4.w);
+      pair_test(j >> 1, p1x, p1y, true, base);
     }
-    if (j < jend) {
+    if (j < jend) {   // an odd horizon's last step
       z4 = philox_normals(d, ctr, k, j >> 1);
-      step(j, z4.x, z4.y);
+      advance(j, z4.x, z4.y);
+      pair_test(j >> 1, s0, s1, false, base);
       ++j;
     }
-    ja = jb;
+    ra = rb;
   }
   if (!ok) {
     give_up_replan(d.ctl);

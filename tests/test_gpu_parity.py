@@ -122,10 +122,10 @@ def test_stage_parity_track_table_in_runs(check_j0):
 @pytest.mark.parametrize("check_j0", [0, 1])
 def test_stage_parity_track_rows_longer_than_the_default_buffer(check_j0):
     """1200 discs of radius 0.3 m centred within 0.25 m of the start (T = 8):
-    every row of the packed track table holds 1200 or more entries (19 KB),
-    more than the rollout kernel's default 8 KB entry buffer; the launch's
-    shared memory is sized for the largest row and the table arrives one row
-    per run."""
+    every row of the packed track table (a pair of steps) holds 1200 or more
+    entries (38 KB), more than the rollout kernel's default 8 KB entry buffer;
+    the launch's shared memory is sized for the largest row and the table
+    arrives one row per run."""
     sc = W.make("di_static", seed=0, check_j0=check_j0, T=8, K=1024)
     rng = np.random.default_rng(7)
     n_extra = 1200
@@ -137,7 +137,7 @@ def test_stage_parity_track_rows_longer_than_the_default_buffer(check_j0):
     sc["radius"] = np.concatenate([sc["radius"], np.full(n_extra, 0.3)])
     diag, errs = _check_replan(sc)
     assert diag["status"] == 0
-    assert diag["col_tests"] >= 8 * n_extra and diag["n_col"] > 0
+    assert diag["col_tests"] >= 4 * n_extra and diag["n_col"] > 0   # (4 pair rows)
     print("PARITY long rows", diag["col_tests"], errs)
 
 
