@@ -336,7 +336,9 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
     const int e_lo = off[q + 1] - base, e_hi = off[q + 2] - base;
     bool may = !two;
     if (two) {
-#pragma unroll 4
+      // (unrolled by two: 0.1395 against 0.1414 ms per pipelined step with
+      // four, 0.1462 with none, 0.1421 with eight)
+#pragma unroll 2
       for (int e = e_lo; e < e_hi; ++e) {
         const float4 t = buf[2 * e];
         const float dx = s0 - t.x, dy = s1 - t.y;
