@@ -29,7 +29,7 @@ namespace cem {
 // the row offsets (a count pass, a scan of the row counts, a write pass).
 // Arm: every row holds every obstacle as (x, y, z, r_o + r_robot), rows of
 // track_stride entries, then the row counts.
-__global__ void k_tracks(KArgs a) {
+__global__ void __launch_bounds__(1024) k_tracks(KArgs a) {   // (launched with 1024 threads)
   // the rollout kernel that follows may be scheduled at once: its CTAs load
   // the nominal and then wait for this grid to complete (measured: 1.2 %
   // shorter pipelined steps than scheduling it after the table is written)
