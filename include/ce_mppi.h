@@ -130,7 +130,10 @@ typedef struct {
   float v_obs[3];  /* velocity estimate of the reference obstacle (Eq. 17)        */
   unsigned long long counter; /* replan counter this replan used                  */
   int col_tests;   /* obstacle tests per rollout over the horizon after the reach */
-                   /* culling of the track builder (at most T * n_obs)           */
+                   /* culling of the track builder: 2-D robots one per obstacle  */
+                   /* of a pair of steps (at most ceil(T/2) * n_obs; the exact   */
+                   /* tests of a pair that may collide come on top), the arm     */
+                   /* one per obstacle and step (T * n_obs)                      */
 } ce_mppi_diag;
 
 /* Inputs and outputs of one replan, all in device memory. */
