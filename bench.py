@@ -505,8 +505,8 @@ POST_BYTES_PER_ROLLOUT = {2: 40 + 36, 3: 40 + 44}
 # timing covers: k_post over one pipelined half (8 instances), the rollout
 # kernel over all 16 instances (the stage-by-stage profile launch).  None: not
 # captured for the current build.
-NCU_TRAFFIC = {("unicycle", "k_post"): 2400000, ("unicycle", "rollout"): 87296,
-               ("arm", "k_post"): None, ("arm", "rollout"): 8759040,
+NCU_TRAFFIC = {("unicycle", "k_post"): 2400256, ("unicycle", "rollout"): 545536,
+               ("arm", "k_post"): None, ("arm", "rollout"): 8188928,
                ("arm", "k_update"): 50712320}
 
 
