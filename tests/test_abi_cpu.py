@@ -119,6 +119,12 @@ def test_batch_run_part_rejects_bad_arguments():
     assert "NULL" in L.ce_mppi_last_error().decode()
 
 
+def test_neg2ln_stage_rejects_null_output():
+    L = pkg.lib()
+    assert L.ce_mppi_neg2ln_dev(None, None) == 1
+    assert "NULL" in L.ce_mppi_last_error().decode()
+
+
 def test_twelve_d_arm_dims_and_parameters_accepted_by_validation():
     # dyn 3 passes the host-side checks up to the device allocation (no GPU
     # here: creation then fails with a CUDA or memory status, not INVALID_ARG)
