@@ -263,7 +263,11 @@ ce_status_t ce_mppi_batch_run_host(ce_mppi_batch* b, const float* x0s, const flo
  * next replan must follow part 1.  Between the two, the instances' state is
  * held on the device, so the halves of two batches of independent instances
  * can be interleaved (one batch's rollouts over the other's clustering), for
- * example on two streams inside the caller's own CUDA graph.  The results are
+ * example on two streams inside the caller's own CUDA graph.  Part 0 may also
+ * be queued as its two launches: part 2 = the obstacle tracks alone, part 3
+ * = the rollouts alone (after part 2 of the same replan); the tracks of the
+ * next replan need only part 1 of the previous one, so they can run beside
+ * other work instead of at the head of the rollouts.  The results are
  * bitwise those of ce_mppi_batch_run.  Errors: INVALID_ARG, CUDA.            */
 ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream);
 /* ce_mppi_batch_run_part with, for part 1, an event `started` (a cudaEvent_t

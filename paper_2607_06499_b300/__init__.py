@@ -308,7 +308,8 @@ class Batch:
         _check(lib().ce_mppi_batch_set_post_ctas(self.b, int(n)))
 
     def run_part(self, part: int, stream=None, started=None):
-        """Half a replan (0: tracks + rollouts, 1: clustering + update) on stream.
+        """Half a replan (0: tracks + rollouts, 1: clustering + update; 2: the
+        tracks alone, 3: the rollouts alone) on stream.
         started (part 1): a torch.cuda.Event(enable_timing=False) that fires once
         every CTA of the clustering kernel has begun execution (the event must
         exist: recorded once before)."""

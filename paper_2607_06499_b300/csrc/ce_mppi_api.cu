@@ -150,7 +150,7 @@ void run_chain(int dyn, const KArgs& base, const int2* troll, int n_roll, const 
   a.tiles = troll;
   a.tprefix = pre_roll;
   a.n_tiles = n_roll;
-  launch_rollout(dyn, a, smem_roll, s);
+  launch_rollout(dyn, a, smem_roll, s, true);
   // The fused kernel applies the update when few weights are nonzero; a dense
   // one (many nonzero weights: the arms' small costs, a no-collision replan
   // with close costs) is left to the tiled update kernel that follows over the
@@ -868,8 +868,8 @@ ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream) {
 
 ce_status_t ce_mppi_batch_run_part_ev(ce_mppi_batch* b, int part, void* stream, void* started) {
   if (!b) return fail(CE_MPPI_ERR_INVALID_ARG, "NULL batch");
-  if (part != 0 && part != 1) return fail(CE_MPPI_ERR_INVALID_ARG, "part must be 0 or 1");
-  if (part == 0 && started) return fail(CE_MPPI_ERR_INVALID_ARG, "started event is for part 1");
+  if (part < 0 || part > 3) return fail(CE_MPPI_ERR_INVALID_ARG, "part must be 0, 1, 2 or 3");
+  if (part != 1 && started) return fail(CE_MPPI_ERR_INVALID_ARG, "started event is for part 1");
   cudaEvent_t ev = static_cast<cudaEvent_t>(started);
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->stream;
   KArgs a;
@@ -879,11 +879,13 @@ ce_status_t ce_mppi_batch_run_part_ev(ce_mppi_batch* b, int part, void* stream, 
   a.n_inst = (int)b->hs.size();
   a.n_conc = a.n_inst;
   a.post_ctas = b->post_ctas;
-  if (part == 0) {
-    launch_tracks(a, s);
-    a.tiles = b->dtiles_roll;
-    a.n_tiles = b->n_roll;
-    launch_rollout(b->dyn, a, b->smem_roll, s);
+  if (part != 1) {
+    if (part != 3) launch_tracks(a, s);
+    if (part != 2) {
+      a.tiles = b->dtiles_roll;
+      a.n_tiles = b->n_roll;
+      launch_rollout(b->dyn, a, b->smem_roll, s, part == 0);
+    }
   } else {
     const bool fused = launch_post(a, b->max_cells, s, ev);   // (as in a whole replan's chain)
     if (!fused) {
@@ -915,7 +917,7 @@ ce_status_t ce_mppi_batch_profile(ce_mppi_batch* b, float* stage_ms) {
   cudaEventRecord(ev[1], s);
   a.tiles = b->dtiles_roll;
   a.n_tiles = b->n_roll;
-  launch_rollout(b->dyn, a, b->smem_roll, s);
+  launch_rollout(b->dyn, a, b->smem_roll, s, true);
   cudaEventRecord(ev[2], s);
   launch_prune(a, s);
   cudaEventRecord(ev[3], s);

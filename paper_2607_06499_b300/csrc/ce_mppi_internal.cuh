@@ -445,7 +445,10 @@ __device__ __forceinline__ float rot_angle(const float R[9], const float* Rg) {
 // ---------------------------------------------------------------- launchers
 // Host-side launchers of each stage (defined in the .cu files).
 void launch_tracks(const KArgs& a, cudaStream_t s);
-void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s);
+// after_tracks: the track kernel precedes in the stream, the rollouts are
+// launched as its programmatic dependents (else as a plain launch: a
+// programmatic edge would tie them to whatever kernel precedes instead)
+void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s, bool after_tracks);
 // (started: an optional launch-completion event of the launch)
 void launch_prune(const KArgs& a, cudaStream_t s, cudaEvent_t started = nullptr);
 void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s);

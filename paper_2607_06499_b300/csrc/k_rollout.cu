@@ -764,10 +764,11 @@ void configure_rollout() {
 }
 
 // The rollout kernels are launched as programmatic dependents of the track
-// kernel that precedes them in the stream (see pdl_wait).
+// kernel when it precedes them in the stream (dependent; see pdl_wait), else
+// as plain launches (their pdl_wait then returns at once).
 template <typename K>
 static void launch_dependent(K kern, int grid, int block, int smem, cudaStream_t s,
-                             const KArgs& a) {
+                             const KArgs& a, bool dependent) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)block);
@@ -777,19 +778,21 @@ static void launch_dependent(K kern, int grid, int block, int smem, cudaStream_t
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = dependent ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s) {
+void launch_rollout(int dyn, const KArgs& a, int smem_bytes, cudaStream_t s, bool after_tracks) {
   if (dyn == CE_DYN_DOUBLE_INT_2D)
-    launch_dependent(k_rollout2d<0>, a.n_tiles, kRolloutThreads, smem_bytes, s, a);
+    launch_dependent(k_rollout2d<0>, a.n_tiles, kRolloutThreads, smem_bytes, s, a, after_tracks);
   else if (dyn == CE_DYN_UNICYCLE)
-    launch_dependent(k_rollout2d<1>, a.n_tiles, kRolloutThreads, smem_bytes, s, a);
+    launch_dependent(k_rollout2d<1>, a.n_tiles, kRolloutThreads, smem_bytes, s, a, after_tracks);
   else if (dyn == CE_DYN_ARM6_KIN)
-    launch_dependent(k_rollout_arm<false>, a.n_tiles, kArmWarps * 32, smem_bytes, s, a);
+    launch_dependent(k_rollout_arm<false>, a.n_tiles, kArmWarps * 32, smem_bytes, s, a,
+                     after_tracks);
   else
-    launch_dependent(k_rollout_arm<true>, a.n_tiles, kArmWarps * 32, smem_bytes, s, a);
+    launch_dependent(k_rollout_arm<true>, a.n_tiles, kArmWarps * 32, smem_bytes, s, a,
+                     after_tracks);
 }
 
 void launch_philox(unsigned long long seed, unsigned long long counter, int K, int nblk,

@@ -65,9 +65,11 @@ def test_benchmark_configuration_against_the_oracle():
     bA = pkg.Batch(planners[:HALF], reqs[:HALF], use_graph=False)
     bB = pkg.Batch(planners[HALF:], reqs[HALF:], use_graph=False)
     side = torch.cuda.Stream()
+    trk = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
     # (as in the benchmark: each half's rollouts wait for the other half's
-    # clustering kernel to have begun on all its CTAs)
+    # clustering kernel to have begun on all its CTAs; a half's track kernel
+    # runs on a third stream right after its clustering + update)
     started = [torch.cuda.Event(enable_timing=False) for _ in range(2)]
     for e in started:
         e.record()
@@ -76,16 +78,23 @@ def test_benchmark_configuration_against_the_oracle():
         main = torch.cuda.current_stream()
         side.wait_stream(main)
         bB.run_part(1, main, started=started[1])
+        trk.wait_stream(main)
+        bB.run_part(2, trk)
         side.wait_event(started[1])
-        bA.run_part(0, side)
+        bA.run_part(3, side)
         main.wait_stream(side)
         side.wait_stream(main)
         bA.run_part(1, main, started=started[0])
         side.wait_event(started[0])
-        bB.run_part(0, side)
+        side.wait_stream(trk)
+        trk.wait_stream(main)
+        bA.run_part(2, trk)
+        bB.run_part(3, side)
+        main.wait_stream(trk)
         main.wait_stream(side)
     torch.cuda.synchronize()
     bB.run_part(0, torch.cuda.current_stream())   # B's first tracks + rollouts
+    bA.run_part(2, torch.cuda.current_stream())   # A's first tracks
     checked, nocol, dense = [], None, None
     modes = {}
     for r in range(LONG):
