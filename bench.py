@@ -529,6 +529,17 @@ def update_roofline(res: dict, m: int, hbm: float, pk_kind: str, wl_name: str):
             "nonzero_weights_mean": float(np.mean(res["update_nnz"]))}
 
 
+def early_tracks(args, wl_name: str) -> int:
+    """The track kernels' place in the pipelined halves (see --early-tracks);
+    by default both halves' early for the 2-D robots, the second half's for
+    the arms (measured: arm 0.4451 / 0.4452 / 0.4564 ms per step for 0 / 1 /
+    2)."""
+    e = int(getattr(args, "early_tracks", -1))
+    if e >= 0:
+        return e
+    return 1 if wl_name in ("arm", "arm12") else 2
+
+
 def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: int, dist,
                  steps: int, warmup: int, flush, profile: bool):
     """Build the workload's device-resident closed-loop episodes, time `steps`
@@ -586,7 +597,7 @@ def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: 
         bB.set_post_ctas(args.pipe_post_ctas)
         side = torch.cuda.Stream()
         trk = torch.cuda.Stream()
-        early = int(getattr(args, "early_tracks", 2))
+        early = early_tracks(args, wl_name)
         graph = torch.cuda.CUDAGraph()
         # each half's rollouts wait for the other half's clustering kernel to
         # have begun on all its CTAs (launch-completion events), so that the
@@ -648,7 +659,7 @@ def run_workload(pkg, torch, args, wl_name: str, dev, stream, rank: int, world: 
     def prologue():
         if pipe:
             pipe[1].run_part(0, stream)   # B's first tracks + rollouts, untimed
-            if args.pipeline == 1 and getattr(args, "early_tracks", 2) == 2:
+            if args.pipeline == 1 and early_tracks(args, wl_name) == 2:
                 pipe[0].run_part(2, stream)   # A's first tracks
 
     def step():
@@ -764,12 +775,13 @@ def main() -> None:
                     help="1: two halves of the episodes software-pipelined in one graph, "
                          "joined after each phase; 2: the same halves as two chains "
                          "joined once per step")
-    ap.add_argument("--early-tracks", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--early-tracks", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="1: the second half's track kernel right after its clustering + "
                          "update, on a third stream, rather than at the head of its rollouts; "
                          "2: both halves' (the first's at the end of each replay; over whole "
                          "episodes 0.1341 against 0.1357 and 0.1386 ms per step, over their "
-                         "first 20 replans 0.126 against 0.120)")
+                         "first 20 replans 0.126 against 0.120); -1: 2 for the 2-D robots, "
+                         "1 for the arms")
     ap.add_argument("--post-first", type=int, default=1, choices=[0, 1],
                     help="1: each half's tracks + rollouts wait on the other half's "
                          "clustering kernel having begun on all its CTAs")
@@ -948,7 +960,7 @@ def main() -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": bench_config(args.workload, world, regen),
         "run": {"pipeline": args.pipeline, "post_first": args.post_first,
-                "early_tracks": args.early_tracks,
+                "early_tracks": early_tracks(args, args.workload),
                 "pipe_post_ctas": args.pipe_post_ctas,
                 "batch_config": res["batch_config"],
                 "l2": "flushed between timed steps (256 MB write)"},
