@@ -400,8 +400,14 @@ __device__ __forceinline__ void arm_fk(const float q[6], float O[7][3], float R[
   O[0][0] = O[0][1] = O[0][2] = 0.0f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
+    // the joint's sine and cosine on the special-function unit: absolute
+    // error ~2^-21.4 for |q| <= pi, growing in proportion to |q| beyond
+    // (~1e-6 at 2 pi), so a frame origin moves by ~1e-6 m at most over the
+    // ~1.3 m chain: below the 1e-5 m band of the collision parity and far
+    // below the position tolerance (the full-accuracy call cost 4.3 % of
+    // the arm's pipelined step)
     float st, ct;
-    sincosf(q[i], &st, &ct);
+    __sincosf(q[i], &st, &ct);
     const float ca = dh_ca(i), sa = dh_sa(i), ai = dh_a(i), di = dh_d(i);
     // A = [[ct, -st ca, st sa, a ct], [st, ct ca, -ct sa, a st], [0, sa, ca, d]]
     const float A00 = ct, A01 = -st * ca, A02 = st * sa, A03 = ai * ct;
