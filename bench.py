@@ -506,7 +506,7 @@ POST_BYTES_PER_ROLLOUT = {2: 40 + 36, 3: 40 + 44}
 # kernel over all 16 instances (the stage-by-stage profile launch).  None: not
 # captured for the current build.
 NCU_TRAFFIC = {("unicycle", "k_post"): 2400256, ("unicycle", "rollout"): 545536,
-               ("arm", "k_post"): None, ("arm", "rollout"): 8188928,
+               ("arm", "k_post"): None, ("arm", "rollout"): 5862144,
                ("arm", "k_update"): 50712320}
 
 
