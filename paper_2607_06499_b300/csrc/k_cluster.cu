@@ -2136,6 +2136,9 @@ __device__ __forceinline__ void select_stage(const KArgs& a, SelSmem& sm, bool f
   cluster.sync();   // the list, the range partials and the nonzero count are complete
   if (fused && tid == 0 && rank == 0) ctl->dbcyc[12] = clock64();   // (stage clock stamp)
   if (rank != 0) return;
+  // the update kernel that follows may be scheduled now (the other ranks
+  // have left): its CTAs wait for this grid's completion (pdl_wait)
+  pdl_trigger();
   if (fused && tid == 0) ctl->dbcyc[13] = clock64();
   // rank 0: Z in range order, the list by ascending k, the control block
   if (wid == 0) {
@@ -2435,6 +2438,7 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   __shared__ int last;
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
+  pdl_wait();   // (launched as a programmatic dependent of the clustering kernel)
   if (d.ctl->updated) return;   // done by the fused per-instance kernel
   if (d.ctl->rejected) {        // inputs refused by the track kernel: no update
     if (tile.y == 0) refuse_replan(d, req_of(a, tile.x));
@@ -2762,8 +2766,21 @@ void launch_select(const KArgs& a, cudaStream_t s) {
   launch_clustered(k_select, cl, a.n_inst, kBlock, 0, s, nullptr, a);
 }
 
+// A programmatic dependent of the kernel before it in the stream (the fused
+// clustering kernel, or the selection kernel): scheduled once that kernel's
+// rank-0 CTAs reach their tail, it waits for its completion (pdl_wait).
 void launch_update(const KArgs& a, cudaStream_t s) {
-  k_update<<<a.n_tiles, kUpdateWarps * 32, 0, s>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)a.n_tiles);
+  cfg.blockDim = dim3((unsigned)(kUpdateWarps * 32));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_update, a);
 }
 
 void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, float cell_inv,
