@@ -576,6 +576,76 @@ def test_batch_run_in_two_parts_same_bits(ctas):
         obj.close()
 
 
+def test_batch_run_with_the_tracks_apart_same_bits():
+    """The benchmark's schedule of the halves: a half's track kernel (part 2)
+    on a third stream right after its clustering + update, its rollouts
+    (part 3) later on their own; the bits of whole replans."""
+    scs = [W.make("unicycle_blocked", seed=s, K=3000, n_replans=4) for s in range(4)]
+
+    def setup():
+        pls, reqs = [], []
+        for sc in scs:
+            pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
+            pl.set_nominal(sc["U0"])
+            n_obs = sc["radius"].shape[0]
+            rq = dict(x0=torch.tensor(sc["x0"], dtype=torch.float32, device="cuda"),
+                      hist=torch.tensor(sc["obs"], dtype=torch.float32, device="cuda").contiguous(),
+                      radius=torch.tensor(sc["radius"], dtype=torch.float32, device="cuda"),
+                      u_out=torch.zeros((sc["cfg"]["T"], 2), device="cuda"), obs_step=n_obs * 2)
+            rq["x_next"] = rq["x0"]
+            pls.append(pl)
+            reqs.append(rq)
+        return pls, reqs
+
+    pls, reqs = setup()
+    whole = pkg.Batch(pls, reqs, use_graph=False)
+    ref = []
+    for _ in range(3):
+        whole.run()
+        torch.cuda.synchronize()
+        ref.append([(r["u_out"].cpu().numpy().copy(), r["x0"].cpu().numpy().copy()) for r in reqs])
+    whole.close()
+    for pl in pls:
+        pl.close()
+
+    pls, reqs = setup()
+    bA = pkg.Batch(pls[:2], reqs[:2], use_graph=False)
+    bB = pkg.Batch(pls[2:], reqs[2:], use_graph=False)
+    main, side, trk = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    bB.run_part(0, main)   # B's replan 0: tracks + rollouts
+    bA.run_part(2, main)   # A's tracks of replan 0
+    got = []
+    for s in range(3):
+        side.wait_stream(main)
+        bB.run_part(1, main)              # B's replan s: clustering + update
+        if s < 2:
+            trk.wait_stream(main)
+            bB.run_part(2, trk)           # B's tracks of replan s + 1
+        bA.run_part(3, side)              # A's rollouts of replan s
+        main.wait_stream(side)
+        side.wait_stream(main)
+        bA.run_part(1, main)              # A's replan s: clustering + update
+        if s < 2:
+            side.wait_stream(trk)
+            trk.wait_stream(main)
+            bA.run_part(2, trk)           # A's tracks of replan s + 1
+            bB.run_part(3, side)          # B's rollouts of replan s + 1
+        main.wait_stream(side)
+        main.wait_stream(trk)
+        torch.cuda.synchronize()
+        got.append([(r["u_out"].cpu().numpy().copy(), r["x0"].cpu().numpy().copy()) for r in reqs])
+    for s in range(3):
+        for i in range(4):
+            assert np.array_equal(got[s][i][0], ref[s][i][0]), (s, i)
+            assert np.array_equal(got[s][i][1], ref[s][i][1]), (s, i)
+    ev = torch.cuda.Event(enable_timing=False)
+    ev.record()
+    with pytest.raises(pkg.CeError):   # (a started event belongs to part 1 only)
+        bA.run_part(0, main, started=ev)
+    for obj in [bA, bB] + pls:
+        obj.close()
+
+
 def test_set_post_ctas_rejected_for_a_graph_batch():
     sc = W.make("unicycle", seed=0, K=1024)
     pl = pkg.Planner(sc["cfg"], n_obs_max=sc["radius"].shape[0])
