@@ -259,10 +259,14 @@ __device__ __forceinline__ float4 normals4(uint4 w) {
   return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
 }
 
+__device__ __forceinline__ float4 philox_normals(uint2 key, unsigned long long ctr, int k,
+                                                 int b) {
+  const uint4 c = make_uint4((uint32_t)k, (uint32_t)b, (uint32_t)ctr, (uint32_t)(ctr >> 32));
+  return normals4(philox10(c, key));
+}
 __device__ __forceinline__ float4 philox_normals(const InstDesc& d, unsigned long long ctr,
                                                  int k, int b) {
-  const uint4 c = make_uint4((uint32_t)k, (uint32_t)b, (uint32_t)ctr, (uint32_t)(ctr >> 32));
-  return normals4(philox10(c, make_uint2(d.seed_lo, d.seed_hi)));
+  return philox_normals(make_uint2(d.seed_lo, d.seed_hi), ctr, k, b);
 }
 
 // The sampled control clip(u + sigma z) of Eq. 3 (the rollouts and the

@@ -310,6 +310,10 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
   const int k = tile.y * kRolloutThreads + threadIdx.x;
   const bool act = k < d.K && ok;
   const unsigned long long ctr = *d.counter;
+  // the Philox key in registers: the step loop's stores may alias the
+  // descriptor, which would otherwise be read again for every block
+  // (0.1344 -> 0.1336 ms per pipelined step over whole episodes)
+  const uint2 key = make_uint2(d.seed_lo, d.seed_hi);
 
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   if (act) {
@@ -447,14 +451,14 @@ __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(
     // normals 2j, 2j+1 of step j are elements (2j) % 4, (2j) % 4 + 1 of
     // Philox block j / 2: a pair of steps per block (runs start on even steps)
     for (; j + 1 < jend; j += 2) {
-      z4 = philox_normals(d, ctr, k, j >> 1);
+      z4 = philox_normals(key, ctr, k, j >> 1);
       advance(j, z4.x, z4.y);
       const float p1x = s0, p1y = s1;
       advance(j + 1, z4.z, z4.w);
       pair_test(j >> 1, p1x, p1y, true, base);
     }
     if (j < jend) {   // an odd horizon's last step
-      z4 = philox_normals(d, ctr, k, j >> 1);
+      z4 = philox_normals(key, ctr, k, j >> 1);
       advance(j, z4.x, z4.y);
       pair_test(j >> 1, s0, s1, false, base);
       ++j;
