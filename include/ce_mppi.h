@@ -267,8 +267,13 @@ ce_status_t ce_mppi_batch_run_host(ce_mppi_batch* b, const float* x0s, const flo
  * be queued as its two launches: part 2 = the obstacle tracks alone, part 3
  * = the rollouts alone (after part 2 of the same replan); the tracks of the
  * next replan need only part 1 of the previous one, so they can run beside
- * other work instead of at the head of the rollouts.  The results are
- * bitwise those of ce_mppi_batch_run.  Errors: INVALID_ARG, CUDA.            */
+ * other work instead of at the head of the rollouts.  Part 2 is launched as
+ * a programmatic dependent of the kernel before it in stream order (part 1's
+ * update kernel, which lets it be scheduled early; the track kernel waits for
+ * that grid's completion before it reads the state), so queue it directly
+ * behind part 1, not behind a wait on another stream's launch-completion
+ * event (its grid would then wait for that kernel's completion).  The results
+ * are bitwise those of ce_mppi_batch_run.  Errors: INVALID_ARG, CUDA.        */
 ce_status_t ce_mppi_batch_run_part(ce_mppi_batch* b, int part, void* stream);
 /* ce_mppi_batch_run_part with, for part 1, an event `started` (a cudaEvent_t
  * created with cudaEventDisableTiming, or NULL) that the clustering kernel's

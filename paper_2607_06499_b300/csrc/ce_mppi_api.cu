@@ -880,7 +880,7 @@ ce_status_t ce_mppi_batch_run_part_ev(ce_mppi_batch* b, int part, void* stream, 
   a.n_conc = a.n_inst;
   a.post_ctas = b->post_ctas;
   if (part != 1) {
-    if (part != 3) launch_tracks(a, s);
+    if (part != 3) launch_tracks(a, s, part == 2);
     if (part != 2) {
       a.tiles = b->dtiles_roll;
       a.n_tiles = b->n_roll;

@@ -454,7 +454,9 @@ __device__ __forceinline__ float rot_angle(const float R[9], const float* Rg) {
 
 // ---------------------------------------------------------------- launchers
 // Host-side launchers of each stage (defined in the .cu files).
-void launch_tracks(const KArgs& a, cudaStream_t s);
+// after_update: a programmatic dependent of the update kernel before it in
+// the stream (a pipelined half's next replan, see ce_mppi_batch_run_part)
+void launch_tracks(const KArgs& a, cudaStream_t s, bool after_update = false);
 // after_tracks: the track kernel precedes in the stream, the rollouts are
 // launched as its programmatic dependents (else as a plain launch: a
 // programmatic edge would tie them to whatever kernel precedes instead)

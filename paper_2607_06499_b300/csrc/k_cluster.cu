@@ -2436,6 +2436,9 @@ __global__ void __launch_bounds__(kUpdateWarps * 32) k_update(KArgs a) {
   __shared__ float wtile[kUpdChunkArm];   // arm, eps' stored: the warps' lists of
   __shared__ int rtile[kUpdChunkArm];     // nonzero weights and their rows
   __shared__ int last;
+  // a track kernel launched behind this one (a pipelined half's next replan)
+  // may be scheduled at once; it waits for this grid's completion
+  pdl_trigger();
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
   pdl_wait();   // (launched as a programmatic dependent of the clustering kernel)

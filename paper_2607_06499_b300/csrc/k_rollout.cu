@@ -37,7 +37,6 @@ __global__ void __launch_bounds__(1024) k_tracks(KArgs a) {   // (launched with 
   const int inst = blockIdx.x;
   const InstDesc& d = desc_of(a, inst);
   const Req r = req_of(a, inst);
-  const float* h = hist_of(r, d);
   // every parameter read into registers ahead of the kernel's first store
   // (a later read would wait behind the stores it might alias)
   const int n_obs = r.n_obs, p = d.p, H = d.H, T = d.T, dyn = d.dyn, dn = d.n;
@@ -49,6 +48,12 @@ __global__ void __launch_bounds__(1024) k_tracks(KArgs a) {   // (launched with 
   float4* const tracks = d.tracks;
   const bool arm = is_arm(dyn);
   const bool di = dyn == CE_DYN_DOUBLE_INT_2D;
+  // (launched as a programmatic dependent of the previous replan's update
+  // kernel, a pipelined half's next replan: the replan counter, the state and
+  // the control block are that grid's until it completes; descriptor and
+  // request above are the host's)
+  pdl_wait();
+  const float* h = hist_of(r, d);
   const float x0 = r.x0[0], y0 = r.x0[1];
   const float vx0 = di ? r.x0[2] : 0.f;
   const float vy0 = di ? r.x0[3] : 0.f;
@@ -754,7 +759,26 @@ __global__ void k_neg2ln(float* out) {
 // ------------------------------------------------------------------ launchers
 int rollout_threads(int dyn) { return is_arm(dyn) ? kArmWarps * 32 : kRolloutThreads; }
 
-void launch_tracks(const KArgs& a, cudaStream_t s) { k_tracks<<<a.n_inst, 1024, 0, s>>>(a); }
+void launch_tracks(const KArgs& a, cudaStream_t s, bool after_update) {
+  if (!after_update) {
+    k_tracks<<<a.n_inst, 1024, 0, s>>>(a);
+    return;
+  }
+  // scheduled while the update kernel before it in the stream runs (that
+  // grid lets it be at its start); it waits for that grid's completion
+  // before reading the state (pdl_wait)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)a.n_inst);
+  cfg.blockDim = dim3(1024u);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_tracks, a);
+}
 
 void configure_rollout() {
   cudaFuncSetAttribute(k_rollout2d<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
