@@ -2223,6 +2223,11 @@ __device__ void refuse_replan(const InstDesc& d, const Req& r) {
 __global__ void __maxnreg__(64) k_post(KArgs a) {
   extern __shared__ __align__(16) int smem_post[];
   cg::cluster_group cluster = cg::this_cluster();
+  // launched as a programmatic dependent of the rollout kernel before it in
+  // the stream, which lets it be scheduled once every rollout CTA has begun:
+  // its CTAs take the SMs as the rollouts' last CTAs leave them and wait here
+  // for that grid's completion (its records, the control block)
+  pdl_wait();
   {
     // (the flag is the track kernel's, the same for every CTA of the cluster)
     const int inst = blockIdx.x / cluster.num_blocks();
@@ -2690,14 +2695,19 @@ static int fit_class(int nc) { return nc <= kFitCells[0] ? 0 : nc <= kFitCells[1
 
 template <typename... Args>
 static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int threads, size_t smem,
-                             cudaStream_t s, cudaEvent_t started, Args... args) {
+                             cudaStream_t s, cudaEvent_t started, bool dependent, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_inst * cl));
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[3];
   unsigned n = 0;
+  if (dependent) {   // (the kernel waits for the grid before it: pdl_wait)
+    at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
   if (cl > 1) {   // (one CTA per instance: no cluster)
     at[n].id = cudaLaunchAttributeClusterDimension;
     at[n].val.clusterDim.x = (unsigned)cl;
@@ -2718,7 +2728,7 @@ static void launch_clustered(void (*kern)(Args...), int cl, int n_inst, int thre
 
 void launch_prune(const KArgs& a, cudaStream_t s, cudaEvent_t started) {
   const int cl = cluster_ctas(g_fit_prune, a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_prune, cl, a.n_inst, kBlock, 0, s, started, a);
+  launch_clustered(k_prune, cl, a.n_inst, kBlock, 0, s, started, false, a);
 }
 
 // (2-D sets may take the angular method, whose tables are kAngSmemInts ints)
@@ -2736,7 +2746,7 @@ bool launch_post(const KArgs& a, int max_cells, cudaStream_t s, cudaEvent_t star
   const ClusterFit& f = g_fit_post[fc];
   if (f.max_active[0] == 0) return false;   // (the launch would not fit)
   const int cl = a.post_ctas > 0 ? a.post_ctas : cluster_ctas(f, a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, started, a);
+  launch_clustered(k_post, cl, a.n_inst, kBlock, smem, s, started, true, a);
   return true;
 }
 
@@ -2761,12 +2771,12 @@ void launch_dbscan(const KArgs& a, int max_cells, cudaStream_t s) {
   const int fc = fit_class(max_cells);
   const size_t smem = dbscan_smem(kFitCells[fc]);
   const int cl = cluster_ctas(g_fit_db[fc], a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, nullptr, a);
+  launch_clustered(k_dbscan, cl, a.n_inst, kBlock, smem, s, nullptr, false, a);
 }
 
 void launch_select(const KArgs& a, cudaStream_t s) {
   const int cl = cluster_ctas(g_fit_select, a.n_conc > 0 ? a.n_conc : a.n_inst);
-  launch_clustered(k_select, cl, a.n_inst, kBlock, 0, s, nullptr, a);
+  launch_clustered(k_select, cl, a.n_inst, kBlock, 0, s, nullptr, false, a);
 }
 
 // A programmatic dependent of the kernel before it in the stream (the fused
@@ -2804,7 +2814,7 @@ void launch_dbscan_standalone(const float* z, int n, int ld, int p, float eps2, 
   const int fc = fit_class(nc);
   const size_t smem = dbscan_smem(kFitCells[fc]);
   const int cl = cluster_ctas(g_fit_db[fc], 1);
-  launch_clustered(k_dbscan_standalone, cl, 1, kBlock, smem, s, nullptr, z, n, ld, p, eps2, cell_inv, G, R,
+  launch_clustered(k_dbscan_standalone, cl, 1, kBlock, smem, s, nullptr, false, z, n, ld, p, eps2, cell_inv, G, R,
                    min_pts, labels, n_clusters, w);
 }
 

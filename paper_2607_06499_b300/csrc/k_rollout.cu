@@ -273,6 +273,9 @@ __device__ __forceinline__ bool stage_tracks(const InstDesc& d, int n_obs, float
 template <int DYN>
 __global__ void __launch_bounds__(kRolloutThreads, kRolloutMinCtas) k_rollout2d(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the clustering kernel that follows may be scheduled once every CTA of
+  // this grid has begun (it waits for the grid's completion)
+  pdl_trigger();
   __shared__ uint64_t bar;
   __shared__ int whole;
   const int2 tile = tile_of(a);
@@ -605,6 +608,7 @@ template <bool ACC>   // ACC: 12-D state with joint-acceleration input
 __global__ void __launch_bounds__(kArmWarps * 32, 2) k_rollout_arm(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
+  pdl_trigger();   // (as in k_rollout2d: the clustering kernel may be scheduled)
   const int2 tile = tile_of(a);
   const InstDesc& d = desc_of(a, tile.x);
   const Req r = req_of(a, tile.x);
