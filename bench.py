@@ -505,9 +505,9 @@ POST_BYTES_PER_ROLLOUT = {2: 40 + 36, 3: 40 + 44}
 # timing covers: k_post over one pipelined half (8 instances), the rollout
 # kernel over all 16 instances (the stage-by-stage profile launch).  None: not
 # captured for the current build.
-NCU_TRAFFIC = {("unicycle", "k_post"): 2399232, ("unicycle", "rollout"): 545536,
-               ("arm", "k_post"): None, ("arm", "rollout"): 5862144,
-               ("arm", "k_update"): 50697984}
+NCU_TRAFFIC = {("unicycle", "k_post"): 2398976, ("unicycle", "rollout"): 89600,
+               ("arm", "k_post"): None, ("arm", "rollout"): 6018816,
+               ("arm", "k_update"): 50703616}
 
 
 def update_roofline(res: dict, m: int, hbm: float, pk_kind: str, wl_name: str):
