@@ -151,75 +151,108 @@ __global__ void __launch_bounds__(1024) k_tracks(KArgs a) {   // (launched with 
   // slack: a rollout within R of o(j1) at time j1 is within R' of o(j2) at
   // time j2, so one test at the pair's end (against R') finds every pair
   // that may hold a collision, and only those are tested exactly.
-  // Pass 0 counts the kept entries of each row, pass 1 writes them.
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int rw = wid; rw <= Q; rw += nw) {
-      const int j1 = rw == 0 ? 0 : 2 * rw - 1;
-      const bool two = rw > 0 && j1 + 1 <= T;
-      const int j2 = two ? j1 + 1 : j1;
-      float c1x, c1y, r1, c2x, c2y, r2;
-      disc(j1, &c1x, &c1y, &r1);
-      disc(j2, &c2x, &c2y, &r2);
-      const float t1 = (float)j1 * dt, t2 = (float)j2 * dt;
-      // the largest move of the position over step j1 (unicycle: max |v| dt;
-      // double integrator: (|v0| + j1 dt |a|max) dt)
-      const float smax = di ? (v0n + (float)j1 * dt * amax) * dt : m0 * dt;
-      int cnt = pass ? roff[rw] : 0;
-      for (int o0 = 0; o0 < n_obs; o0 += 32) {
-        const int o = o0 + lane;
-        bool keep = false;
-        float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
-        if (o < n_obs) {
-          float4 pv;
-          float R;
-          if (o < kObsSmem) {
-            pv = opv[o];
-            R = orr[o];
-          } else {
-            obstacle(o, &pv, &R);
-          }
-          const float o1x = pv.x + pv.z * t1, o1y = pv.y + pv.w * t1;
-          const float o2x = pv.x + pv.z * t2, o2y = pv.y + pv.w * t2;
-          const float reach1 = r1 + R + 1e-3f * (1.0f + r1);
-          const float reach2 = r2 + R + 1e-3f * (1.0f + r2);
-          const float d1x = o1x - c1x, d1y = o1y - c1y, d2x = o2x - c2x, d2y = o2y - c2y;
-          keep = d1x * d1x + d1y * d1y <= reach1 * reach1 ||
-                 d2x * d2x + d2y * d2y <= reach2 * reach2;
-          const float mx = o2x - o1x, my = o2y - o1y;
-          const float Rc = R + smax + sqrtf(mx * mx + my * my) + 1e-3f * (1.0f + r2);
-          ea = make_float4(o2x, o2y, Rc * Rc, __int_as_float(o));
-          eb = make_float4(o1x, o1y, R * R, 0.f);
-          if (rw == 0) ea.z = R * R;   // (row 0: an exact test only)
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, keep);
-        if (pass && keep) {
-          const int e = cnt + __popc(b & ((1u << lane) - 1u));
-          ent[2 * e] = ea;
-          ent[2 * e + 1] = eb;
-        }
-        cnt += __popc(b);
-      }
-      if (!pass && lane == 0) roff[rw] = cnt;
+  // The entry of obstacle o in row rw; true where it is kept.
+  auto entry = [&](int rw, int o, float4* ea, float4* eb) -> bool {
+    const int j1 = rw == 0 ? 0 : 2 * rw - 1;
+    const bool two = rw > 0 && j1 + 1 <= T;
+    const int j2 = two ? j1 + 1 : j1;
+    float c1x, c1y, r1, c2x, c2y, r2;
+    disc(j1, &c1x, &c1y, &r1);
+    disc(j2, &c2x, &c2y, &r2);
+    const float t1 = (float)j1 * dt, t2 = (float)j2 * dt;
+    // the largest move of the position over step j1 (unicycle: max |v| dt;
+    // double integrator: (|v0| + j1 dt |a|max) dt)
+    const float smax = di ? (v0n + (float)j1 * dt * amax) * dt : m0 * dt;
+    float4 pv;
+    float R;
+    if (o < kObsSmem) {
+      pv = opv[o];
+      R = orr[o];
+    } else {
+      obstacle(o, &pv, &R);
     }
-    __syncthreads();
-    if (!pass && wid == 0) {
-      // exclusive scan of the Q + 1 row counts, 32 at a time with a carry
-      int carry = 0;
-      for (int j0 = 0; j0 <= Q; j0 += 32) {
-        const int j = j0 + lane;
-        const int v = j <= Q ? roff[j] : 0;
-        int x = v;
+    const float o1x = pv.x + pv.z * t1, o1y = pv.y + pv.w * t1;
+    const float o2x = pv.x + pv.z * t2, o2y = pv.y + pv.w * t2;
+    const float reach1 = r1 + R + 1e-3f * (1.0f + r1);
+    const float reach2 = r2 + R + 1e-3f * (1.0f + r2);
+    const float d1x = o1x - c1x, d1y = o1y - c1y, d2x = o2x - c2x, d2y = o2y - c2y;
+    const bool keep = d1x * d1x + d1y * d1y <= reach1 * reach1 ||
+                      d2x * d2x + d2y * d2y <= reach2 * reach2;
+    const float mx = o2x - o1x, my = o2y - o1y;
+    const float Rc = R + smax + sqrtf(mx * mx + my * my) + 1e-3f * (1.0f + r2);
+    *ea = make_float4(o2x, o2y, rw == 0 ? R * R : Rc * Rc, __int_as_float(o));   // (row 0: an exact test only)
+    *eb = make_float4(o1x, o1y, R * R, 0.f);
+    return keep;
+  };
+  // exclusive scan of the Q + 1 row counts (warp 0), 32 at a time with a carry
+  auto scan_rows = [&]() {
+    if (wid != 0) return;
+    int carry = 0;
+    for (int j0 = 0; j0 <= Q; j0 += 32) {
+      const int j = j0 + lane;
+      const int v = j <= Q ? roff[j] : 0;
+      int x = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
-        }
-        if (j <= Q) roff[j] = carry + x - v;
-        carry += __shfl_sync(0xffffffffu, x, 31);
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      if (lane == 0) roff[Q + 1] = carry;
+      if (j <= Q) roff[j] = carry + x - v;
+      carry += __shfl_sync(0xffffffffu, x, 31);
     }
+    if (lane == 0) roff[Q + 1] = carry;
+  };
+  if (Q + 1 <= nw && n_obs <= 64) {
+    // one row per warp, at most two obstacles per lane: the entries stay in
+    // registers from the count to the write, computed once
+    const int rw = wid;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ea0 = z4, eb0 = z4, ea1 = z4, eb1 = z4;
+    bool k0 = false, k1 = false;
+    if (rw <= Q) {
+      if (lane < n_obs) k0 = entry(rw, lane, &ea0, &eb0);
+      if (32 + lane < n_obs) k1 = entry(rw, 32 + lane, &ea1, &eb1);
+    }
+    const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+    if (rw <= Q && lane == 0) roff[rw] = __popc(b0) + __popc(b1);
     __syncthreads();
+    scan_rows();
+    __syncthreads();
+    if (rw <= Q) {
+      const unsigned lt = (1u << lane) - 1u;
+      const int e0 = roff[rw] + __popc(b0 & lt), e1 = roff[rw] + __popc(b0) + __popc(b1 & lt);
+      if (k0) {
+        ent[2 * e0] = ea0;
+        ent[2 * e0 + 1] = eb0;
+      }
+      if (k1) {
+        ent[2 * e1] = ea1;
+        ent[2 * e1 + 1] = eb1;
+      }
+    }
+  } else {
+    // pass 0 counts the kept entries of each row, pass 1 writes them
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int rw = wid; rw <= Q; rw += nw) {
+        int cnt = pass ? roff[rw] : 0;
+        for (int o0 = 0; o0 < n_obs; o0 += 32) {
+          const int o = o0 + lane;
+          float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
+          const bool keep = o < n_obs && entry(rw, o, &ea, &eb);
+          const unsigned b = __ballot_sync(0xffffffffu, keep);
+          if (pass && keep) {
+            const int e = cnt + __popc(b & ((1u << lane) - 1u));
+            ent[2 * e] = ea;
+            ent[2 * e + 1] = eb;
+          }
+          cnt += __popc(b);
+        }
+        if (!pass && lane == 0) roff[rw] = cnt;
+      }
+      __syncthreads();
+      if (!pass) scan_rows();
+      __syncthreads();
+    }
   }
   for (int j = threadIdx.x; j <= Q + 1; j += blockDim.x) off[j] = roff[j];
   // obstacle tests of a rollout at the pairs' ends (row 0 only with check_j0;
